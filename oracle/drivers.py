@@ -1,0 +1,135 @@
+"""Alg. 1 (single-path) and Alg. 2 (multi-path) on the FP64 MPS (oracle side; test
+infrastructure only).
+
+Single path (Alg. 1, Sec. "Single-path simulation"): start from |0...0>, c = 0, p = 1,
+F = 1; compress each non-empty chunk (F *= f); at a measurement compute (p_0, p_1) at the
+orthogonality centre, draw u = Philox(seed, shot, ordinal), take m = 0 iff u < p_0, collapse,
+p *= p_m, c_j := m.
+
+Multi path (Alg. 2, Sec. "Multi-path simulation"): every branch compresses its chunk; at a
+measurement every branch spawns the children m in {0, 1} with p_m > P_EPS (m = 0 first,
+parents in list order) with p_{gamma m} = p_gamma p_m, F copied; then, if more than M
+branches are active, the M with the largest p are kept (ties: ``topk_select``).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import List, Optional
+
+import numpy as np
+
+from circuits import Circuit, Measure
+from .layers import blocks_mpo, chunk_blocks, chunk_circuit
+from .mps import MPS, collapse, compress, measure_probs, product_zero
+from .philox import uniform
+from .statevector import FLAG_WINDOW, P_EPS, topk_select
+
+
+@dataclass
+class Params:
+    chi_max: int = 8
+    tol: float = 1e-10
+    sweeps: int = 2
+    k: int = 0  # maximum ops per chunk (0: one-layer rule only)
+
+
+@dataclass
+class ShotResult:
+    p: float
+    F: float
+    c: np.ndarray
+    mps: MPS
+    outcomes: List[int]
+    p0s: List[float]
+    flagged: List[int]
+    fids: List[float]
+
+
+def run_single_path(circ: Circuit, prm: Params, seed: int, shot: int,
+                    stop_after_flag: bool = False) -> ShotResult:
+    n, steps = chunk_circuit(circ, prm.k)
+    mps = product_zero(n)
+    c = np.zeros(circ.n_cbits, dtype=np.int64)
+    p, F = 1.0, 1.0
+    outcomes, p0s, flagged, fids = [], [], [], []
+    ordinal = 0
+    for st in steps:
+        if isinstance(st, Measure):
+            r0, r1 = measure_probs(mps, st.qubit)
+            p0 = r0 / (r0 + r1)
+            u = uniform(seed, shot, ordinal)
+            m = 0 if u < p0 else 1
+            if abs(u - p0) < FLAG_WINDOW:
+                flagged.append(ordinal)
+            pm = p0 if m == 0 else 1.0 - p0
+            if pm <= P_EPS:
+                raise FloatingPointError("collapse onto an outcome of zero probability")
+            collapse(mps, st.qubit, m, r0 if m == 0 else r1)
+            p *= pm
+            c[st.cbit] = m
+            outcomes.append(m)
+            p0s.append(p0)
+            ordinal += 1
+            if flagged and stop_after_flag:
+                break
+        else:
+            blocks, empty = chunk_blocks(n, st, c)
+            if empty:
+                continue
+            mps, info = compress(mps, blocks, blocks_mpo(n, blocks), prm.chi_max, prm.tol,
+                                 prm.sweeps)
+            F *= info.f
+            fids.append(info.f)
+    return ShotResult(p, F, c, mps, outcomes, p0s, flagged, fids)
+
+
+@dataclass
+class MPBranch:
+    p: float
+    F: float
+    c: np.ndarray
+    mps: MPS
+    path: List[int] = field(default_factory=list)
+
+
+def run_multi_path(circ: Circuit, prm: Params, M: Optional[int] = None,
+                   max_steps: Optional[int] = None) -> List[MPBranch]:
+    n, steps = chunk_circuit(circ, prm.k)
+    Lst = [MPBranch(1.0, 1.0, np.zeros(circ.n_cbits, dtype=np.int64), product_zero(n))]
+    for si, st in enumerate(steps):
+        if max_steps is not None and si >= max_steps:
+            break
+        if isinstance(st, Measure):
+            nxt = []
+            for b in Lst:
+                r0, r1 = measure_probs(b.mps, st.qubit)
+                tot = r0 + r1
+                for m, rm in ((0, r0), (1, r1)):
+                    pm = rm / tot
+                    if pm > P_EPS:
+                        child = b.mps.copy()
+                        collapse(child, st.qubit, m, rm)
+                        c = b.c.copy()
+                        c[st.cbit] = m
+                        nxt.append(MPBranch(b.p * pm, b.F, c, child, b.path + [m]))
+            Lst = nxt
+            if M is not None and len(Lst) > M:
+                keep = topk_select([b.p for b in Lst], M)
+                Lst = [Lst[i] for i in keep]
+        else:
+            for b in Lst:
+                blocks, empty = chunk_blocks(n, st, b.c)
+                if empty:
+                    continue
+                b.mps, info = compress(b.mps, blocks, blocks_mpo(n, blocks), prm.chi_max,
+                                       prm.tol, prm.sweeps)
+                b.F *= info.f
+    return Lst
+
+
+def multipath_fidelity(branches: List[MPBranch]) -> float:
+    """Ensemble fidelity: branch fidelities weighted by branch probabilities
+    (Sec. "Random dynamic circuits": normalised by the branch probabilities)."""
+    ps = np.array([b.p for b in branches])
+    fs = np.array([b.F for b in branches])
+    return float((ps * fs).sum() / ps.sum())

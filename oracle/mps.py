@@ -1,0 +1,268 @@
+"""O2: FP64 matrix product states and the variational compression step (oracle side;
+test infrastructure only).
+
+MPS (Sec. "Representing pure quantum states with tensor networks", paragraph "Matrix
+Product States"): sites T[0..n-1], T[j] of shape [chi_j, 2, chi_{j+1}], chi_0 = chi_n = 1,
+psi[s_0..s_{n-1}] = T[0][:, s_0, :] ... T[n-1][:, s_{n-1}, :].  The object also records
+its orthogonality centre c: sites left of c are left-orthonormal, sites right of c are
+right-orthonormal.
+
+Compression step (Sec. "Simulating unitary quantum circuits with DMRG", Defs. "Unitary
+chunk" and "Compression step"): given the ket A (normalised) and the chunk's MPO W, fit a
+bra B of bond dimension <= chi_max maximising |<B|W A>|^2 by optimising one tensor at a
+time with the others fixed: the environment F of a site is the overlap network with that
+bra tensor removed, the optimum is F / sqrt(<F|F>), and the partial fidelity is
+f = |<B|W A>|^2.
+
+The paper states only the one-site update.  Readings used for what it leaves open:
+
+1. Initial guess (this is where bond dimensions grow).  The chunk is a single layer of
+   disjoint blocks; the initial bra is A with every block applied gate-by-gate in
+   canonical form, two-qubit blocks followed by a truncated SVD of the two-site tensor
+   (keep the smallest rank k <= chi_max whose discarded weight sum_{i>=k} s_i^2 is
+   <= tol * sum_i s_i^2).  Without truncation this guess is the exact W|A>.
+2. Then s one-site sweeps against the exact target W|A> (W the chunk's MPO): left to
+   right first, alternating; each site takes F / ||F|| re-orthonormalised by QR (LQ when
+   moving right to left), the triangular factor being dropped because the next site's
+   update is recomputed from the environments.  One direction is one sweep; with s even
+   the centre ends at site 0, with s odd at site n-1.  Bond dimensions do not change in
+   the sweeps.
+3. f is ||F||^2 at the last update of the last sweep: B is normalised with every other
+   site orthonormal, W unitary and A normalised, so ||F|| = |<B|W A>|.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+from typing import List
+
+import numpy as np
+
+EINSUM = dict(optimize=True)
+
+
+@dataclass
+class MPS:
+    T: List[np.ndarray]
+    centre: int = 0
+
+    @property
+    def n(self) -> int:
+        return len(self.T)
+
+    def bonds(self) -> List[int]:
+        return [1] + [t.shape[2] for t in self.T[:-1]] + [1]
+
+    def copy(self) -> "MPS":
+        return MPS([t.copy() for t in self.T], self.centre)
+
+
+def product_zero(n: int) -> MPS:
+    """|0...0> (Alg. 1 / Alg. 2 initial state): all bonds 1."""
+    T = []
+    for _ in range(n):
+        t = np.zeros((1, 2, 1), dtype=np.complex128)
+        t[0, 0, 0] = 1.0
+        T.append(t)
+    return MPS(T, 0)
+
+
+def to_dense(mps: MPS) -> np.ndarray:
+    """Contract the chain into the order-n amplitude tensor (tests only)."""
+    v = mps.T[0]
+    for t in mps.T[1:]:
+        v = np.tensordot(v, t, axes=([v.ndim - 1], [0]))
+    return v.reshape((2,) * mps.n)
+
+
+# ----------------------------------------------------------------------------- gauge moves
+
+
+def qr_hop_right(mps: MPS, j: int) -> None:
+    """Move the centre from j to j+1: T_j = Q R, T_j := Q, T_{j+1} := R T_{j+1}."""
+    t = mps.T[j]
+    al, _, ar = t.shape
+    Q, R = np.linalg.qr(t.reshape(al * 2, ar))
+    mps.T[j] = Q.reshape(al, 2, Q.shape[1])
+    mps.T[j + 1] = np.einsum("ka,asb->ksb", R, mps.T[j + 1])
+    mps.centre = j + 1
+
+
+def lq_hop_left(mps: MPS, j: int) -> None:
+    """Move the centre from j to j-1: T_j = L Q (as al x (2 ar)), T_j := Q,
+    T_{j-1} := T_{j-1} L."""
+    t = mps.T[j]
+    al, _, ar = t.shape
+    Qh, Rh = np.linalg.qr(t.reshape(al, 2 * ar).conj().T)
+    mps.T[j] = Qh.conj().T.reshape(Qh.shape[1], 2, ar)
+    mps.T[j - 1] = np.einsum("asb,bk->ask", mps.T[j - 1], Rh.conj().T)
+    mps.centre = j - 1
+
+
+def move_centre(mps: MPS, target: int) -> None:
+    while mps.centre < target:
+        qr_hop_right(mps, mps.centre)
+    while mps.centre > target:
+        lq_hop_left(mps, mps.centre)
+
+
+# ----------------------------------------------------------------------------- measurement
+
+
+def measure_probs(mps: MPS, q: int):
+    """p_m = <psi|P_m^{Q_q}|psi> (Sec. "Mid-circuit measurements"), evaluated at the
+    orthogonality centre moved to q.  Returns the raw slice weights (r_0, r_1); their sum
+    is the squared norm (1 up to rounding)."""
+    move_centre(mps, q)
+    t = mps.T[q]
+    r0 = float(np.vdot(t[:, 0, :], t[:, 0, :]).real)
+    r1 = float(np.vdot(t[:, 1, :], t[:, 1, :]).real)
+    return r0, r1
+
+
+def collapse(mps: MPS, q: int, m: int, r_m: float) -> None:
+    """P_m on the physical leg of the centre tensor q, rescaled by 1/sqrt(r_m) so the
+    state has norm 1 (Sec. "Mid-circuit measurements": only the local tensor changes)."""
+    assert mps.centre == q
+    t = mps.T[q].copy()
+    t[:, 1 - m, :] = 0.0
+    mps.T[q] = t / np.sqrt(r_m)
+
+
+# ----------------------------------------------------------------------------- compression
+
+
+def env_left(L, B, W, A):
+    """L_{j+1}[c,e,x] = sum L_j[b,d,a] conj(B_j[b,s,c]) W_j[d,s,t,e] A_j[a,t,x]."""
+    return np.einsum("bda,bsc,dste,atx->cex", L, B.conj(), W, A, **EINSUM)
+
+
+def env_right(R, B, W, A):
+    """R_j[b,d,a] = sum R_{j+1}[c,e,x] conj(B_j[b,s,c]) W_j[d,s,t,e] A_j[a,t,x]."""
+    return np.einsum("cex,bsc,dste,atx->bda", R, B.conj(), W, A, **EINSUM)
+
+
+def site_env(L, W, A, R):
+    """F_j[b,s,c] = sum L_j[b,d,a] W_j[d,s,t,e] A_j[a,t,x] R_{j+1}[c,e,x]."""
+    return np.einsum("bda,dste,atx,cex->bsc", L, W, A, R, **EINSUM)
+
+
+def trunc_rank(s: np.ndarray, cap: int, tol: float) -> int:
+    """Smallest k >= 1 with sum_{i>=k} s_i^2 <= tol * sum_i s_i^2, then min(k, cap)."""
+    w = s.astype(np.float64) ** 2
+    total = float(w.sum())
+    tail = np.concatenate([np.cumsum(w[::-1])[::-1], [0.0]])  # tail[k] = sum_{i>=k}
+    k = 1
+    while k < len(s) and tail[k] > tol * total:
+        k += 1
+    return max(1, min(k, cap, len(s)))
+
+
+@dataclass
+class CompressInfo:
+    f: float
+    fidelities_per_sweep: List[float]
+    guess_weights: List[float]
+
+
+def initial_guess(A: MPS, blocks, chi_max: int, tol: float):
+    """Initial bra: the chunk applied block by block to a copy of A, right to left, in
+    canonical form (the usual gate-by-gate update).  A two-qubit block G on (q, q+1):
+    move the centre to q+1, Theta[a,s,u,b] = sum G[s,u,t,v] A_q[a,t,x] A_{q+1}[x,v,b],
+    truncated SVD of Theta as (2 chi_q) x (2 chi_{q+2}) with rank ``trunc_rank(s, chi_max,
+    tol)``, B_q := U S / ||S||, B_{q+1} := Vh (centre q).  A single-qubit block U on q:
+    B_q[a,s,b] = sum_t U[s,t] A_q[a,t,b].  Returns (B, kept weights)."""
+    B = A.copy()
+    kept = []
+    for q, G in sorted(blocks, key=lambda x: -x[0]):
+        if G.shape == (2, 2):
+            B.T[q] = np.einsum("st,atb->asb", G, B.T[q])
+            continue
+        move_centre(B, q + 1)
+        th = np.einsum("asx,xtb->astb", B.T[q], B.T[q + 1])
+        th = np.einsum("uvst,astb->auvb", G.reshape(2, 2, 2, 2), th)
+        al, br = th.shape[0], th.shape[3]
+        U, s, Vh = np.linalg.svd(th.reshape(al * 2, 2 * br), full_matrices=False)
+        k = trunc_rank(s, chi_max, tol)
+        w = float(np.sum(s[:k] ** 2))
+        kept.append(w / float(np.sum(s ** 2)))
+        B.T[q] = (U[:, :k] * (s[None, :k] / np.sqrt(w))).reshape(al, 2, k)
+        B.T[q + 1] = Vh[:k].reshape(k, 2, br)
+        B.centre = q
+    return B, kept
+
+
+def compress(A: MPS, blocks, W, chi_max: int, tol: float, sweeps: int):
+    """CompressionStep (Sec. "Simulating unitary quantum circuits with DMRG") with the
+    readings in the module header.  ``blocks`` is the chunk as [(q, 4x4 or 2x2 matrix)],
+    W its MPO.  A is not modified.  Returns (B, info), B normalised with centre 0 (sweeps
+    even) or n-1 (odd)."""
+    assert sweeps >= 1
+    n = A.n
+    B0, kept = initial_guess(A, blocks, chi_max, tol)
+    move_centre(B0, 0)
+    B = B0.T
+    one = np.ones((1, 1, 1), dtype=np.complex128)
+    L: List = [None] * (n + 1)
+    R: List = [None] * (n + 1)
+    L[0] = one
+    R[n] = one
+    for j in range(n - 1, 0, -1):
+        R[j] = env_right(R[j + 1], B[j], W[j], A.T[j])
+    fids = []
+    centre = 0
+    for sw in range(sweeps):
+        if sw % 2 == 0:  # left to right
+            for j in range(0, n - 1):
+                F = site_env(L[j], W[j], A.T[j], R[j + 1])
+                bl, br = F.shape[0], F.shape[2]
+                Q, _ = np.linalg.qr(F.reshape(bl * 2, br))
+                B[j] = Q.reshape(bl, 2, Q.shape[1])
+                L[j + 1] = env_left(L[j], B[j], W[j], A.T[j])
+            F = site_env(L[n - 1], W[n - 1], A.T[n - 1], R[n])
+            nrm2 = float(np.vdot(F, F).real)
+            B[n - 1] = F / np.sqrt(nrm2)
+            centre = n - 1
+        else:  # right to left
+            for j in range(n - 1, 0, -1):
+                F = site_env(L[j], W[j], A.T[j], R[j + 1])
+                bl, br = F.shape[0], F.shape[2]
+                Qh, _ = np.linalg.qr(F.reshape(bl, 2 * br).conj().T)
+                B[j] = Qh.conj().T.reshape(Qh.shape[1], 2, br)
+                R[j] = env_right(R[j + 1], B[j], W[j], A.T[j])
+            F = site_env(L[0], W[0], A.T[0], R[1])
+            nrm2 = float(np.vdot(F, F).real)
+            B[0] = F / np.sqrt(nrm2)
+            centre = 0
+        fids.append(nrm2)
+    return MPS(B, centre), CompressInfo(fids[-1], fids, kept)
+
+
+# ----------------------------------------------------------------------------- exact mode
+
+
+def apply_mpo_exact(A: MPS, W, svd_tol: float = 1e-14) -> MPS:
+    """Exact W|A>: site-wise product with bonds chi*D, then an SVD sweep that drops only
+    singular values below svd_tol * s_max (exact up to rounding).  Centre ends at 0."""
+    n = A.n
+    T = []
+    for j in range(n):
+        a, w = A.T[j], W[j]
+        t = np.einsum("dste,atx->adsxe", w, a, **EINSUM)
+        T.append(t.reshape(a.shape[0] * w.shape[0], 2, a.shape[2] * w.shape[3]))
+    out = MPS(T, n - 1)
+    out.centre = n - 1  # not canonical yet: sweep QR left to right, then SVD back
+    for j in range(n - 1):
+        t = out.T[j]
+        al, _, ar = t.shape
+        Q, R = np.linalg.qr(t.reshape(al * 2, ar))
+        out.T[j] = Q.reshape(al, 2, Q.shape[1])
+        out.T[j + 1] = np.einsum("ka,asb->ksb", R, out.T[j + 1])
+    for j in range(n - 1, 0, -1):
+        t = out.T[j]
+        al, _, ar = t.shape
+        U, s, Vh = np.linalg.svd(t.reshape(al, 2 * ar), full_matrices=False)
+        k = max(1, int(np.sum(s > svd_tol * s[0])))
+        out.T[j] = Vh[:k].reshape(k, 2, ar)
+        out.T[j - 1] = np.einsum("asb,bk->ask", out.T[j - 1], U[:, :k] * s[None, :k])
+    out.centre = 0
+    return out

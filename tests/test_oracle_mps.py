@@ -1,0 +1,252 @@
+"""Pins of the MPS oracle (O2): gauge moves, measurement, the chunk MPO and the
+compression step against the state-vector oracle, dense brute force, Eckart-Young and the
+invariants the method fixes (f <= 1, f non-decreasing over sweeps, exactness when chi is
+large enough)."""
+import itertools
+
+import numpy as np
+import pytest
+
+import circuits as C
+from conftest import read_golden_rows
+from oracle import drivers as D, layers as LY, mps as M, statevector as SV
+
+
+def random_mps(rng, n, chi):
+    bonds = [1] + [min(chi, 2 ** min(b, n - b)) for b in range(1, n)] + [1]
+    T = [rng.standard_normal((bonds[j], 2, bonds[j + 1]))
+         + 1j * rng.standard_normal((bonds[j], 2, bonds[j + 1])) for j in range(n)]
+    m = M.MPS(T, n - 1)
+    # canonicalise (centre 0) and normalise
+    for j in range(n - 1, 0, -1):
+        M.lq_hop_left(m, j)
+    m.T[0] /= np.linalg.norm(m.T[0])
+    return m
+
+
+def dense(m):
+    return M.to_dense(m).reshape(-1)
+
+
+def test_product_zero():
+    v = dense(M.product_zero(4))
+    assert v[0] == 1 and np.count_nonzero(v) == 1
+
+
+@pytest.mark.parametrize("n,chi", [(4, 4), (6, 3)])
+def test_gauge_moves_preserve_state_and_orthonormality(n, chi):
+    rng = np.random.default_rng(n * 10 + chi)
+    m = random_mps(rng, n, chi)
+    v0 = dense(m)
+    for tgt in [n - 1, 2, 0, n - 2]:
+        M.move_centre(m, tgt)
+        np.testing.assert_allclose(dense(m), v0, atol=1e-12)
+        for j in range(tgt):  # left-orthonormal
+            t = m.T[j]
+            g = np.einsum("asb,asc->bc", t.conj(), t)
+            np.testing.assert_allclose(g, np.eye(g.shape[0]), atol=1e-12)
+        for j in range(tgt + 1, n):  # right-orthonormal
+            t = m.T[j]
+            g = np.einsum("asb,csb->ac", t, t.conj())
+            np.testing.assert_allclose(g, np.eye(g.shape[0]), atol=1e-12)
+
+
+def test_measure_and_collapse_match_statevector():
+    rng = np.random.default_rng(5)
+    n = 5
+    m = random_mps(rng, n, 4)
+    psi = M.to_dense(m)
+    for q in [3, 0, 4, 2]:
+        r0, r1 = M.measure_probs(m, q)
+        s0, s1 = SV.probabilities(psi, q)
+        assert abs(r0 - s0) < 1e-12 and abs(r1 - s1) < 1e-12
+    M.measure_probs(m, 2)
+    r0, r1 = M.measure_probs(m, 2)
+    M.collapse(m, 2, 1, r1)
+    want = SV.project(psi, 2, 1, SV.probabilities(psi, 2)[1])
+    np.testing.assert_allclose(M.to_dense(m), want, atol=1e-12)
+
+
+def test_blocks_mpo_matches_dense_layer():
+    rng = np.random.default_rng(3)
+    n = 5
+    chunk = [C.Gate((1,), C.haar_unitary(rng, 2)),
+             C.Gate((1, 2), C.haar_su4(rng)),
+             C.Gate((4, 3), C.CNOT),
+             C.Gate((0,), C.H),
+             C.Gate((2,), C.X, cond=C.Cond((0,), "xor", 1)),
+             C.Gate((3,), C.Z, cond=C.Cond((0,), "xor", 0))]
+    for c0 in (0, 1):
+        c = np.array([c0])
+        blocks, empty = LY.chunk_blocks(n, chunk, c)
+        assert not empty
+        W = LY.blocks_mpo(n, blocks)
+        got = LY.chunk_unitary_dense(n, W)
+        # brute force: apply the applied gates in order to every basis vector
+        want = np.zeros((2 ** n, 2 ** n), dtype=np.complex128)
+        for col in range(2 ** n):
+            e = np.zeros(2 ** n, dtype=np.complex128)
+            e[col] = 1
+            v = e.reshape((2,) * n)
+            for g in chunk:
+                if SV.cond_holds(g.cond, c):
+                    v = SV.apply_gate(v, g.qubits, g.matrix)
+            want[:, col] = v.reshape(-1)
+        np.testing.assert_allclose(got, want, atol=1e-12)
+        # CNOT has operator-Schmidt rank 2
+        assert W[3].shape[3] == 2
+
+
+def test_chunking_rules():
+    circ = C.ghz_dynamic(7)
+    n, steps = LY.chunk_circuit(circ)
+    kinds = ["M" if isinstance(s, C.Measure) else len(s) for s in steps]
+    # H+CNOT layer, second CNOT layer, 3 measurements, feed-forward X layer,
+    # 3 reset measurements, reset X layer
+    assert kinds == [7, 3, "M", "M", "M", 3, "M", "M", "M", 3]
+    circ = C.Circuit(3, 0, [C.Gate((0, 1), C.CNOT), C.Gate((1, 2), C.CNOT)])
+    assert len(LY.chunk_circuit(circ)[1]) == 2
+    assert len(LY.chunk_circuit(circ, k=1)[1]) == 2
+    circ = C.Circuit(4, 0, [C.Gate((0, 1), C.CNOT), C.Gate((2, 3), C.CNOT), C.Gate((0,), C.H)])
+    assert len(LY.chunk_circuit(circ)[1]) == 1
+    assert len(LY.chunk_circuit(circ, k=2)[1]) == 2
+
+
+def _layer_blocks(rng, n, parity):
+    return [(q, C.haar_su4(rng)) for q in range(parity, n - 1, 2)]
+
+
+@pytest.mark.parametrize("n", [4, 7])
+def test_compress_exact_regime_equals_statevector(n):
+    rng = np.random.default_rng(n)
+    A = random_mps(rng, n, 2)
+    blocks = _layer_blocks(rng, n, 1) + [(0, C.haar_unitary(rng, 2))]
+    W = LY.blocks_mpo(n, blocks)
+    want = LY.chunk_unitary_dense(n, W) @ dense(A)
+    for s in (1, 2, 3):
+        B, info = M.compress(A.copy(), blocks, W, 64, 0.0, s)
+        assert abs(info.f - 1.0) < 1e-12
+        assert abs(abs(np.vdot(dense(B), want)) - 1.0) < 1e-12
+        assert B.centre == (0 if s % 2 == 0 else n - 1)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_compress_truncated_fidelity_definition_and_monotone(seed):
+    rng = np.random.default_rng(seed)
+    n = 8
+    A = random_mps(rng, n, 3)  # bonds <= chi_max, as every compression leaves them
+    blocks = _layer_blocks(rng, n, seed % 2)
+    W = LY.blocks_mpo(n, blocks)
+    target = LY.chunk_unitary_dense(n, W) @ dense(A)
+    fs = []
+    for s in range(1, 7):
+        B, info = M.compress(A.copy(), blocks, W, 3, 0.0, s)
+        # f is |<B|W A>|^2, recomputed densely; B normalised
+        assert abs(np.linalg.norm(dense(B)) - 1.0) < 1e-12
+        assert abs(abs(np.vdot(dense(B), target)) ** 2 - info.f) < 1e-12
+        assert info.f <= 1.0 + 1e-12
+        assert all(b <= 3 for b in B.bonds())
+        fs.append(info.f)
+        # the per-sweep record is non-decreasing too
+        assert all(y >= x - 1e-12 for x, y in zip(info.fidelities_per_sweep,
+                                                   info.fidelities_per_sweep[1:]))
+    assert all(y >= x - 1e-12 for x, y in zip(fs, fs[1:]))
+    assert fs[-1] < 1.0 - 1e-6  # truncation really happened
+
+
+def test_compress_two_sites_is_eckart_young():
+    rng = np.random.default_rng(11)
+    A = random_mps(rng, 2, 2)
+    G = C.haar_su4(rng)
+    blocks = [(0, G)]
+    W = LY.blocks_mpo(2, blocks)
+    target = (G @ dense(A)).reshape(2, 2)
+    s = np.linalg.svd(target, compute_uv=False)
+    B, info = M.compress(A.copy(), blocks, W, 1, 0.0, 2)
+    assert abs(info.f - s[0] ** 2) < 1e-12
+
+
+def test_compress_converges_to_optimal_middle_truncation():
+    # n = 4, chi_max = 2: only the middle bond (exact rank 4) needs truncating, so the global
+    # optimum is the rank-2 SVD truncation of the exact state at that bond.
+    rng = np.random.default_rng(4)
+    n = 4
+    A = random_mps(rng, n, 2)
+    blocks = [(1, C.haar_su4(rng))]
+    W = LY.blocks_mpo(n, blocks)
+    target = LY.chunk_unitary_dense(n, W) @ dense(A)
+    s = np.linalg.svd(target.reshape(4, 4), compute_uv=False)
+    B, info = M.compress(A.copy(), blocks, W, 2, 0.0, 12)
+    assert abs(info.f - (s[0] ** 2 + s[1] ** 2)) < 1e-9
+
+
+def test_truncation_rank_rule():
+    s = np.array([0.8, 0.5, 0.3, 1e-6, 1e-9])
+    assert M.trunc_rank(s, 10, 0.0) == 5
+    assert M.trunc_rank(s, 10, 1e-10) == 3    # 1e-12 + 1e-18 discarded relative to ~0.98
+    assert M.trunc_rank(s, 2, 1e-10) == 2
+    assert M.trunc_rank(np.array([1.0, 0.0]), 4, 1e-12) == 1
+
+
+def test_apply_mpo_exact_matches_dense():
+    rng = np.random.default_rng(8)
+    n = 6
+    A = random_mps(rng, n, 4)
+    blocks = _layer_blocks(rng, n, 0)
+    W = LY.blocks_mpo(n, blocks)
+    B = M.apply_mpo_exact(A, W)
+    np.testing.assert_allclose(dense(B), LY.chunk_unitary_dense(n, W) @ dense(A), atol=1e-12)
+
+
+# ----------------------------------------------------------------------------- drivers
+
+
+@pytest.mark.parametrize("circ", [C.teleport(2), C.ghz_dynamic(9), C.ghz_dynamic(10),
+                                  C.brickwork(8, 6, 0.2, 5)], ids=lambda c: c.name)
+def test_single_path_mps_equals_statevector(circ):
+    prm = D.Params(chi_max=64, tol=1e-12, sweeps=2)
+    for shot in range(3):
+        r = D.run_single_path(circ, prm, 17, shot)
+        s = SV.run_single_path(circ, 17, shot)
+        assert r.outcomes == s.outcomes
+        assert abs(r.p - s.p) < 1e-12
+        assert abs(r.F - 1.0) < 1e-10
+        assert abs(abs(np.vdot(M.to_dense(r.mps), s.psi)) ** 2 - 1.0) < 1e-10
+
+
+@pytest.mark.parametrize("row", read_golden_rows("ghz_paper.txt")[:3])
+def test_multi_path_mps_ghz(row):
+    n, r, npaths = (int(x) for x in row)
+    circ = C.ghz_dynamic(n)
+    prm = D.Params(chi_max=4, tol=1e-10, sweeps=2)  # the paper's chi = 4 for GHZ
+    br = D.run_multi_path(circ, prm)
+    assert len(br) == npaths
+    for b in br:
+        assert abs(b.p - 2.0 ** -r) < 1e-12
+        assert abs(b.F - 1.0) < 1e-10
+    assert abs(D.multipath_fidelity(br) - 1.0) < 1e-10
+
+
+def test_multi_path_mps_equals_statevector_with_topm():
+    circ = C.brickwork(6, 5, 0.3, 2)
+    prm = D.Params(chi_max=64, tol=1e-12, sweeps=2)
+    for Mcap in (None, 4):
+        a = D.run_multi_path(circ, prm, M=Mcap)
+        b = SV.run_multi_path(circ, M=Mcap)
+        assert [x.path for x in a] == [y.path for y in b]
+        for x, y in zip(a, b):
+            assert abs(x.p - y.p) < 1e-12
+            assert abs(abs(np.vdot(M.to_dense(x.mps), y.psi)) ** 2 - 1) < 1e-10
+
+
+def test_teleport_chi2_paper_setting():
+    # the paper's teleport setting chi = 2, s = 2 reproduces the circuit semantics
+    circ = C.teleport(3)
+    br = D.run_multi_path(circ, D.Params(chi_max=2, tol=1e-10, sweeps=2))
+    assert len(br) == 4
+    inp = circ.meta["input"]
+    for b in br:
+        assert abs(b.p - 0.25) < 1e-12
+        psi = M.to_dense(b.mps)
+        bob = psi[b.path[0], b.path[1], :]
+        assert abs(abs(np.vdot(bob, inp)) ** 2 - 1.0) < 1e-12
