@@ -1,0 +1,206 @@
+/*
+ * libdcs -- dynamic-circuit MPS simulation on one B300 (sm_103a): C ABI.
+ *
+ * The operations follow the paper "Tensor Network Simulation of Dynamic Circuits":
+ *   - branch state {(p_gamma, c_gamma, psi_gamma)}     (Def. "State of a dynamic circuit")
+ *   - InitializeState |0...0>, c = 0, p = 1, F = 1      (Alg. 1 / Alg. 2, initialisation)
+ *   - CompressionStep of one unitary chunk, F *= f      (Sec. "Simulating unitary quantum
+ *                                                        circuits with DMRG", Defs. "Unitary
+ *                                                        chunk", "Compression step")
+ *   - MeasureProb / Measure / Collapse                  (Sec. "Mid-circuit measurements")
+ *   - classically controlled operations                 (Sec. "Classically controlled
+ *                                                        operations")
+ *   - reset = measure + conditional X                   (Sec. "Reset operations")
+ *   - chunk construction                                (Sec. "Handling unitary chunks in
+ *                                                        dynamic circuits")
+ *   - single-path and multi-path strategies, TopK       (Alg. 1, Alg. 2)
+ *
+ * Conventions
+ *   - Every call returns dcs_status_t; dcs_last_error(ctx) describes the last failure.
+ *   - Device work is enqueued on the stream given to dcs_create and is asynchronous unless
+ *     a call says it synchronises (the ones that fill host buffers).
+ *   - The caller owns the device arena (at least dcs_arena_bytes() bytes, 256-byte aligned)
+ *     and all host buffers.  The library allocates no device memory; it keeps host
+ *     metadata and a pinned host staging buffer per context.
+ *   - Qubit q is MPS site q; two-qubit gates act on neighbouring qubits.
+ *   - Slots: in single-path mode a slot is one shot (independent run of Alg. 1); in
+ *     multi-path mode slots hold the branches of the list L of Alg. 2.
+ *   - Complex numbers are stored as (re, im) pairs; tensors on the device are complex64,
+ *     probabilities and fidelities float64.
+ */
+#ifndef DCS_H
+#define DCS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* dcs_stream_t; /* a cudaStream_t */
+
+typedef enum {
+  DCS_OK = 0,
+  DCS_ERR_INVALID = 1,     /* bad argument or configuration */
+  DCS_ERR_OOM = 2,         /* arena or slot pool too small */
+  DCS_ERR_ZERO_PROB = 3,   /* collapse onto an outcome with p_m <= 1e-12 (per-slot flag) */
+  DCS_ERR_NUMERICAL = 4,   /* NaN/Inf in a norm, probability or fidelity (per-slot flag) */
+  DCS_ERR_TIMEOUT = 5,     /* a bounded device wait gave up */
+  DCS_ERR_CUDA = 6,        /* a CUDA runtime call failed */
+  DCS_ERR_UNSUPPORTED = 7  /* valid request outside what this build implements */
+} dcs_status_t;
+
+/* classical register: up to 64 * DCS_CWORDS bits per slot */
+#define DCS_CWORDS 8
+/* largest number of qubits (MPS sites) */
+#define DCS_MAX_QUBITS 128
+/* largest bond dimension of the fused small-chi kernels */
+#define DCS_MAX_CHI_FUSED 32
+
+typedef enum { DCS_COND_NONE = 0, DCS_COND_XOR = 1, DCS_COND_AND = 2 } dcs_cond_op;
+
+/* phi(c) of a classically controlled operation: XOR (parity) or AND of the bits set in
+ * mask, compared with value (0 or 1).  op == DCS_COND_NONE: always true. */
+typedef struct {
+  uint64_t mask[DCS_CWORDS];
+  int32_t op;
+  int32_t value;
+} dcs_cond;
+
+typedef enum {
+  DCS_OP_GATE1 = 1,   /* 2x2 unitary on q0 */
+  DCS_OP_GATE2 = 2,   /* 4x4 unitary on (q0, q1), |q0 - q1| = 1, basis |s_q0 s_q1> */
+  DCS_OP_MEASURE = 3, /* measure q0 into cbit */
+  DCS_OP_RESET = 4    /* reset q0 through cbit (measure into cbit, X if cbit == 1) */
+} dcs_op_kind;
+
+/* One circuit operation.  m holds the gate matrix row-major as (re, im) pairs:
+ * m[2*(r*d + c)] = Re U[r][c], m[2*(r*d + c) + 1] = Im U[r][c], d = 2 or 4. */
+typedef struct {
+  int32_t kind;
+  int32_t q0;
+  int32_t q1;
+  int32_t cbit;
+  double m[32];
+  dcs_cond cond;
+} dcs_op;
+
+typedef enum { DCS_PREC_FP32 = 0 } dcs_precision;
+
+typedef struct {
+  int32_t n_qubits;     /* 1 .. DCS_MAX_QUBITS */
+  int32_t chi_max;      /* bond-dimension cap (the paper's chi) */
+  double tol;           /* relative discarded weight allowed per truncation */
+  int32_t sweeps;       /* one-site sweeps per compression step (the paper's s), >= 1 */
+  int32_t chunk_k;      /* maximum operations per chunk (the paper's k); 0 = one layer */
+  int32_t precision;    /* dcs_precision */
+  int32_t n_cbits;      /* classical register size m, <= 64 * DCS_CWORDS */
+  int32_t n_slots;      /* shots (single-path) or branch-pool capacity (multi-path) */
+  uint64_t seed;        /* key of the counter-based outcome sampler */
+} dcs_config;
+
+/* Per-slot result flags (dcs_get_results). */
+#define DCS_FLAG_DRAW_NEAR_THRESHOLD 1u /* some draw had |u - p_0| < 1e-6 */
+#define DCS_FLAG_ZERO_PROB 2u           /* a collapse was refused (p_m <= 1e-12) */
+#define DCS_FLAG_NUMERICAL 4u           /* NaN/Inf met in a norm or probability */
+#define DCS_FLAG_TOPK_NEAR_TIE 8u       /* TopK cut through keys within one bucket */
+
+typedef struct dcs_ctx_s* dcs_ctx_t;
+
+/* Bytes of device arena dcs_create needs for cfg (all slots, MPS pair, environment
+ * caches, per-slot state, circuit program).  0 if cfg is invalid. */
+size_t dcs_arena_bytes(const dcs_config* cfg);
+
+/* InitializeTN: bind a context to the caller's device arena and stream.  Carves the arena;
+ * does not touch device memory.  cfg is copied.  Fails with DCS_ERR_OOM if arena_bytes <
+ * dcs_arena_bytes(cfg), DCS_ERR_UNSUPPORTED if chi_max > DCS_MAX_CHI_FUSED. */
+dcs_status_t dcs_create(dcs_ctx_t* ctx, const dcs_config* cfg, void* dev_arena,
+                        size_t arena_bytes, dcs_stream_t stream);
+
+/* Releases host resources of ctx; the arena stays the caller's. */
+dcs_status_t dcs_destroy(dcs_ctx_t ctx);
+
+/* Message of the last failing call on ctx (never NULL). */
+const char* dcs_last_error(dcs_ctx_t ctx);
+
+/* InitializeState (Alg. 1 / Alg. 2 first line): every slot of the first n_active gets
+ * |0...0>, c = 0, p = 1, F = 1, centre 0.  multipath = 0: n_active shots, shot id of slot
+ * i = shot0 + i (the sampler's counter); multipath = 1: one branch (n_active must be 1),
+ * the rest of the pool free. */
+dcs_status_t dcs_init_state(dcs_ctx_t ctx, int n_active, int multipath, uint64_t shot0);
+
+/* CompressionStep for one chunk on every active slot.  gates: n_gates GATE1/GATE2 ops that
+ * form one chunk (disjoint nearest-neighbour blocks: no qubit in two two-qubit gates);
+ * conditions are evaluated per slot on its register, and a slot on which every gate is
+ * skipped is left unchanged (no compression, f = 1).  Otherwise the ket is replaced by
+ * the compressed bra and F *= f.  fid_out: optional DEVICE pointer to n_slots doubles
+ * receiving f per slot (1 for skipped slots).  Returns DCS_ERR_INVALID if the gates do
+ * not form one chunk. */
+dcs_status_t dcs_apply_layer(dcs_ctx_t ctx, const dcs_op* gates, int n_gates,
+                             double* fid_out);
+
+/* MeasureProb: p_0 = <psi|P_0|psi> / <psi|psi> of qubit for every active slot (moves the
+ * orthogonality centre to qubit).  p0_out: DEVICE pointer to n_slots doubles (inactive
+ * slots untouched). */
+dcs_status_t dcs_measure_prob(dcs_ctx_t ctx, int qubit, double* p0_out);
+
+/* Single-path Measure (Alg. 1): per shot, u = Philox4x32-10(key = seed, counter =
+ * (meas_idx, 0, shot id)) as a 53-bit double, m = 0 iff u < p_0, Collapse onto m
+ * (P_m / sqrt(p_m)), p *= p_m, c[cbit] = m.  Draws with |u - p_0| < 1e-6 set
+ * DCS_FLAG_DRAW_NEAR_THRESHOLD; p_m <= 1e-12 sets DCS_FLAG_ZERO_PROB and leaves the slot
+ * uncollapsed. */
+dcs_status_t dcs_measure_sample(dcs_ctx_t ctx, int qubit, int cbit, uint64_t meas_idx);
+
+/* Collapse onto given outcomes (tests, replay of a recorded path): outcome is a HOST
+ * array of n_slots bytes (0/1).  p *= p_m, c[cbit] = m, same error flags. */
+dcs_status_t dcs_collapse(dcs_ctx_t ctx, int qubit, int cbit, const uint8_t* outcome);
+
+/* Multi-path measurement (Alg. 2): every active branch gamma spawns the children gamma m,
+ * m in {0, 1} with p_m > eps, in list order (children of earlier branches first, m = 0
+ * before m = 1): p_{gamma m} = p_gamma p_m, c[cbit] = m, F copied, MPS = Collapse(m).
+ * Fails with DCS_ERR_OOM (state unchanged) if the children exceed the pool. */
+dcs_status_t dcs_branch_split(dcs_ctx_t ctx, int qubit, int cbit, double eps);
+
+/* TopKByWeight (Alg. 2): if more than M branches are active keep the M with the largest
+ * p_gamma, compared through the key round(p / (1e-5 * max p)); equal keys keep list order.
+ * The retained branches keep their relative order; p is not renormalised. */
+dcs_status_t dcs_branch_topk(dcs_ctx_t ctx, int M);
+
+/* Synchronises and copies results to HOST buffers (each may be NULL): for the active slots
+ * in list order, p (n doubles), F (n doubles), the register (n * DCS_CWORDS words), flags
+ * (n bytes), and the number n of active slots. */
+dcs_status_t dcs_get_results(dcs_ctx_t ctx, double* p, double* fid, uint64_t* cbits,
+                             int* n_active, uint8_t* flags);
+
+/* Checkpoint: synchronises and writes the MPS of active slot `slot` (list position) to a
+ * HOST buffer: int32 n, int32 bonds[n+1], int32 centre, then the site tensors
+ * [chi_l][2][chi_r] as complex64.  *bytes is the capacity on input and the size written
+ * on output; host_buf == NULL only queries the size. */
+dcs_status_t dcs_export_mps(dcs_ctx_t ctx, int slot, void* host_buf, size_t* bytes);
+
+/* Restore a slot's MPS from the dcs_export_mps format (bonds must not exceed the caps). */
+dcs_status_t dcs_import_mps(dcs_ctx_t ctx, int slot, const void* host_buf, size_t bytes);
+
+/* Runs a whole dynamic circuit (ops in order) from the current state: resets are lowered
+ * to measurement + conditional X; operations are grouped into chunks (a chunk closes at a
+ * measurement, before a two-qubit gate touching a qubit that already carries one in the
+ * chunk, and at chunk_k operations); each chunk is one dcs_apply_layer; runs of
+ * measurements are sampled (single-path, measurement ordinals counted from meas_idx0) or
+ * split and pruned to M branches (multi-path, M = max_branches; 0 = no pruning).  The
+ * circuit's tables are copied to the device once per call.  Asynchronous. */
+dcs_status_t dcs_run_circuit(dcs_ctx_t ctx, const dcs_op* ops, int n_ops, uint64_t meas_idx0,
+                             int max_branches);
+
+/* Number of kernels this context launched since it was created (a host-side count). */
+uint64_t dcs_kernel_launches(dcs_ctx_t ctx);
+
+/* Bytes this context copied host -> device (circuit tables, forced outcomes) since it was
+ * created. */
+uint64_t dcs_bytes_uploaded(dcs_ctx_t ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DCS_H */

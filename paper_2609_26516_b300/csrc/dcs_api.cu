@@ -1,0 +1,791 @@
+// Host side of the libdcs C ABI (declared in include/dcs.h): context and arena layout,
+// chunk construction, the per-chunk tables (with the FP64 operator-Schmidt split of every
+// two-qubit gate) and the single-/multi-path drivers of Alg. 1 and Alg. 2.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "dcs_kernels.cuh"
+
+using cd = std::complex<double>;
+using namespace dcs;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr size_t kProgBytes = 32ull << 20;  // device copy of one call's tables
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+struct Layout {
+  size_t mps0, mps1, lc, rc, bonds, centre, ketbuf, p, F, rr, creg, flags, shot, order, count,
+      status, plan, prog, total;
+  int chi_cap, site_stride, env_stride;
+  size_t mps_slot_stride, env_slot_stride;
+};
+
+bool valid_cfg(const dcs_config* c) {
+  return c && c->n_qubits >= 1 && c->n_qubits <= DCS_MAX_QUBITS && c->chi_max >= 1 &&
+         c->sweeps >= 1 && c->n_slots >= 1 && c->n_cbits >= 0 && c->n_cbits <= 64 * DCS_CWORDS &&
+         c->tol >= 0.0 && c->chunk_k >= 0 && c->precision == DCS_PREC_FP32;
+}
+
+Layout make_layout(const dcs_config* c) {
+  Layout L{};
+  const size_t n = (size_t)c->n_qubits, S = (size_t)c->n_slots;
+  L.chi_cap = fused_chi(c->chi_max);
+  L.site_stride = 2 * L.chi_cap * L.chi_cap;
+  L.env_stride = 4 * L.chi_cap * L.chi_cap;
+  L.mps_slot_stride = n * (size_t)L.site_stride;
+  L.env_slot_stride = (n + 1) * (size_t)L.env_stride;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = align_up(off + bytes);
+    return o;
+  };
+  L.mps0 = take(S * L.mps_slot_stride * sizeof(float2));
+  L.mps1 = take(S * L.mps_slot_stride * sizeof(float2));
+  L.lc = take(S * L.env_slot_stride * sizeof(float2));
+  L.rc = take(S * L.env_slot_stride * sizeof(float2));
+  L.bonds = take(S * 2 * (n + 1) * sizeof(int32_t));
+  L.centre = take(S * sizeof(int32_t));
+  L.ketbuf = take(S * sizeof(int32_t));
+  L.p = take(S * sizeof(double));
+  L.F = take(S * sizeof(double));
+  L.rr = take(S * 2 * sizeof(double));
+  L.creg = take(S * DCS_CWORDS * sizeof(uint64_t));
+  L.flags = take(S * sizeof(uint32_t));
+  L.shot = take(S * sizeof(uint64_t));
+  L.order = take(S * sizeof(int32_t));
+  L.count = take(sizeof(int32_t));
+  L.status = take(sizeof(int32_t));
+  L.plan = take((PLAN_HDR + 4 * S) * sizeof(int32_t));
+  L.prog = take(kProgBytes);
+  L.total = off;
+  return L;
+}
+
+// ----------------------------------------------------------------------------- 4x4 SVD
+// One-sided Jacobi SVD of a 4x4 complex matrix in FP64: M V = U Sigma.  Returns sigma
+// (descending), the columns of M V (= U Sigma) and V, reordered accordingly.
+void svd4(const cd M[16], double sig[4], cd MV[16], cd Vm[16]) {
+  cd X[16], V[16];
+  for (int i = 0; i < 16; ++i) {
+    X[i] = M[i];
+    V[i] = (i / 4 == i % 4) ? 1.0 : 0.0;
+  }
+  // X, V row-major [row][col]; rotate columns
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0;
+    for (int i = 0; i < 4; ++i)
+      for (int j = i + 1; j < 4; ++j) {
+        double a = 0, b = 0;
+        cd g = 0;
+        for (int r = 0; r < 4; ++r) {
+          a += std::norm(X[r * 4 + i]);
+          b += std::norm(X[r * 4 + j]);
+          g += std::conj(X[r * 4 + i]) * X[r * 4 + j];
+        }
+        const double ag = std::abs(g);
+        if (ag <= 1e-15 * std::sqrt(a * b) || ag == 0.0) continue;
+        off = std::max(off, ag / std::sqrt(a * b));
+        const double zeta = (b - a) / (2 * ag);
+        const double t = (zeta >= 0 ? 1.0 : -1.0) / (std::fabs(zeta) + std::sqrt(1 + zeta * zeta));
+        const double c = 1 / std::sqrt(1 + t * t), s = c * t;
+        const cd ph = std::conj(g) / ag;
+        for (int r = 0; r < 4; ++r) {
+          const cd xi = X[r * 4 + i], xj = ph * X[r * 4 + j];
+          X[r * 4 + i] = c * xi - s * xj;
+          X[r * 4 + j] = s * xi + c * xj;
+          const cd vi = V[r * 4 + i], vj = ph * V[r * 4 + j];
+          V[r * 4 + i] = c * vi - s * vj;
+          V[r * 4 + j] = s * vi + c * vj;
+        }
+      }
+    if (off < 1e-15) break;
+  }
+  double nrm[4];
+  int idx[4] = {0, 1, 2, 3};
+  for (int j = 0; j < 4; ++j) {
+    double s = 0;
+    for (int r = 0; r < 4; ++r) s += std::norm(X[r * 4 + j]);
+    nrm[j] = std::sqrt(s);
+  }
+  std::stable_sort(idx, idx + 4, [&](int a, int b) { return nrm[a] > nrm[b]; });
+  for (int k = 0; k < 4; ++k) {
+    sig[k] = nrm[idx[k]];
+    for (int r = 0; r < 4; ++r) {
+      MV[r * 4 + k] = X[r * 4 + idx[k]];
+      Vm[r * 4 + k] = V[r * 4 + idx[k]];
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------- program
+struct Step {
+  int kind;  // 0 layer, 1 measurement run
+  int idx;   // layer index, or first DMeas
+  int n;     // number of measurements
+};
+
+struct Program {
+  std::vector<DLayer> layers;
+  std::vector<DBlock> blocks;
+  std::vector<DGate1> g1;
+  std::vector<DCond> conds;
+  std::vector<DMeas> meas;
+  std::vector<Step> steps;
+};
+
+DCond to_dcond(const dcs_cond& c) {
+  DCond d;
+  std::memset(&d, 0, sizeof(d));
+  for (int w = 0; w < DCS_CWORDS; ++w) d.mask[w] = c.mask[w];
+  d.op = c.op;
+  d.value = c.value;
+  return d;
+}
+
+// Normalised gate: qubits ascending, matrix over |s_lo s_hi>.
+void gate_matrix(const dcs_op& o, cd* m, int& lo) {
+  if (o.kind == DCS_OP_GATE1) {
+    lo = o.q0;
+    for (int i = 0; i < 4; ++i) m[i] = cd(o.m[2 * i], o.m[2 * i + 1]);
+    return;
+  }
+  cd g[16];
+  for (int i = 0; i < 16; ++i) g[i] = cd(o.m[2 * i], o.m[2 * i + 1]);
+  if (o.q0 < o.q1) {
+    lo = o.q0;
+    for (int i = 0; i < 16; ++i) m[i] = g[i];
+  } else {
+    lo = o.q1;
+    // swap the two tensor factors on both the output and the input side
+    for (int oa = 0; oa < 2; ++oa)
+      for (int ob = 0; ob < 2; ++ob)
+        for (int ia = 0; ia < 2; ++ia)
+          for (int ib = 0; ib < 2; ++ib)
+            m[(oa * 2 + ob) * 4 + (ia * 2 + ib)] = g[(ob * 2 + oa) * 4 + (ib * 2 + ia)];
+  }
+}
+
+DGate1 to_dgate1(const cd* m, const dcs_cond& c) {
+  DGate1 g;
+  for (int i = 0; i < 4; ++i) g.u[i] = make_float2((float)m[i].real(), (float)m[i].imag());
+  g.cond = to_dcond(c);
+  return g;
+}
+
+// Tables of one chunk (gates in circuit order).  Returns "" or an error message.
+std::string build_layer(Program& P, int n, const std::vector<dcs_op>& gates) {
+  DLayer L;
+  std::memset(&L, 0, sizeof(L));
+  std::vector<int> pair_of(n, -1);   // left qubit of the two-qubit gate touching q
+  std::vector<int> two_pos(n, -1);   // position of that gate in the chunk
+  for (size_t i = 0; i < gates.size(); ++i) {
+    const dcs_op& o = gates[i];
+    if (o.kind != DCS_OP_GATE2) continue;
+    const int lo = std::min(o.q0, o.q1), hi = std::max(o.q0, o.q1);
+    if (hi - lo != 1) return "two-qubit gates must act on neighbouring qubits";
+    if (pair_of[lo] >= 0 || pair_of[hi] >= 0) return "a qubit carries two two-qubit gates in one chunk";
+    pair_of[lo] = lo;
+    pair_of[hi] = lo;
+    two_pos[lo] = two_pos[hi] = (int)i;
+  }
+  L.uncond = 0;
+  L.cond_off = (int)P.conds.size();
+  for (const dcs_op& o : gates) {
+    if (o.cond.op == DCS_COND_NONE) L.uncond = 1;
+    else P.conds.push_back(to_dcond(o.cond));
+  }
+  L.n_conds = (int)P.conds.size() - L.cond_off;
+  L.blk_off = (int)P.blocks.size();
+  // blocks in decreasing q
+  std::vector<int> lefts;
+  for (int q = 0; q < n; ++q)
+    if (pair_of[q] == q) lefts.push_back(q);
+  std::sort(lefts.rbegin(), lefts.rend());
+  for (size_t bi = 0; bi < lefts.size(); ++bi) {
+    const int q = lefts[bi];
+    const dcs_op& o2 = gates[two_pos[q]];
+    DBlock B;
+    std::memset(&B, 0, sizeof(B));
+    B.q = q;
+    cd G[16];
+    int lo;
+    gate_matrix(o2, G, lo);
+    for (int i = 0; i < 16; ++i) B.G[i] = make_float2((float)G[i].real(), (float)G[i].imag());
+    B.cond = to_dcond(o2.cond);
+    // operator-Schmidt split: M[(o0 i0), (o1 i1)] = G[(o0 o1), (i0 i1)]
+    cd M[16], MV[16], Vm[16];
+    double sig[4];
+    for (int o0 = 0; o0 < 2; ++o0)
+      for (int i0 = 0; i0 < 2; ++i0)
+        for (int o1 = 0; o1 < 2; ++o1)
+          for (int i1 = 0; i1 < 2; ++i1)
+            M[(o0 * 2 + i0) * 4 + (o1 * 2 + i1)] = G[(o0 * 2 + o1) * 4 + (i0 * 2 + i1)];
+    svd4(M, sig, MV, Vm);
+    int D = 0;
+    for (int k = 0; k < 4; ++k)
+      if (sig[k] > 1e-14 * sig[0]) ++D;
+    if (D < 1) D = 1;
+    B.D = D;
+    for (int d = 0; d < D; ++d) {
+      const double sq = std::sqrt(sig[d]);
+      for (int r = 0; r < 4; ++r) {
+        const cd wl = MV[r * 4 + d] / sq;              // U sqrt(sigma)
+        const cd wr = sq * std::conj(Vm[r * 4 + d]);   // sqrt(sigma) V^H
+        B.WL[r * 4 + d] = make_float2((float)wl.real(), (float)wl.imag());
+        B.WR[d * 4 + r] = make_float2((float)wr.real(), (float)wr.imag());
+      }
+    }
+    // single-qubit gates on q (side 0) and q+1 (side 1), before / after the two-qubit gate
+    for (int side = 0; side < 2; ++side) {
+      const int qq = q + side;
+      B.pre_off[side] = (int)P.g1.size();
+      for (int i = 0; i < two_pos[q]; ++i)
+        if (gates[i].kind == DCS_OP_GATE1 && gates[i].q0 == qq) {
+          cd m[4];
+          int l2;
+          gate_matrix(gates[i], m, l2);
+          P.g1.push_back(to_dgate1(m, gates[i].cond));
+        }
+      B.pre_n[side] = (int)P.g1.size() - B.pre_off[side];
+      B.post_off[side] = (int)P.g1.size();
+      for (size_t i = two_pos[q] + 1; i < gates.size(); ++i)
+        if (gates[i].kind == DCS_OP_GATE1 && gates[i].q0 == qq) {
+          cd m[4];
+          int l2;
+          gate_matrix(gates[i], m, l2);
+          P.g1.push_back(to_dgate1(m, gates[i].cond));
+        }
+      B.post_n[side] = (int)P.g1.size() - B.post_off[side];
+    }
+    L.site[q].kind = 2;
+    L.site[q].blk = (int)bi;
+    L.site[q + 1].kind = 3;
+    L.site[q + 1].blk = (int)bi;
+    P.blocks.push_back(B);
+  }
+  L.n_blocks = (int)lefts.size();
+  for (int q = 0; q < n; ++q) {
+    if (pair_of[q] >= 0) continue;
+    const int off = (int)P.g1.size();
+    for (const dcs_op& o : gates)
+      if (o.kind == DCS_OP_GATE1 && o.q0 == q) {
+        cd m[4];
+        int l2;
+        gate_matrix(o, m, l2);
+        P.g1.push_back(to_dgate1(m, o.cond));
+      }
+    const int cnt = (int)P.g1.size() - off;
+    if (cnt > 0) {
+      L.site[q].kind = 1;
+      L.site[q].g_off = off;
+      L.site[q].g_n = cnt;
+    }
+  }
+  P.layers.push_back(L);
+  P.steps.push_back({0, (int)P.layers.size() - 1, 0});
+  return "";
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------------------- context
+struct dcs_ctx_s {
+  dcs_config cfg{};
+  Layout lay{};
+  cudaStream_t stream = nullptr;
+  char* arena = nullptr;
+  DevCtx dev{};
+  char* stage = nullptr;
+  size_t stage_bytes = 0;
+  cudaEvent_t stage_done = nullptr;
+  bool stage_pending = false;
+  std::string err;
+  uint64_t launches = 0;
+  uint64_t uploaded = 0;
+  int multipath = 0;
+};
+
+namespace {
+
+dcs_status_t fail(dcs_ctx_t c, dcs_status_t s, const std::string& m) {
+  if (c) c->err = m;
+  return s;
+}
+
+dcs_status_t cuda_check(dcs_ctx_t c, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return DCS_OK;
+  return fail(c, DCS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// Copy a program's tables to the device program region; fills the device pointers.
+struct DevProg {
+  const DLayer* layers;
+  const DBlock* blocks;
+  const DGate1* g1;
+  const DCond* conds;
+  const DMeas* meas;
+  const uint8_t* bytes;
+};
+
+dcs_status_t upload(dcs_ctx_t c, const Program& P, const std::vector<uint8_t>& extra, DevProg& out) {
+  size_t off = 0;
+  auto sz = [&](size_t b) {
+    const size_t o = off;
+    off = align_up(off + b);
+    return o;
+  };
+  const size_t oL = sz(P.layers.size() * sizeof(DLayer));
+  const size_t oB = sz(P.blocks.size() * sizeof(DBlock));
+  const size_t oG = sz(P.g1.size() * sizeof(DGate1));
+  const size_t oC = sz(P.conds.size() * sizeof(DCond));
+  const size_t oM = sz(P.meas.size() * sizeof(DMeas));
+  const size_t oX = sz(extra.size());
+  const size_t total = off;
+  if (total > kProgBytes) return fail(c, DCS_ERR_OOM, "circuit tables exceed the program region");
+  if (c->stage_pending) {
+    cudaError_t e = cudaEventSynchronize(c->stage_done);
+    if (e != cudaSuccess) return cuda_check(c, e, "cudaEventSynchronize");
+    c->stage_pending = false;
+  }
+  if (total > c->stage_bytes) {
+    if (c->stage) cudaFreeHost(c->stage);
+    c->stage = nullptr;
+    cudaError_t e = cudaMallocHost(&c->stage, total);
+    if (e != cudaSuccess) return cuda_check(c, e, "cudaMallocHost");
+    c->stage_bytes = total;
+  }
+  auto put = [&](size_t o, const void* src, size_t b) {
+    if (b) std::memcpy(c->stage + o, src, b);
+  };
+  put(oL, P.layers.data(), P.layers.size() * sizeof(DLayer));
+  put(oB, P.blocks.data(), P.blocks.size() * sizeof(DBlock));
+  put(oG, P.g1.data(), P.g1.size() * sizeof(DGate1));
+  put(oC, P.conds.data(), P.conds.size() * sizeof(DCond));
+  put(oM, P.meas.data(), P.meas.size() * sizeof(DMeas));
+  put(oX, extra.data(), extra.size());
+  char* dprog = c->arena + c->lay.prog;
+  if (total) {
+    cudaError_t e = cudaMemcpyAsync(dprog, c->stage, total, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_check(c, e, "cudaMemcpyAsync(tables)");
+    cudaEventRecord(c->stage_done, c->stream);
+    c->stage_pending = true;
+    c->uploaded += total;
+  }
+  out.layers = reinterpret_cast<const DLayer*>(dprog + oL);
+  out.blocks = reinterpret_cast<const DBlock*>(dprog + oB);
+  out.g1 = reinterpret_cast<const DGate1*>(dprog + oG);
+  out.conds = reinterpret_cast<const DCond*>(dprog + oC);
+  out.meas = reinterpret_cast<const DMeas*>(dprog + oM);
+  out.bytes = reinterpret_cast<const uint8_t*>(dprog + oX);
+  return DCS_OK;
+}
+
+dcs_status_t post_launch(dcs_ctx_t c, const char* what) {
+  cudaError_t e = cudaGetLastError();
+  return cuda_check(c, e, what);
+}
+
+dcs_status_t check_gate(dcs_ctx_t c, const dcs_op& o) {
+  const int n = c->cfg.n_qubits;
+  if (o.kind == DCS_OP_GATE1) {
+    if (o.q0 < 0 || o.q0 >= n) return fail(c, DCS_ERR_INVALID, "qubit out of range");
+  } else if (o.kind == DCS_OP_GATE2) {
+    if (o.q0 < 0 || o.q0 >= n || o.q1 < 0 || o.q1 >= n || std::abs(o.q0 - o.q1) != 1)
+      return fail(c, DCS_ERR_INVALID, "two-qubit gates must act on neighbouring qubits");
+  } else if (o.kind == DCS_OP_MEASURE || o.kind == DCS_OP_RESET) {
+    if (o.q0 < 0 || o.q0 >= n) return fail(c, DCS_ERR_INVALID, "qubit out of range");
+    if (o.cbit < 0 || o.cbit >= c->cfg.n_cbits) return fail(c, DCS_ERR_INVALID, "cbit out of range");
+  } else {
+    return fail(c, DCS_ERR_INVALID, "unknown operation kind");
+  }
+  if (o.cond.op != DCS_COND_NONE && o.cond.op != DCS_COND_XOR && o.cond.op != DCS_COND_AND)
+    return fail(c, DCS_ERR_INVALID, "unknown condition op");
+  if ((o.kind == DCS_OP_MEASURE || o.kind == DCS_OP_RESET) && o.cond.op != DCS_COND_NONE)
+    return fail(c, DCS_ERR_INVALID, "measurements cannot be classically controlled");
+  return DCS_OK;
+}
+
+dcs_status_t run_steps(dcs_ctx_t c, const Program& P, int max_branches,
+                       double* fid_out) {
+  DevProg dp;
+  std::vector<uint8_t> none;
+  dcs_status_t st = upload(c, P, none, dp);
+  if (st != DCS_OK) return st;
+  for (const Step& s : P.steps) {
+    if (s.kind == 0) {
+      launch_compress(c->dev, dp.layers + s.idx, dp.blocks, dp.g1, dp.conds, fid_out, c->stream);
+      c->launches++;
+      if ((st = post_launch(c, "compress")) != DCS_OK) return st;
+    } else if (!c->multipath) {
+      launch_measure(c->dev, dp.meas + s.idx, s.n, MEAS_SAMPLE, nullptr, nullptr, c->stream);
+      c->launches++;
+      if ((st = post_launch(c, "measure")) != DCS_OK) return st;
+    } else {
+      for (int i = 0; i < s.n; ++i) {
+        const DMeas& m = P.meas[s.idx + i];
+        launch_measure(c->dev, dp.meas + s.idx + i, 1, MEAS_PROB, nullptr, nullptr, c->stream);
+        c->launches++;
+        int l = 0;
+        launch_branch_split(c->dev, m.q, m.cbit, 1e-12, max_branches, c->stream, &l);
+        c->launches += l;
+        if ((st = post_launch(c, "branch split")) != DCS_OK) return st;
+      }
+    }
+  }
+  return DCS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t dcs_arena_bytes(const dcs_config* cfg) {
+  if (!valid_cfg(cfg) || fused_chi(cfg->chi_max) == 0) return 0;
+  return make_layout(cfg).total;
+}
+
+dcs_status_t dcs_create(dcs_ctx_t* out, const dcs_config* cfg, void* dev_arena, size_t bytes,
+                        dcs_stream_t stream) {
+  if (!out) return DCS_ERR_INVALID;
+  *out = nullptr;
+  if (!valid_cfg(cfg)) return DCS_ERR_INVALID;
+  if (fused_chi(cfg->chi_max) == 0) return DCS_ERR_UNSUPPORTED;
+  const Layout lay = make_layout(cfg);
+  if (!dev_arena || bytes < lay.total) return DCS_ERR_OOM;
+  if (reinterpret_cast<uintptr_t>(dev_arena) % kAlign) return DCS_ERR_INVALID;
+  dcs_ctx_s* c = new dcs_ctx_s();
+  c->cfg = *cfg;
+  c->lay = lay;
+  c->stream = reinterpret_cast<cudaStream_t>(stream);
+  c->arena = static_cast<char*>(dev_arena);
+  DevCtx& d = c->dev;
+  d.n = cfg->n_qubits;
+  d.chi_cap = lay.chi_cap;
+  d.n_slots = cfg->n_slots;
+  d.site_stride = lay.site_stride;
+  d.env_stride = lay.env_stride;
+  d.mps_slot_stride = lay.mps_slot_stride;
+  d.env_slot_stride = lay.env_slot_stride;
+  char* a = c->arena;
+  d.mps[0] = reinterpret_cast<float2*>(a + lay.mps0);
+  d.mps[1] = reinterpret_cast<float2*>(a + lay.mps1);
+  d.Lc = reinterpret_cast<float2*>(a + lay.lc);
+  d.Rc = reinterpret_cast<float2*>(a + lay.rc);
+  d.bonds = reinterpret_cast<int32_t*>(a + lay.bonds);
+  d.centre = reinterpret_cast<int32_t*>(a + lay.centre);
+  d.ketbuf = reinterpret_cast<int32_t*>(a + lay.ketbuf);
+  d.p = reinterpret_cast<double*>(a + lay.p);
+  d.F = reinterpret_cast<double*>(a + lay.F);
+  d.rr = reinterpret_cast<double*>(a + lay.rr);
+  d.creg = reinterpret_cast<uint64_t*>(a + lay.creg);
+  d.flags = reinterpret_cast<uint32_t*>(a + lay.flags);
+  d.shot = reinterpret_cast<uint64_t*>(a + lay.shot);
+  d.order = reinterpret_cast<int32_t*>(a + lay.order);
+  d.count = reinterpret_cast<int32_t*>(a + lay.count);
+  d.status = reinterpret_cast<int32_t*>(a + lay.status);
+  d.plan = reinterpret_cast<int32_t*>(a + lay.plan);
+  d.seed = cfg->seed;
+  d.chi_max = cfg->chi_max;
+  d.tol = cfg->tol;
+  d.sweeps = cfg->sweeps;
+  if (cudaEventCreateWithFlags(&c->stage_done, cudaEventDisableTiming) != cudaSuccess) {
+    delete c;
+    return DCS_ERR_CUDA;
+  }
+  *out = c;
+  return DCS_OK;
+}
+
+dcs_status_t dcs_destroy(dcs_ctx_t c) {
+  if (!c) return DCS_ERR_INVALID;
+  if (c->stage_pending) cudaEventSynchronize(c->stage_done);
+  if (c->stage) cudaFreeHost(c->stage);
+  if (c->stage_done) cudaEventDestroy(c->stage_done);
+  delete c;
+  return DCS_OK;
+}
+
+const char* dcs_last_error(dcs_ctx_t c) { return c ? c->err.c_str() : "null context"; }
+
+uint64_t dcs_kernel_launches(dcs_ctx_t c) { return c ? c->launches : 0; }
+
+uint64_t dcs_bytes_uploaded(dcs_ctx_t c) { return c ? c->uploaded : 0; }
+
+dcs_status_t dcs_init_state(dcs_ctx_t c, int n_active, int multipath, uint64_t shot0) {
+  if (!c) return DCS_ERR_INVALID;
+  if (n_active < 1 || n_active > c->cfg.n_slots) return fail(c, DCS_ERR_INVALID, "n_active out of range");
+  if (multipath && n_active != 1) return fail(c, DCS_ERR_INVALID, "multi-path starts from one branch");
+  c->multipath = multipath ? 1 : 0;
+  launch_init(c->dev, n_active, c->multipath, shot0, c->stream);
+  c->launches++;
+  return post_launch(c, "init");
+}
+
+dcs_status_t dcs_apply_layer(dcs_ctx_t c, const dcs_op* gates, int n_gates, double* fid_out) {
+  if (!c || (n_gates > 0 && !gates)) return fail(c, DCS_ERR_INVALID, "null argument");
+  std::vector<dcs_op> g(gates, gates + n_gates);
+  for (const dcs_op& o : g) {
+    if (o.kind != DCS_OP_GATE1 && o.kind != DCS_OP_GATE2)
+      return fail(c, DCS_ERR_INVALID, "dcs_apply_layer takes gates only");
+    dcs_status_t st = check_gate(c, o);
+    if (st != DCS_OK) return st;
+  }
+  if (g.empty()) return DCS_OK;
+  Program P;
+  std::string e = build_layer(P, c->cfg.n_qubits, g);
+  if (!e.empty()) return fail(c, DCS_ERR_INVALID, e);
+  return run_steps(c, P, 0, fid_out);
+}
+
+static dcs_status_t measure_common(dcs_ctx_t c, int qubit, int cbit, uint64_t ord, int mode,
+                                   const uint8_t* forced, double* p0_out) {
+  if (!c) return DCS_ERR_INVALID;
+  if (qubit < 0 || qubit >= c->cfg.n_qubits) return fail(c, DCS_ERR_INVALID, "qubit out of range");
+  if (mode != MEAS_PROB && (cbit < 0 || cbit >= c->cfg.n_cbits))
+    return fail(c, DCS_ERR_INVALID, "cbit out of range");
+  Program P;
+  P.meas.push_back({qubit, cbit, ord});
+  std::vector<uint8_t> extra;
+  if (forced) extra.assign(forced, forced + c->cfg.n_slots);
+  DevProg dp;
+  dcs_status_t st = upload(c, P, extra, dp);
+  if (st != DCS_OK) return st;
+  launch_measure(c->dev, dp.meas, 1, mode, forced ? dp.bytes : nullptr, p0_out, c->stream);
+  c->launches++;
+  return post_launch(c, "measure");
+}
+
+dcs_status_t dcs_measure_prob(dcs_ctx_t c, int qubit, double* p0_out) {
+  return measure_common(c, qubit, 0, 0, MEAS_PROB, nullptr, p0_out);
+}
+
+dcs_status_t dcs_measure_sample(dcs_ctx_t c, int qubit, int cbit, uint64_t meas_idx) {
+  if (c && c->multipath) return fail(c, DCS_ERR_INVALID, "sampling is single-path only");
+  return measure_common(c, qubit, cbit, meas_idx, MEAS_SAMPLE, nullptr, nullptr);
+}
+
+dcs_status_t dcs_collapse(dcs_ctx_t c, int qubit, int cbit, const uint8_t* outcome) {
+  if (!c || !outcome) return fail(c, DCS_ERR_INVALID, "null argument");
+  return measure_common(c, qubit, cbit, 0, MEAS_FORCED, outcome, nullptr);
+}
+
+dcs_status_t dcs_branch_split(dcs_ctx_t c, int qubit, int cbit, double eps) {
+  if (!c) return DCS_ERR_INVALID;
+  if (!c->multipath) return fail(c, DCS_ERR_INVALID, "branch split needs multi-path mode");
+  dcs_status_t st = measure_common(c, qubit, cbit, 0, MEAS_PROB, nullptr, nullptr);
+  if (st != DCS_OK) return st;
+  int l = 0;
+  launch_branch_split(c->dev, qubit, cbit, eps, 0, c->stream, &l);
+  c->launches += l;
+  return post_launch(c, "branch split");
+}
+
+dcs_status_t dcs_branch_topk(dcs_ctx_t c, int M) {
+  if (!c || M < 1) return fail(c, DCS_ERR_INVALID, "M must be >= 1");
+  if (!c->multipath) return fail(c, DCS_ERR_INVALID, "TopK needs multi-path mode");
+  launch_branch_topk(c->dev, M, c->stream);
+  c->launches++;
+  return post_launch(c, "topk");
+}
+
+dcs_status_t dcs_get_results(dcs_ctx_t c, double* p, double* fid, uint64_t* cbits, int* n_active,
+                             uint8_t* flags) {
+  if (!c) return DCS_ERR_INVALID;
+  dcs_status_t st = cuda_check(c, cudaStreamSynchronize(c->stream), "synchronize");
+  if (st != DCS_OK) return st;
+  const int S = c->cfg.n_slots;
+  int cnt = 0, status = 0;
+  cudaMemcpy(&cnt, c->dev.count, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaMemcpy(&status, c->dev.status, sizeof(int), cudaMemcpyDeviceToHost);
+  std::vector<int> order(S);
+  cudaMemcpy(order.data(), c->dev.order, S * sizeof(int), cudaMemcpyDeviceToHost);
+  if (n_active) *n_active = cnt;
+  auto gather = [&](void* dst, const void* src, size_t esz, size_t per) {
+    if (!dst) return;
+    std::vector<uint8_t> tmp((size_t)S * esz * per);
+    cudaMemcpy(tmp.data(), src, tmp.size(), cudaMemcpyDeviceToHost);
+    for (int i = 0; i < cnt; ++i)
+      std::memcpy(static_cast<uint8_t*>(dst) + (size_t)i * esz * per,
+                  tmp.data() + (size_t)order[i] * esz * per, esz * per);
+  };
+  gather(p, c->dev.p, sizeof(double), 1);
+  gather(fid, c->dev.F, sizeof(double), 1);
+  gather(cbits, c->dev.creg, sizeof(uint64_t), DCS_CWORDS);
+  if (flags) {
+    std::vector<uint32_t> fl(S);
+    cudaMemcpy(fl.data(), c->dev.flags, S * sizeof(uint32_t), cudaMemcpyDeviceToHost);
+    for (int i = 0; i < cnt; ++i) flags[i] = (uint8_t)fl[order[i]];
+  }
+  st = cuda_check(c, cudaGetLastError(), "result copy");
+  if (st != DCS_OK) return st;
+  if (status & (1 << DCS_ERR_OOM)) return fail(c, DCS_ERR_OOM, "branch pool exhausted");
+  if (status & (1 << DCS_ERR_UNSUPPORTED)) return fail(c, DCS_ERR_UNSUPPORTED, "branch pool above 1024 slots");
+  return DCS_OK;
+}
+
+static dcs_status_t slot_of(dcs_ctx_t c, int pos, int& slot, int& kb, std::vector<int>& bonds,
+                            int& centre) {
+  dcs_status_t st = cuda_check(c, cudaStreamSynchronize(c->stream), "synchronize");
+  if (st != DCS_OK) return st;
+  int cnt = 0;
+  cudaMemcpy(&cnt, c->dev.count, sizeof(int), cudaMemcpyDeviceToHost);
+  if (pos < 0 || pos >= cnt) return fail(c, DCS_ERR_INVALID, "slot is not active");
+  cudaMemcpy(&slot, c->dev.order + pos, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaMemcpy(&kb, c->dev.ketbuf + slot, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaMemcpy(&centre, c->dev.centre + slot, sizeof(int), cudaMemcpyDeviceToHost);
+  const int n = c->cfg.n_qubits;
+  bonds.assign(n + 1, 0);
+  cudaMemcpy(bonds.data(), c->dev.bonds + ((size_t)slot * 2 + kb) * (n + 1), (n + 1) * sizeof(int),
+             cudaMemcpyDeviceToHost);
+  return cuda_check(c, cudaGetLastError(), "slot query");
+}
+
+dcs_status_t dcs_export_mps(dcs_ctx_t c, int pos, void* host_buf, size_t* bytes) {
+  if (!c || !bytes) return fail(c, DCS_ERR_INVALID, "null argument");
+  int slot, kb, centre;
+  std::vector<int> b;
+  dcs_status_t st = slot_of(c, pos, slot, kb, b, centre);
+  if (st != DCS_OK) return st;
+  const int n = c->cfg.n_qubits;
+  size_t need = sizeof(int32_t) * (n + 3);
+  for (int j = 0; j < n; ++j) need += sizeof(float2) * (size_t)b[j] * 2 * b[j + 1];
+  if (!host_buf) {
+    *bytes = need;
+    return DCS_OK;
+  }
+  if (*bytes < need) return fail(c, DCS_ERR_INVALID, "export buffer too small");
+  char* o = static_cast<char*>(host_buf);
+  int32_t hdr = n;
+  std::memcpy(o, &hdr, 4);
+  std::memcpy(o + 4, b.data(), 4 * (n + 1));
+  std::memcpy(o + 4 * (n + 2), &centre, 4);
+  size_t off = 4 * (size_t)(n + 3);
+  for (int j = 0; j < n; ++j) {
+    const size_t len = (size_t)b[j] * 2 * b[j + 1];
+    cudaMemcpy(o + off, c->dev.mps[kb] + (size_t)slot * c->dev.mps_slot_stride + (size_t)j * c->dev.site_stride,
+               len * sizeof(float2), cudaMemcpyDeviceToHost);
+    off += len * sizeof(float2);
+  }
+  *bytes = need;
+  return cuda_check(c, cudaGetLastError(), "export");
+}
+
+dcs_status_t dcs_import_mps(dcs_ctx_t c, int pos, const void* host_buf, size_t bytes) {
+  if (!c || !host_buf) return fail(c, DCS_ERR_INVALID, "null argument");
+  int slot, kb, centre_old;
+  std::vector<int> bo;
+  dcs_status_t st = slot_of(c, pos, slot, kb, bo, centre_old);
+  if (st != DCS_OK) return st;
+  const int n = c->cfg.n_qubits;
+  const char* in = static_cast<const char*>(host_buf);
+  if (bytes < sizeof(int32_t) * (n + 3)) return fail(c, DCS_ERR_INVALID, "import buffer too small");
+  int32_t hn;
+  std::memcpy(&hn, in, 4);
+  if (hn != n) return fail(c, DCS_ERR_INVALID, "qubit count mismatch");
+  std::vector<int> b(n + 1);
+  std::memcpy(b.data(), in + 4, 4 * (n + 1));
+  int32_t centre;
+  std::memcpy(&centre, in + 4 * (n + 2), 4);
+  if (b[0] != 1 || b[n] != 1 || centre < 0 || centre >= n)
+    return fail(c, DCS_ERR_INVALID, "malformed MPS header");
+  size_t need = sizeof(int32_t) * (n + 3);
+  for (int j = 0; j <= n; ++j)
+    if (b[j] < 1 || b[j] > c->dev.chi_cap) return fail(c, DCS_ERR_INVALID, "bond above capacity");
+  for (int j = 0; j < n; ++j) need += sizeof(float2) * (size_t)b[j] * 2 * b[j + 1];
+  if (bytes < need) return fail(c, DCS_ERR_INVALID, "import buffer too small");
+  size_t off = 4 * (size_t)(n + 3);
+  for (int j = 0; j < n; ++j) {
+    const size_t len = (size_t)b[j] * 2 * b[j + 1];
+    cudaMemcpy(c->dev.mps[kb] + (size_t)slot * c->dev.mps_slot_stride + (size_t)j * c->dev.site_stride,
+               in + off, len * sizeof(float2), cudaMemcpyHostToDevice);
+    off += len * sizeof(float2);
+  }
+  cudaMemcpy(c->dev.bonds + ((size_t)slot * 2 + kb) * (n + 1), b.data(), (n + 1) * sizeof(int),
+             cudaMemcpyHostToDevice);
+  cudaMemcpy(c->dev.centre + slot, &centre, sizeof(int), cudaMemcpyHostToDevice);
+  return cuda_check(c, cudaGetLastError(), "import");
+}
+
+dcs_status_t dcs_run_circuit(dcs_ctx_t c, const dcs_op* ops, int n_ops, uint64_t meas_idx0,
+                             int max_branches) {
+  if (!c || (n_ops > 0 && !ops)) return fail(c, DCS_ERR_INVALID, "null argument");
+  const int n = c->cfg.n_qubits;
+  // lower resets, validate
+  std::vector<dcs_op> lo;
+  lo.reserve(n_ops + 8);
+  for (int i = 0; i < n_ops; ++i) {
+    dcs_status_t st = check_gate(c, ops[i]);
+    if (st != DCS_OK) return st;
+    if (ops[i].kind == DCS_OP_RESET) {
+      dcs_op m = ops[i];
+      m.kind = DCS_OP_MEASURE;
+      lo.push_back(m);
+      dcs_op x;
+      std::memset(&x, 0, sizeof(x));
+      x.kind = DCS_OP_GATE1;
+      x.q0 = ops[i].q0;
+      x.q1 = -1;
+      x.m[2] = 1.0;  // X = [[0, 1], [1, 0]]
+      x.m[4] = 1.0;
+      x.cond.op = DCS_COND_XOR;
+      x.cond.value = 1;
+      x.cond.mask[ops[i].cbit >> 6] = 1ull << (ops[i].cbit & 63);
+      lo.push_back(x);
+    } else {
+      lo.push_back(ops[i]);
+    }
+  }
+  // chunks (Sec. "Handling unitary chunks in dynamic circuits", one-layer reading)
+  Program P;
+  std::vector<dcs_op> cur;
+  std::vector<char> busy(n, 0);
+  auto close = [&]() -> std::string {
+    std::string e;
+    if (!cur.empty()) e = build_layer(P, n, cur);
+    cur.clear();
+    std::fill(busy.begin(), busy.end(), 0);
+    return e;
+  };
+  uint64_t ord = meas_idx0;
+  for (const dcs_op& o : lo) {
+    if (o.kind == DCS_OP_MEASURE) {
+      std::string e = close();
+      if (!e.empty()) return fail(c, DCS_ERR_INVALID, e);
+      if (!P.steps.empty() && P.steps.back().kind == 1) {
+        P.steps.back().n++;
+      } else {
+        P.steps.push_back({1, (int)P.meas.size(), 1});
+      }
+      P.meas.push_back({o.q0, o.cbit, ord++});
+      continue;
+    }
+    if (o.kind == DCS_OP_GATE2 && (busy[o.q0] || busy[o.q1])) {
+      std::string e = close();
+      if (!e.empty()) return fail(c, DCS_ERR_INVALID, e);
+    }
+    if (c->cfg.chunk_k > 0 && (int)cur.size() >= c->cfg.chunk_k) {
+      std::string e = close();
+      if (!e.empty()) return fail(c, DCS_ERR_INVALID, e);
+    }
+    cur.push_back(o);
+    if (o.kind == DCS_OP_GATE2) busy[o.q0] = busy[o.q1] = 1;
+  }
+  std::string e = close();
+  if (!e.empty()) return fail(c, DCS_ERR_INVALID, e);
+  if (P.layers.size() * sizeof(DLayer) > kProgBytes / 2)
+    return fail(c, DCS_ERR_OOM, "too many chunks for one call");
+  return run_steps(c, P, max_branches, nullptr);
+}
+
+}  // extern "C"

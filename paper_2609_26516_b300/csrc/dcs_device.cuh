@@ -1,0 +1,337 @@
+// Device building blocks of libdcs (sm_103a): complex arithmetic, the counter-based
+// outcome sampler, CTA-level linear algebra on shared-memory tiles (Householder QR,
+// one-sided Jacobi SVD) and the four contractions of a site update.
+//
+// Every routine here is executed by all NT threads of a CTA and ends with a __syncthreads()
+// unless stated otherwise.  Matrices in shared memory are column-major with a leading
+// dimension `ld` unless stated otherwise; complex numbers are float2 (x = re, y = im).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dcs {
+
+// ----------------------------------------------------------------------------- complex
+__device__ __forceinline__ float2 cz() { return make_float2(0.f, 0.f); }
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// conj(a) * b
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+  return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float cabs2(float2 a) { return a.x * a.x + a.y * a.y; }
+// |a|^2 with the squares taken in FP64 (no FP32 underflow for tiny entries)
+__device__ __forceinline__ double cabs2d(float2 a) {
+  return (double)a.x * (double)a.x + (double)a.y * (double)a.y;
+}
+// acc += a * b
+__device__ __forceinline__ void cfma(float2& acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(-a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(a.y, b.x, acc.y);
+}
+// acc += conj(a) * b
+__device__ __forceinline__ void cfmac(float2& acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(-a.y, b.x, acc.y);
+}
+
+// ----------------------------------------------------------------------------- sampler
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): multipliers 0xD2511F53, 0xCD9E8D57,
+// Weyl increments 0x9E3779B9, 0xBB67AE85.  Counter (ordinal, 0, shot lo, shot hi), key
+// (seed lo, seed hi); the uniform is ((w0 >> 5) * 2^26 + (w1 >> 6)) * 2^-53.
+__device__ __forceinline__ double philox_uniform(uint64_t seed, uint64_t shot, uint64_t ordinal) {
+  uint32_t c0 = (uint32_t)ordinal, c1 = 0u, c2 = (uint32_t)shot, c3 = (uint32_t)(shot >> 32);
+  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+    const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+  }
+  const uint64_t hi = (uint64_t)(c0 >> 5), lo = (uint64_t)(c1 >> 6);
+  return (double)(hi * 67108864ull + lo) * (1.0 / 9007199254740992.0);
+}
+
+// ----------------------------------------------------------------------------- reductions
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (NT > 32) {
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    v = 0.0;
+#pragma unroll
+    for (int i = 0; i < NT / 32; ++i) v += red[i];
+  }
+  __syncthreads();
+  return v;
+}
+
+// ----------------------------------------------------------------------------- QR
+// Householder QR of X (m x n, column-major, ld >= m) in place: Q (m x r, column-major, ldq)
+// is formed explicitly (r = min(m, n)), and if R != nullptr the factor R (r x n, row-major,
+// ldr) is written.  Reflector k is H_k = I - 2 u_k u_k^H with the unit vector
+// u_k = (x - alpha_k e_1) / ||x - alpha_k e_1|| stored in X[k:, k], where x is the current
+// column below the diagonal and alpha_k = -(x_0/|x_0|) ||x||, so H_k x = alpha_k e_1.
+// Norms are accumulated from FP64 squares and the reflector is normalised in FP64, so H_k
+// stays unitary to FP32 rounding whatever the column's magnitude (a column of tiny
+// rounding noise included).  Scratch: tau[r] (1 or 0), alpha[r], red[NT/32] (double).
+template <int NT>
+__device__ int cta_qr(float2* X, int m, int n, int ld, float2* Q, int ldq, float2* R, int ldr,
+                      float* tau, float2* alpha, double* red) {
+  const int r = m < n ? m : n;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int NW = NT / 32;
+  for (int k = 0; k < r; ++k) {
+    double s = 0.0;
+    for (int i = k + threadIdx.x; i < m; i += NT) s += cabs2d(X[i + k * ld]);
+    s = block_sum<NT>(s, red);
+    const float2 x0 = X[k + k * ld];
+    const double nrm = sqrt(s);
+    const double a0 = sqrt(cabs2d(x0));
+    // v = x - alpha e_1, ||v||^2 = 2 nrm (nrm + |x_0|); u = v / ||v||
+    const double vn = sqrt(2.0 * nrm * (nrm + a0));
+    const bool skip = !(vn > 0.0);
+    __syncthreads();
+    if (!skip) {
+      double ar, ai;
+      if (a0 > 0.0) {
+        ar = -(double)x0.x / a0 * nrm;
+        ai = -(double)x0.y / a0 * nrm;
+      } else {
+        ar = -nrm;
+        ai = 0.0;
+      }
+      for (int i = k + threadIdx.x; i < m; i += NT) {
+        const float2 xi = X[i + k * ld];
+        double vr = xi.x, vi = xi.y;
+        if (i == k) {
+          vr -= ar;
+          vi -= ai;
+        }
+        X[i + k * ld] = make_float2((float)(vr / vn), (float)(vi / vn));
+      }
+      if (threadIdx.x == 0) {
+        tau[k] = 2.f;
+        alpha[k] = make_float2((float)ar, (float)ai);
+      }
+    } else if (threadIdx.x == 0) {
+      tau[k] = 0.f;
+      alpha[k] = cz();
+    }
+    __syncthreads();
+    if (!skip) {
+      for (int j = k + 1 + warp; j < n; j += NW) {
+        float2 d = cz();
+        for (int i = k + lane; i < m; i += 32) cfmac(d, X[i + k * ld], X[i + j * ld]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          d.x += __shfl_xor_sync(0xffffffffu, d.x, o);
+          d.y += __shfl_xor_sync(0xffffffffu, d.y, o);
+        }
+        d = cscale(d, 2.f);
+        for (int i = k + lane; i < m; i += 32) {
+          float2 v = X[i + k * ld];
+          float2 a = X[i + j * ld];
+          a.x -= v.x * d.x - v.y * d.y;
+          a.y -= v.x * d.y + v.y * d.x;
+          X[i + j * ld] = a;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (R != nullptr) {
+    for (int idx = threadIdx.x; idx < r * n; idx += NT) {
+      const int i = idx / n, j = idx % n;
+      float2 v;
+      if (j < i) v = cz();
+      else if (j == i) v = tau[i] != 0.f ? alpha[i] : X[i + i * ld];
+      else v = X[i + j * ld];
+      R[i * ldr + j] = v;
+    }
+  }
+  // Q = H_0 ... H_{r-1} [I_r; 0]
+  for (int idx = threadIdx.x; idx < m * r; idx += NT) {
+    const int i = idx % m, j = idx / m;
+    Q[i + j * ldq] = make_float2(i == j ? 1.f : 0.f, 0.f);
+  }
+  __syncthreads();
+  for (int k = r - 1; k >= 0; --k) {
+    if (tau[k] != 0.f) {
+      for (int j = k + warp; j < r; j += NW) {
+        float2 d = cz();
+        for (int i = k + lane; i < m; i += 32) cfmac(d, X[i + k * ld], Q[i + j * ldq]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          d.x += __shfl_xor_sync(0xffffffffu, d.x, o);
+          d.y += __shfl_xor_sync(0xffffffffu, d.y, o);
+        }
+        d = cscale(d, 2.f);
+        for (int i = k + lane; i < m; i += 32) {
+          float2 v = X[i + k * ld];
+          float2 a = Q[i + j * ldq];
+          a.x -= v.x * d.x - v.y * d.y;
+          a.y -= v.x * d.y + v.y * d.x;
+          Q[i + j * ldq] = a;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  return r;
+}
+
+// ----------------------------------------------------------------------------- SVD
+// One-sided (Hestenes) Jacobi SVD of X (m x n, column-major, ld): rotates pairs of columns
+// until they are mutually orthogonal, X V = U Sigma, accumulating the unitary V (n x n,
+// column-major, ldv).  Pairs follow the circle-method tournament so each round rotates
+// disjoint pairs in parallel, one group of G lanes per pair.  A pair (i, j) with
+// Gram [[a, g], [conj g, b]] is rotated when |g| > thr sqrt(a b):
+// zeta = (b - a) / (2|g|), t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1+t^2),
+// s = c t, x_i' = c x_i - s e^{-i phi} x_j, x_j' = s x_i + c e^{-i phi} x_j, g = |g| e^{i phi}.
+// Afterwards sig2[j] = ||x_j||^2 (FP64) and perm[0..n) lists columns by decreasing norm
+// (ties: lower index first).  Scratch: red[NT/32], flag (int).
+template <int NT>
+__device__ void cta_jacobi_svd(float2* X, int m, int n, int ld, float2* V, int ldv,
+                               double* sig2, int* perm, int* flag, double* red) {
+  for (int idx = threadIdx.x; idx < n * n; idx += NT) {
+    const int i = idx % n, j = idx / n;
+    V[i + j * ldv] = make_float2(i == j ? 1.f : 0.f, 0.f);
+  }
+  __syncthreads();
+  const int N = (n + 1) & ~1;  // players, padded to even
+  const int npairs = N / 2;
+  int G = 32;
+  while (G > 1 && (NT / G) < npairs) G >>= 1;
+  const int ngroups = NT / G;
+  const int grp = threadIdx.x / G, gl = threadIdx.x % G;
+  const float thr = 2e-7f;
+  for (int sweep = 0; sweep < 60 && N >= 2; ++sweep) {
+    if (threadIdx.x == 0) *flag = 0;
+    __syncthreads();
+    for (int rnd = 0; rnd < N - 1; ++rnd) {
+      for (int pbase = 0; pbase < npairs; pbase += ngroups) {
+        const int p = pbase + grp;
+        int ci = -1, cj = -1;
+        if (p < npairs) {
+          if (p == 0) {
+            ci = rnd;
+            cj = N - 1;
+          } else {
+            ci = (rnd + p) % (N - 1);
+            cj = (rnd - p + (N - 1)) % (N - 1);
+          }
+          if (ci > cj) {
+            const int t = ci;
+            ci = cj;
+            cj = t;
+          }
+        }
+        const bool valid = (p < npairs) && (cj < n);
+        float a = 0.f, b = 0.f;
+        float2 g = cz();
+        if (valid) {
+          for (int i = gl; i < m; i += G) {
+            const float2 xi = X[i + ci * ld], xj = X[i + cj * ld];
+            a += cabs2(xi);
+            b += cabs2(xj);
+            cfmac(g, xi, xj);
+          }
+        }
+        // reduce within the group of G lanes (all lanes take part in the shuffles)
+        for (int o = G / 2; o > 0; o >>= 1) {
+          a += __shfl_xor_sync(0xffffffffu, a, o);
+          b += __shfl_xor_sync(0xffffffffu, b, o);
+          g.x += __shfl_xor_sync(0xffffffffu, g.x, o);
+          g.y += __shfl_xor_sync(0xffffffffu, g.y, o);
+        }
+        const float ag = sqrtf(cabs2(g));
+        if (valid && ag > thr * sqrtf(a * b) && ag > 0.f) {
+          const float zeta = (b - a) / (2.f * ag);
+          const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+          const float c = rsqrtf(1.f + t * t);
+          const float s = c * t;
+          const float2 ph = make_float2(g.x / ag, -g.y / ag);  // e^{-i phi}
+          for (int i = gl; i < m; i += G) {
+            const float2 xi = X[i + ci * ld];
+            const float2 xj = cmul(ph, X[i + cj * ld]);
+            X[i + ci * ld] = make_float2(c * xi.x - s * xj.x, c * xi.y - s * xj.y);
+            X[i + cj * ld] = make_float2(s * xi.x + c * xj.x, s * xi.y + c * xj.y);
+          }
+          for (int i = gl; i < n; i += G) {
+            const float2 vi = V[i + ci * ldv];
+            const float2 vj = cmul(ph, V[i + cj * ldv]);
+            V[i + ci * ldv] = make_float2(c * vi.x - s * vj.x, c * vi.y - s * vj.y);
+            V[i + cj * ldv] = make_float2(s * vi.x + c * vj.x, s * vi.y + c * vj.y);
+          }
+          if (gl == 0) *flag = 1;
+        }
+      }
+      __syncthreads();
+    }
+    if (*flag == 0) break;
+    __syncthreads();
+  }
+  // column norms (FP64) and ordering
+  for (int j = threadIdx.x; j < n; j += NT) {
+    double s = 0.0;
+    for (int i = 0; i < m; ++i) s += cabs2d(X[i + j * ld]);
+    sig2[j] = s;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < n; j += NT) {
+    int rank = 0;
+    const double sj = sig2[j];
+    for (int i = 0; i < n; ++i) {
+      const double si = sig2[i];
+      rank += (si > sj) || (si == sj && i < j);
+    }
+    perm[rank] = j;
+  }
+  __syncthreads();
+}
+
+// Smallest k >= 1 with sum_{i >= k} w_(i) <= tol * sum_i w_i, w_(i) the values in
+// decreasing order (through perm), capped at cap and n.  Suffix sums are accumulated from
+// the smallest value up.  Evaluated by one thread in FP64.
+__device__ __forceinline__ int trunc_rank(const double* w, const int* perm, int n, int cap,
+                                          double tol) {
+  double total = 0.0;
+  for (int i = 0; i < n; ++i) total += w[i];
+  int k = 1;
+  double s = 0.0;
+  for (int i = n - 1; i >= 1; --i) {
+    s += w[perm[i]];
+    if (s > tol * total) {
+      k = i + 1;
+      break;
+    }
+  }
+  if (k > cap) k = cap;
+  if (k > n) k = n;
+  if (k < 1) k = 1;
+  return k;
+}
+
+}  // namespace dcs

@@ -1,0 +1,1057 @@
+// Kernels of libdcs for sm_103a: one CTA per slot (shot or branch) runs a whole
+// CompressionStep, measurement or branch update with the MPS tiles staged in shared memory
+// (bond dimension up to DCS_MAX_CHI_FUSED).
+//
+// Compression step (Sec. "Simulating unitary quantum circuits with DMRG"): the bra starts
+// as the chunk applied block by block to the ket in canonical form, each two-qubit block
+// followed by a truncated SVD (keep the smallest rank whose discarded weight is
+// <= tol * total, at most chi_max); then `sweeps` one-site sweeps against the exact target
+// W|A>: each site takes F / ||F|| (Sec. above: the optimum of max <T|F>), made orthonormal
+// by Householder QR, and the last site gives f = ||F||^2 = |<B|W A>|^2.
+//
+// Right-to-left steps reuse the left-to-right code on the mirrored chain: a site tensor
+// A[a][t][x] is read as A'[x][t][a], an MPO tensor W[d][s][t][e] as W'[e][s][t][d], and the
+// right environment R[c][e][x] plays the role of the left one.  (Reversing the chain leaves
+// the overlap network unchanged.)
+#include <cstdio>
+
+#include "dcs_device.cuh"
+#include "dcs_kernels.cuh"
+
+namespace dcs {
+
+// ----------------------------------------------------------------------------- helpers
+
+__device__ __forceinline__ bool cond_holds(const DCond& cd, const uint64_t* c) {
+  if (cd.op == DCS_COND_NONE) return true;
+  if (cd.op == DCS_COND_XOR) {
+    int par = 0;
+#pragma unroll
+    for (int w = 0; w < DCS_CWORDS; ++w) par ^= __popcll(c[w] & cd.mask[w]) & 1;
+    return par == cd.value;
+  }
+  bool all = true;
+#pragma unroll
+  for (int w = 0; w < DCS_CWORDS; ++w) all = all && ((c[w] & cd.mask[w]) == cd.mask[w]);
+  return (int)all == cd.value;
+}
+
+// U := product of the applicable single-qubit gates g[off .. off+n) (later gates on the left)
+__device__ void prod1q(const DGate1* g, int off, int n, const uint64_t* c, float2* U) {
+  U[0] = make_float2(1.f, 0.f);
+  U[1] = cz();
+  U[2] = cz();
+  U[3] = make_float2(1.f, 0.f);
+  for (int i = 0; i < n; ++i) {
+    const DGate1& G = g[off + i];
+    if (!cond_holds(G.cond, c)) continue;
+    float2 o[4];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        float2 a = cz();
+        cfma(a, G.u[r * 2 + 0], U[0 * 2 + k]);
+        cfma(a, G.u[r * 2 + 1], U[1 * 2 + k]);
+        o[r * 2 + k] = a;
+      }
+#pragma unroll
+    for (int i2 = 0; i2 < 4; ++i2) U[i2] = o[i2];
+  }
+}
+
+// W of site j for register c into W[dl][s][t][dr] (row-major); returns dl, dr.  One thread.
+__device__ void build_W(int j, const DLayer* L, const DBlock* BK, const DGate1* G1,
+                        const uint64_t* c, float2* W, int* dl_out, int* dr_out) {
+  const DSite& st = L->site[j];
+  if (st.kind == 0 || st.kind == 1) {
+    float2 U[4];
+    if (st.kind == 1) {
+      prod1q(G1, st.g_off, st.g_n, c, U);
+    } else {
+      U[0] = make_float2(1.f, 0.f);
+      U[1] = cz();
+      U[2] = cz();
+      U[3] = make_float2(1.f, 0.f);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) W[i] = U[i];
+    *dl_out = 1;
+    *dr_out = 1;
+    return;
+  }
+  const DBlock& b = BK[L->blk_off + st.blk];
+  const int side = (st.kind == 2) ? 0 : 1;
+  float2 Pre[4], Post[4];
+  prod1q(G1, b.pre_off[side], b.pre_n[side], c, Pre);
+  prod1q(G1, b.post_off[side], b.post_n[side], c, Post);
+  const bool on = cond_holds(b.cond, c);
+  const int D = b.D;
+  for (int d = 0; d < D; ++d)
+    for (int so = 0; so < 2; ++so)
+      for (int si = 0; si < 2; ++si) {
+        float2 acc = cz();
+        for (int u = 0; u < 2; ++u)
+          for (int v = 0; v < 2; ++v) {
+            float2 core;
+            if (on) {
+              core = side == 0 ? b.WL[(u * 2 + v) * 4 + d] : b.WR[(d * 2 + u) * 2 + v];
+            } else {
+              core = make_float2((u == v && d == 0) ? 1.f : 0.f, 0.f);
+            }
+            cfma(acc, cmul(Post[so * 2 + u], core), Pre[v * 2 + si]);
+          }
+        if (side == 0) W[(so * 2 + si) * D + d] = acc;   // [0][so][si][d]
+        else W[(d * 2 + so) * 2 + si] = acc;             // [d][so][si][0]
+      }
+  *dl_out = side == 0 ? 1 : D;
+  *dr_out = side == 0 ? D : 1;
+}
+
+// G_blk = (Post_q x Post_{q+1}) G2 (Pre_q x Pre_{q+1}), row-major 4x4.  One thread.
+__device__ void build_block(const DBlock& b, const DGate1* G1, const uint64_t* c, float2* G) {
+  float2 Pre0[4], Post0[4], Pre1[4], Post1[4];
+  prod1q(G1, b.pre_off[0], b.pre_n[0], c, Pre0);
+  prod1q(G1, b.post_off[0], b.post_n[0], c, Post0);
+  prod1q(G1, b.pre_off[1], b.pre_n[1], c, Pre1);
+  prod1q(G1, b.post_off[1], b.post_n[1], c, Post1);
+  const bool on = cond_holds(b.cond, c);
+  float2 M[16];
+  // M = G2 (Pre0 x Pre1)
+  for (int o = 0; o < 4; ++o)
+    for (int i = 0; i < 4; ++i) {
+      const int t0 = i >> 1, t1 = i & 1;
+      float2 acc = cz();
+      for (int k = 0; k < 4; ++k) {
+        const int b0 = k >> 1, b1 = k & 1;
+        const float2 g = on ? b.G[o * 4 + k] : make_float2(o == k ? 1.f : 0.f, 0.f);
+        cfma(acc, g, cmul(Pre0[b0 * 2 + t0], Pre1[b1 * 2 + t1]));
+      }
+      M[o * 4 + i] = acc;
+    }
+  for (int o = 0; o < 4; ++o)
+    for (int i = 0; i < 4; ++i) {
+      const int s0 = o >> 1, s1 = o & 1;
+      float2 acc = cz();
+      for (int k = 0; k < 4; ++k) {
+        const int a0 = k >> 1, a1 = k & 1;
+        cfma(acc, cmul(Post0[s0 * 2 + a0], Post1[s1 * 2 + a1]), M[k * 4 + i]);
+      }
+      G[o * 4 + i] = acc;
+    }
+}
+
+__device__ __forceinline__ float2* site_ptr(const DevCtx& c, int buf, int slot, int j) {
+  return c.mps[buf] + (size_t)slot * c.mps_slot_stride + (size_t)j * c.site_stride;
+}
+__device__ __forceinline__ float2* env_ptr(float2* base, const DevCtx& c, int slot, int j) {
+  return base + (size_t)slot * c.env_slot_stride + (size_t)j * c.env_stride;
+}
+__device__ __forceinline__ int* bonds_ptr(const DevCtx& c, int slot, int buf) {
+  return c.bonds + ((size_t)slot * 2 + buf) * (c.n + 1);
+}
+
+template <int NT>
+__device__ __forceinline__ void gcopy(float2* dst, const float2* src, int n) {
+  for (int i = threadIdx.x; i < n; i += NT) dst[i] = src[i];
+}
+
+// ----------------------------------------------------------------------------- contractions
+// C1: T[b][d][t][x] = sum_a E[b][d][a] S[a][t][x]; T strides (2 Dm nx, 2 nx, nx, 1).
+template <int NT>
+__device__ void c1_env_site(const float2* E, const float2* S, float2* T, int nb, int nd, int na,
+                            int nx, int Dm) {
+  const int tot = nb * nd * 2 * nx;
+  for (int idx = threadIdx.x; idx < tot; idx += NT) {
+    const int x = idx % nx;
+    int r = idx / nx;
+    const int t = r & 1;
+    r >>= 1;
+    const int d = r % nd, b = r / nd;
+    const float2* e = E + (b * nd + d) * na;
+    const float2* s = S + t * nx + x;
+    float2 acc = cz();
+    for (int a = 0; a < na; ++a) cfma(acc, e[a], s[a * 2 * nx]);
+    T[b * 2 * Dm * nx + (d * 2 + t) * nx + x] = acc;
+  }
+  __syncthreads();
+}
+
+// C2 (in place): per fiber (b, x), T2[b][s][e][x] = sum_{d,t} T1[b][d][t][x] W[d][s][t][e].
+template <int NT>
+__device__ void c2_mix(float2* T, const float2* W, int nb, int nd, int ne, int nx, int Dm) {
+  for (int idx = threadIdx.x; idx < nb * nx; idx += NT) {
+    const int x = idx % nx, b = idx / nx;
+    float2* base = T + b * 2 * Dm * nx + x;
+    float2 v[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = (m < 2 * nd) ? base[m * nx] : cz();
+    float2 w[8];
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        float2 acc = cz();
+        if (e < ne) {
+#pragma unroll
+          for (int d = 0; d < 4; ++d)
+#pragma unroll
+            for (int t = 0; t < 2; ++t)
+              if (d < nd) cfma(acc, v[d * 2 + t], W[((d * 2 + s) * 2 + t) * ne + e]);
+        }
+        w[s * 4 + e] = acc;
+      }
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if (e < ne) base[(s * ne + e) * nx] = w[s * 4 + e];
+  }
+  __syncthreads();
+}
+
+// C3: F[(b s) + c ldx] = sum_{e,x} T2[b][s][e][x] R[c][e][x]   (column-major, ldx = 2 nb)
+template <int NT>
+__device__ void c3_site_env(const float2* T, const float2* R, float2* F, int nb, int ne, int nx,
+                            int nc, int Dm) {
+  const int K = ne * nx;
+  const int tot = nb * 2 * nc;
+  for (int idx = threadIdx.x; idx < tot; idx += NT) {
+    const int row = idx % (2 * nb), col = idx / (2 * nb);
+    const int b = row >> 1, s = row & 1;
+    const float2* t = T + b * 2 * Dm * nx + s * ne * nx;
+    const float2* r = R + col * K;
+    float2 acc = cz();
+    for (int k = 0; k < K; ++k) cfma(acc, t[k], r[k]);
+    F[row + col * 2 * nb] = acc;
+  }
+  __syncthreads();
+}
+
+// C4: Enew[c][e][x] = sum_{b,s} conj(Q[(b s) + c ldq]) T2[b][s][e][x],  c < k
+template <int NT>
+__device__ void c4_env_update(const float2* Q, int ldq, const float2* T, float2* En, int nb,
+                              int ne, int nx, int k, int Dm) {
+  const int tot = k * ne * nx;
+  for (int idx = threadIdx.x; idx < tot; idx += NT) {
+    const int x = idx % nx;
+    const int r = idx / nx;
+    const int e = r % ne, cc = r / ne;
+    float2 acc = cz();
+    for (int b = 0; b < nb; ++b)
+#pragma unroll
+      for (int s = 0; s < 2; ++s)
+        cfmac(acc, Q[(b * 2 + s) + cc * ldq], T[b * 2 * Dm * nx + (s * ne + e) * nx + x]);
+    En[idx] = acc;
+  }
+  __syncthreads();
+}
+
+// ----------------------------------------------------------------------------- shared memory
+template <int C, int NT>
+struct Smem {
+  float2* E;   // 4 C^2  environment (in / out)
+  float2* S;   // 2 C^2  site tensor
+  float2* T;   // 8 C^2  T1/T2, or Theta + V
+  float2* R;   // 4 C^2  far environment, or Q
+  float2* F;   // 2 C^2  F (QR work)
+  float2* W;   // 64     MPO tensor of the site
+  float2* W2;  // 64     mirrored MPO tensor
+  float2* G;   // 16     block matrix / single-qubit gate
+  float2* alph;
+  double* red;
+  double* sig2;
+  double* dv;  // scalar broadcast
+  float* tau;
+  int* perm;
+  int* bnd;    // bonds being modified [n+1]
+  int* abnd;   // bonds of the ket [n+1]
+  int* iv;     // small ints
+  uint64_t* creg;
+  static constexpr size_t bytes() {
+    return sizeof(float2) * (20 * C * C + 64 + 64 + 16 + 2 * C) + sizeof(double) * (32 + 2 * C + 8) +
+           sizeof(float) * 2 * C + sizeof(int) * (2 * C + 2 * (DCS_MAX_QUBITS + 1) + 16) +
+           sizeof(uint64_t) * DCS_CWORDS + 64;
+  }
+  __device__ void carve(unsigned char* raw) {
+    uint64_t* c64 = reinterpret_cast<uint64_t*>(raw);
+    creg = c64;
+    double* d = reinterpret_cast<double*>(c64 + DCS_CWORDS);
+    red = d;
+    sig2 = red + 32;
+    dv = sig2 + 2 * C;
+    float2* f2 = reinterpret_cast<float2*>(dv + 8);
+    E = f2;
+    S = E + 4 * C * C;
+    T = S + 2 * C * C;
+    R = T + 8 * C * C;
+    F = R + 4 * C * C;
+    W = F + 2 * C * C;
+    W2 = W + 64;
+    G = W2 + 64;
+    alph = G + 16;
+    tau = reinterpret_cast<float*>(alph + 2 * C);
+    perm = reinterpret_cast<int*>(tau + 2 * C);
+    bnd = perm + 2 * C;
+    abnd = bnd + DCS_MAX_QUBITS + 1;
+    iv = abnd + DCS_MAX_QUBITS + 1;
+  }
+};
+
+// ----------------------------------------------------------------------------- gauge moves
+// Move the orthogonality centre of MPS buffer `buf` of `slot` from j to j+1:
+// T_j = Q R (as (2 b_j) x b_{j+1}), T_j := Q, T_{j+1} := R T_{j+1}.
+template <int C, int NT>
+__device__ void hop_right(const DevCtx& c, Smem<C, NT>& sm, int buf, int slot, int j) {
+  int* b = sm.bnd;
+  const int bl = b[j], br = b[j + 1], bn = b[j + 2];
+  const int m = 2 * bl;
+  const float2* src = site_ptr(c, buf, slot, j);
+  for (int idx = threadIdx.x; idx < m * br; idx += NT) {
+    const int row = idx / br, x = idx % br;  // row = a*2 + s
+    sm.F[row + x * m] = src[idx];
+  }
+  __syncthreads();
+  const int r = cta_qr<NT>(sm.F, m, br, m, sm.R, m, sm.E, br, sm.tau, sm.alph, sm.red);
+  float2* dst = site_ptr(c, buf, slot, j);
+  for (int idx = threadIdx.x; idx < m * r; idx += NT) {
+    const int row = idx / r, k = idx % r;
+    dst[idx] = sm.R[row + k * m];
+  }
+  const float2* nx = site_ptr(c, buf, slot, j + 1);
+  gcopy<NT>(sm.S, nx, br * 2 * bn);
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < r * 2 * bn; idx += NT) {
+    const int k = idx / (2 * bn), col = idx % (2 * bn);
+    float2 acc = cz();
+    for (int x = 0; x < br; ++x) cfma(acc, sm.E[k * br + x], sm.S[x * 2 * bn + col]);
+    sm.T[idx] = acc;
+  }
+  __syncthreads();
+  gcopy<NT>(site_ptr(c, buf, slot, j + 1), sm.T, r * 2 * bn);
+  __syncthreads();
+  if (threadIdx.x == 0) b[j + 1] = r;
+  __syncthreads();
+}
+
+// Move the centre from j to j-1 (mirrored hop): T_j[a][t][x] read as (x t) x a = Q' R',
+// T_j[k][t][x] := Q'[(x t), k], T_{j-1}[a'][s][k] := sum_a T_{j-1}[a'][s][a] R'[k][a].
+template <int C, int NT>
+__device__ void hop_left(const DevCtx& c, Smem<C, NT>& sm, int buf, int slot, int j) {
+  int* b = sm.bnd;
+  const int bl = b[j], br = b[j + 1], bp = b[j - 1];
+  const int m = 2 * br;
+  const float2* src = site_ptr(c, buf, slot, j);
+  for (int idx = threadIdx.x; idx < bl * 2 * br; idx += NT) {
+    const int x = idx % br, t = (idx / br) & 1, a = idx / (2 * br);
+    sm.F[(x * 2 + t) + a * m] = src[idx];
+  }
+  __syncthreads();
+  const int r = cta_qr<NT>(sm.F, m, bl, m, sm.R, m, sm.E, bl, sm.tau, sm.alph, sm.red);
+  float2* dst = site_ptr(c, buf, slot, j);
+  for (int idx = threadIdx.x; idx < r * 2 * br; idx += NT) {
+    const int x = idx % br, t = (idx / br) & 1, k = idx / (2 * br);
+    dst[idx] = sm.R[(x * 2 + t) + k * m];
+  }
+  gcopy<NT>(sm.S, site_ptr(c, buf, slot, j - 1), bp * 2 * bl);
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < bp * 2 * r; idx += NT) {
+    const int k = idx % r, row = idx / r;
+    float2 acc = cz();
+    for (int a = 0; a < bl; ++a) cfma(acc, sm.S[row * bl + a], sm.E[k * bl + a]);
+    sm.T[idx] = acc;
+  }
+  __syncthreads();
+  gcopy<NT>(site_ptr(c, buf, slot, j - 1), sm.T, bp * 2 * r);
+  __syncthreads();
+  if (threadIdx.x == 0) b[j] = r;
+  __syncthreads();
+}
+
+template <int C, int NT>
+__device__ void move_centre(const DevCtx& c, Smem<C, NT>& sm, int buf, int slot, int& centre,
+                            int target) {
+  while (centre < target) {
+    hop_right<C, NT>(c, sm, buf, slot, centre);
+    ++centre;
+  }
+  while (centre > target) {
+    hop_left<C, NT>(c, sm, buf, slot, centre);
+    --centre;
+  }
+}
+
+// ----------------------------------------------------------------------------- compression
+template <int C, int NT>
+__global__ void __launch_bounds__(NT) k_compress(DevCtx c, const DLayer* __restrict__ L,
+                                                 const DBlock* __restrict__ BK,
+                                                 const DGate1* __restrict__ G1,
+                                                 const DCond* __restrict__ CD, double* fid_out) {
+  const int pos = blockIdx.x;
+  if (pos >= *c.count) return;
+  const int slot = c.order[pos];
+  extern __shared__ __align__(16) unsigned char smraw[];
+  Smem<C, NT> sm;
+  sm.carve(smraw);
+  const int n = c.n;
+  if (threadIdx.x < DCS_CWORDS) sm.creg[threadIdx.x] = c.creg[(size_t)slot * DCS_CWORDS + threadIdx.x];
+  __syncthreads();
+  // a slot on which every gate of the chunk is skipped is left unchanged
+  if (!L->uncond) {
+    if (threadIdx.x == 0) {
+      int any = 0;
+      for (int i = 0; i < L->n_conds && !any; ++i) any = cond_holds(CD[L->cond_off + i], sm.creg);
+      sm.iv[4] = any;
+    }
+    __syncthreads();
+    if (!sm.iv[4]) {
+      if (threadIdx.x == 0 && fid_out) fid_out[slot] = 1.0;
+      return;
+    }
+  }
+  const int kb = c.ketbuf[slot], bb = 1 - kb;
+  const int* kbonds = bonds_ptr(c, slot, kb);
+  for (int i = threadIdx.x; i <= n; i += NT) {
+    sm.abnd[i] = kbonds[i];
+    sm.bnd[i] = kbonds[i];
+  }
+  __syncthreads();
+  int centre = c.centre[slot];
+  // ---- initial guess: copy the ket, then apply the chunk block by block
+  for (int j = 0; j < n; ++j)
+    gcopy<NT>(site_ptr(c, bb, slot, j), site_ptr(c, kb, slot, j), sm.abnd[j] * 2 * sm.abnd[j + 1]);
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    if (L->site[j].kind != 1) continue;
+    if (threadIdx.x == 0) prod1q(G1, L->site[j].g_off, L->site[j].g_n, sm.creg, sm.G);
+    __syncthreads();
+    float2* p = site_ptr(c, bb, slot, j);
+    const int bl = sm.bnd[j], br = sm.bnd[j + 1];
+    for (int idx = threadIdx.x; idx < bl * br; idx += NT) {
+      const int a = idx / br, x = idx % br;
+      const float2 v0 = p[(a * 2 + 0) * br + x], v1 = p[(a * 2 + 1) * br + x];
+      float2 o0 = cz(), o1 = cz();
+      cfma(o0, sm.G[0], v0);
+      cfma(o0, sm.G[1], v1);
+      cfma(o1, sm.G[2], v0);
+      cfma(o1, sm.G[3], v1);
+      p[(a * 2 + 0) * br + x] = o0;
+      p[(a * 2 + 1) * br + x] = o1;
+    }
+    __syncthreads();
+  }
+  for (int ib = 0; ib < L->n_blocks; ++ib) {
+    const DBlock& blk = BK[L->blk_off + ib];
+    const int q = blk.q;
+    move_centre<C, NT>(c, sm, bb, slot, centre, q + 1);
+    const int b0 = sm.bnd[q], b1 = sm.bnd[q + 1], b2 = sm.bnd[q + 2];
+    gcopy<NT>(sm.S, site_ptr(c, bb, slot, q), b0 * 2 * b1);
+    gcopy<NT>(sm.F, site_ptr(c, bb, slot, q + 1), b1 * 2 * b2);
+    if (threadIdx.x == 0) build_block(blk, G1, sm.creg, sm.G);
+    __syncthreads();
+    const int m = 2 * b0, nn = 2 * b2;
+    float2* X = sm.T;
+    float2* V = sm.T + 4 * C * C;
+    // P[(a t), (v b)] = sum_x B_q[a][t][x] B_{q+1}[x][v][b]
+    for (int idx = threadIdx.x; idx < m * nn; idx += NT) {
+      const int row = idx % m, col = idx / m;
+      float2 acc = cz();
+      for (int x = 0; x < b1; ++x) cfma(acc, sm.S[row * b1 + x], sm.F[x * nn + col]);
+      X[row + col * m] = acc;
+    }
+    __syncthreads();
+    // Theta[(a s), (u b)] = sum_{t v} G[(s u), (t v)] P[(a t), (v b)]  (in place per (a, b))
+    for (int idx = threadIdx.x; idx < b0 * b2; idx += NT) {
+      const int a = idx / b2, bcol = idx % b2;
+      float2 in[4], out[4];
+#pragma unroll
+      for (int t = 0; t < 2; ++t)
+#pragma unroll
+        for (int v = 0; v < 2; ++v) in[t * 2 + v] = X[(a * 2 + t) + (v * b2 + bcol) * m];
+#pragma unroll
+      for (int o = 0; o < 4; ++o) {
+        float2 acc = cz();
+#pragma unroll
+        for (int i = 0; i < 4; ++i) cfma(acc, sm.G[o * 4 + i], in[i]);
+        out[o] = acc;
+      }
+#pragma unroll
+      for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int u = 0; u < 2; ++u) X[(a * 2 + s) + (u * b2 + bcol) * m] = out[s * 2 + u];
+    }
+    __syncthreads();
+    cta_jacobi_svd<NT>(X, m, nn, m, V, nn, sm.sig2, sm.perm, &sm.iv[5], sm.red);
+    if (threadIdx.x == 0) {
+      const int k = trunc_rank(sm.sig2, sm.perm, nn, c.chi_max, c.tol);
+      double w = 0.0;
+      for (int i = 0; i < k; ++i) w += sm.sig2[sm.perm[i]];
+      sm.iv[6] = k;
+      sm.dv[0] = w;
+    }
+    __syncthreads();
+    const int k = sm.iv[6];
+    const float inv = (float)(1.0 / sqrt(sm.dv[0]));
+    float2* pq = site_ptr(c, bb, slot, q);
+    for (int idx = threadIdx.x; idx < m * k; idx += NT) {
+      const int row = idx / k, kk = idx % k;
+      pq[idx] = cscale(X[row + sm.perm[kk] * m], inv);
+    }
+    float2* pq1 = site_ptr(c, bb, slot, q + 1);
+    for (int idx = threadIdx.x; idx < k * nn; idx += NT) {
+      const int kk = idx / nn, col = idx % nn;
+      pq1[idx] = cconj(V[col + sm.perm[kk] * nn]);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) sm.bnd[q + 1] = k;
+    centre = q;
+    __syncthreads();
+  }
+  move_centre<C, NT>(c, sm, bb, slot, centre, 0);
+  // ---- right environments of the guess: R_j for j = n-1 .. 1 (mirrored env updates)
+  int* bt = sm.bnd;
+  int* at = sm.abnd;
+  if (threadIdx.x == 0) sm.E[0] = make_float2(1.f, 0.f);
+  __syncthreads();
+  for (int j = n - 1; j >= 1; --j) {
+    if (threadIdx.x == 0) build_W(j, L, BK, G1, sm.creg, sm.W, &sm.iv[0], &sm.iv[1]);
+    __syncthreads();
+    const int dl = sm.iv[0], dr = sm.iv[1], Dm = dl > dr ? dl : dr;
+    for (int i = threadIdx.x; i < dr * 4 * dl; i += NT) {  // W'[e][s][t][d] = W[d][s][t][e]
+      const int d = i % dl, st = (i / dl) % 4, e = i / (4 * dl);
+      sm.W2[i] = sm.W[(d * 4 + st) * dr + e];
+    }
+    const float2* A = site_ptr(c, kb, slot, j);
+    const int al = at[j], ar = at[j + 1];
+    for (int idx = threadIdx.x; idx < al * 2 * ar; idx += NT) {  // S'[x][t][a] = A[a][t][x]
+      const int x = idx % ar, t = (idx / ar) & 1, a = idx / (2 * ar);
+      sm.S[(x * 2 + t) * al + a] = A[idx];
+    }
+    const float2* Bj = site_ptr(c, bb, slot, j);
+    const int bl = bt[j], br = bt[j + 1];
+    const int ldq = 2 * br;
+    for (int idx = threadIdx.x; idx < bl * 2 * br; idx += NT) {  // Q'[(c s), b] = B[b][s][c]
+      const int x = idx % br, s = (idx / br) & 1, bq = idx / (2 * br);
+      sm.R[(x * 2 + s) + bq * ldq] = Bj[idx];
+    }
+    __syncthreads();
+    c1_env_site<NT>(sm.E, sm.S, sm.T, br, dr, ar, al, Dm);
+    c2_mix<NT>(sm.T, sm.W2, br, dr, dl, al, Dm);
+    c4_env_update<NT>(sm.R, ldq, sm.T, sm.E, br, dl, al, bl, Dm);
+    gcopy<NT>(env_ptr(c.Rc, c, slot, j), sm.E, bl * dl * al);
+    __syncthreads();
+  }
+  // ---- one-site sweeps
+  double fval = 0.0;
+  for (int sw = 0; sw < c.sweeps; ++sw) {
+    if (threadIdx.x == 0) sm.E[0] = make_float2(1.f, 0.f);
+    __syncthreads();
+    if ((sw & 1) == 0) {  // left to right
+      for (int j = 0; j < n; ++j) {
+        if (threadIdx.x == 0) build_W(j, L, BK, G1, sm.creg, sm.W, &sm.iv[0], &sm.iv[1]);
+        __syncthreads();
+        const int dl = sm.iv[0], dr = sm.iv[1], Dm = dl > dr ? dl : dr;
+        const int nb = bt[j], nc = bt[j + 1], na = at[j], nx = at[j + 1];
+        gcopy<NT>(sm.S, site_ptr(c, kb, slot, j), na * 2 * nx);
+        if (j < n - 1) gcopy<NT>(sm.R, env_ptr(c.Rc, c, slot, j + 1), nc * dr * nx);
+        else if (threadIdx.x == 0) sm.R[0] = make_float2(1.f, 0.f);
+        __syncthreads();
+        c1_env_site<NT>(sm.E, sm.S, sm.T, nb, dl, na, nx, Dm);
+        c2_mix<NT>(sm.T, sm.W, nb, dl, dr, nx, Dm);
+        c3_site_env<NT>(sm.T, sm.R, sm.F, nb, dr, nx, nc, Dm);
+        const int m = 2 * nb;
+        float2* dst = site_ptr(c, bb, slot, j);
+        if (j < n - 1) {
+          const int r = cta_qr<NT>(sm.F, m, nc, m, sm.R, m, nullptr, 0, sm.tau, sm.alph, sm.red);
+          for (int idx = threadIdx.x; idx < m * r; idx += NT) {
+            const int row = idx / r, k = idx % r;
+            dst[idx] = sm.R[row + k * m];
+          }
+          c4_env_update<NT>(sm.R, m, sm.T, sm.E, nb, dr, nx, r, Dm);
+          gcopy<NT>(env_ptr(c.Lc, c, slot, j + 1), sm.E, r * dr * nx);
+          __syncthreads();
+          if (threadIdx.x == 0) bt[j + 1] = r;
+          __syncthreads();
+        } else {
+          double s2 = 0.0;
+          for (int i = threadIdx.x; i < m; i += NT) s2 += cabs2d(sm.F[i]);
+          s2 = block_sum<NT>(s2, sm.red);
+          const float inv = (float)(1.0 / sqrt(s2));
+          for (int i = threadIdx.x; i < m; i += NT) dst[i] = cscale(sm.F[i], inv);
+          fval = s2;
+          __syncthreads();
+        }
+      }
+      centre = n - 1;
+    } else {  // right to left, mirrored
+      for (int j = n - 1; j >= 0; --j) {
+        if (threadIdx.x == 0) build_W(j, L, BK, G1, sm.creg, sm.W, &sm.iv[0], &sm.iv[1]);
+        __syncthreads();
+        const int dl = sm.iv[0], dr = sm.iv[1], Dm = dl > dr ? dl : dr;
+        for (int i = threadIdx.x; i < dr * 4 * dl; i += NT) {
+          const int d = i % dl, st = (i / dl) % 4, e = i / (4 * dl);
+          sm.W2[i] = sm.W[(d * 4 + st) * dr + e];
+        }
+        const int nb = bt[j + 1], nc = bt[j], na = at[j + 1], nx = at[j];
+        const float2* A = site_ptr(c, kb, slot, j);
+        for (int idx = threadIdx.x; idx < nx * 2 * na; idx += NT) {
+          const int x = idx % na, t = (idx / na) & 1, a = idx / (2 * na);
+          sm.S[(x * 2 + t) * nx + a] = A[idx];
+        }
+        if (j > 0) gcopy<NT>(sm.R, env_ptr(c.Lc, c, slot, j), nc * dl * nx);
+        else if (threadIdx.x == 0) sm.R[0] = make_float2(1.f, 0.f);
+        __syncthreads();
+        c1_env_site<NT>(sm.E, sm.S, sm.T, nb, dr, na, nx, Dm);
+        c2_mix<NT>(sm.T, sm.W2, nb, dr, dl, nx, Dm);
+        c3_site_env<NT>(sm.T, sm.R, sm.F, nb, dl, nx, nc, Dm);
+        const int m = 2 * nb;
+        float2* dst = site_ptr(c, bb, slot, j);
+        if (j > 0) {
+          const int r = cta_qr<NT>(sm.F, m, nc, m, sm.R, m, nullptr, 0, sm.tau, sm.alph, sm.red);
+          // B_j[k][s][c] = Q'[(c s), k]
+          for (int idx = threadIdx.x; idx < r * 2 * nb; idx += NT) {
+            const int cc = idx % nb, s = (idx / nb) & 1, k = idx / (2 * nb);
+            dst[idx] = sm.R[(cc * 2 + s) + k * m];
+          }
+          c4_env_update<NT>(sm.R, m, sm.T, sm.E, nb, dl, nx, r, Dm);
+          gcopy<NT>(env_ptr(c.Rc, c, slot, j), sm.E, r * dl * nx);
+          __syncthreads();
+          if (threadIdx.x == 0) bt[j] = r;
+          __syncthreads();
+        } else {
+          double s2 = 0.0;
+          for (int i = threadIdx.x; i < m; i += NT) s2 += cabs2d(sm.F[i]);
+          s2 = block_sum<NT>(s2, sm.red);
+          const float inv = (float)(1.0 / sqrt(s2));
+          for (int idx = threadIdx.x; idx < m; idx += NT) {  // B_0[0][s][c] = F'[(c s), 0]
+            const int cc = idx % nb, s = idx / nb;
+            dst[idx] = cscale(sm.F[cc * 2 + s], inv);
+          }
+          fval = s2;
+          __syncthreads();
+        }
+      }
+      centre = 0;
+    }
+  }
+  // ---- the bra becomes the ket
+  int* obonds = bonds_ptr(c, slot, bb);
+  for (int i = threadIdx.x; i <= n; i += NT) obonds[i] = bt[i];
+  if (threadIdx.x == 0) {
+    c.centre[slot] = centre;
+    c.ketbuf[slot] = bb;
+    if (!(fval == fval) || fval > 1e300) c.flags[slot] |= DCS_FLAG_NUMERICAL;
+    c.F[slot] *= fval;
+    if (fid_out) fid_out[slot] = fval;
+  }
+}
+
+// ----------------------------------------------------------------------------- measurement
+// mode MEAS_SAMPLE: u = Philox(seed, shot, ordinal), m = 0 iff u < p_0 (Alg. 1 Measure);
+// MEAS_FORCED: m = forced[slot]; MEAS_PROB: only p_0 (MeasureProb) and the slice weights.
+// p_m = <psi|P_m|psi> is evaluated at the orthogonality centre moved to q; Collapse zeroes
+// the other slice of the centre tensor and rescales by 1/sqrt(r_m) (Sec. "Mid-circuit
+// measurements").
+template <int C, int NT>
+__global__ void __launch_bounds__(NT) k_measure(DevCtx c, const DMeas* __restrict__ meas,
+                                                int n_meas, int mode,
+                                                const uint8_t* __restrict__ forced,
+                                                double* p0_out) {
+  const int pos = blockIdx.x;
+  if (pos >= *c.count) return;
+  const int slot = c.order[pos];
+  extern __shared__ __align__(16) unsigned char smraw[];
+  Smem<C, NT> sm;
+  sm.carve(smraw);
+  const int n = c.n;
+  const int kb = c.ketbuf[slot];
+  int* kbonds = bonds_ptr(c, slot, kb);
+  for (int i = threadIdx.x; i <= n; i += NT) sm.bnd[i] = kbonds[i];
+  __syncthreads();
+  int centre = c.centre[slot];
+  for (int im = 0; im < n_meas; ++im) {
+    const int q = meas[im].q;
+    move_centre<C, NT>(c, sm, kb, slot, centre, q);
+    const int bl = sm.bnd[q], br = sm.bnd[q + 1];
+    float2* A = site_ptr(c, kb, slot, q);
+    double s0 = 0.0, s1 = 0.0;
+    for (int idx = threadIdx.x; idx < bl * 2 * br; idx += NT) {
+      const double w = cabs2d(A[idx]);
+      if ((idx / br) & 1) s1 += w;
+      else s0 += w;
+    }
+    s0 = block_sum<NT>(s0, sm.red);
+    s1 = block_sum<NT>(s1, sm.red);
+    const double tot = s0 + s1;
+    const double p0 = s0 / tot;
+    if (mode == MEAS_PROB) {
+      if (threadIdx.x == 0) {
+        if (p0_out) p0_out[slot] = p0;
+        c.rr[2 * (size_t)slot] = s0;
+        c.rr[2 * (size_t)slot + 1] = s1;
+        if (!(p0 == p0)) c.flags[slot] |= DCS_FLAG_NUMERICAL;
+      }
+      continue;
+    }
+    int m;
+    if (mode == MEAS_SAMPLE) {
+      const double u = philox_uniform(c.seed, c.shot[slot], meas[im].ordinal);
+      m = (u < p0) ? 0 : 1;
+      if (threadIdx.x == 0 && fabs(u - p0) < 1e-6) c.flags[slot] |= DCS_FLAG_DRAW_NEAR_THRESHOLD;
+    } else {
+      m = forced[slot] ? 1 : 0;
+    }
+    const double pm = m ? (1.0 - p0) : p0;
+    const double rm = m ? s1 : s0;
+    if (!(pm > 1e-12)) {
+      if (threadIdx.x == 0) c.flags[slot] |= (pm == pm) ? DCS_FLAG_ZERO_PROB : DCS_FLAG_NUMERICAL;
+      __syncthreads();
+      continue;
+    }
+    const float sc = (float)(1.0 / sqrt(rm));
+    for (int idx = threadIdx.x; idx < bl * 2 * br; idx += NT) {
+      const int s = (idx / br) & 1;
+      A[idx] = (s == m) ? cscale(A[idx], sc) : cz();
+    }
+    if (threadIdx.x == 0) {
+      c.p[slot] *= pm;
+      const int cb = meas[im].cbit;
+      uint64_t& w = c.creg[(size_t)slot * DCS_CWORDS + (cb >> 6)];
+      w = (w & ~(1ull << (cb & 63))) | ((uint64_t)m << (cb & 63));
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i <= n; i += NT) kbonds[i] = sm.bnd[i];
+  if (threadIdx.x == 0) c.centre[slot] = centre;
+}
+
+// ----------------------------------------------------------------------------- init
+__global__ void k_init(DevCtx c, int n_active, int multipath, uint64_t shot0) {
+  const int slot = blockIdx.x;
+  const int n = c.n;
+  if (slot >= c.n_slots) return;
+  if (slot == 0 && threadIdx.x == 0) {
+    *c.count = multipath ? 1 : n_active;
+    *c.status = 0;
+  }
+  if (threadIdx.x == 0) c.order[slot] = slot;
+  const bool active = multipath ? (slot == 0) : (slot < n_active);
+  if (!active) return;
+  for (int i = threadIdx.x; i <= n; i += blockDim.x) {
+    bonds_ptr(c, slot, 0)[i] = 1;
+    bonds_ptr(c, slot, 1)[i] = 1;
+  }
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    float2* p = site_ptr(c, 0, slot, j);
+    p[0] = make_float2(1.f, 0.f);
+    p[1] = cz();
+  }
+  if (threadIdx.x < DCS_CWORDS) c.creg[(size_t)slot * DCS_CWORDS + threadIdx.x] = 0ull;
+  if (threadIdx.x == 0) {
+    c.centre[slot] = 0;
+    c.ketbuf[slot] = 0;
+    c.p[slot] = 1.0;
+    c.F[slot] = 1.0;
+    c.flags[slot] = 0u;
+    c.shot[slot] = shot0 + (uint64_t)slot;
+    c.rr[2 * (size_t)slot] = 1.0;
+    c.rr[2 * (size_t)slot + 1] = 0.0;
+  }
+}
+
+// ----------------------------------------------------------------------------- branches
+// TopK selection key (Alg. 2 "keep the M branches with largest p", ties read as list order):
+// key = round(p / (1e-5 * max p)); a larger key wins, equal keys keep the earlier position.
+__device__ __forceinline__ long long topk_key(double p, double pmax) {
+  return (long long)floor(p / (1e-5 * pmax) + 0.5);
+}
+
+// One CTA.  Children of the current list (parent positions in order, m = 0 before m = 1,
+// kept when p_m > eps), optionally pruned to M, assigned to slots: the first kept child of a
+// parent inherits the parent's slot, a second one takes a free slot (copied from the
+// parent before the collapses run).
+__global__ void k_branch_plan(DevCtx c, double eps, int M, int cbit) {
+  __shared__ int s_nchild[1024];
+  __shared__ int s_start[1025];
+  __shared__ double s_cp[2048];
+  __shared__ int s_keep[2048];
+  __shared__ int s_slot[2048];
+  __shared__ int s_free[1024];
+  __shared__ int s_nfree, s_err;
+  __shared__ double s_pmax;
+  const int cnt = *c.count;
+  const int ns = c.n_slots;
+  if (threadIdx.x == 0) {
+    s_err = 0;
+    if (ns > 1024) s_err = 1;
+  }
+  __syncthreads();
+  if (s_err) {
+    if (threadIdx.x == 0) *c.status |= 1 << DCS_ERR_UNSUPPORTED;
+    return;
+  }
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+    const int slot = c.order[i];
+    const double r0 = c.rr[2 * (size_t)slot], r1 = c.rr[2 * (size_t)slot + 1];
+    const double p0 = r0 / (r0 + r1), p1 = 1.0 - p0;
+    s_nchild[i] = (p0 > eps) + (p1 > eps);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    s_start[0] = 0;
+    for (int i = 0; i < cnt; ++i) s_start[i + 1] = s_start[i] + s_nchild[i];
+  }
+  __syncthreads();
+  const int nch = s_start[cnt];
+  if (nch > ns || nch > 2048) {
+    if (threadIdx.x == 0) {
+      *c.status |= 1 << DCS_ERR_OOM;
+      c.plan[0] = 0;
+      c.plan[1] = 0;
+      c.plan[2] = cnt;
+    }
+    return;
+  }
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+    const int slot = c.order[i];
+    const double r0 = c.rr[2 * (size_t)slot], r1 = c.rr[2 * (size_t)slot + 1];
+    const double p0 = r0 / (r0 + r1), p1 = 1.0 - p0;
+    int k = s_start[i];
+    if (p0 > eps) s_cp[k++] = c.p[slot] * p0;
+    if (p1 > eps) s_cp[k++] = c.p[slot] * p1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double pm = 0.0;
+    for (int i = 0; i < nch; ++i) pm = fmax(pm, s_cp[i]);
+    s_pmax = pm;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nch; i += blockDim.x) {
+    int keep = 1;
+    if (M > 0 && nch > M) {
+      const long long ki = topk_key(s_cp[i], s_pmax);
+      int rank = 0;
+      for (int j = 0; j < nch; ++j) {
+        const long long kj = topk_key(s_cp[j], s_pmax);
+        rank += (kj > ki) || (kj == ki && j < i);
+      }
+      keep = rank < M;
+    }
+    s_keep[i] = keep;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // free slots: not used by any parent, or by a parent none of whose children is kept
+    int used_mark[1];
+    (void)used_mark;
+    s_nfree = 0;
+    for (int s = 0; s < ns; ++s) s_free[s] = 1;
+    for (int i = 0; i < cnt; ++i) {
+      bool any = false;
+      for (int k = s_start[i]; k < s_start[i + 1]; ++k) any = any || s_keep[k];
+      if (any) s_free[c.order[i]] = 0;
+    }
+    int nf = 0;
+    for (int s = 0; s < ns; ++s)
+      if (s_free[s]) s_free[nf++] = s;
+    int* copy = c.plan + PLAN_HDR;
+    int* coll = c.plan + PLAN_HDR + 2 * ns;
+    int ncopy = 0, ncoll = 0, newc = 0;
+    int fi = 0;
+    for (int i = 0; i < cnt; ++i) {
+      const int slot = c.order[i];
+      const double r0 = c.rr[2 * (size_t)slot], r1 = c.rr[2 * (size_t)slot + 1];
+      const double p0 = r0 / (r0 + r1), p1 = 1.0 - p0;
+      int k = s_start[i];
+      bool parent_taken = false;
+      for (int m = 0; m < 2; ++m) {
+        const double pmv = m ? p1 : p0;
+        if (!(pmv > eps)) continue;
+        if (s_keep[k]) {
+          int dst;
+          if (!parent_taken) {
+            dst = slot;
+            parent_taken = true;
+          } else {
+            dst = s_free[fi++];
+            copy[2 * ncopy] = slot;
+            copy[2 * ncopy + 1] = dst;
+            ++ncopy;
+          }
+          coll[2 * ncoll] = dst;
+          coll[2 * ncoll + 1] = m;
+          ++ncoll;
+          s_slot[newc++] = dst;
+        }
+        ++k;
+      }
+    }
+    c.plan[0] = ncopy;
+    c.plan[1] = ncoll;
+    c.plan[2] = newc;
+    for (int i = 0; i < newc; ++i) c.order[i] = s_slot[i];
+    *c.count = newc;
+    (void)cbit;
+  }
+}
+
+// Copy a whole branch (ket MPS, bonds, centre, register, p, F, rr, flags) src -> dst.
+__global__ void k_branch_copy(DevCtx c) {
+  const int i = blockIdx.x;
+  if (i >= c.plan[0]) return;
+  const int src = c.plan[PLAN_HDR + 2 * i], dst = c.plan[PLAN_HDR + 2 * i + 1];
+  const int n = c.n;
+  const int kb = c.ketbuf[src];
+  const int* sb = bonds_ptr(c, src, kb);
+  for (int j = 0; j < n; ++j) {
+    const int len = sb[j] * 2 * sb[j + 1];
+    const float2* s = site_ptr(c, kb, src, j);
+    float2* d = site_ptr(c, kb, dst, j);
+    for (int e = threadIdx.x; e < len; e += blockDim.x) d[e] = s[e];
+  }
+  int* db = bonds_ptr(c, dst, kb);
+  for (int j = threadIdx.x; j <= n; j += blockDim.x) db[j] = sb[j];
+  if (threadIdx.x < DCS_CWORDS)
+    c.creg[(size_t)dst * DCS_CWORDS + threadIdx.x] = c.creg[(size_t)src * DCS_CWORDS + threadIdx.x];
+  if (threadIdx.x == 0) {
+    c.ketbuf[dst] = kb;
+    c.centre[dst] = c.centre[src];
+    c.p[dst] = c.p[src];
+    c.F[dst] = c.F[src];
+    c.rr[2 * (size_t)dst] = c.rr[2 * (size_t)src];
+    c.rr[2 * (size_t)dst + 1] = c.rr[2 * (size_t)src + 1];
+    c.flags[dst] = c.flags[src];
+    c.shot[dst] = c.shot[src];
+  }
+}
+
+// Collapse each planned child onto its outcome (centre already at q from MeasureProb).
+__global__ void k_branch_collapse(DevCtx c, int q, int cbit) {
+  const int i = blockIdx.x;
+  if (i >= c.plan[1]) return;
+  const int ns = c.n_slots;
+  const int slot = c.plan[PLAN_HDR + 2 * ns + 2 * i], m = c.plan[PLAN_HDR + 2 * ns + 2 * i + 1];
+  const int kb = c.ketbuf[slot];
+  const int* b = bonds_ptr(c, slot, kb);
+  const int bl = b[q], br = b[q + 1];
+  const double r0 = c.rr[2 * (size_t)slot], r1 = c.rr[2 * (size_t)slot + 1];
+  const double rm = m ? r1 : r0;
+  const double pm = rm / (r0 + r1);
+  const float sc = (float)(1.0 / sqrt(rm));
+  float2* A = site_ptr(c, kb, slot, q);
+  for (int idx = threadIdx.x; idx < bl * 2 * br; idx += blockDim.x) {
+    const int s = (idx / br) & 1;
+    A[idx] = (s == m) ? cscale(A[idx], sc) : cz();
+  }
+  if (threadIdx.x == 0) {
+    c.p[slot] *= pm;
+    uint64_t& w = c.creg[(size_t)slot * DCS_CWORDS + (cbit >> 6)];
+    w = (w & ~(1ull << (cbit & 63))) | ((uint64_t)m << (cbit & 63));
+  }
+}
+
+// TopK on the current list (one CTA).
+__global__ void k_branch_topk(DevCtx c, int M) {
+  __shared__ int s_keep[1024];
+  __shared__ int s_ord[1024];
+  __shared__ double s_pmax;
+  const int cnt = *c.count;
+  if (cnt <= M || cnt > 1024) return;
+  if (threadIdx.x == 0) {
+    double pm = 0.0;
+    for (int i = 0; i < cnt; ++i) pm = fmax(pm, c.p[c.order[i]]);
+    s_pmax = pm;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+    const long long ki = topk_key(c.p[c.order[i]], s_pmax);
+    int rank = 0;
+    for (int j = 0; j < cnt; ++j) {
+      const long long kj = topk_key(c.p[c.order[j]], s_pmax);
+      rank += (kj > ki) || (kj == ki && j < i);
+    }
+    s_keep[i] = rank < M;
+    s_ord[i] = c.order[i];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int k = 0;
+    for (int i = 0; i < cnt; ++i)
+      if (s_keep[i]) c.order[k++] = s_ord[i];
+    *c.count = k;
+  }
+}
+
+// ----------------------------------------------------------------------------- launchers
+int fused_chi(int chi_max) {
+  if (chi_max <= 4) return 4;
+  if (chi_max <= 8) return 8;
+  if (chi_max <= 16) return 16;
+  if (chi_max <= 32) return 32;
+  return 0;
+}
+
+template <int C, int NT>
+static void compress_c(const DevCtx& c, const DLayer* L, const DBlock* B, const DGate1* G1,
+                       const DCond* CD, double* fid_out, cudaStream_t s) {
+  const size_t sm = Smem<C, NT>::bytes();
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_compress<C, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    attr = true;
+  }
+  k_compress<C, NT><<<c.n_slots, NT, sm, s>>>(c, L, B, G1, CD, fid_out);
+}
+
+template <int C, int NT>
+static void measure_c(const DevCtx& c, const DMeas* meas, int n_meas, int mode,
+                      const uint8_t* forced, double* p0_out, cudaStream_t s) {
+  const size_t sm = Smem<C, NT>::bytes();
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_measure<C, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    attr = true;
+  }
+  k_measure<C, NT><<<c.n_slots, NT, sm, s>>>(c, meas, n_meas, mode, forced, p0_out);
+}
+
+void launch_init(const DevCtx& c, int n_active, int multipath, uint64_t shot0, cudaStream_t s) {
+  k_init<<<c.n_slots, 64, 0, s>>>(c, n_active, multipath, shot0);
+}
+
+void launch_compress(const DevCtx& c, const DLayer* L, const DBlock* B, const DGate1* G1,
+                     const DCond* CD, double* fid_out, cudaStream_t s) {
+  switch (c.chi_cap) {
+    case 4: compress_c<4, 32>(c, L, B, G1, CD, fid_out, s); break;
+    case 8: compress_c<8, 32>(c, L, B, G1, CD, fid_out, s); break;
+    case 16: compress_c<16, 64>(c, L, B, G1, CD, fid_out, s); break;
+    case 32: compress_c<32, 128>(c, L, B, G1, CD, fid_out, s); break;
+    default: break;
+  }
+}
+
+void launch_measure(const DevCtx& c, const DMeas* meas, int n_meas, int mode,
+                    const uint8_t* forced, double* p0_out, cudaStream_t s) {
+  switch (c.chi_cap) {
+    case 4: measure_c<4, 32>(c, meas, n_meas, mode, forced, p0_out, s); break;
+    case 8: measure_c<8, 32>(c, meas, n_meas, mode, forced, p0_out, s); break;
+    case 16: measure_c<16, 64>(c, meas, n_meas, mode, forced, p0_out, s); break;
+    case 32: measure_c<32, 128>(c, meas, n_meas, mode, forced, p0_out, s); break;
+    default: break;
+  }
+}
+
+void launch_branch_split(const DevCtx& c, int q, int cbit, double eps, int M, cudaStream_t s,
+                         int* launches) {
+  k_branch_plan<<<1, 256, 0, s>>>(c, eps, M, cbit);
+  k_branch_copy<<<c.n_slots, 128, 0, s>>>(c);
+  k_branch_collapse<<<c.n_slots, 128, 0, s>>>(c, q, cbit);
+  *launches += 3;
+}
+
+void launch_branch_topk(const DevCtx& c, int M, cudaStream_t s) {
+  k_branch_topk<<<1, 256, 0, s>>>(c, M);
+}
+
+}  // namespace dcs

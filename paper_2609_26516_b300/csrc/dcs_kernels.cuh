@@ -1,0 +1,110 @@
+// Data layout shared by the host API and the kernels of libdcs.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/dcs.h"
+
+namespace dcs {
+
+// A condition phi(c) (Sec. "Classically controlled operations").
+struct DCond {
+  uint64_t mask[DCS_CWORDS];
+  int32_t op;     // dcs_cond_op
+  int32_t value;  // 0 / 1
+};
+
+// A single-qubit gate U (row-major [out][in]) applied iff cond holds.
+struct DGate1 {
+  float2 u[4];
+  DCond cond;
+};
+
+// A two-qubit block on (q, q+1): the chunk's only two-qubit gate on these qubits, G2, with
+// its operator-Schmidt factors, and the single-qubit gates before / after it on q and q+1.
+struct DBlock {
+  int32_t q;
+  int32_t D;        // operator-Schmidt rank of G2 (1..4)
+  float2 G[16];     // G2, row-major over |s_q s_{q+1}>: G[(o0*2+o1)*4 + (i0*2+i1)]
+  float2 WL[16];    // WL[(u*2+v)*4 + d]: left factor, out u, in v
+  float2 WR[16];    // WR[(d*2+u)*2 + v]: right factor
+  DCond cond;       // condition of G2 (op NONE: unconditional)
+  int32_t pre_off[2], pre_n[2], post_off[2], post_n[2];  // into the DGate1 array
+};
+
+// Per-site description of a chunk.
+struct DSite {
+  int32_t kind;  // 0 untouched, 1 single-qubit gates only, 2 left of a block, 3 right of a block
+  int32_t blk;   // block index (kind 2, 3)
+  int32_t g_off, g_n;  // single-qubit gates (kind 1)
+};
+
+// One chunk (a layer of disjoint blocks).
+struct DLayer {
+  DSite site[DCS_MAX_QUBITS];
+  int32_t n_blocks;
+  int32_t blk_off;    // into the DBlock array; blocks sorted by decreasing q
+  int32_t uncond;     // some gate is unconditional: never empty
+  int32_t cond_off;   // all conditions of the chunk (for the empty test), into DCond array
+  int32_t n_conds;
+};
+
+// One mid-circuit measurement of a run.
+struct DMeas {
+  int32_t q;
+  int32_t cbit;
+  uint64_t ordinal;
+};
+
+// Device view of a context (passed by value to every kernel).
+struct DevCtx {
+  int32_t n;         // sites
+  int32_t chi_cap;   // slot capacity per bond (>= chi_max)
+  int32_t n_slots;
+  int32_t site_stride;       // complex elements per site (2 chi_cap^2)
+  int32_t env_stride;        // complex elements per environment (4 chi_cap^2)
+  size_t mps_slot_stride;    // complex elements per slot per MPS buffer
+  size_t env_slot_stride;    // complex elements per slot per environment cache
+  float2* mps[2];            // MPS buffer pair
+  float2* Lc;                // left environment cache
+  float2* Rc;                // right environment cache
+  int32_t* bonds;            // [slot][2][n+1]
+  int32_t* centre;           // [slot]
+  int32_t* ketbuf;           // [slot] which MPS buffer holds the ket
+  double* p;                 // [slot] path probability p_gamma
+  double* F;                 // [slot] estimated fidelity F~ (product of f)
+  double* rr;                // [slot][2] slice weights r_0, r_1 of the last MeasureProb
+  uint64_t* creg;            // [slot][DCS_CWORDS]
+  uint32_t* flags;           // [slot]
+  uint64_t* shot;            // [slot] sampler counter of the shot
+  int32_t* order;            // [n_slots] list order of active slots
+  int32_t* count;            // number of active slots
+  int32_t* status;           // context-wide error bits
+  int32_t* plan;             // branch plan scratch
+  uint64_t seed;
+  int32_t chi_max;
+  double tol;
+  int32_t sweeps;
+};
+
+// plan layout (int32 words): [0] n_copy, [1] n_coll, [2] new count,
+// then copy pairs (src, dst) x n_slots, then collapse records (slot, m) x n_slots.
+constexpr int PLAN_HDR = 4;
+
+void launch_init(const DevCtx& c, int n_active, int multipath, uint64_t shot0, cudaStream_t s);
+void launch_compress(const DevCtx& c, const DLayer* L, const DBlock* B, const DGate1* G1,
+                     const DCond* C, double* fid_out, cudaStream_t s);
+void launch_measure(const DevCtx& c, const DMeas* meas, int n_meas, int mode,
+                    const uint8_t* forced, double* p0_out, cudaStream_t s);
+void launch_branch_split(const DevCtx& c, int q, int cbit, double eps, int M,
+                         cudaStream_t s, int* launches);
+void launch_branch_topk(const DevCtx& c, int M, cudaStream_t s);
+int fused_chi(int chi_max);
+
+// measurement modes
+constexpr int MEAS_SAMPLE = 0;
+constexpr int MEAS_FORCED = 1;
+constexpr int MEAS_PROB = 2;
+
+}  // namespace dcs

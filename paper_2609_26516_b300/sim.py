@@ -1,0 +1,211 @@
+"""Python binding of libdcs: the same calls as the C ABI (include/dcs.h), with PyTorch
+providing the device arena and the stream.  Argument marshalling only: every step of the
+simulation runs in the library's CUDA kernels."""
+from __future__ import annotations
+
+import ctypes
+from typing import Iterable, List, Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _native as N
+
+
+class DCSError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"libdcs {N.STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+def _cond(cond) -> N.dcs_cond:
+    c = N.dcs_cond()
+    if cond is None:
+        c.op = N.COND_NONE
+        return c
+    c.op = {"xor": N.COND_XOR, "and": N.COND_AND}[cond.op]
+    c.value = int(cond.value)
+    for b in cond.bits:
+        c.mask[b >> 6] |= 1 << (b & 63)
+    return c
+
+
+def encode_ops(ops: Sequence) -> ctypes.Array:
+    """circuits.Gate / Measure / Reset records -> dcs_op array."""
+    from circuits import Gate, Measure, Reset  # input records only
+
+    arr = (N.dcs_op * max(1, len(ops)))()
+    for i, o in enumerate(ops):
+        d = arr[i]
+        if isinstance(o, Gate):
+            m = np.asarray(o.matrix, dtype=np.complex128).reshape(-1)
+            d.kind = N.OP_GATE1 if len(o.qubits) == 1 else N.OP_GATE2
+            d.q0 = o.qubits[0]
+            d.q1 = o.qubits[1] if len(o.qubits) == 2 else -1
+            for k, z in enumerate(m):
+                d.m[2 * k] = float(z.real)
+                d.m[2 * k + 1] = float(z.imag)
+            d.cond = _cond(o.cond)
+        elif isinstance(o, (Measure, Reset)):
+            d.kind = N.OP_MEASURE if isinstance(o, Measure) else N.OP_RESET
+            d.q0 = o.qubit
+            d.q1 = -1
+            d.cbit = o.cbit
+            d.cond = _cond(None)
+        else:
+            raise TypeError(o)
+    return arr
+
+
+def bits_of(cwords: np.ndarray, n_bits: int) -> np.ndarray:
+    """Unpack [n, CWORDS] uint64 registers into [n, n_bits] uint8."""
+    cw = np.asarray(cwords, dtype=np.uint64)
+    out = np.zeros((cw.shape[0], n_bits), dtype=np.uint8)
+    for b in range(n_bits):
+        out[:, b] = ((cw[:, b >> 6] >> np.uint64(b & 63)) & np.uint64(1)).astype(np.uint8)
+    return out
+
+
+class Simulator:
+    """One libdcs context: n_slots shots (single-path) or a branch pool (multi-path)."""
+
+    def __init__(self, n_qubits: int, chi_max: int, n_slots: int, n_cbits: int,
+                 tol: float = 1e-10, sweeps: int = 2, seed: int = 0, chunk_k: int = 0,
+                 device: str = "cuda:0", stream: Optional[torch.cuda.Stream] = None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("libdcs needs a CUDA device; there is no CPU path")
+        self.lib = N.load()
+        self.cfg = N.dcs_config(n_qubits=n_qubits, chi_max=chi_max, tol=tol, sweeps=sweeps,
+                                chunk_k=chunk_k, precision=0, n_cbits=n_cbits,
+                                n_slots=n_slots, seed=seed)
+        self.device = torch.device(device)
+        nbytes = self.lib.dcs_arena_bytes(ctypes.byref(self.cfg))
+        if nbytes == 0:
+            raise DCSError(N.ERR_INVALID if chi_max <= N.MAX_CHI_FUSED else N.ERR_UNSUPPORTED,
+                           "configuration rejected")
+        self.arena_bytes = nbytes
+        self.arena = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        base = self.arena.data_ptr()
+        self._base = (base + 255) // 256 * 256
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.ctx = ctypes.c_void_p()
+        st = self.lib.dcs_create(ctypes.byref(self.ctx), ctypes.byref(self.cfg),
+                                 ctypes.c_void_p(self._base), nbytes,
+                                 ctypes.c_void_p(self.stream.cuda_stream))
+        if st != N.OK:
+            raise DCSError(st, "dcs_create failed")
+        self.n_qubits, self.n_slots, self.n_cbits = n_qubits, n_slots, n_cbits
+
+    # ------------------------------------------------------------------ plumbing
+    def _check(self, st: int):
+        if st != N.OK:
+            raise DCSError(st, self.lib.dcs_last_error(self.ctx).decode())
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None and self.ctx.value:
+            self.lib.dcs_destroy(self.ctx)
+            self.ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def launches(self) -> int:
+        return int(self.lib.dcs_kernel_launches(self.ctx))
+
+    @property
+    def bytes_uploaded(self) -> int:
+        return int(self.lib.dcs_bytes_uploaded(self.ctx))
+
+    # ------------------------------------------------------------------ calls
+    def init_state(self, n_active: int, multipath: bool = False, shot0: int = 0):
+        self._check(self.lib.dcs_init_state(self.ctx, n_active, int(multipath), shot0))
+
+    def run_circuit(self, circ_or_ops, meas_idx0: int = 0, max_branches: int = 0):
+        ops = circ_or_ops.ops if hasattr(circ_or_ops, "ops") else circ_or_ops
+        arr = encode_ops(ops)
+        self._check(self.lib.dcs_run_circuit(self.ctx, arr, len(ops), meas_idx0, max_branches))
+
+    def run_encoded(self, arr, n_ops: int, meas_idx0: int = 0, max_branches: int = 0):
+        self._check(self.lib.dcs_run_circuit(self.ctx, arr, n_ops, meas_idx0, max_branches))
+
+    def apply_layer(self, gates: Sequence, fid_out: Optional[torch.Tensor] = None):
+        arr = encode_ops(gates)
+        ptr = ctypes.c_void_p(fid_out.data_ptr()) if fid_out is not None else None
+        self._check(self.lib.dcs_apply_layer(self.ctx, arr, len(gates), ptr))
+
+    def measure_prob(self, qubit: int) -> torch.Tensor:
+        out = torch.full((self.n_slots,), float("nan"), dtype=torch.float64, device=self.device)
+        self._check(self.lib.dcs_measure_prob(self.ctx, qubit, ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def measure_sample(self, qubit: int, cbit: int, meas_idx: int):
+        self._check(self.lib.dcs_measure_sample(self.ctx, qubit, cbit, meas_idx))
+
+    def collapse(self, qubit: int, cbit: int, outcomes: Iterable[int]):
+        o = np.zeros(self.n_slots, dtype=np.uint8)
+        vals = np.asarray(list(outcomes), dtype=np.uint8)
+        o[: len(vals)] = vals
+        buf = (ctypes.c_uint8 * self.n_slots).from_buffer_copy(o.tobytes())
+        self._check(self.lib.dcs_collapse(self.ctx, qubit, cbit, buf))
+
+    def branch_split(self, qubit: int, cbit: int, eps: float = 1e-12):
+        self._check(self.lib.dcs_branch_split(self.ctx, qubit, cbit, eps))
+
+    def branch_topk(self, M: int):
+        self._check(self.lib.dcs_branch_topk(self.ctx, M))
+
+    def results(self) -> dict:
+        S = self.n_slots
+        p = np.zeros(S, dtype=np.float64)
+        F = np.zeros(S, dtype=np.float64)
+        cw = np.zeros((S, N.CWORDS), dtype=np.uint64)
+        fl = np.zeros(S, dtype=np.uint8)
+        cnt = ctypes.c_int(0)
+        self._check(self.lib.dcs_get_results(
+            self.ctx, p.ctypes.data_as(ctypes.c_void_p), F.ctypes.data_as(ctypes.c_void_p),
+            cw.ctypes.data_as(ctypes.c_void_p), ctypes.byref(cnt),
+            fl.ctypes.data_as(ctypes.c_void_p)))
+        n = cnt.value
+        return {"n_active": n, "p": p[:n], "F": F[:n], "cwords": cw[:n], "flags": fl[:n],
+                "bits": bits_of(cw[:n], self.n_cbits)}
+
+    def export_mps(self, pos: int):
+        """(bonds, centre, [tensors [chi_l, 2, chi_r] complex64]) of active slot ``pos``."""
+        size = ctypes.c_size_t(0)
+        self._check(self.lib.dcs_export_mps(self.ctx, pos, None, ctypes.byref(size)))
+        buf = (ctypes.c_uint8 * size.value)()
+        self._check(self.lib.dcs_export_mps(self.ctx, pos, buf, ctypes.byref(size)))
+        raw = bytes(buf)
+        n = int(np.frombuffer(raw, dtype=np.int32, count=1)[0])
+        bonds = np.frombuffer(raw, dtype=np.int32, count=n + 1, offset=4).copy()
+        centre = int(np.frombuffer(raw, dtype=np.int32, count=1, offset=4 * (n + 2))[0])
+        off = 4 * (n + 3)
+        T: List[np.ndarray] = []
+        for j in range(n):
+            cnt = int(bonds[j]) * 2 * int(bonds[j + 1])
+            t = np.frombuffer(raw, dtype=np.complex64, count=cnt, offset=off).copy()
+            T.append(t.reshape(int(bonds[j]), 2, int(bonds[j + 1])))
+            off += cnt * 8
+        return bonds, centre, T
+
+    def import_mps(self, pos: int, tensors: Sequence[np.ndarray], centre: int):
+        n = len(tensors)
+        bonds = [1] + [int(t.shape[2]) for t in tensors[:-1]] + [1]
+        parts = [np.array([n], dtype=np.int32).tobytes(), np.array(bonds, dtype=np.int32).tobytes(),
+                 np.array([centre], dtype=np.int32).tobytes()]
+        parts += [np.ascontiguousarray(t, dtype=np.complex64).tobytes() for t in tensors]
+        raw = b"".join(parts)
+        buf = (ctypes.c_uint8 * len(raw)).from_buffer_copy(raw)
+        self._check(self.lib.dcs_import_mps(self.ctx, pos, buf, len(raw)))
+
+
+def mps_to_dense(tensors: Sequence[np.ndarray]) -> np.ndarray:
+    """Contract exported MPS tensors into the 2^n amplitude vector (small n, host FP64)."""
+    v = np.asarray(tensors[0], dtype=np.complex128)
+    for t in tensors[1:]:
+        v = np.tensordot(v, np.asarray(t, dtype=np.complex128), axes=([v.ndim - 1], [0]))
+    return v.reshape(-1)

@@ -1,0 +1,109 @@
+"""The C ABI without a GPU: the library builds and loads, exports every function declared in
+include/dcs.h, its struct layouts match the Python binding, and the host-only argument
+checks answer as documented."""
+import ctypes
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "dcs.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2609_26516_b300 import build
+    build.build()
+    from paper_2609_26516_b300 import _native as N
+    return N.load()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(dcs_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for want in ["dcs_create", "dcs_destroy", "dcs_init_state", "dcs_apply_layer",
+                 "dcs_measure_prob", "dcs_measure_sample", "dcs_collapse", "dcs_branch_split",
+                 "dcs_branch_topk", "dcs_get_results", "dcs_export_mps", "dcs_import_mps",
+                 "dcs_run_circuit", "dcs_arena_bytes", "dcs_last_error"]:
+        assert want in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2609_26516_b300 import _native as N
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert name in N.SIGNATURES, f"binding lacks {name}"
+
+
+def test_struct_layout_matches_binding(tmp_path):
+    from paper_2609_26516_b300 import _native as N
+    prog = r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "dcs.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(dcs_op), offsetof(dcs_op, m),
+         offsetof(dcs_op, cond), sizeof(dcs_cond), sizeof(dcs_config),
+         offsetof(dcs_config, tol), offsetof(dcs_config, seed));
+  return 0;
+}
+'''
+    c = tmp_path / "layout.c"
+    c.write_text(prog)
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(c), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    got = [int(x) for x in out]
+    want = [ctypes.sizeof(N.dcs_op), N.dcs_op.m.offset, N.dcs_op.cond.offset,
+            ctypes.sizeof(N.dcs_cond), ctypes.sizeof(N.dcs_config), N.dcs_config.tol.offset,
+            N.dcs_config.seed.offset]
+    assert got == want
+
+
+def _cfg(N, **kw):
+    base = dict(n_qubits=64, chi_max=8, tol=1e-10, sweeps=2, chunk_k=0, precision=0, n_cbits=64,
+                n_slots=10000, seed=1)
+    base.update(kw)
+    return N.dcs_config(**base)
+
+
+def test_arena_bytes_and_argument_checks(lib):
+    from paper_2609_26516_b300 import _native as N
+    cfg = _cfg(N)
+    nb = lib.dcs_arena_bytes(ctypes.byref(cfg))
+    # two MPS buffers + two environment caches dominate: 10^4 slots x (2*64*128 + 2*65*256) x 8 B
+    assert nb > 10000 * (2 * 64 * 128 + 2 * 65 * 256) * 8
+    assert nb < 2 * 10000 * (2 * 64 * 128 + 2 * 65 * 256) * 8
+    assert lib.dcs_arena_bytes(ctypes.byref(_cfg(N, n_qubits=0))) == 0
+    assert lib.dcs_arena_bytes(ctypes.byref(_cfg(N, chi_max=64))) == 0
+    assert lib.dcs_arena_bytes(ctypes.byref(_cfg(N, n_cbits=513))) == 0
+    ctx = ctypes.c_void_p()
+    assert lib.dcs_create(ctypes.byref(ctx), ctypes.byref(_cfg(N, sweeps=0)), None, 0, None) == N.ERR_INVALID
+    assert lib.dcs_create(ctypes.byref(ctx), ctypes.byref(_cfg(N, chi_max=64)), None, 0, None) == N.ERR_UNSUPPORTED
+    assert lib.dcs_create(ctypes.byref(ctx), ctypes.byref(cfg), None, 0, None) == N.ERR_OOM
+    assert lib.dcs_last_error(None) == b"null context"
+
+
+def test_encode_ops_round_trip():
+    import numpy as np
+    import circuits as C
+    from paper_2609_26516_b300.sim import encode_ops
+    from paper_2609_26516_b300 import _native as N
+    circ = C.teleport(1)
+    arr = encode_ops(circ.ops)
+    g = circ.ops[2]  # CNOT(1, 2)
+    d = arr[2]
+    assert d.kind == N.OP_GATE2 and (d.q0, d.q1) == (1, 2)
+    m = np.array(d.m[:32]).reshape(16, 2)
+    np.testing.assert_array_equal(m[:, 0] + 1j * m[:, 1], g.matrix.reshape(-1))
+    cx = arr[7]
+    assert cx.cond.op == N.COND_XOR and cx.cond.mask[0] == 0b10 and cx.cond.value == 1
+    assert arr[5].kind == N.OP_MEASURE and arr[5].cbit == 0

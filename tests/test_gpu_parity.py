@@ -1,0 +1,221 @@
+"""Parity of the CUDA path (through the libdcs C ABI) with the FP64 oracle.
+
+Bars (tolerances of the accuracy contract): measurement outcomes bit-exact except draws
+the oracle flags (|u - p_0| < 1e-6); probabilities within 1e-5 absolute; state fidelity
+|<psi_gpu|psi_oracle>|^2 >= 1 - 1e-6 (gauge-invariant: MPS tensors are compared only
+through the state they represent); the estimated fidelity F within ``f_tol``."""
+import numpy as np
+import pytest
+
+import circuits as C
+from oracle import drivers as D, mps as OM, statevector as SV
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+P_TOL = 1e-5
+STATE_TOL = 1e-6
+# The estimated fidelity F = prod f has no tolerance in the accuracy contract.  Each f is
+# the end of an FP32 chain of n site updates, so its rounding error grows like n u
+# (u = 2^-24); the bound allows 8 u per site update plus 1e-5.
+U32 = 2.0 ** -24
+
+
+def f_tol(n_sites, n_compressions):
+    return 1e-5 + 8 * U32 * n_sites * max(1, n_compressions)
+
+
+def _sim(n, chi, slots, ncb, tol=1e-10, sweeps=2, seed=1):
+    from paper_2609_26516_b300 import Simulator
+    return Simulator(n, chi, slots, max(ncb, 1), tol=tol, sweeps=sweeps, seed=seed)
+
+
+def _overlap(A, B):
+    """<A|B> of two MPS by transfer matrices (host FP64, any n)."""
+    E = np.ones((1, 1), dtype=np.complex128)
+    for a, b in zip(A, B):
+        E = np.einsum("xy,xsu,ysv->uv", E, np.conj(np.asarray(a, dtype=np.complex128)),
+                      np.asarray(b, dtype=np.complex128))
+    return E[0, 0]
+
+
+def _state_fid(sim, pos, ref_mps):
+    _, _, T = sim.export_mps(pos)
+    ab = _overlap(T, ref_mps.T)
+    aa = _overlap(T, T).real
+    bb = _overlap(ref_mps.T, ref_mps.T).real
+    return abs(ab) ** 2 / (aa * bb)
+
+
+def _single_path_parity(circ, chi, shots, check_shots, seed=1, tol=1e-10, sweeps=2,
+                        state_check=True):
+    sim = _sim(circ.n_qubits, chi, shots, circ.n_cbits, tol, sweeps, seed)
+    sim.init_state(shots)
+    sim.run_circuit(circ)
+    res = sim.results()
+    assert res["n_active"] == shots
+    prm = D.Params(chi_max=chi, tol=tol, sweeps=sweeps)
+    compared = 0
+    for s in check_shots:
+        ref = D.run_single_path(circ, prm, seed, s)
+        if ref.flagged:
+            continue
+        compared += 1
+        assert res["bits"][s].tolist() == [int(x) for x in ref.c], f"shot {s}"
+        if state_check:
+            bonds, _, _ = sim.export_mps(s)
+            assert list(bonds) == ref.mps.bonds(), f"shot {s}: bond dimensions differ"
+            assert _state_fid(sim, s, ref.mps) >= 1 - STATE_TOL
+        assert abs(res["p"][s] - ref.p) < P_TOL
+        assert abs(res["F"][s] - ref.F) < f_tol(circ.n_qubits, len(ref.fids))
+    assert compared >= len(check_shots) // 2
+    return sim, res
+
+
+def test_teleport_single_path_1000_shots():
+    circ = C.teleport(1)
+    sim, res = _single_path_parity(circ, 4, 1000, list(range(0, 1000, 37)))
+    # the four paths at 1/4 each: 1000 shots land within 5 sigma
+    paths = res["bits"][:, 0] * 2 + res["bits"][:, 1]
+    counts = np.bincount(paths, minlength=4)
+    assert np.all(np.abs(counts - 250) < 5 * np.sqrt(1000 * 0.25 * 0.75))
+    assert np.all(np.abs(res["p"] - 0.25) < P_TOL)
+
+
+@pytest.mark.parametrize("n", [9, 20])
+def test_ghz_single_path_small(n):
+    circ = C.ghz_dynamic(n)
+    _single_path_parity(circ, 8, 64, list(range(0, 64, 9)))
+
+
+def test_ghz64_full_config_sampled_shots():
+    circ = C.ghz_dynamic(64)
+    shots = 10000
+    sim = _sim(64, 8, shots, circ.n_cbits)
+    sim.init_state(shots)
+    sim.run_circuit(circ)
+    res = sim.results()
+    prm = D.Params(chi_max=8)
+    r = circ.meta["r"]
+    assert np.all(np.abs(res["p"] - 2.0 ** -r) < P_TOL * 2.0 ** -r)
+    assert np.all(np.abs(res["F"] - 1.0) < f_tol(64, 4))
+    for s in (0, 4999, 9999):
+        ref = D.run_single_path(circ, prm, 1, s)
+        assert res["bits"][s].tolist() == [int(x) for x in ref.c]
+        assert _state_fid(sim, s, ref.mps) >= 1 - STATE_TOL
+
+
+# tol = 0 is not a parity case: FP32 rounding leaves singular values ~1e-7 where FP64 has
+# exact zeros, so the two sides would keep different (noise) bond directions.
+@pytest.mark.parametrize("chi,tol", [(8, 1e-10), (5, 1e-10), (32, 1e-12)])
+def test_brickwork_single_path(chi, tol):
+    circ = C.brickwork(10, 8, 0.2, 3)
+    _single_path_parity(circ, chi, 16, list(range(16)), tol=tol)
+
+
+def test_brickwork_three_sweeps_and_ragged():
+    circ = C.brickwork(7, 6, 0.25, 11)
+    _single_path_parity(circ, 3, 8, list(range(8)), sweeps=3)
+
+
+def test_multi_path_ghz_topm():
+    circ = C.ghz_dynamic(9)
+    for M in (4, 16):
+        sim = _sim(9, 8, 2 * M, circ.n_cbits)
+        sim.init_state(1, multipath=True)
+        sim.run_circuit(circ, max_branches=M)
+        res = sim.results()
+        ref = D.run_multi_path(circ, D.Params(chi_max=8), M=M)
+        assert res["n_active"] == len(ref)
+        for i, b in enumerate(ref):
+            assert res["bits"][i].tolist() == [int(x) for x in b.c]
+            assert abs(res["p"][i] - b.p) < P_TOL
+            assert _state_fid(sim, i, b.mps) >= 1 - STATE_TOL
+
+
+def test_multi_path_brickwork_uneven():
+    circ = C.brickwork(8, 6, 0.2, 5)
+    M = 8
+    sim = _sim(8, 8, 2 * M, circ.n_cbits)
+    sim.init_state(1, multipath=True)
+    sim.run_circuit(circ, max_branches=M)
+    res = sim.results()
+    ref = D.run_multi_path(circ, D.Params(chi_max=8), M=M)
+    assert res["n_active"] == len(ref)
+    for i, b in enumerate(ref):
+        assert res["bits"][i].tolist() == [int(x) for x in b.c]
+        assert _state_fid(sim, i, b.mps) >= 1 - STATE_TOL
+        assert abs(res["p"][i] - b.p) < P_TOL
+        assert abs(res["F"][i] - b.F) < f_tol(8, 6)
+
+
+def test_teleport_multi_path_pool_exhaustion():
+    circ = C.teleport(2)
+    from paper_2609_26516_b300 import DCSError
+    sim = _sim(3, 4, 2, circ.n_cbits)  # four paths do not fit in two slots
+    sim.init_state(1, multipath=True)
+    sim.run_circuit(circ)
+    with pytest.raises(DCSError):
+        sim.results()
+
+
+def test_measure_prob_and_forced_collapse():
+    circ = C.brickwork(6, 4, 0.0, 2)
+    sim = _sim(6, 8, 4, 2)
+    sim.init_state(4)
+    sim.run_circuit(circ)
+    p0 = sim.measure_prob(3).cpu().numpy()
+    ref = D.run_single_path(circ, D.Params(chi_max=8), 1, 0)
+    r0, r1 = OM.measure_probs(ref.mps, 3)
+    assert np.all(np.abs(p0 - r0 / (r0 + r1)) < P_TOL)
+    sim.collapse(3, 0, [0, 1, 0, 1])
+    res = sim.results()
+    assert res["bits"][:, 0].tolist() == [0, 1, 0, 1]
+    for s, m in enumerate([0, 1, 0, 1]):
+        mm = ref.mps.copy()
+        OM.measure_probs(mm, 3)
+        OM.collapse(mm, 3, m, r0 if m == 0 else r1)
+        assert abs(res["p"][s] - (r0 if m == 0 else r1) / (r0 + r1)) < P_TOL
+        assert _state_fid(sim, s, mm) >= 1 - STATE_TOL
+
+
+def test_empty_chunk_leaves_slot_unchanged():
+    # X on q0 conditioned on c0 == 1; no slot has c0 set, so nothing is compressed
+    g = [C.Gate((0,), C.X, cond=C.Cond((0,), "xor", 1))]
+    sim = _sim(4, 4, 3, 1)
+    sim.init_state(3)
+    fid = torch.zeros(3, dtype=torch.float64, device="cuda")
+    sim.apply_layer(g, fid)
+    assert torch.all(fid == 1.0)
+    res = sim.results()
+    assert np.all(res["F"] == 1.0)
+    _, _, T = sim.export_mps(0)
+    assert abs(T[0][0, 0, 0] - 1) < 1e-7
+
+
+def test_export_import_round_trip():
+    circ = C.brickwork(6, 5, 0.0, 4)
+    sim = _sim(6, 8, 2, 1)
+    sim.init_state(2)
+    sim.run_circuit(circ)
+    b, c, T = sim.export_mps(0)
+    sim.import_mps(1, T, c)
+    b2, c2, T2 = sim.export_mps(1)
+    assert list(b) == list(b2) and c == c2
+    for x, y in zip(T, T2):
+        assert np.array_equal(x, y)
+
+
+def test_single_qubit_chain_and_launch_count():
+    # n = 1: a lone qubit, Hadamard then a measurement
+    circ = C.Circuit(1, 1, [C.Gate((0,), C.H), C.Measure(0, 0)])
+    sim = _sim(1, 4, 256, 1)
+    sim.init_state(256)
+    before = sim.launches
+    sim.run_circuit(circ)
+    res = sim.results()
+    assert sim.launches - before == 2
+    assert np.all(np.abs(res["p"] - 0.5) < P_TOL)
+    for s in range(0, 256, 17):
+        ref = SV.run_single_path(circ, 1, s)
+        assert res["bits"][s, 0] == ref.outcomes[0]
