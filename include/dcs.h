@@ -199,6 +199,45 @@ uint64_t dcs_kernel_launches(dcs_ctx_t ctx);
  * created. */
 uint64_t dcs_bytes_uploaded(dcs_ctx_t ctx);
 
+/* ---------------------------------------------------------------------------------------
+ * Allocation-free compression (the paper has no counterpart to this call).
+ *
+ * For callers that cannot allocate device memory -- code running under a framework that
+ * owns the whole GPU through its own pool, or inside a section where cudaMalloc would
+ * synchronise the device or is not allowed -- this one call runs the same compression step
+ * as dcs_apply_layer on a single MPS without a context and without allocating anything.
+ * Its working memory is a fixed device array of DCS_NOALLOC_SCRATCH_BYTES inside the
+ * library, which every GPU that loads the library holds until the process exits.
+ *
+ *   n_qubits <= DCS_NOALLOC_MAX_QUBITS, chi_max <= DCS_NOALLOC_MAX_CHI and
+ *   n_gates <= DCS_NOALLOC_MAX_GATES; larger requests return DCS_ERR_OOM (too big for the
+ *   fixed scratch), malformed ones DCS_ERR_INVALID.
+ *   gates: one chunk, as for dcs_apply_layer (HOST array).
+ *   creg: HOST pointer to DCS_CWORDS words of the classical register that the gates'
+ *   conditions read, or NULL for all zeros.
+ *   ket: DEVICE buffer of the input MPS, site j at complex64 offset j * 2 * Cc^2, Cc = 4 if
+ *   chi_max <= 4 else 8, each site packed row-major as [chi_l][2][chi_r]; ket_bonds: DEVICE
+ *   int32[n_qubits + 1]; ket_centre: its orthogonality centre (host int).  Read only.
+ *   bra, bra_bonds, bra_centre (may be NULL), f: DEVICE outputs in the same layout; f is one
+ *   double.  If every gate is skipped by its condition, the ket is copied through, f = 1.
+ *
+ * The first call on a device looks up the scratch array's device address for that device
+ * (with the device current); make that first call before any stream capture.  Calls share
+ * the scratch and it keeps the last call's contents, so calls that overlap on the GPU (on
+ * different streams) race.  The call copies the chunk's tables from static host storage and
+ * returns after they have been staged, which waits for earlier work on the stream.
+ * --------------------------------------------------------------------------------------- */
+#define DCS_NOALLOC_MAX_QUBITS 64
+#define DCS_NOALLOC_MAX_CHI 8
+#define DCS_NOALLOC_MAX_GATES 256
+#define DCS_NOALLOC_SCRATCH_BYTES (512u * 1024u)
+
+dcs_status_t dcs_compress_noalloc(int32_t n_qubits, int32_t chi_max, double tol, int32_t sweeps,
+                                  const dcs_op* gates, int32_t n_gates, const uint64_t* creg,
+                                  const void* ket, const int32_t* ket_bonds, int32_t ket_centre,
+                                  void* bra, int32_t* bra_bonds, int32_t* bra_centre, double* f,
+                                  dcs_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

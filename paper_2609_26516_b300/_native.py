@@ -60,6 +60,9 @@ SIGNATURES = {
     "dcs_run_circuit": (_c.c_int, [_P, _c.POINTER(dcs_op), _c.c_int, _c.c_uint64, _c.c_int]),
     "dcs_kernel_launches": (_c.c_uint64, [_P]),
     "dcs_bytes_uploaded": (_c.c_uint64, [_P]),
+    "dcs_compress_noalloc": (_c.c_int, [_c.c_int32, _c.c_int32, _c.c_double, _c.c_int32,
+                                        _c.POINTER(dcs_op), _c.c_int32, _P, _P, _P, _c.c_int32,
+                                        _P, _P, _P, _P, _P]),
 }
 
 _lib = None

@@ -9,7 +9,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libdcs.so")
-SOURCES = ["dcs_api.cu", "dcs_kernels.cu"]
+SOURCES = ["dcs_api.cu", "dcs_kernels.cu", "dcs_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
