@@ -115,6 +115,17 @@ struct dcs_ctx_s {
   uint64_t launches = 0;
   uint64_t uploaded = 0;
   int multipath = 0;
+  // Upper bound on every bond dimension any slot can have, per bond, tracked from the
+  // circuit alone: a two-qubit block on (q, q+1) makes bond q+1 at most
+  // min(chi_max, 2 ub[q], 2 ub[q+2], 2^min(q+1, n-q-1)) (the truncated SVD of a
+  // (2 chi_q) x (2 chi_{q+2}) matrix); QR steps, measurements and single-qubit gates never
+  // raise a bond.  The shared-memory tile of a launch is the smallest one above this bound.
+  std::vector<int> ub;
+  int tile() const {
+    int m = 1;
+    for (int v : ub) m = std::max(m, v);
+    return fused_chi(m);
+  }
 };
 
 namespace {
@@ -217,6 +228,17 @@ dcs_status_t check_gate(dcs_ctx_t c, const dcs_op& o) {
   return DCS_OK;
 }
 
+void grow_bounds(dcs_ctx_t c, const Program& P, const DLayer& L) {
+  const int n = c->cfg.n_qubits;
+  std::vector<int>& ub = c->ub;
+  for (int b = 0; b < L.n_blocks; ++b) {
+    const int q = P.blocks[L.blk_off + b].q;
+    const int e = std::min(q + 1, n - q - 1);
+    const int hil = e >= 30 ? (1 << 30) : (1 << e);
+    ub[q + 1] = std::min({c->cfg.chi_max, 2 * ub[q], 2 * ub[q + 2], hil});
+  }
+}
+
 dcs_status_t run_steps(dcs_ctx_t c, const Program& P, int max_branches,
                        double* fid_out) {
   DevProg dp;
@@ -225,17 +247,21 @@ dcs_status_t run_steps(dcs_ctx_t c, const Program& P, int max_branches,
   if (st != DCS_OK) return st;
   for (const Step& s : P.steps) {
     if (s.kind == 0) {
-      launch_compress(c->dev, dp.layers + s.idx, dp.blocks, dp.g1, dp.conds, fid_out, c->stream);
+      grow_bounds(c, P, P.layers[s.idx]);
+      launch_compress(c->dev, c->tile(), dp.layers + s.idx, dp.blocks, dp.g1, dp.conds, fid_out,
+                      c->stream);
       c->launches++;
       if ((st = post_launch(c, "compress")) != DCS_OK) return st;
     } else if (!c->multipath) {
-      launch_measure(c->dev, dp.meas + s.idx, s.n, MEAS_SAMPLE, nullptr, nullptr, c->stream);
+      launch_measure(c->dev, c->tile(), dp.meas + s.idx, s.n, MEAS_SAMPLE, nullptr, nullptr,
+                     c->stream);
       c->launches++;
       if ((st = post_launch(c, "measure")) != DCS_OK) return st;
     } else {
       for (int i = 0; i < s.n; ++i) {
         const DMeas& m = P.meas[s.idx + i];
-        launch_measure(c->dev, dp.meas + s.idx + i, 1, MEAS_PROB, nullptr, nullptr, c->stream);
+        launch_measure(c->dev, c->tile(), dp.meas + s.idx + i, 1, MEAS_PROB, nullptr, nullptr,
+                       c->stream);
         c->launches++;
         int l = 0;
         launch_branch_split(c->dev, m.q, m.cbit, 1e-12, max_branches, c->stream, &l);
@@ -300,6 +326,7 @@ dcs_status_t dcs_create(dcs_ctx_t* out, const dcs_config* cfg, void* dev_arena, 
   d.chi_max = cfg->chi_max;
   d.tol = cfg->tol;
   d.sweeps = cfg->sweeps;
+  c->ub.assign(cfg->n_qubits + 1, 1);
   if (cudaEventCreateWithFlags(&c->stage_done, cudaEventDisableTiming) != cudaSuccess) {
     delete c;
     return DCS_ERR_CUDA;
@@ -328,6 +355,7 @@ dcs_status_t dcs_init_state(dcs_ctx_t c, int n_active, int multipath, uint64_t s
   if (n_active < 1 || n_active > c->cfg.n_slots) return fail(c, DCS_ERR_INVALID, "n_active out of range");
   if (multipath && n_active != 1) return fail(c, DCS_ERR_INVALID, "multi-path starts from one branch");
   c->multipath = multipath ? 1 : 0;
+  c->ub.assign(c->cfg.n_qubits + 1, 1);
   launch_init(c->dev, n_active, c->multipath, shot0, c->stream);
   c->launches++;
   return post_launch(c, "init");
@@ -362,7 +390,8 @@ static dcs_status_t measure_common(dcs_ctx_t c, int qubit, int cbit, uint64_t or
   DevProg dp;
   dcs_status_t st = upload(c, P, extra, dp);
   if (st != DCS_OK) return st;
-  launch_measure(c->dev, dp.meas, 1, mode, forced ? dp.bytes : nullptr, p0_out, c->stream);
+  launch_measure(c->dev, c->tile(), dp.meas, 1, mode, forced ? dp.bytes : nullptr, p0_out,
+                 c->stream);
   c->launches++;
   return post_launch(c, "measure");
 }
@@ -515,6 +544,7 @@ dcs_status_t dcs_import_mps(dcs_ctx_t c, int pos, const void* host_buf, size_t b
   cudaMemcpy(c->dev.bonds + ((size_t)slot * 2 + kb) * (n + 1), b.data(), (n + 1) * sizeof(int),
              cudaMemcpyHostToDevice);
   cudaMemcpy(c->dev.centre + slot, &centre, sizeof(int), cudaMemcpyHostToDevice);
+  for (int j = 0; j <= n; ++j) c->ub[j] = std::max(c->ub[j], b[j]);
   return cuda_check(c, cudaGetLastError(), "import");
 }
 

@@ -87,15 +87,33 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return v;
 }
 
+template <int NT>
+__device__ __forceinline__ float block_sumf(float v, float* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (NT > 32) {
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    v = 0.f;
+#pragma unroll
+    for (int i = 0; i < NT / 32; ++i) v += red[i];
+  }
+  __syncthreads();
+  return v;
+}
+
 // ----------------------------------------------------------------------------- QR
 // Householder QR of X (m x n, column-major, ld >= m) in place: Q (m x r, column-major, ldq)
 // is formed explicitly (r = min(m, n)), and if R != nullptr the factor R (r x n, row-major,
 // ldr) is written.  Reflector k is H_k = I - 2 u_k u_k^H with the unit vector
 // u_k = (x - alpha_k e_1) / ||x - alpha_k e_1|| stored in X[k:, k], where x is the current
 // column below the diagonal and alpha_k = -(x_0/|x_0|) ||x||, so H_k x = alpha_k e_1.
-// Norms are accumulated from FP64 squares and the reflector is normalised in FP64, so H_k
-// stays unitary to FP32 rounding whatever the column's magnitude (a column of tiny
-// rounding noise included).  Scratch: tau[r] (1 or 0), alpha[r], red[NT/32] (double).
+// The reflector is normalised explicitly, so H_k stays unitary to FP32 rounding whatever
+// the column's magnitude; a column whose FP32 squared norm is below 1e-30 (a column of
+// rounding noise, where FP32 squares can underflow) is normalised from FP64 squares.
+// Scratch: tau[r] (2 or 0), alpha[r], red[NT/32] (double).
 template <int NT>
 __device__ int cta_qr(float2* X, int m, int n, int ld, float2* Q, int ldq, float2* R, int ldr,
                       float* tau, float2* alpha, double* red) {
@@ -103,41 +121,77 @@ __device__ int cta_qr(float2* X, int m, int n, int ld, float2* Q, int ldq, float
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int NW = NT / 32;
   for (int k = 0; k < r; ++k) {
-    double s = 0.0;
-    for (int i = k + threadIdx.x; i < m; i += NT) s += cabs2d(X[i + k * ld]);
-    s = block_sum<NT>(s, red);
+    // FP32 norm; a column whose squared norm is below 1e-30 (where FP32 squares of its
+    // entries may underflow) is redone from FP64 squares
+    float s32 = 0.f;
+    for (int i = k + threadIdx.x; i < m; i += NT) s32 += cabs2(X[i + k * ld]);
+    s32 = block_sumf<NT>(s32, reinterpret_cast<float*>(red));
     const float2 x0 = X[k + k * ld];
-    const double nrm = sqrt(s);
-    const double a0 = sqrt(cabs2d(x0));
-    // v = x - alpha e_1, ||v||^2 = 2 nrm (nrm + |x_0|); u = v / ||v||
-    const double vn = sqrt(2.0 * nrm * (nrm + a0));
-    const bool skip = !(vn > 0.0);
-    __syncthreads();
-    if (!skip) {
-      double ar, ai;
-      if (a0 > 0.0) {
-        ar = -(double)x0.x / a0 * nrm;
-        ai = -(double)x0.y / a0 * nrm;
+    bool skip;
+    if (s32 > 1e-30f) {
+      const float nrm = sqrtf(s32);
+      // |x_0| without underflow: alpha = -(x_0/|x_0|) nrm must have modulus nrm exactly
+      const float a0 = hypotf(x0.x, x0.y);
+      const float vn = sqrtf(2.f * nrm * (nrm + a0));  // ||x - alpha e_1||
+      const float inv = 1.f / vn;
+      float ar, ai;
+      if (a0 > 0.f) {
+        ar = -x0.x / a0 * nrm;
+        ai = -x0.y / a0 * nrm;
       } else {
         ar = -nrm;
-        ai = 0.0;
+        ai = 0.f;
       }
+      __syncthreads();
       for (int i = k + threadIdx.x; i < m; i += NT) {
-        const float2 xi = X[i + k * ld];
-        double vr = xi.x, vi = xi.y;
+        float2 v = X[i + k * ld];
         if (i == k) {
-          vr -= ar;
-          vi -= ai;
+          v.x -= ar;
+          v.y -= ai;
         }
-        X[i + k * ld] = make_float2((float)(vr / vn), (float)(vi / vn));
+        X[i + k * ld] = make_float2(v.x * inv, v.y * inv);
       }
       if (threadIdx.x == 0) {
         tau[k] = 2.f;
-        alpha[k] = make_float2((float)ar, (float)ai);
+        alpha[k] = make_float2(ar, ai);
       }
-    } else if (threadIdx.x == 0) {
-      tau[k] = 0.f;
-      alpha[k] = cz();
+      skip = false;
+    } else {
+      double s = 0.0;
+      for (int i = k + threadIdx.x; i < m; i += NT) s += cabs2d(X[i + k * ld]);
+      s = block_sum<NT>(s, red);
+      const double nrm = sqrt(s);
+      const double a0 = sqrt(cabs2d(x0));
+      // v = x - alpha e_1, ||v||^2 = 2 nrm (nrm + |x_0|); u = v / ||v||
+      const double vn = sqrt(2.0 * nrm * (nrm + a0));
+      skip = !(vn > 0.0);
+      __syncthreads();
+      if (!skip) {
+        double ar, ai;
+        if (a0 > 0.0) {
+          ar = -(double)x0.x / a0 * nrm;
+          ai = -(double)x0.y / a0 * nrm;
+        } else {
+          ar = -nrm;
+          ai = 0.0;
+        }
+        for (int i = k + threadIdx.x; i < m; i += NT) {
+          const float2 xi = X[i + k * ld];
+          double vr = xi.x, vi = xi.y;
+          if (i == k) {
+            vr -= ar;
+            vi -= ai;
+          }
+          X[i + k * ld] = make_float2((float)(vr / vn), (float)(vi / vn));
+        }
+        if (threadIdx.x == 0) {
+          tau[k] = 2.f;
+          alpha[k] = make_float2((float)ar, (float)ai);
+        }
+      } else if (threadIdx.x == 0) {
+        tau[k] = 0.f;
+        alpha[k] = cz();
+      }
     }
     __syncthreads();
     if (!skip) {
@@ -207,10 +261,10 @@ __device__ int cta_qr(float2* X, int m, int n, int ld, float2* Q, int ldq, float
 // until they are mutually orthogonal, X V = U Sigma, accumulating the unitary V (n x n,
 // column-major, ldv).  Pairs follow the circle-method tournament so each round rotates
 // disjoint pairs in parallel, one group of G lanes per pair.  A pair (i, j) with
-// Gram [[a, g], [conj g, b]] is rotated when |g| > thr sqrt(a b):
+// Gram [[a, g], [conj g, b]] is rotated when |g| > 2 sqrt(m) eps sqrt(a b):
 // zeta = (b - a) / (2|g|), t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1+t^2),
 // s = c t, x_i' = c x_i - s e^{-i phi} x_j, x_j' = s x_i + c e^{-i phi} x_j, g = |g| e^{i phi}.
-// Afterwards sig2[j] = ||x_j||^2 (FP64) and perm[0..n) lists columns by decreasing norm
+// Afterwards sig2[j] = ||x_j||^2 and perm[0..n) lists columns by decreasing norm
 // (ties: lower index first).  Scratch: red[NT/32], flag (int).
 template <int NT>
 __device__ void cta_jacobi_svd(float2* X, int m, int n, int ld, float2* V, int ldv,
@@ -226,8 +280,10 @@ __device__ void cta_jacobi_svd(float2* X, int m, int n, int ld, float2* V, int l
   while (G > 1 && (NT / G) < npairs) G >>= 1;
   const int ngroups = NT / G;
   const int grp = threadIdx.x / G, gl = threadIdx.x % G;
-  const float thr = 2e-7f;
-  for (int sweep = 0; sweep < 60 && N >= 2; ++sweep) {
+  // convergence: |g| <= 2 sqrt(m) eps32 sqrt(a b), the FP32 rounding level of the computed
+  // inner product (the column-orthogonality test of one-sided Jacobi codes)
+  const float thr = 2.f * sqrtf((float)m) * 5.96e-8f;
+  for (int sweep = 0; sweep < 30 && N >= 2; ++sweep) {
     if (threadIdx.x == 0) *flag = 0;
     __syncthreads();
     for (int rnd = 0; rnd < N - 1; ++rnd) {
@@ -266,7 +322,7 @@ __device__ void cta_jacobi_svd(float2* X, int m, int n, int ld, float2* V, int l
           g.x += __shfl_xor_sync(0xffffffffu, g.x, o);
           g.y += __shfl_xor_sync(0xffffffffu, g.y, o);
         }
-        const float ag = sqrtf(cabs2(g));
+        const float ag = hypotf(g.x, g.y);  // the phase g/|g| must have modulus 1
         if (valid && ag > thr * sqrtf(a * b) && ag > 0.f) {
           const float zeta = (b - a) / (2.f * ag);
           const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
@@ -295,9 +351,9 @@ __device__ void cta_jacobi_svd(float2* X, int m, int n, int ld, float2* V, int l
   }
   // column norms (FP64) and ordering
   for (int j = threadIdx.x; j < n; j += NT) {
-    double s = 0.0;
-    for (int i = 0; i < m; ++i) s += cabs2d(X[i + j * ld]);
-    sig2[j] = s;
+    float s = 0.f;
+    for (int i = 0; i < m; ++i) s += cabs2(X[i + j * ld]);
+    sig2[j] = (double)s;
   }
   __syncthreads();
   for (int j = threadIdx.x; j < n; j += NT) {
@@ -315,7 +371,7 @@ __device__ void cta_jacobi_svd(float2* X, int m, int n, int ld, float2* V, int l
 // Smallest k >= 1 with sum_{i >= k} w_(i) <= tol * sum_i w_i, w_(i) the values in
 // decreasing order (through perm), capped at cap and n.  Suffix sums are accumulated from
 // the smallest value up.  Evaluated by one thread in FP64.
-__device__ __forceinline__ int trunc_rank(const double* w, const int* perm, int n, int cap,
+__device__ __noinline__ int trunc_rank(const double* w, const int* perm, int n, int cap,
                                           double tol) {
   double total = 0.0;
   for (int i = 0; i < n; ++i) total += w[i];

@@ -37,7 +37,7 @@ __device__ __forceinline__ bool cond_holds(const DCond& cd, const uint64_t* c) {
 }
 
 // U := product of the applicable single-qubit gates g[off .. off+n) (later gates on the left)
-__device__ void prod1q(const DGate1* g, int off, int n, const uint64_t* c, float2* U) {
+__device__ __noinline__ void prod1q(const DGate1* g, int off, int n, const uint64_t* c, float2* U) {
   U[0] = make_float2(1.f, 0.f);
   U[1] = cz();
   U[2] = cz();
@@ -61,7 +61,7 @@ __device__ void prod1q(const DGate1* g, int off, int n, const uint64_t* c, float
 }
 
 // W of site j for register c into W[dl][s][t][dr] (row-major); returns dl, dr.  One thread.
-__device__ void build_W(int j, const DLayer* L, const DBlock* BK, const DGate1* G1,
+__device__ __noinline__ void build_W(int j, const DLayer* L, const DBlock* BK, const DGate1* G1,
                         const uint64_t* c, float2* W, int* dl_out, int* dr_out) {
   const DSite& st = L->site[j];
   if (st.kind == 0 || st.kind == 1) {
@@ -109,7 +109,7 @@ __device__ void build_W(int j, const DLayer* L, const DBlock* BK, const DGate1* 
 }
 
 // G_blk = (Post_q x Post_{q+1}) G2 (Pre_q x Pre_{q+1}), row-major 4x4.  One thread.
-__device__ void build_block(const DBlock& b, const DGate1* G1, const uint64_t* c, float2* G) {
+__device__ __noinline__ void build_block(const DBlock& b, const DGate1* G1, const uint64_t* c, float2* G) {
   float2 Pre0[4], Post0[4], Pre1[4], Post1[4];
   prod1q(G1, b.pre_off[0], b.pre_n[0], c, Pre0);
   prod1q(G1, b.post_off[0], b.post_n[0], c, Post0);
@@ -382,8 +382,14 @@ __device__ void move_centre(const DevCtx& c, Smem<C, NT>& sm, int buf, int slot,
 }
 
 // ----------------------------------------------------------------------------- compression
+// one warp per CTA for the small tiles: at most 64 registers so 32 CTAs fit an SM
+template <int NT>
+struct MinBlocks {
+  static constexpr int value = NT == 32 ? 32 : (NT == 64 ? 16 : 4);
+};
+
 template <int C, int NT>
-__global__ void __launch_bounds__(NT) k_compress(DevCtx c, const DLayer* __restrict__ L,
+__global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_compress(DevCtx c, const DLayer* __restrict__ L,
                                                  const DBlock* __restrict__ BK,
                                                  const DGate1* __restrict__ G1,
                                                  const DCond* __restrict__ CD, double* fid_out) {
@@ -653,7 +659,7 @@ __global__ void __launch_bounds__(NT) k_compress(DevCtx c, const DLayer* __restr
 // the other slice of the centre tensor and rescales by 1/sqrt(r_m) (Sec. "Mid-circuit
 // measurements").
 template <int C, int NT>
-__global__ void __launch_bounds__(NT) k_measure(DevCtx c, const DMeas* __restrict__ meas,
+__global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_measure(DevCtx c, const DMeas* __restrict__ meas,
                                                 int n_meas, int mode,
                                                 const uint8_t* __restrict__ forced,
                                                 double* p0_out) {
@@ -1020,9 +1026,9 @@ void launch_init(const DevCtx& c, int n_active, int multipath, uint64_t shot0, c
   k_init<<<c.n_slots, 64, 0, s>>>(c, n_active, multipath, shot0);
 }
 
-void launch_compress(const DevCtx& c, const DLayer* L, const DBlock* B, const DGate1* G1,
-                     const DCond* CD, double* fid_out, cudaStream_t s) {
-  switch (c.chi_cap) {
+void launch_compress(const DevCtx& c, int tile_chi, const DLayer* L, const DBlock* B,
+                     const DGate1* G1, const DCond* CD, double* fid_out, cudaStream_t s) {
+  switch (tile_chi) {
     case 4: compress_c<4, 32>(c, L, B, G1, CD, fid_out, s); break;
     case 8: compress_c<8, 32>(c, L, B, G1, CD, fid_out, s); break;
     case 16: compress_c<16, 64>(c, L, B, G1, CD, fid_out, s); break;
@@ -1031,9 +1037,9 @@ void launch_compress(const DevCtx& c, const DLayer* L, const DBlock* B, const DG
   }
 }
 
-void launch_measure(const DevCtx& c, const DMeas* meas, int n_meas, int mode,
+void launch_measure(const DevCtx& c, int tile_chi, const DMeas* meas, int n_meas, int mode,
                     const uint8_t* forced, double* p0_out, cudaStream_t s) {
-  switch (c.chi_cap) {
+  switch (tile_chi) {
     case 4: measure_c<4, 32>(c, meas, n_meas, mode, forced, p0_out, s); break;
     case 8: measure_c<8, 32>(c, meas, n_meas, mode, forced, p0_out, s); break;
     case 16: measure_c<16, 64>(c, meas, n_meas, mode, forced, p0_out, s); break;

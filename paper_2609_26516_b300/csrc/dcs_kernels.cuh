@@ -93,9 +93,10 @@ struct DevCtx {
 constexpr int PLAN_HDR = 4;
 
 void launch_init(const DevCtx& c, int n_active, int multipath, uint64_t shot0, cudaStream_t s);
-void launch_compress(const DevCtx& c, const DLayer* L, const DBlock* B, const DGate1* G1,
-                     const DCond* C, double* fid_out, cudaStream_t s);
-void launch_measure(const DevCtx& c, const DMeas* meas, int n_meas, int mode,
+// tile_chi: shared-memory tile (4, 8, 16 or 32), at least every bond the launch can meet
+void launch_compress(const DevCtx& c, int tile_chi, const DLayer* L, const DBlock* B,
+                     const DGate1* G1, const DCond* C, double* fid_out, cudaStream_t s);
+void launch_measure(const DevCtx& c, int tile_chi, const DMeas* meas, int n_meas, int mode,
                     const uint8_t* forced, double* p0_out, cudaStream_t s);
 void launch_branch_split(const DevCtx& c, int q, int cbit, double eps, int M,
                          cudaStream_t s, int* launches);

@@ -227,7 +227,7 @@ extern "C" dcs_status_t dcs_compress_noalloc(int32_t n_qubits, int32_t chi_max, 
          cudaMemcpyAsync(dc, g_prog.conds.data(), sizeof(DCond) * g_prog.conds.size(),
                          cudaMemcpyHostToDevice, s) != cudaSuccess))
       return DCS_ERR_CUDA;
-    launch_compress(d, dl, db, dg, dc, f, s);
+    launch_compress(d, C, dl, db, dg, dc, f, s);
     if (cudaGetLastError() != cudaSuccess) return DCS_ERR_CUDA;
   } else {
     // an empty chunk: nothing to compress, f = 1
