@@ -55,8 +55,11 @@ typedef enum {
 #define DCS_CWORDS 8
 /* largest number of qubits (MPS sites) */
 #define DCS_MAX_QUBITS 128
-/* largest bond dimension of the fused small-chi kernels */
+/* largest bond dimension held in shared memory; above it the tiles live in a per-slot
+ * global work area */
 #define DCS_MAX_CHI_FUSED 32
+/* largest bond dimension */
+#define DCS_MAX_CHI 1024
 
 typedef enum { DCS_COND_NONE = 0, DCS_COND_XOR = 1, DCS_COND_AND = 2 } dcs_cond_op;
 
@@ -88,6 +91,12 @@ typedef struct {
 
 typedef enum { DCS_PREC_FP32 = 0 } dcs_precision;
 
+typedef enum {
+  DCS_PATH_AUTO = 0,    /* shared-memory tiles up to chi_max = 32, global tiles above */
+  DCS_PATH_SHARED = 1,  /* shared-memory tiles (chi_max <= 32) */
+  DCS_PATH_GLOBAL = 2   /* per-slot global work area, tiled GEMM contractions */
+} dcs_kernel_path;
+
 typedef struct {
   int32_t n_qubits;     /* 1 .. DCS_MAX_QUBITS */
   int32_t chi_max;      /* bond-dimension cap (the paper's chi) */
@@ -95,6 +104,7 @@ typedef struct {
   int32_t sweeps;       /* one-site sweeps per compression step (the paper's s), >= 1 */
   int32_t chunk_k;      /* maximum operations per chunk (the paper's k); 0 = one layer */
   int32_t precision;    /* dcs_precision */
+  int32_t kernel_path;  /* dcs_kernel_path */
   int32_t n_cbits;      /* classical register size m, <= 64 * DCS_CWORDS */
   int32_t n_slots;      /* shots (single-path) or branch-pool capacity (multi-path) */
   uint64_t seed;        /* key of the counter-based outcome sampler */

@@ -10,6 +10,8 @@ LIB_PATH = os.path.join(HERE, "libdcs.so")
 CWORDS = 8
 MAX_QUBITS = 128
 MAX_CHI_FUSED = 32
+MAX_CHI = 1024
+PATH_AUTO, PATH_SHARED, PATH_GLOBAL = 0, 1, 2
 
 OK, ERR_INVALID, ERR_OOM, ERR_ZERO_PROB, ERR_NUMERICAL, ERR_TIMEOUT, ERR_CUDA, ERR_UNSUPPORTED = range(8)
 STATUS_NAMES = ["OK", "INVALID", "OOM", "ZERO_PROB", "NUMERICAL", "TIMEOUT", "CUDA", "UNSUPPORTED"]
@@ -36,6 +38,7 @@ class dcs_config(ctypes.Structure):
     _fields_ = [("n_qubits", ctypes.c_int32), ("chi_max", ctypes.c_int32),
                 ("tol", ctypes.c_double), ("sweeps", ctypes.c_int32),
                 ("chunk_k", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("kernel_path", ctypes.c_int32),
                 ("n_cbits", ctypes.c_int32), ("n_slots", ctypes.c_int32),
                 ("seed", ctypes.c_uint64)]
 

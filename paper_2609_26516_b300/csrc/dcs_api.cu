@@ -26,7 +26,9 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
   size_t mps0, mps1, lc, rc, bonds, centre, ketbuf, p, F, rr, creg, flags, shot, order, count,
-      status, plan, prog, total;
+      status, plan, prog, work, total;
+  bool big;
+  size_t work_stride;
   int chi_cap, site_stride, env_stride;
   size_t mps_slot_stride, env_slot_stride;
 };
@@ -34,13 +36,27 @@ struct Layout {
 bool valid_cfg(const dcs_config* c) {
   return c && c->n_qubits >= 1 && c->n_qubits <= DCS_MAX_QUBITS && c->chi_max >= 1 &&
          c->sweeps >= 1 && c->n_slots >= 1 && c->n_cbits >= 0 && c->n_cbits <= 64 * DCS_CWORDS &&
-         c->tol >= 0.0 && c->chunk_k >= 0 && c->precision == DCS_PREC_FP32;
+         c->tol >= 0.0 && c->chunk_k >= 0 && c->precision == DCS_PREC_FP32 &&
+         c->kernel_path >= DCS_PATH_AUTO && c->kernel_path <= DCS_PATH_GLOBAL;
+}
+
+// shared-memory tiles or the global work area; false if chi_max cannot be held
+bool pick_path(const dcs_config* c, bool& big) {
+  if (c->chi_max > DCS_MAX_CHI) return false;
+  if (c->kernel_path == DCS_PATH_SHARED) {
+    big = false;
+    return fused_chi(c->chi_max) != 0;
+  }
+  big = c->kernel_path == DCS_PATH_GLOBAL || fused_chi(c->chi_max) == 0;
+  return true;
 }
 
 Layout make_layout(const dcs_config* c) {
   Layout L{};
   const size_t n = (size_t)c->n_qubits, S = (size_t)c->n_slots;
-  L.chi_cap = fused_chi(c->chi_max);
+  pick_path(c, L.big);
+  L.chi_cap = L.big ? big_chi(c->chi_max) : fused_chi(c->chi_max);
+  L.work_stride = L.big ? big_work_elems(L.chi_cap) : 0;
   L.site_stride = 2 * L.chi_cap * L.chi_cap;
   L.env_stride = 4 * L.chi_cap * L.chi_cap;
   L.mps_slot_stride = n * (size_t)L.site_stride;
@@ -69,6 +85,7 @@ Layout make_layout(const dcs_config* c) {
   L.status = take(sizeof(int32_t));
   L.plan = take((PLAN_HDR + 4 * S) * sizeof(int32_t));
   L.prog = take(kProgBytes);
+  L.work = take(S * L.work_stride * sizeof(float2));
   L.total = off;
   return L;
 }
@@ -278,7 +295,8 @@ dcs_status_t run_steps(dcs_ctx_t c, const Program& P, int max_branches,
 extern "C" {
 
 size_t dcs_arena_bytes(const dcs_config* cfg) {
-  if (!valid_cfg(cfg) || fused_chi(cfg->chi_max) == 0) return 0;
+  bool big;
+  if (!valid_cfg(cfg) || !pick_path(cfg, big)) return 0;
   return make_layout(cfg).total;
 }
 
@@ -287,7 +305,8 @@ dcs_status_t dcs_create(dcs_ctx_t* out, const dcs_config* cfg, void* dev_arena, 
   if (!out) return DCS_ERR_INVALID;
   *out = nullptr;
   if (!valid_cfg(cfg)) return DCS_ERR_INVALID;
-  if (fused_chi(cfg->chi_max) == 0) return DCS_ERR_UNSUPPORTED;
+  bool big;
+  if (!pick_path(cfg, big)) return DCS_ERR_UNSUPPORTED;
   const Layout lay = make_layout(cfg);
   if (!dev_arena || bytes < lay.total) return DCS_ERR_OOM;
   if (reinterpret_cast<uintptr_t>(dev_arena) % kAlign) return DCS_ERR_INVALID;
@@ -322,6 +341,8 @@ dcs_status_t dcs_create(dcs_ctx_t* out, const dcs_config* cfg, void* dev_arena, 
   d.count = reinterpret_cast<int32_t*>(a + lay.count);
   d.status = reinterpret_cast<int32_t*>(a + lay.status);
   d.plan = reinterpret_cast<int32_t*>(a + lay.plan);
+  d.work = lay.big ? reinterpret_cast<float2*>(a + lay.work) : nullptr;
+  d.work_stride = lay.work_stride;
   d.seed = cfg->seed;
   d.chi_max = cfg->chi_max;
   d.tol = cfg->tol;

@@ -247,18 +247,24 @@ __device__ void c4_env_update(const float2* Q, int ldq, const float2* T, float2*
   __syncthreads();
 }
 
-// ----------------------------------------------------------------------------- shared memory
-template <int C, int NT>
-struct Smem {
-  float2* E;   // 4 C^2  environment (in / out)
-  float2* S;   // 2 C^2  site tensor
-  float2* T;   // 8 C^2  T1/T2, or Theta + V
-  float2* R;   // 4 C^2  far environment, or Q
-  float2* F;   // 2 C^2  F (QR work)
+// ----------------------------------------------------------------------------- working set
+// Working set of one slot.  The small arrays always live in shared memory.  The five large
+// tiles (E 4C^2, S 2C^2, T 8C^2, R 4C^2, F 2C^2 complex) live in shared memory for tile
+// capacity C <= 32, and in the slot's global work area above that, where T2 (8C^2, the
+// mixed T of the large-tile path) and the GEMM staging tiles are added.
+struct Work {
+  float2* E;   // environment (in / out)
+  float2* S;   // site tensor
+  float2* T;   // T1/T2 (small path), T1 (large path), or Theta + V
+  float2* R;   // far environment, or Q
+  float2* F;   // F (QR work)
+  float2* T2;  // mixed T (large path)
   float2* W;   // 64     MPO tensor of the site
   float2* W2;  // 64     mirrored MPO tensor
   float2* G;   // 16     block matrix / single-qubit gate
   float2* alph;
+  float2* gA;  // GEMM staging tiles (large path)
+  float2* gB;
   double* red;
   double* sig2;
   double* dv;  // scalar broadcast
@@ -268,41 +274,139 @@ struct Smem {
   int* abnd;   // bonds of the ket [n+1]
   int* iv;     // small ints
   uint64_t* creg;
-  static constexpr size_t bytes() {
-    return sizeof(float2) * (20 * C * C + 64 + 64 + 16 + 2 * C) + sizeof(double) * (32 + 2 * C + 8) +
-           sizeof(float) * 2 * C + sizeof(int) * (2 * C + 2 * (DCS_MAX_QUBITS + 1) + 16) +
-           sizeof(uint64_t) * DCS_CWORDS + 64;
-  }
-  __device__ void carve(unsigned char* raw) {
-    uint64_t* c64 = reinterpret_cast<uint64_t*>(raw);
-    creg = c64;
-    double* d = reinterpret_cast<double*>(c64 + DCS_CWORDS);
-    red = d;
-    sig2 = red + 32;
-    dv = sig2 + 2 * C;
-    float2* f2 = reinterpret_cast<float2*>(dv + 8);
-    E = f2;
-    S = E + 4 * C * C;
-    T = S + 2 * C * C;
-    R = T + 8 * C * C;
-    F = R + 4 * C * C;
-    W = F + 2 * C * C;
-    W2 = W + 64;
-    G = W2 + 64;
-    alph = G + 16;
-    tau = reinterpret_cast<float*>(alph + 2 * C);
-    perm = reinterpret_cast<int*>(tau + 2 * C);
-    bnd = perm + 2 * C;
-    abnd = bnd + DCS_MAX_QUBITS + 1;
-    iv = abnd + DCS_MAX_QUBITS + 1;
-  }
+  int C;       // tile capacity
 };
+
+constexpr int GBM = 64, GBN = 64, GBK = 16;  // CTA GEMM tile
+
+__host__ __device__ inline size_t work_small_bytes(int C, bool big) {
+  return sizeof(float2) * (64 + 64 + 16 + 2 * C + (big ? (GBM + GBN) * GBK : 0)) +
+         sizeof(double) * (32 + 2 * C + 8) + sizeof(float) * 2 * C +
+         sizeof(int) * (2 * C + 2 * (DCS_MAX_QUBITS + 1) + 16) + sizeof(uint64_t) * DCS_CWORDS + 64;
+}
+__host__ __device__ inline size_t work_tile_elems(int C, bool big) {
+  return (size_t)(big ? 28 : 20) * C * C;
+}
+
+__device__ void carve(Work& w, unsigned char* raw, int C, float2* big_area) {
+  w.C = C;
+  uint64_t* c64 = reinterpret_cast<uint64_t*>(raw);
+  w.creg = c64;
+  double* d = reinterpret_cast<double*>(c64 + DCS_CWORDS);
+  w.red = d;
+  w.sig2 = w.red + 32;
+  w.dv = w.sig2 + 2 * C;
+  float2* f2 = reinterpret_cast<float2*>(w.dv + 8);
+  w.W = f2;
+  w.W2 = w.W + 64;
+  w.G = w.W2 + 64;
+  w.alph = w.G + 16;
+  float2* tiles = w.alph + 2 * C;
+  if (big_area) {
+    w.gA = tiles;
+    w.gB = w.gA + GBM * GBK;
+    tiles = w.gB + GBK * GBN;
+  } else {
+    w.gA = w.gB = nullptr;
+  }
+  float2* t = big_area ? big_area : tiles;
+  w.E = t;
+  w.S = w.E + 4 * C * C;
+  w.T = w.S + 2 * C * C;
+  w.R = w.T + 8 * C * C;
+  w.F = w.R + 4 * C * C;
+  w.T2 = big_area ? w.F + 2 * C * C : nullptr;
+  float2* after = big_area ? tiles : w.F + 2 * C * C;
+  w.tau = reinterpret_cast<float*>(after);
+  w.perm = reinterpret_cast<int*>(w.tau + 2 * C);
+  w.bnd = w.perm + 2 * C;
+  w.abnd = w.bnd + DCS_MAX_QUBITS + 1;
+  w.iv = w.abnd + DCS_MAX_QUBITS + 1;
+}
+
+// ----------------------------------------------------------------------------- CTA GEMM
+// C[m, n] = sum_k opA(m, k) opB(k, n) with opA(m, k) = A[m sam + k sak] (conjugated if
+// conjA), opB(k, n) = B[k sbk + n sbn] (conjugated if conjB), C[m scm + n scn].  FP32 SIMT
+// with 64 x 64 x 16 shared-memory tiles; each thread owns an 8-element micro tile.
+template <int NT>
+__device__ void cta_cgemm(int M, int N, int K, const float2* A, int sam, int sak, bool conjA,
+                          const float2* B, int sbk, int sbn, bool conjB, float2* Cm, int scm,
+                          int scn, float2* sA, float2* sB) {
+  static_assert((GBM * GBN) % NT == 0, "tile / threads");
+  constexpr int PER = GBM * GBN / NT;  // outputs per thread
+  const int tid = threadIdx.x;
+  for (int m0 = 0; m0 < M; m0 += GBM)
+    for (int n0 = 0; n0 < N; n0 += GBN) {
+      float2 acc[PER];
+#pragma unroll
+      for (int i = 0; i < PER; ++i) acc[i] = cz();
+      for (int k0 = 0; k0 < K; k0 += GBK) {
+        // stage A tile (GBM x GBK) as sA[m][k] and B tile (GBK x GBN) as sB[k][n]
+        for (int idx = tid; idx < GBM * GBK; idx += NT) {
+          int mm, kk;
+          if (sak == 1) {
+            mm = idx / GBK;
+            kk = idx % GBK;
+          } else {
+            kk = idx / GBM;
+            mm = idx % GBM;
+          }
+          const int gm = m0 + mm, gk = k0 + kk;
+          float2 v = cz();
+          if (gm < M && gk < K) {
+            v = A[(size_t)gm * sam + (size_t)gk * sak];
+            if (conjA) v.y = -v.y;
+          }
+          sA[mm * GBK + kk] = v;
+        }
+        for (int idx = tid; idx < GBK * GBN; idx += NT) {
+          int kk, nn;
+          if (sbn == 1) {
+            kk = idx / GBN;
+            nn = idx % GBN;
+          } else {
+            nn = idx / GBK;
+            kk = idx % GBK;
+          }
+          const int gk = k0 + kk, gn = n0 + nn;
+          float2 v = cz();
+          if (gk < K && gn < N) {
+            v = B[(size_t)gk * sbk + (size_t)gn * sbn];
+            if (conjB) v.y = -v.y;
+          }
+          sB[kk * GBN + nn] = v;
+        }
+        __syncthreads();
+        // thread tid owns rows (tid / (GBN / 2)) * ... : PER outputs in one row, PER columns
+        const int row = tid / (GBN / PER);
+        const int col0 = (tid % (GBN / PER)) * PER;
+#pragma unroll 4
+        for (int kk = 0; kk < GBK; ++kk) {
+          const float2 a = sA[row * GBK + kk];
+#pragma unroll
+          for (int i = 0; i < PER; ++i) cfma(acc[i], a, sB[kk * GBN + col0 + i]);
+        }
+        __syncthreads();
+      }
+      const int row = tid / (GBN / PER);
+      const int col0 = (tid % (GBN / PER)) * PER;
+      const int gm = m0 + row;
+      if (gm < M) {
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+          const int gn = n0 + col0 + i;
+          if (gn < N) Cm[(size_t)gm * scm + (size_t)gn * scn] = acc[i];
+        }
+      }
+    }
+  __syncthreads();
+}
 
 // ----------------------------------------------------------------------------- gauge moves
 // Move the orthogonality centre of MPS buffer `buf` of `slot` from j to j+1:
 // T_j = Q R (as (2 b_j) x b_{j+1}), T_j := Q, T_{j+1} := R T_{j+1}.
-template <int C, int NT>
-__device__ void hop_right(const DevCtx& c, Smem<C, NT>& sm, int buf, int slot, int j) {
+template <int NT>
+__device__ void hop_right(const DevCtx& c, Work& sm, int buf, int slot, int j) {
   int* b = sm.bnd;
   const int bl = b[j], br = b[j + 1], bn = b[j + 2];
   const int m = 2 * bl;
@@ -319,15 +423,20 @@ __device__ void hop_right(const DevCtx& c, Smem<C, NT>& sm, int buf, int slot, i
     dst[idx] = sm.R[row + k * m];
   }
   const float2* nx = site_ptr(c, buf, slot, j + 1);
-  gcopy<NT>(sm.S, nx, br * 2 * bn);
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < r * 2 * bn; idx += NT) {
-    const int k = idx / (2 * bn), col = idx % (2 * bn);
-    float2 acc = cz();
-    for (int x = 0; x < br; ++x) cfma(acc, sm.E[k * br + x], sm.S[x * 2 * bn + col]);
-    sm.T[idx] = acc;
+  if (sm.gA) {  // large tiles: R (r x br) times T_{j+1} (br x 2 bn) as a tiled GEMM
+    cta_cgemm<NT>(r, 2 * bn, br, sm.E, br, 1, false, nx, 2 * bn, 1, false, sm.T, 2 * bn, 1,
+                  sm.gA, sm.gB);
+  } else {
+    gcopy<NT>(sm.S, nx, br * 2 * bn);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < r * 2 * bn; idx += NT) {
+      const int k = idx / (2 * bn), col = idx % (2 * bn);
+      float2 acc = cz();
+      for (int x = 0; x < br; ++x) cfma(acc, sm.E[k * br + x], sm.S[x * 2 * bn + col]);
+      sm.T[idx] = acc;
+    }
+    __syncthreads();
   }
-  __syncthreads();
   gcopy<NT>(site_ptr(c, buf, slot, j + 1), sm.T, r * 2 * bn);
   __syncthreads();
   if (threadIdx.x == 0) b[j + 1] = r;
@@ -336,8 +445,8 @@ __device__ void hop_right(const DevCtx& c, Smem<C, NT>& sm, int buf, int slot, i
 
 // Move the centre from j to j-1 (mirrored hop): T_j[a][t][x] read as (x t) x a = Q' R',
 // T_j[k][t][x] := Q'[(x t), k], T_{j-1}[a'][s][k] := sum_a T_{j-1}[a'][s][a] R'[k][a].
-template <int C, int NT>
-__device__ void hop_left(const DevCtx& c, Smem<C, NT>& sm, int buf, int slot, int j) {
+template <int NT>
+__device__ void hop_left(const DevCtx& c, Work& sm, int buf, int slot, int j) {
   int* b = sm.bnd;
   const int bl = b[j], br = b[j + 1], bp = b[j - 1];
   const int m = 2 * br;
@@ -353,30 +462,36 @@ __device__ void hop_left(const DevCtx& c, Smem<C, NT>& sm, int buf, int slot, in
     const int x = idx % br, t = (idx / br) & 1, k = idx / (2 * br);
     dst[idx] = sm.R[(x * 2 + t) + k * m];
   }
-  gcopy<NT>(sm.S, site_ptr(c, buf, slot, j - 1), bp * 2 * bl);
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < bp * 2 * r; idx += NT) {
-    const int k = idx % r, row = idx / r;
-    float2 acc = cz();
-    for (int a = 0; a < bl; ++a) cfma(acc, sm.S[row * bl + a], sm.E[k * bl + a]);
-    sm.T[idx] = acc;
+  if (sm.gA) {  // large tiles: T_{j-1} ((2 bp) x bl) times R'^T (bl x r)
+    __syncthreads();
+    cta_cgemm<NT>(2 * bp, r, bl, site_ptr(c, buf, slot, j - 1), bl, 1, false, sm.E, 1, bl, false,
+                  sm.T, r, 1, sm.gA, sm.gB);
+  } else {
+    gcopy<NT>(sm.S, site_ptr(c, buf, slot, j - 1), bp * 2 * bl);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < bp * 2 * r; idx += NT) {
+      const int k = idx % r, row = idx / r;
+      float2 acc = cz();
+      for (int a = 0; a < bl; ++a) cfma(acc, sm.S[row * bl + a], sm.E[k * bl + a]);
+      sm.T[idx] = acc;
+    }
+    __syncthreads();
   }
-  __syncthreads();
   gcopy<NT>(site_ptr(c, buf, slot, j - 1), sm.T, bp * 2 * r);
   __syncthreads();
   if (threadIdx.x == 0) b[j] = r;
   __syncthreads();
 }
 
-template <int C, int NT>
-__device__ void move_centre(const DevCtx& c, Smem<C, NT>& sm, int buf, int slot, int& centre,
+template <int NT>
+__device__ void move_centre(const DevCtx& c, Work& sm, int buf, int slot, int& centre,
                             int target) {
   while (centre < target) {
-    hop_right<C, NT>(c, sm, buf, slot, centre);
+    hop_right<NT>(c, sm, buf, slot, centre);
     ++centre;
   }
   while (centre > target) {
-    hop_left<C, NT>(c, sm, buf, slot, centre);
+    hop_left<NT>(c, sm, buf, slot, centre);
     --centre;
   }
 }
@@ -385,11 +500,12 @@ __device__ void move_centre(const DevCtx& c, Smem<C, NT>& sm, int buf, int slot,
 // one warp per CTA for the small tiles: at most 64 registers so 32 CTAs fit an SM
 template <int NT>
 struct MinBlocks {
-  static constexpr int value = NT == 32 ? 32 : (NT == 64 ? 16 : 4);
+  static constexpr int value = NT == 32 ? 32 : (NT == 64 ? 16 : (NT == 128 ? 4 : 1));
 };
 
-template <int C, int NT>
-__global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_compress(DevCtx c, const DLayer* __restrict__ L,
+template <int NT>
+__global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_compress(DevCtx c, int C,
+                                                 const DLayer* __restrict__ L,
                                                  const DBlock* __restrict__ BK,
                                                  const DGate1* __restrict__ G1,
                                                  const DCond* __restrict__ CD, double* fid_out) {
@@ -397,8 +513,8 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_compress(DevCtx c,
   if (pos >= *c.count) return;
   const int slot = c.order[pos];
   extern __shared__ __align__(16) unsigned char smraw[];
-  Smem<C, NT> sm;
-  sm.carve(smraw);
+  Work sm;
+  carve(sm, smraw, C, nullptr);
   const int n = c.n;
   if (threadIdx.x < DCS_CWORDS) sm.creg[threadIdx.x] = c.creg[(size_t)slot * DCS_CWORDS + threadIdx.x];
   __syncthreads();
@@ -449,7 +565,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_compress(DevCtx c,
   for (int ib = 0; ib < L->n_blocks; ++ib) {
     const DBlock& blk = BK[L->blk_off + ib];
     const int q = blk.q;
-    move_centre<C, NT>(c, sm, bb, slot, centre, q + 1);
+    move_centre<NT>(c, sm, bb, slot, centre, q + 1);
     const int b0 = sm.bnd[q], b1 = sm.bnd[q + 1], b2 = sm.bnd[q + 2];
     gcopy<NT>(sm.S, site_ptr(c, bb, slot, q), b0 * 2 * b1);
     gcopy<NT>(sm.F, site_ptr(c, bb, slot, q + 1), b1 * 2 * b2);
@@ -513,7 +629,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_compress(DevCtx c,
     centre = q;
     __syncthreads();
   }
-  move_centre<C, NT>(c, sm, bb, slot, centre, 0);
+  move_centre<NT>(c, sm, bb, slot, centre, 0);
   // ---- right environments of the guess: R_j for j = n-1 .. 1 (mirrored env updates)
   int* bt = sm.bnd;
   int* at = sm.abnd;
@@ -652,14 +768,307 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_compress(DevCtx c,
   }
 }
 
+// ----------------------------------------------------------------------------- large tiles
+constexpr int BIG_NT = 512;
+
+// T2[b][s][e][x] = sum_{d,t} T1(b, d, t, x) W(d, s, t, e) with T1 at
+// b*ib + d*id + t*it + x*ix and T2 natural (b-stride 2 ne nx); mirrored: the coefficient is
+// W[e][s][t][d] (the MPO read right to left).
+template <int NT>
+__device__ void mix_big(const float2* T1, int ib, int id, int it, int ix, float2* T2, const float2* W,
+                        int nb, int nd, int ne, int nx, bool mirrored) {
+  for (int idx = threadIdx.x; idx < nb * nx; idx += NT) {
+    const int x = idx % nx, b = idx / nx;
+    float2 v[8];
+#pragma unroll
+    for (int d = 0; d < 4; ++d)
+#pragma unroll
+      for (int t = 0; t < 2; ++t)
+        v[d * 2 + t] = d < nd ? T1[(size_t)b * ib + d * id + t * it + (size_t)x * ix] : cz();
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        if (e >= ne) continue;
+        float2 acc = cz();
+#pragma unroll
+        for (int d = 0; d < 4; ++d)
+#pragma unroll
+          for (int t = 0; t < 2; ++t) {
+            if (d >= nd) continue;
+            const float2 w = mirrored ? W[((e * 2 + s) * 2 + t) * nd + d] : W[((d * 2 + s) * 2 + t) * ne + e];
+            cfma(acc, v[d * 2 + t], w);
+          }
+        T2[(size_t)b * 2 * ne * nx + (s * ne + e) * nx + x] = acc;
+      }
+  }
+  __syncthreads();
+}
+
+// The compression step of k_compress with the large tiles in the slot's global work area
+// and every contraction a tiled CTA GEMM on natural layouts:
+//   T1[(b d),(t x)] = E[(b d), a] A[a, (t x)],  T2 = mix(T1, W),
+//   F[(b s), c] = T2[(b s), (e x)] R[c, (e x)]^T,  E'[c, (e x)] = Q^H[c, (b s)] T2[(b s), (e x)];
+// right-to-left steps read the same products on the mirrored chain.
+template <int NT>
+__global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const DLayer* __restrict__ L,
+                                                        const DBlock* __restrict__ BK,
+                                                        const DGate1* __restrict__ G1,
+                                                        const DCond* __restrict__ CD, double* fid_out) {
+  const int pos = blockIdx.x;
+  if (pos >= *c.count) return;
+  const int slot = c.order[pos];
+  extern __shared__ __align__(16) unsigned char smraw[];
+  Work sm;
+  carve(sm, smraw, C, c.work + (size_t)slot * c.work_stride);
+  const int n = c.n;
+  if (threadIdx.x < DCS_CWORDS) sm.creg[threadIdx.x] = c.creg[(size_t)slot * DCS_CWORDS + threadIdx.x];
+  __syncthreads();
+  if (!L->uncond) {
+    if (threadIdx.x == 0) {
+      int any = 0;
+      for (int i = 0; i < L->n_conds && !any; ++i) any = cond_holds(CD[L->cond_off + i], sm.creg);
+      sm.iv[4] = any;
+    }
+    __syncthreads();
+    if (!sm.iv[4]) {
+      if (threadIdx.x == 0 && fid_out) fid_out[slot] = 1.0;
+      return;
+    }
+  }
+  const int kb = c.ketbuf[slot], bb = 1 - kb;
+  const int* kbonds = bonds_ptr(c, slot, kb);
+  for (int i = threadIdx.x; i <= n; i += NT) {
+    sm.abnd[i] = kbonds[i];
+    sm.bnd[i] = kbonds[i];
+  }
+  __syncthreads();
+  int centre = c.centre[slot];
+  int* bt = sm.bnd;
+  int* at = sm.abnd;
+  // ---- initial guess: the chunk applied block by block to a copy of the ket
+  for (int j = 0; j < n; ++j)
+    gcopy<NT>(site_ptr(c, bb, slot, j), site_ptr(c, kb, slot, j), at[j] * 2 * at[j + 1]);
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    if (L->site[j].kind != 1) continue;
+    if (threadIdx.x == 0) prod1q(G1, L->site[j].g_off, L->site[j].g_n, sm.creg, sm.G);
+    __syncthreads();
+    float2* p = site_ptr(c, bb, slot, j);
+    const int bl = bt[j], br = bt[j + 1];
+    for (int idx = threadIdx.x; idx < bl * br; idx += NT) {
+      const int a = idx / br, x = idx % br;
+      const float2 v0 = p[(a * 2 + 0) * br + x], v1 = p[(a * 2 + 1) * br + x];
+      float2 o0 = cz(), o1 = cz();
+      cfma(o0, sm.G[0], v0);
+      cfma(o0, sm.G[1], v1);
+      cfma(o1, sm.G[2], v0);
+      cfma(o1, sm.G[3], v1);
+      p[(a * 2 + 0) * br + x] = o0;
+      p[(a * 2 + 1) * br + x] = o1;
+    }
+    __syncthreads();
+  }
+  for (int ib = 0; ib < L->n_blocks; ++ib) {
+    const DBlock& blk = BK[L->blk_off + ib];
+    const int q = blk.q;
+    move_centre<NT>(c, sm, bb, slot, centre, q + 1);
+    const int b0 = bt[q], b1 = bt[q + 1], b2 = bt[q + 2];
+    if (threadIdx.x == 0) build_block(blk, G1, sm.creg, sm.G);
+    const int m = 2 * b0, nn = 2 * b2;
+    float2* X = sm.T;           // m x nn, column-major (fits in T + T2: 4 C^2)
+    float2* V = sm.T2;          // nn x nn
+    // P[(a t), (v b)] = B_q[(a t), x] B_{q+1}[x, (v b)]
+    cta_cgemm<NT>(m, nn, b1, site_ptr(c, bb, slot, q), b1, 1, false, site_ptr(c, bb, slot, q + 1),
+                  nn, 1, false, X, 1, m, sm.gA, sm.gB);
+    for (int idx = threadIdx.x; idx < b0 * b2; idx += NT) {
+      const int a = idx / b2, bcol = idx % b2;
+      float2 in[4], out[4];
+#pragma unroll
+      for (int t = 0; t < 2; ++t)
+#pragma unroll
+        for (int v = 0; v < 2; ++v) in[t * 2 + v] = X[(a * 2 + t) + (size_t)(v * b2 + bcol) * m];
+#pragma unroll
+      for (int o = 0; o < 4; ++o) {
+        float2 acc = cz();
+#pragma unroll
+        for (int i = 0; i < 4; ++i) cfma(acc, sm.G[o * 4 + i], in[i]);
+        out[o] = acc;
+      }
+#pragma unroll
+      for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int u = 0; u < 2; ++u) X[(a * 2 + s) + (size_t)(u * b2 + bcol) * m] = out[s * 2 + u];
+    }
+    __syncthreads();
+    cta_jacobi_svd<NT>(X, m, nn, m, V, nn, sm.sig2, sm.perm, &sm.iv[5], sm.red);
+    if (threadIdx.x == 0) {
+      const int kk = trunc_rank(sm.sig2, sm.perm, nn, c.chi_max, c.tol);
+      double w = 0.0;
+      for (int i = 0; i < kk; ++i) w += sm.sig2[sm.perm[i]];
+      sm.iv[6] = kk;
+      sm.dv[0] = w;
+    }
+    __syncthreads();
+    const int kk = sm.iv[6];
+    const float inv = (float)(1.0 / sqrt(sm.dv[0]));
+    float2* pq = site_ptr(c, bb, slot, q);
+    for (int idx = threadIdx.x; idx < m * kk; idx += NT) {
+      const int row = idx / kk, k2 = idx % kk;
+      pq[idx] = cscale(X[row + (size_t)sm.perm[k2] * m], inv);
+    }
+    float2* pq1 = site_ptr(c, bb, slot, q + 1);
+    for (int idx = threadIdx.x; idx < kk * nn; idx += NT) {
+      const int k2 = idx / nn, col = idx % nn;
+      pq1[idx] = cconj(V[col + (size_t)sm.perm[k2] * nn]);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) bt[q + 1] = kk;
+    centre = q;
+    __syncthreads();
+  }
+  move_centre<NT>(c, sm, bb, slot, centre, 0);
+  // ---- right environments of the guess (mirrored env updates with B given)
+  if (threadIdx.x == 0) sm.E[0] = make_float2(1.f, 0.f);
+  __syncthreads();
+  for (int j = n - 1; j >= 1; --j) {
+    if (threadIdx.x == 0) build_W(j, L, BK, G1, sm.creg, sm.W, &sm.iv[0], &sm.iv[1]);
+    __syncthreads();
+    const int dl = sm.iv[0], dr = sm.iv[1];
+    const float2* A = site_ptr(c, kb, slot, j);
+    const int al = at[j], ar = at[j + 1];
+    const float2* Bj = site_ptr(c, bb, slot, j);
+    const int bl = bt[j], br = bt[j + 1];
+    const int ldq = 2 * br;
+    for (int idx = threadIdx.x; idx < bl * 2 * br; idx += NT) {  // Q'[(c s), b] = B[b][s][c]
+      const int x = idx % br, s = (idx / br) & 1, bq = idx / (2 * br);
+      sm.R[(x * 2 + s) + (size_t)bq * ldq] = Bj[idx];
+    }
+    // T1[(c e), (a t)] = sum_x E[(c e), x] A[(a t), x]
+    cta_cgemm<NT>(br * dr, 2 * al, ar, sm.E, ar, 1, false, A, 1, ar, false, sm.T, 2 * al, 1,
+                  sm.gA, sm.gB);
+    // T2[c][s][d][a] from T1[c][e][a][t]: fibre (c, a), incoming MPO index e, outgoing d
+    mix_big<NT>(sm.T, dr * 2 * al, 2 * al, 1, 2, sm.T2, sm.W, br, dr, dl, al, true);
+    // R_j[b, (d a)] = sum_{(c s)} conj(Q'[(c s), b]) T2[(c s), (d a)]
+    cta_cgemm<NT>(bl, dl * al, 2 * br, sm.R, ldq, 1, true, sm.T2, dl * al, 1, false, sm.E, dl * al,
+                  1, sm.gA, sm.gB);
+    gcopy<NT>(env_ptr(c.Rc, c, slot, j), sm.E, bl * dl * al);
+    __syncthreads();
+  }
+  // ---- one-site sweeps
+  double fval = 0.0;
+  for (int sw = 0; sw < c.sweeps; ++sw) {
+    if (threadIdx.x == 0) sm.E[0] = make_float2(1.f, 0.f);
+    __syncthreads();
+    if ((sw & 1) == 0) {  // left to right
+      for (int j = 0; j < n; ++j) {
+        if (threadIdx.x == 0) build_W(j, L, BK, G1, sm.creg, sm.W, &sm.iv[0], &sm.iv[1]);
+        __syncthreads();
+        const int dl = sm.iv[0], dr = sm.iv[1];
+        const int nb = bt[j], nc = bt[j + 1], na = at[j], nx = at[j + 1];
+        const float2* A = site_ptr(c, kb, slot, j);
+        const float2* Rn = sm.R;
+        if (j < n - 1) Rn = env_ptr(c.Rc, c, slot, j + 1);
+        else if (threadIdx.x == 0) sm.R[0] = make_float2(1.f, 0.f);
+        __syncthreads();
+        cta_cgemm<NT>(nb * dl, 2 * nx, na, sm.E, na, 1, false, A, 2 * nx, 1, false, sm.T, 2 * nx, 1,
+                      sm.gA, sm.gB);
+        mix_big<NT>(sm.T, dl * 2 * nx, 2 * nx, nx, 1, sm.T2, sm.W, nb, dl, dr, nx, false);
+        const int m = 2 * nb;
+        cta_cgemm<NT>(m, nc, dr * nx, sm.T2, dr * nx, 1, false, Rn, 1, dr * nx, false, sm.F, 1, m,
+                      sm.gA, sm.gB);
+        float2* dst = site_ptr(c, bb, slot, j);
+        if (j < n - 1) {
+          const int r = cta_qr<NT>(sm.F, m, nc, m, sm.R, m, nullptr, 0, sm.tau, sm.alph, sm.red);
+          for (int idx = threadIdx.x; idx < m * r; idx += NT) {
+            const int row = idx / r, k2 = idx % r;
+            dst[idx] = sm.R[row + (size_t)k2 * m];
+          }
+          cta_cgemm<NT>(r, dr * nx, m, sm.R, m, 1, true, sm.T2, dr * nx, 1, false, sm.E, dr * nx, 1,
+                        sm.gA, sm.gB);
+          gcopy<NT>(env_ptr(c.Lc, c, slot, j + 1), sm.E, r * dr * nx);
+          __syncthreads();
+          if (threadIdx.x == 0) bt[j + 1] = r;
+          __syncthreads();
+        } else {
+          double s2 = 0.0;
+          for (int i = threadIdx.x; i < m; i += NT) s2 += cabs2d(sm.F[i]);
+          s2 = block_sum<NT>(s2, sm.red);
+          const float inv = (float)(1.0 / sqrt(s2));
+          for (int i = threadIdx.x; i < m; i += NT) dst[i] = cscale(sm.F[i], inv);
+          fval = s2;
+          __syncthreads();
+        }
+      }
+      centre = n - 1;
+    } else {  // right to left, mirrored
+      for (int j = n - 1; j >= 0; --j) {
+        if (threadIdx.x == 0) build_W(j, L, BK, G1, sm.creg, sm.W, &sm.iv[0], &sm.iv[1]);
+        __syncthreads();
+        const int dl = sm.iv[0], dr = sm.iv[1];
+        const int nb = bt[j + 1], nc = bt[j], na = at[j + 1], nx = at[j];
+        const float2* A = site_ptr(c, kb, slot, j);
+        const float2* Ln = sm.R;
+        if (j > 0) Ln = env_ptr(c.Lc, c, slot, j);
+        else if (threadIdx.x == 0) sm.R[0] = make_float2(1.f, 0.f);
+        __syncthreads();
+        // T1[(c e), (a t)] = sum_x E[(c e), x] A[(a t), x]
+        cta_cgemm<NT>(nb * dr, 2 * nx, na, sm.E, na, 1, false, A, 1, na, false, sm.T, 2 * nx, 1,
+                      sm.gA, sm.gB);
+        mix_big<NT>(sm.T, dr * 2 * nx, 2 * nx, 1, 2, sm.T2, sm.W, nb, dr, dl, nx, true);
+        const int m = 2 * nb;
+        // F'[(c s), b] = sum_{(d a)} T2[(c s), (d a)] L[b, (d a)]
+        cta_cgemm<NT>(m, nc, dl * nx, sm.T2, dl * nx, 1, false, Ln, 1, dl * nx, false, sm.F, 1, m,
+                      sm.gA, sm.gB);
+        float2* dst = site_ptr(c, bb, slot, j);
+        if (j > 0) {
+          const int r = cta_qr<NT>(sm.F, m, nc, m, sm.R, m, nullptr, 0, sm.tau, sm.alph, sm.red);
+          for (int idx = threadIdx.x; idx < r * 2 * nb; idx += NT) {
+            const int cc = idx % nb, s = (idx / nb) & 1, k2 = idx / (2 * nb);
+            dst[idx] = sm.R[(cc * 2 + s) + (size_t)k2 * m];
+          }
+          cta_cgemm<NT>(r, dl * nx, m, sm.R, m, 1, true, sm.T2, dl * nx, 1, false, sm.E, dl * nx, 1,
+                        sm.gA, sm.gB);
+          gcopy<NT>(env_ptr(c.Rc, c, slot, j), sm.E, r * dl * nx);
+          __syncthreads();
+          if (threadIdx.x == 0) bt[j] = r;
+          __syncthreads();
+        } else {
+          double s2 = 0.0;
+          for (int i = threadIdx.x; i < m; i += NT) s2 += cabs2d(sm.F[i]);
+          s2 = block_sum<NT>(s2, sm.red);
+          const float inv = (float)(1.0 / sqrt(s2));
+          for (int idx = threadIdx.x; idx < m; idx += NT) {
+            const int cc = idx % nb, s = idx / nb;
+            dst[idx] = cscale(sm.F[cc * 2 + s], inv);
+          }
+          fval = s2;
+          __syncthreads();
+        }
+      }
+      centre = 0;
+    }
+  }
+  int* obonds = bonds_ptr(c, slot, bb);
+  for (int i = threadIdx.x; i <= n; i += NT) obonds[i] = bt[i];
+  if (threadIdx.x == 0) {
+    c.centre[slot] = centre;
+    c.ketbuf[slot] = bb;
+    if (!(fval == fval) || fval > 1e300) c.flags[slot] |= DCS_FLAG_NUMERICAL;
+    c.F[slot] *= fval;
+    if (fid_out) fid_out[slot] = fval;
+  }
+}
+
 // ----------------------------------------------------------------------------- measurement
 // mode MEAS_SAMPLE: u = Philox(seed, shot, ordinal), m = 0 iff u < p_0 (Alg. 1 Measure);
 // MEAS_FORCED: m = forced[slot]; MEAS_PROB: only p_0 (MeasureProb) and the slice weights.
 // p_m = <psi|P_m|psi> is evaluated at the orthogonality centre moved to q; Collapse zeroes
 // the other slice of the centre tensor and rescales by 1/sqrt(r_m) (Sec. "Mid-circuit
 // measurements").
-template <int C, int NT>
-__global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_measure(DevCtx c, const DMeas* __restrict__ meas,
+template <int NT, bool BIG>
+__global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_measure(DevCtx c, int C,
+                                                const DMeas* __restrict__ meas,
                                                 int n_meas, int mode,
                                                 const uint8_t* __restrict__ forced,
                                                 double* p0_out) {
@@ -667,8 +1076,8 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_measure(DevCtx c, 
   if (pos >= *c.count) return;
   const int slot = c.order[pos];
   extern __shared__ __align__(16) unsigned char smraw[];
-  Smem<C, NT> sm;
-  sm.carve(smraw);
+  Work sm;
+  carve(sm, smraw, C, BIG ? c.work + (size_t)slot * c.work_stride : nullptr);
   const int n = c.n;
   const int kb = c.ketbuf[slot];
   int* kbonds = bonds_ptr(c, slot, kb);
@@ -677,7 +1086,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_measure(DevCtx c, 
   int centre = c.centre[slot];
   for (int im = 0; im < n_meas; ++im) {
     const int q = meas[im].q;
-    move_centre<C, NT>(c, sm, kb, slot, centre, q);
+    move_centre<NT>(c, sm, kb, slot, centre, q);
     const int bl = sm.bnd[q], br = sm.bnd[q + 1];
     float2* A = site_ptr(c, kb, slot, q);
     double s0 = 0.0, s1 = 0.0;
@@ -998,28 +1407,31 @@ int fused_chi(int chi_max) {
   return 0;
 }
 
-template <int C, int NT>
-static void compress_c(const DevCtx& c, const DLayer* L, const DBlock* B, const DGate1* G1,
+int big_chi(int chi_max) { return (chi_max + 7) / 8 * 8; }
+
+size_t big_work_elems(int chi_cap) { return work_tile_elems(chi_cap, true); }
+
+template <int NT>
+static void compress_c(const DevCtx& c, int C, const DLayer* L, const DBlock* B, const DGate1* G1,
                        const DCond* CD, double* fid_out, cudaStream_t s) {
-  const size_t sm = Smem<C, NT>::bytes();
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_compress<C, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    attr = true;
-  }
-  k_compress<C, NT><<<c.n_slots, NT, sm, s>>>(c, L, B, G1, CD, fid_out);
+  const size_t sm = work_small_bytes(C, false) + sizeof(float2) * work_tile_elems(C, false);
+  cudaFuncSetAttribute(k_compress<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_compress<NT><<<c.n_slots, NT, sm, s>>>(c, C, L, B, G1, CD, fid_out);
 }
 
-template <int C, int NT>
-static void measure_c(const DevCtx& c, const DMeas* meas, int n_meas, int mode,
+static void compress_big(const DevCtx& c, const DLayer* L, const DBlock* B, const DGate1* G1,
+                         const DCond* CD, double* fid_out, cudaStream_t s) {
+  const size_t sm = work_small_bytes(c.chi_cap, true);
+  cudaFuncSetAttribute(k_compress_big<BIG_NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_compress_big<BIG_NT><<<c.n_slots, BIG_NT, sm, s>>>(c, c.chi_cap, L, B, G1, CD, fid_out);
+}
+
+template <int NT, bool BIG>
+static void measure_c(const DevCtx& c, int C, const DMeas* meas, int n_meas, int mode,
                       const uint8_t* forced, double* p0_out, cudaStream_t s) {
-  const size_t sm = Smem<C, NT>::bytes();
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_measure<C, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    attr = true;
-  }
-  k_measure<C, NT><<<c.n_slots, NT, sm, s>>>(c, meas, n_meas, mode, forced, p0_out);
+  const size_t sm = work_small_bytes(C, BIG) + (BIG ? 0 : sizeof(float2) * work_tile_elems(C, false));
+  cudaFuncSetAttribute(k_measure<NT, BIG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_measure<NT, BIG><<<c.n_slots, NT, sm, s>>>(c, C, meas, n_meas, mode, forced, p0_out);
 }
 
 void launch_init(const DevCtx& c, int n_active, int multipath, uint64_t shot0, cudaStream_t s) {
@@ -1028,22 +1440,30 @@ void launch_init(const DevCtx& c, int n_active, int multipath, uint64_t shot0, c
 
 void launch_compress(const DevCtx& c, int tile_chi, const DLayer* L, const DBlock* B,
                      const DGate1* G1, const DCond* CD, double* fid_out, cudaStream_t s) {
+  if (c.work) {
+    compress_big(c, L, B, G1, CD, fid_out, s);
+    return;
+  }
   switch (tile_chi) {
-    case 4: compress_c<4, 32>(c, L, B, G1, CD, fid_out, s); break;
-    case 8: compress_c<8, 32>(c, L, B, G1, CD, fid_out, s); break;
-    case 16: compress_c<16, 64>(c, L, B, G1, CD, fid_out, s); break;
-    case 32: compress_c<32, 128>(c, L, B, G1, CD, fid_out, s); break;
+    case 4: compress_c<32>(c, 4, L, B, G1, CD, fid_out, s); break;
+    case 8: compress_c<32>(c, 8, L, B, G1, CD, fid_out, s); break;
+    case 16: compress_c<64>(c, 16, L, B, G1, CD, fid_out, s); break;
+    case 32: compress_c<128>(c, 32, L, B, G1, CD, fid_out, s); break;
     default: break;
   }
 }
 
 void launch_measure(const DevCtx& c, int tile_chi, const DMeas* meas, int n_meas, int mode,
                     const uint8_t* forced, double* p0_out, cudaStream_t s) {
+  if (c.work) {
+    measure_c<BIG_NT, true>(c, c.chi_cap, meas, n_meas, mode, forced, p0_out, s);
+    return;
+  }
   switch (tile_chi) {
-    case 4: measure_c<4, 32>(c, meas, n_meas, mode, forced, p0_out, s); break;
-    case 8: measure_c<8, 32>(c, meas, n_meas, mode, forced, p0_out, s); break;
-    case 16: measure_c<16, 64>(c, meas, n_meas, mode, forced, p0_out, s); break;
-    case 32: measure_c<32, 128>(c, meas, n_meas, mode, forced, p0_out, s); break;
+    case 4: measure_c<32, false>(c, 4, meas, n_meas, mode, forced, p0_out, s); break;
+    case 8: measure_c<32, false>(c, 8, meas, n_meas, mode, forced, p0_out, s); break;
+    case 16: measure_c<64, false>(c, 16, meas, n_meas, mode, forced, p0_out, s); break;
+    case 32: measure_c<128, false>(c, 32, meas, n_meas, mode, forced, p0_out, s); break;
     default: break;
   }
 }

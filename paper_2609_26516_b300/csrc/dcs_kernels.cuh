@@ -82,6 +82,8 @@ struct DevCtx {
   int32_t* count;            // number of active slots
   int32_t* status;           // context-wide error bits
   int32_t* plan;             // branch plan scratch
+  float2* work;              // per-slot work area of the large-tile kernels (nullptr: small)
+  size_t work_stride;        // complex elements per slot of `work`
   uint64_t seed;
   int32_t chi_max;
   double tol;
@@ -101,7 +103,9 @@ void launch_measure(const DevCtx& c, int tile_chi, const DMeas* meas, int n_meas
 void launch_branch_split(const DevCtx& c, int q, int cbit, double eps, int M,
                          cudaStream_t s, int* launches);
 void launch_branch_topk(const DevCtx& c, int M, cudaStream_t s);
-int fused_chi(int chi_max);
+int fused_chi(int chi_max);          // shared-memory tile for chi_max (0 if above 32)
+int big_chi(int chi_max);            // slot capacity per bond of the large-tile path
+size_t big_work_elems(int chi_cap);  // complex elements of one slot's work area
 
 // measurement modes
 constexpr int MEAS_SAMPLE = 0;

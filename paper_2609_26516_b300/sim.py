@@ -71,17 +71,19 @@ class Simulator:
 
     def __init__(self, n_qubits: int, chi_max: int, n_slots: int, n_cbits: int,
                  tol: float = 1e-10, sweeps: int = 2, seed: int = 0, chunk_k: int = 0,
-                 device: str = "cuda:0", stream: Optional[torch.cuda.Stream] = None):
+                 device: str = "cuda:0", stream: Optional[torch.cuda.Stream] = None,
+                 kernel_path: int = 0):
         if not torch.cuda.is_available():
             raise RuntimeError("libdcs needs a CUDA device; there is no CPU path")
         self.lib = N.load()
         self.cfg = N.dcs_config(n_qubits=n_qubits, chi_max=chi_max, tol=tol, sweeps=sweeps,
-                                chunk_k=chunk_k, precision=0, n_cbits=n_cbits,
+                                chunk_k=chunk_k, precision=0, kernel_path=kernel_path,
+                                n_cbits=n_cbits,
                                 n_slots=n_slots, seed=seed)
         self.device = torch.device(device)
         nbytes = self.lib.dcs_arena_bytes(ctypes.byref(self.cfg))
         if nbytes == 0:
-            raise DCSError(N.ERR_INVALID if chi_max <= N.MAX_CHI_FUSED else N.ERR_UNSUPPORTED,
+            raise DCSError(N.ERR_INVALID if chi_max <= N.MAX_CHI else N.ERR_UNSUPPORTED,
                            "configuration rejected")
         self.arena_bytes = nbytes
         self.arena = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)

@@ -83,11 +83,12 @@ def test_arena_bytes_and_argument_checks(lib):
     assert nb > 10000 * (2 * 64 * 128 + 2 * 65 * 256) * 8
     assert nb < 2 * 10000 * (2 * 64 * 128 + 2 * 65 * 256) * 8
     assert lib.dcs_arena_bytes(ctypes.byref(_cfg(N, n_qubits=0))) == 0
-    assert lib.dcs_arena_bytes(ctypes.byref(_cfg(N, chi_max=64))) == 0
+    assert lib.dcs_arena_bytes(ctypes.byref(_cfg(N, chi_max=2048))) == 0
+    assert lib.dcs_arena_bytes(ctypes.byref(_cfg(N, chi_max=64, kernel_path=1))) == 0
     assert lib.dcs_arena_bytes(ctypes.byref(_cfg(N, n_cbits=513))) == 0
     ctx = ctypes.c_void_p()
     assert lib.dcs_create(ctypes.byref(ctx), ctypes.byref(_cfg(N, sweeps=0)), None, 0, None) == N.ERR_INVALID
-    assert lib.dcs_create(ctypes.byref(ctx), ctypes.byref(_cfg(N, chi_max=64)), None, 0, None) == N.ERR_UNSUPPORTED
+    assert lib.dcs_create(ctypes.byref(ctx), ctypes.byref(_cfg(N, chi_max=2048)), None, 0, None) == N.ERR_UNSUPPORTED
     assert lib.dcs_create(ctypes.byref(ctx), ctypes.byref(cfg), None, 0, None) == N.ERR_OOM
     assert lib.dcs_last_error(None) == b"null context"
 

@@ -25,9 +25,10 @@ def f_tol(n_sites, n_compressions):
     return 1e-5 + 8 * U32 * n_sites * max(1, n_compressions)
 
 
-def _sim(n, chi, slots, ncb, tol=1e-10, sweeps=2, seed=1):
+def _sim(n, chi, slots, ncb, tol=1e-10, sweeps=2, seed=1, path=0):
     from paper_2609_26516_b300 import Simulator
-    return Simulator(n, chi, slots, max(ncb, 1), tol=tol, sweeps=sweeps, seed=seed)
+    return Simulator(n, chi, slots, max(ncb, 1), tol=tol, sweeps=sweeps, seed=seed,
+                     kernel_path=path)
 
 
 def _overlap(A, B):
@@ -48,8 +49,8 @@ def _state_fid(sim, pos, ref_mps):
 
 
 def _single_path_parity(circ, chi, shots, check_shots, seed=1, tol=1e-10, sweeps=2,
-                        state_check=True):
-    sim = _sim(circ.n_qubits, chi, shots, circ.n_cbits, tol, sweeps, seed)
+                        state_check=True, path=0):
+    sim = _sim(circ.n_qubits, chi, shots, circ.n_cbits, tol, sweeps, seed, path)
     sim.init_state(shots)
     sim.run_circuit(circ)
     res = sim.results()
@@ -219,3 +220,40 @@ def test_single_qubit_chain_and_launch_count():
     for s in range(0, 256, 17):
         ref = SV.run_single_path(circ, 1, s)
         assert res["bits"][s, 0] == ref.outcomes[0]
+
+
+# ----------------------------------------------------------------------------- global tiles
+# kernel_path=2 forces the large-bond kernels (tiles in a per-slot global work area, tiled
+# GEMM contractions) so they are checked on cases the oracle finishes in seconds.
+
+
+@pytest.mark.parametrize("chi,sweeps", [(8, 2), (16, 3)])
+def test_global_tiles_brickwork(chi, sweeps):
+    circ = C.brickwork(10, 8, 0.2, 3)
+    _single_path_parity(circ, chi, 8, list(range(8)), sweeps=sweeps, path=2)
+
+
+def test_global_tiles_ghz_and_teleport():
+    _single_path_parity(C.ghz_dynamic(20), 8, 16, list(range(0, 16, 5)), path=2)
+    _single_path_parity(C.teleport(4), 4, 64, list(range(0, 64, 13)), path=2)
+
+
+def test_global_tiles_ragged_chi_above_shared_limit():
+    # chi_max = 40 is above the shared-memory tiles and not a multiple of the GEMM tile
+    circ = C.brickwork(14, 16, 0.02, 9)  # the middle bonds reach 40 and are truncated
+    _single_path_parity(circ, 40, 3, [0, 1, 2])
+
+
+def test_global_tiles_multi_path():
+    circ = C.brickwork(8, 6, 0.2, 5)
+    M = 8
+    sim = _sim(8, 8, 2 * M, circ.n_cbits, path=2)
+    sim.init_state(1, multipath=True)
+    sim.run_circuit(circ, max_branches=M)
+    res = sim.results()
+    ref = D.run_multi_path(circ, D.Params(chi_max=8), M=M)
+    assert res["n_active"] == len(ref)
+    for i, b in enumerate(ref):
+        assert res["bits"][i].tolist() == [int(x) for x in b.c]
+        assert _state_fid(sim, i, b.mps) >= 1 - STATE_TOL
+        assert abs(res["p"][i] - b.p) < P_TOL
