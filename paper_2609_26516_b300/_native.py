@@ -5,7 +5,7 @@ import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libdcs.so")
+LIB_PATH = os.environ.get("DCS_LIB_PATH", os.path.join(HERE, "libdcs.so"))
 
 CWORDS = 8
 MAX_QUBITS = 128

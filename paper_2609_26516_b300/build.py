@@ -8,7 +8,7 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
-LIB = os.path.join(HERE, "libdcs.so")
+LIB = os.environ.get("DCS_LIB_PATH", os.path.join(HERE, "libdcs.so"))
 SOURCES = ["dcs_api.cu", "dcs_kernels.cu", "dcs_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -28,8 +28,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
         t = os.path.getmtime(LIB)
         if all(os.path.getmtime(d) <= t for d in deps):
             return LIB
+    extra = os.environ.get("DCS_NVCC_FLAGS", "").split()
     cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
-           "-o", LIB + ".tmp", *srcs, "-lcudart"]
+           *extra, "-o", LIB + ".tmp", *srcs, "-lcudart"]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     res = subprocess.run(cmd, capture_output=True, text=True)

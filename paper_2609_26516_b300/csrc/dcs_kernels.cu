@@ -331,7 +331,7 @@ __device__ void carve(Work& w, unsigned char* raw, int C, float2* big_area) {
 template <int NT>
 __device__ void cta_cgemm(int M, int N, int K, const float2* A, int sam, int sak, bool conjA,
                           const float2* B, int sbk, int sbn, bool conjB, float2* Cm, int scm,
-                          int scn, float2* sA, float2* sB) {
+                          int scn, float2* sA, float2* sB, bool accumulate = false) {
   static_assert((GBM * GBN) % NT == 0, "tile / threads");
   constexpr int PER = GBM * GBN / NT;  // outputs per thread
   const int tid = threadIdx.x;
@@ -395,7 +395,10 @@ __device__ void cta_cgemm(int M, int N, int K, const float2* A, int sam, int sak
 #pragma unroll
         for (int i = 0; i < PER; ++i) {
           const int gn = n0 + col0 + i;
-          if (gn < N) Cm[(size_t)gm * scm + (size_t)gn * scn] = acc[i];
+          if (gn < N) {
+            float2* dst = Cm + (size_t)gm * scm + (size_t)gn * scn;
+            *dst = accumulate ? cadd(*dst, acc[i]) : acc[i];
+          }
         }
       }
     }
@@ -771,6 +774,25 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_compress(DevCtx c,
 // ----------------------------------------------------------------------------- large tiles
 constexpr int BIG_NT = 512;
 
+// Optional per-phase cycle counters of the large-tile kernel (built with
+// -DDCS_PHASE_TIMERS; read back with dcs_debug_phase_cycles).  Off in normal builds.
+#ifdef DCS_PHASE_TIMERS
+__device__ unsigned long long g_phase_cycles[16];
+#define PHASE_START() long long _pt = clock64()
+#define PHASE_MARK(i)                                                                     \
+  do {                                                                                    \
+    __syncthreads();                                                                      \
+    if (threadIdx.x == 0) {                                                               \
+      const long long _n = clock64();                                                     \
+      atomicAdd(&g_phase_cycles[i], (unsigned long long)(_n - _pt));                      \
+      _pt = _n;                                                                           \
+    }                                                                                     \
+  } while (0)
+#else
+#define PHASE_START()
+#define PHASE_MARK(i)
+#endif
+
 // T2[b][s][e][x] = sum_{d,t} T1(b, d, t, x) W(d, s, t, e) with T1 at
 // b*ib + d*id + t*it + x*ix and T2 natural (b-stride 2 ne nx); mirrored: the coefficient is
 // W[e][s][t][d] (the MPO read right to left).
@@ -846,6 +868,7 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
   int centre = c.centre[slot];
   int* bt = sm.bnd;
   int* at = sm.abnd;
+  PHASE_START();
   // ---- initial guess: the chunk applied block by block to a copy of the ket
   for (int j = 0; j < n; ++j)
     gcopy<NT>(site_ptr(c, bb, slot, j), site_ptr(c, kb, slot, j), at[j] * 2 * at[j + 1]);
@@ -869,10 +892,12 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
     }
     __syncthreads();
   }
+  PHASE_MARK(0);
   for (int ib = 0; ib < L->n_blocks; ++ib) {
     const DBlock& blk = BK[L->blk_off + ib];
     const int q = blk.q;
     move_centre<NT>(c, sm, bb, slot, centre, q + 1);
+    PHASE_MARK(1);
     const int b0 = bt[q], b1 = bt[q + 1], b2 = bt[q + 2];
     if (threadIdx.x == 0) build_block(blk, G1, sm.creg, sm.G);
     const int m = 2 * b0, nn = 2 * b2;
@@ -901,7 +926,9 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
         for (int u = 0; u < 2; ++u) X[(a * 2 + s) + (size_t)(u * b2 + bcol) * m] = out[s * 2 + u];
     }
     __syncthreads();
+    PHASE_MARK(2);
     cta_jacobi_svd<NT>(X, m, nn, m, V, nn, sm.sig2, sm.perm, &sm.iv[5], sm.red);
+    PHASE_MARK(3);
     if (threadIdx.x == 0) {
       const int kk = trunc_rank(sm.sig2, sm.perm, nn, c.chi_max, c.tol);
       double w = 0.0;
@@ -926,8 +953,10 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
     if (threadIdx.x == 0) bt[q + 1] = kk;
     centre = q;
     __syncthreads();
+    PHASE_MARK(4);
   }
   move_centre<NT>(c, sm, bb, slot, centre, 0);
+  PHASE_MARK(5);
   // ---- right environments of the guess (mirrored env updates with B given)
   if (threadIdx.x == 0) sm.E[0] = make_float2(1.f, 0.f);
   __syncthreads();
@@ -955,6 +984,7 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
     gcopy<NT>(env_ptr(c.Rc, c, slot, j), sm.E, bl * dl * al);
     __syncthreads();
   }
+  PHASE_MARK(6);
   // ---- one-site sweeps
   double fval = 0.0;
   for (int sw = 0; sw < c.sweeps; ++sw) {
@@ -977,9 +1007,11 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
         const int m = 2 * nb;
         cta_cgemm<NT>(m, nc, dr * nx, sm.T2, dr * nx, 1, false, Rn, 1, dr * nx, false, sm.F, 1, m,
                       sm.gA, sm.gB);
+        PHASE_MARK(7);
         float2* dst = site_ptr(c, bb, slot, j);
         if (j < n - 1) {
           const int r = cta_qr<NT>(sm.F, m, nc, m, sm.R, m, nullptr, 0, sm.tau, sm.alph, sm.red);
+          PHASE_MARK(8);
           for (int idx = threadIdx.x; idx < m * r; idx += NT) {
             const int row = idx / r, k2 = idx % r;
             dst[idx] = sm.R[row + (size_t)k2 * m];
@@ -990,6 +1022,7 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
           __syncthreads();
           if (threadIdx.x == 0) bt[j + 1] = r;
           __syncthreads();
+          PHASE_MARK(9);
         } else {
           double s2 = 0.0;
           for (int i = threadIdx.x; i < m; i += NT) s2 += cabs2d(sm.F[i]);
@@ -1020,9 +1053,11 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
         // F'[(c s), b] = sum_{(d a)} T2[(c s), (d a)] L[b, (d a)]
         cta_cgemm<NT>(m, nc, dl * nx, sm.T2, dl * nx, 1, false, Ln, 1, dl * nx, false, sm.F, 1, m,
                       sm.gA, sm.gB);
+        PHASE_MARK(7);
         float2* dst = site_ptr(c, bb, slot, j);
         if (j > 0) {
           const int r = cta_qr<NT>(sm.F, m, nc, m, sm.R, m, nullptr, 0, sm.tau, sm.alph, sm.red);
+          PHASE_MARK(8);
           for (int idx = threadIdx.x; idx < r * 2 * nb; idx += NT) {
             const int cc = idx % nb, s = (idx / nb) & 1, k2 = idx / (2 * nb);
             dst[idx] = sm.R[(cc * 2 + s) + (size_t)k2 * m];
@@ -1033,6 +1068,7 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
           __syncthreads();
           if (threadIdx.x == 0) bt[j] = r;
           __syncthreads();
+          PHASE_MARK(9);
         } else {
           double s2 = 0.0;
           for (int i = threadIdx.x; i < m; i += NT) s2 += cabs2d(sm.F[i]);
@@ -1481,3 +1517,16 @@ void launch_branch_topk(const DevCtx& c, int M, cudaStream_t s) {
 }
 
 }  // namespace dcs
+
+#ifdef DCS_PHASE_TIMERS
+// Debug builds only: the large-tile kernel's per-phase cycle sums (not part of the ABI).
+extern "C" int dcs_debug_phase_cycles(unsigned long long* out, int reset) {
+  if (cudaMemcpyFromSymbol(out, dcs::g_phase_cycles, sizeof(unsigned long long) * 16) != cudaSuccess)
+    return 1;
+  if (reset) {
+    unsigned long long z[16] = {0};
+    cudaMemcpyToSymbol(dcs::g_phase_cycles, z, sizeof(z));
+  }
+  return 0;
+}
+#endif
