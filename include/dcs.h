@@ -89,7 +89,13 @@ typedef struct {
   dcs_cond cond;
 } dcs_op;
 
-typedef enum { DCS_PREC_FP32 = 0 } dcs_precision;
+/* Arithmetic of the large-bond contractions (chi_max > 32 or DCS_PATH_GLOBAL):
+ * DCS_PREC_FP32: FP32 CUDA-core GEMMs; DCS_PREC_TF32X3: tcgen05 tensor-core GEMMs with TF32
+ * inputs split in three products (x = hi + lo) and FP32 accumulation for the initial guess,
+ * the environment cache and every sweep but the last, which runs in FP32 as refinement (its
+ * f is the reported partial fidelity).  The shared-memory kernels (chi_max <= 32) always use
+ * FP32 CUDA cores. */
+typedef enum { DCS_PREC_FP32 = 0, DCS_PREC_TF32X3 = 1 } dcs_precision;
 
 typedef enum {
   DCS_PATH_AUTO = 0,    /* shared-memory tiles up to chi_max = 32, global tiles above */
@@ -208,6 +214,25 @@ uint64_t dcs_kernel_launches(dcs_ctx_t ctx);
 /* Bytes this context copied host -> device (circuit tables, forced outcomes) since it was
  * created. */
 uint64_t dcs_bytes_uploaded(dcs_ctx_t ctx);
+
+/* Complex GEMM, the contraction primitive of the large-bond compression kernels (every
+ * environment and site product of the compression step is one): for each of `batch`
+ * problems b, C_b[m, n] = sum_k opA(m, k) opB(k, n), m < M, n < N, k < K, with
+ * opA(m, k) = A[b sab + m sam + k sak] (conjugated if conjA), opB(k, n) =
+ * B[b sbb + k sbk + n sbn] (conjugated if conjB), written to C[b scb + m scm + n scn].
+ * A, B, C are DEVICE complex64 arrays, strides in elements (each below 2^31).
+ * mode DCS_GEMM_SIMT: FP32 CUDA-core GEMM with shared-memory tiles.
+ * mode DCS_GEMM_TENSOR: tcgen05 tensor-core GEMM (TF32 inputs, FP32 accumulators in tensor
+ * memory) with each operand split as x = hi + lo (3 products), FP32-level accuracy;
+ * err_dev: DEVICE int set to 1 if a bounded completion wait gave up (result invalid).
+ * One CTA per problem; asynchronous on `stream`. */
+#define DCS_GEMM_SIMT 0
+#define DCS_GEMM_TENSOR 1
+dcs_status_t dcs_cgemm(int32_t mode, int32_t batch, int32_t M, int32_t N, int32_t K,
+                       const void* A, int64_t sam, int64_t sak, int64_t sab, int32_t conjA,
+                       const void* B, int64_t sbk, int64_t sbn, int64_t sbb, int32_t conjB,
+                       void* C, int64_t scm, int64_t scn, int64_t scb, int32_t* err_dev,
+                       dcs_stream_t stream);
 
 /* ---------------------------------------------------------------------------------------
  * Allocation-free compression (the paper has no counterpart to this call).

@@ -12,6 +12,8 @@ MAX_QUBITS = 128
 MAX_CHI_FUSED = 32
 MAX_CHI = 1024
 PATH_AUTO, PATH_SHARED, PATH_GLOBAL = 0, 1, 2
+GEMM_SIMT, GEMM_TENSOR = 0, 1
+PREC_FP32, PREC_TF32X3 = 0, 1
 
 OK, ERR_INVALID, ERR_OOM, ERR_ZERO_PROB, ERR_NUMERICAL, ERR_TIMEOUT, ERR_CUDA, ERR_UNSUPPORTED = range(8)
 STATUS_NAMES = ["OK", "INVALID", "OOM", "ZERO_PROB", "NUMERICAL", "TIMEOUT", "CUDA", "UNSUPPORTED"]
@@ -63,6 +65,10 @@ SIGNATURES = {
     "dcs_run_circuit": (_c.c_int, [_P, _c.POINTER(dcs_op), _c.c_int, _c.c_uint64, _c.c_int]),
     "dcs_kernel_launches": (_c.c_uint64, [_P]),
     "dcs_bytes_uploaded": (_c.c_uint64, [_P]),
+    "dcs_cgemm": (_c.c_int, [_c.c_int32, _c.c_int32, _c.c_int32, _c.c_int32, _c.c_int32,
+                             _P, _c.c_int64, _c.c_int64, _c.c_int64, _c.c_int32,
+                             _P, _c.c_int64, _c.c_int64, _c.c_int64, _c.c_int32,
+                             _P, _c.c_int64, _c.c_int64, _c.c_int64, _P, _P]),
     "dcs_compress_noalloc": (_c.c_int, [_c.c_int32, _c.c_int32, _c.c_double, _c.c_int32,
                                         _c.POINTER(dcs_op), _c.c_int32, _P, _P, _P, _c.c_int32,
                                         _P, _P, _P, _P, _P]),

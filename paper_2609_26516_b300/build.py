@@ -9,7 +9,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.environ.get("DCS_LIB_PATH", os.path.join(HERE, "libdcs.so"))
-SOURCES = ["dcs_api.cu", "dcs_kernels.cu", "dcs_noalloc.cu"]
+SOURCES = ["dcs_api.cu", "dcs_kernels.cu", "dcs_noalloc.cu", "dcs_gemm.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -371,7 +371,7 @@ __device__ void cta_jacobi_svd(float2* X, int m, int n, int ld, float2* V, int l
 // Smallest k >= 1 with sum_{i >= k} w_(i) <= tol * sum_i w_i, w_(i) the values in
 // decreasing order (through perm), capped at cap and n.  Suffix sums are accumulated from
 // the smallest value up.  Evaluated by one thread in FP64.
-__device__ __noinline__ int trunc_rank(const double* w, const int* perm, int n, int cap,
+static __device__ __noinline__ int trunc_rank(const double* w, const int* perm, int n, int cap,
                                           double tol) {
   double total = 0.0;
   for (int i = 0; i < n; ++i) total += w[i];

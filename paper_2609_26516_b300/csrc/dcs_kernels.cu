@@ -16,6 +16,7 @@
 #include <cstdio>
 
 #include "dcs_device.cuh"
+#include "dcs_gemm.cuh"
 #include "dcs_kernels.cuh"
 
 namespace dcs {
@@ -265,6 +266,8 @@ struct Work {
   float2* alph;
   float2* gA;  // GEMM staging tiles (large path)
   float2* gB;
+  TcState tc;  // tensor-core GEMM state (large path with precision TF32X3)
+  bool use_tc;
   double* red;
   double* sig2;
   double* dv;  // scalar broadcast
@@ -277,10 +280,10 @@ struct Work {
   int C;       // tile capacity
 };
 
-constexpr int GBM = 64, GBN = 64, GBK = 16;  // CTA GEMM tile
 
-__host__ __device__ inline size_t work_small_bytes(int C, bool big) {
-  return sizeof(float2) * (64 + 64 + 16 + 2 * C + (big ? (GBM + GBN) * GBK : 0)) +
+__host__ __device__ inline size_t work_small_bytes(int C, bool big, bool tc = false) {
+  return (tc ? sizeof(float) * TC_SMEM_FLOATS + 64 : 0) +
+         sizeof(float2) * (64 + 64 + 16 + 2 * C + (big ? (GBM + GBN) * GBK : 0)) +
          sizeof(double) * (32 + 2 * C + 8) + sizeof(float) * 2 * C +
          sizeof(int) * (2 * C + 2 * (DCS_MAX_QUBITS + 1) + 16) + sizeof(uint64_t) * DCS_CWORDS + 64;
 }
@@ -288,8 +291,18 @@ __host__ __device__ inline size_t work_tile_elems(int C, bool big) {
   return (size_t)(big ? 28 : 20) * C * C;
 }
 
-__device__ void carve(Work& w, unsigned char* raw, int C, float2* big_area) {
+__device__ void carve(Work& w, unsigned char* raw, int C, float2* big_area, bool tc = false) {
   w.C = C;
+  w.use_tc = tc;
+  if (tc) {  // tensor-core staging first (16-byte aligned), then its barriers and counters
+    w.tc.stage = reinterpret_cast<float*>(raw);
+    uint64_t* tail = reinterpret_cast<uint64_t*>(w.tc.stage + TC_SMEM_FLOATS);
+    w.tc.mbar = tail;
+    w.tc.uses = reinterpret_cast<int*>(tail + 2);
+    w.tc.tmem = reinterpret_cast<uint32_t*>(w.tc.uses + 2);
+    w.tc.err = reinterpret_cast<int*>(w.tc.tmem + 1);
+    raw += sizeof(float) * TC_SMEM_FLOATS + 64;
+  }
   uint64_t* c64 = reinterpret_cast<uint64_t*>(raw);
   w.creg = c64;
   double* d = reinterpret_cast<double*>(c64 + DCS_CWORDS);
@@ -324,85 +337,19 @@ __device__ void carve(Work& w, unsigned char* raw, int C, float2* big_area) {
   w.iv = w.abnd + DCS_MAX_QUBITS + 1;
 }
 
-// ----------------------------------------------------------------------------- CTA GEMM
-// C[m, n] = sum_k opA(m, k) opB(k, n) with opA(m, k) = A[m sam + k sak] (conjugated if
-// conjA), opB(k, n) = B[k sbk + n sbn] (conjugated if conjB), C[m scm + n scn].  FP32 SIMT
-// with 64 x 64 x 16 shared-memory tiles; each thread owns an 8-element micro tile.
+// Complex GEMM of the large tiles: tensor cores when enabled and the shape fills at least
+// half an MMA tile in M and N, the SIMT tiles otherwise.
 template <int NT>
-__device__ void cta_cgemm(int M, int N, int K, const float2* A, int sam, int sak, bool conjA,
-                          const float2* B, int sbk, int sbn, bool conjB, float2* Cm, int scm,
-                          int scn, float2* sA, float2* sB, bool accumulate = false) {
-  static_assert((GBM * GBN) % NT == 0, "tile / threads");
-  constexpr int PER = GBM * GBN / NT;  // outputs per thread
-  const int tid = threadIdx.x;
-  for (int m0 = 0; m0 < M; m0 += GBM)
-    for (int n0 = 0; n0 < N; n0 += GBN) {
-      float2 acc[PER];
-#pragma unroll
-      for (int i = 0; i < PER; ++i) acc[i] = cz();
-      for (int k0 = 0; k0 < K; k0 += GBK) {
-        // stage A tile (GBM x GBK) as sA[m][k] and B tile (GBK x GBN) as sB[k][n]
-        for (int idx = tid; idx < GBM * GBK; idx += NT) {
-          int mm, kk;
-          if (sak == 1) {
-            mm = idx / GBK;
-            kk = idx % GBK;
-          } else {
-            kk = idx / GBM;
-            mm = idx % GBM;
-          }
-          const int gm = m0 + mm, gk = k0 + kk;
-          float2 v = cz();
-          if (gm < M && gk < K) {
-            v = A[(size_t)gm * sam + (size_t)gk * sak];
-            if (conjA) v.y = -v.y;
-          }
-          sA[mm * GBK + kk] = v;
-        }
-        for (int idx = tid; idx < GBK * GBN; idx += NT) {
-          int kk, nn;
-          if (sbn == 1) {
-            kk = idx / GBN;
-            nn = idx % GBN;
-          } else {
-            nn = idx / GBK;
-            kk = idx % GBK;
-          }
-          const int gk = k0 + kk, gn = n0 + nn;
-          float2 v = cz();
-          if (gk < K && gn < N) {
-            v = B[(size_t)gk * sbk + (size_t)gn * sbn];
-            if (conjB) v.y = -v.y;
-          }
-          sB[kk * GBN + nn] = v;
-        }
-        __syncthreads();
-        // thread tid owns rows (tid / (GBN / 2)) * ... : PER outputs in one row, PER columns
-        const int row = tid / (GBN / PER);
-        const int col0 = (tid % (GBN / PER)) * PER;
-#pragma unroll 4
-        for (int kk = 0; kk < GBK; ++kk) {
-          const float2 a = sA[row * GBK + kk];
-#pragma unroll
-          for (int i = 0; i < PER; ++i) cfma(acc[i], a, sB[kk * GBN + col0 + i]);
-        }
-        __syncthreads();
-      }
-      const int row = tid / (GBN / PER);
-      const int col0 = (tid % (GBN / PER)) * PER;
-      const int gm = m0 + row;
-      if (gm < M) {
-#pragma unroll
-        for (int i = 0; i < PER; ++i) {
-          const int gn = n0 + col0 + i;
-          if (gn < N) {
-            float2* dst = Cm + (size_t)gm * scm + (size_t)gn * scn;
-            *dst = accumulate ? cadd(*dst, acc[i]) : acc[i];
-          }
-        }
-      }
+__device__ __forceinline__ void wgemm(Work& sm, int M, int N, int K, const float2* A, int sam,
+                                      int sak, bool conjA, const float2* B, int sbk, int sbn,
+                                      bool conjB, float2* Cm, int scm, int scn) {
+  if constexpr (NT >= 128) {
+    if (sm.use_tc && M >= 64 && N >= 64 && K >= 16) {
+      cta_cgemm_tc<NT>(M, N, K, A, sam, sak, conjA, B, sbk, sbn, conjB, Cm, scm, scn, sm.tc);
+      return;
     }
-  __syncthreads();
+    cta_cgemm<NT>(M, N, K, A, sam, sak, conjA, B, sbk, sbn, conjB, Cm, scm, scn, sm.gA, sm.gB);
+  }
 }
 
 // ----------------------------------------------------------------------------- gauge moves
@@ -426,9 +373,8 @@ __device__ void hop_right(const DevCtx& c, Work& sm, int buf, int slot, int j) {
     dst[idx] = sm.R[row + k * m];
   }
   const float2* nx = site_ptr(c, buf, slot, j + 1);
-  if (sm.gA) {  // large tiles: R (r x br) times T_{j+1} (br x 2 bn) as a tiled GEMM
-    cta_cgemm<NT>(r, 2 * bn, br, sm.E, br, 1, false, nx, 2 * bn, 1, false, sm.T, 2 * bn, 1,
-                  sm.gA, sm.gB);
+  if (NT >= 128 && sm.gA) {  // large tiles: R (r x br) times T_{j+1} (br x 2 bn), tiled GEMM
+    wgemm<NT>(sm, r, 2 * bn, br, sm.E, br, 1, false, nx, 2 * bn, 1, false, sm.T, 2 * bn, 1);
   } else {
     gcopy<NT>(sm.S, nx, br * 2 * bn);
     __syncthreads();
@@ -465,10 +411,10 @@ __device__ void hop_left(const DevCtx& c, Work& sm, int buf, int slot, int j) {
     const int x = idx % br, t = (idx / br) & 1, k = idx / (2 * br);
     dst[idx] = sm.R[(x * 2 + t) + k * m];
   }
-  if (sm.gA) {  // large tiles: T_{j-1} ((2 bp) x bl) times R'^T (bl x r)
+  if (NT >= 128 && sm.gA) {  // large tiles: T_{j-1} ((2 bp) x bl) times R'^T (bl x r)
     __syncthreads();
-    cta_cgemm<NT>(2 * bp, r, bl, site_ptr(c, buf, slot, j - 1), bl, 1, false, sm.E, 1, bl, false,
-                  sm.T, r, 1, sm.gA, sm.gB);
+    wgemm<NT>(sm, 2 * bp, r, bl, site_ptr(c, buf, slot, j - 1), bl, 1, false, sm.E, 1, bl, false,
+              sm.T, r, 1);
   } else {
     gcopy<NT>(sm.S, site_ptr(c, buf, slot, j - 1), bp * 2 * bl);
     __syncthreads();
@@ -832,7 +778,7 @@ __device__ void mix_big(const float2* T1, int ib, int id, int it, int ix, float2
 //   T1[(b d),(t x)] = E[(b d), a] A[a, (t x)],  T2 = mix(T1, W),
 //   F[(b s), c] = T2[(b s), (e x)] R[c, (e x)]^T,  E'[c, (e x)] = Q^H[c, (b s)] T2[(b s), (e x)];
 // right-to-left steps read the same products on the mirrored chain.
-template <int NT>
+template <int NT, bool TC>
 __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const DLayer* __restrict__ L,
                                                         const DBlock* __restrict__ BK,
                                                         const DGate1* __restrict__ G1,
@@ -842,7 +788,7 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
   const int slot = c.order[pos];
   extern __shared__ __align__(16) unsigned char smraw[];
   Work sm;
-  carve(sm, smraw, C, c.work + (size_t)slot * c.work_stride);
+  carve(sm, smraw, C, c.work + (size_t)slot * c.work_stride, TC);
   const int n = c.n;
   if (threadIdx.x < DCS_CWORDS) sm.creg[threadIdx.x] = c.creg[(size_t)slot * DCS_CWORDS + threadIdx.x];
   __syncthreads();
@@ -858,6 +804,7 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
       return;
     }
   }
+  if (TC) tc_setup(sm.tc);
   const int kb = c.ketbuf[slot], bb = 1 - kb;
   const int* kbonds = bonds_ptr(c, slot, kb);
   for (int i = threadIdx.x; i <= n; i += NT) {
@@ -904,8 +851,8 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
     float2* X = sm.T;           // m x nn, column-major (fits in T + T2: 4 C^2)
     float2* V = sm.T2;          // nn x nn
     // P[(a t), (v b)] = B_q[(a t), x] B_{q+1}[x, (v b)]
-    cta_cgemm<NT>(m, nn, b1, site_ptr(c, bb, slot, q), b1, 1, false, site_ptr(c, bb, slot, q + 1),
-                  nn, 1, false, X, 1, m, sm.gA, sm.gB);
+    wgemm<NT>(sm, m, nn, b1, site_ptr(c, bb, slot, q), b1, 1, false, site_ptr(c, bb, slot, q + 1),
+                  nn, 1, false, X, 1, m);
     for (int idx = threadIdx.x; idx < b0 * b2; idx += NT) {
       const int a = idx / b2, bcol = idx % b2;
       float2 in[4], out[4];
@@ -974,13 +921,12 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
       sm.R[(x * 2 + s) + (size_t)bq * ldq] = Bj[idx];
     }
     // T1[(c e), (a t)] = sum_x E[(c e), x] A[(a t), x]
-    cta_cgemm<NT>(br * dr, 2 * al, ar, sm.E, ar, 1, false, A, 1, ar, false, sm.T, 2 * al, 1,
-                  sm.gA, sm.gB);
+    wgemm<NT>(sm, br * dr, 2 * al, ar, sm.E, ar, 1, false, A, 1, ar, false, sm.T, 2 * al, 1);
     // T2[c][s][d][a] from T1[c][e][a][t]: fibre (c, a), incoming MPO index e, outgoing d
     mix_big<NT>(sm.T, dr * 2 * al, 2 * al, 1, 2, sm.T2, sm.W, br, dr, dl, al, true);
     // R_j[b, (d a)] = sum_{(c s)} conj(Q'[(c s), b]) T2[(c s), (d a)]
-    cta_cgemm<NT>(bl, dl * al, 2 * br, sm.R, ldq, 1, true, sm.T2, dl * al, 1, false, sm.E, dl * al,
-                  1, sm.gA, sm.gB);
+    wgemm<NT>(sm, bl, dl * al, 2 * br, sm.R, ldq, 1, true, sm.T2, dl * al, 1, false, sm.E, dl * al,
+                  1);
     gcopy<NT>(env_ptr(c.Rc, c, slot, j), sm.E, bl * dl * al);
     __syncthreads();
   }
@@ -988,6 +934,9 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
   // ---- one-site sweeps
   double fval = 0.0;
   for (int sw = 0; sw < c.sweeps; ++sw) {
+    // reduced-precision contractions, then the last sweep in FP32 as refinement (its f is
+    // the reported fidelity)
+    sm.use_tc = TC && (sw < c.sweeps - 1);
     if (threadIdx.x == 0) sm.E[0] = make_float2(1.f, 0.f);
     __syncthreads();
     if ((sw & 1) == 0) {  // left to right
@@ -1001,12 +950,10 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
         if (j < n - 1) Rn = env_ptr(c.Rc, c, slot, j + 1);
         else if (threadIdx.x == 0) sm.R[0] = make_float2(1.f, 0.f);
         __syncthreads();
-        cta_cgemm<NT>(nb * dl, 2 * nx, na, sm.E, na, 1, false, A, 2 * nx, 1, false, sm.T, 2 * nx, 1,
-                      sm.gA, sm.gB);
+        wgemm<NT>(sm, nb * dl, 2 * nx, na, sm.E, na, 1, false, A, 2 * nx, 1, false, sm.T, 2 * nx, 1);
         mix_big<NT>(sm.T, dl * 2 * nx, 2 * nx, nx, 1, sm.T2, sm.W, nb, dl, dr, nx, false);
         const int m = 2 * nb;
-        cta_cgemm<NT>(m, nc, dr * nx, sm.T2, dr * nx, 1, false, Rn, 1, dr * nx, false, sm.F, 1, m,
-                      sm.gA, sm.gB);
+        wgemm<NT>(sm, m, nc, dr * nx, sm.T2, dr * nx, 1, false, Rn, 1, dr * nx, false, sm.F, 1, m);
         PHASE_MARK(7);
         float2* dst = site_ptr(c, bb, slot, j);
         if (j < n - 1) {
@@ -1016,8 +963,7 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
             const int row = idx / r, k2 = idx % r;
             dst[idx] = sm.R[row + (size_t)k2 * m];
           }
-          cta_cgemm<NT>(r, dr * nx, m, sm.R, m, 1, true, sm.T2, dr * nx, 1, false, sm.E, dr * nx, 1,
-                        sm.gA, sm.gB);
+          wgemm<NT>(sm, r, dr * nx, m, sm.R, m, 1, true, sm.T2, dr * nx, 1, false, sm.E, dr * nx, 1);
           gcopy<NT>(env_ptr(c.Lc, c, slot, j + 1), sm.E, r * dr * nx);
           __syncthreads();
           if (threadIdx.x == 0) bt[j + 1] = r;
@@ -1046,13 +992,11 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
         else if (threadIdx.x == 0) sm.R[0] = make_float2(1.f, 0.f);
         __syncthreads();
         // T1[(c e), (a t)] = sum_x E[(c e), x] A[(a t), x]
-        cta_cgemm<NT>(nb * dr, 2 * nx, na, sm.E, na, 1, false, A, 1, na, false, sm.T, 2 * nx, 1,
-                      sm.gA, sm.gB);
+        wgemm<NT>(sm, nb * dr, 2 * nx, na, sm.E, na, 1, false, A, 1, na, false, sm.T, 2 * nx, 1);
         mix_big<NT>(sm.T, dr * 2 * nx, 2 * nx, 1, 2, sm.T2, sm.W, nb, dr, dl, nx, true);
         const int m = 2 * nb;
         // F'[(c s), b] = sum_{(d a)} T2[(c s), (d a)] L[b, (d a)]
-        cta_cgemm<NT>(m, nc, dl * nx, sm.T2, dl * nx, 1, false, Ln, 1, dl * nx, false, sm.F, 1, m,
-                      sm.gA, sm.gB);
+        wgemm<NT>(sm, m, nc, dl * nx, sm.T2, dl * nx, 1, false, Ln, 1, dl * nx, false, sm.F, 1, m);
         PHASE_MARK(7);
         float2* dst = site_ptr(c, bb, slot, j);
         if (j > 0) {
@@ -1062,8 +1006,7 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
             const int cc = idx % nb, s = (idx / nb) & 1, k2 = idx / (2 * nb);
             dst[idx] = sm.R[(cc * 2 + s) + (size_t)k2 * m];
           }
-          cta_cgemm<NT>(r, dl * nx, m, sm.R, m, 1, true, sm.T2, dl * nx, 1, false, sm.E, dl * nx, 1,
-                        sm.gA, sm.gB);
+          wgemm<NT>(sm, r, dl * nx, m, sm.R, m, 1, true, sm.T2, dl * nx, 1, false, sm.E, dl * nx, 1);
           gcopy<NT>(env_ptr(c.Rc, c, slot, j), sm.E, r * dl * nx);
           __syncthreads();
           if (threadIdx.x == 0) bt[j] = r;
@@ -1084,6 +1027,10 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
       }
       centre = 0;
     }
+  }
+  if (TC) {
+    if (threadIdx.x == 0 && *sm.tc.err) atomicOr(c.status, 1 << DCS_ERR_TIMEOUT);
+    tc_teardown(sm.tc);
   }
   int* obonds = bonds_ptr(c, slot, bb);
   for (int i = threadIdx.x; i <= n; i += NT) obonds[i] = bt[i];
@@ -1228,7 +1175,7 @@ __global__ void k_branch_plan(DevCtx c, double eps, int M, int cbit) {
   __shared__ int s_keep[2048];
   __shared__ int s_slot[2048];
   __shared__ int s_free[1024];
-  __shared__ int s_nfree, s_err;
+  __shared__ int s_err;
   __shared__ double s_pmax;
   const int cnt = *c.count;
   const int ns = c.n_slots;
@@ -1296,7 +1243,6 @@ __global__ void k_branch_plan(DevCtx c, double eps, int M, int cbit) {
     // free slots: not used by any parent, or by a parent none of whose children is kept
     int used_mark[1];
     (void)used_mark;
-    s_nfree = 0;
     for (int s = 0; s < ns; ++s) s_free[s] = 1;
     for (int i = 0; i < cnt; ++i) {
       bool any = false;
@@ -1457,9 +1403,14 @@ static void compress_c(const DevCtx& c, int C, const DLayer* L, const DBlock* B,
 
 static void compress_big(const DevCtx& c, const DLayer* L, const DBlock* B, const DGate1* G1,
                          const DCond* CD, double* fid_out, cudaStream_t s) {
-  const size_t sm = work_small_bytes(c.chi_cap, true);
-  cudaFuncSetAttribute(k_compress_big<BIG_NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_compress_big<BIG_NT><<<c.n_slots, BIG_NT, sm, s>>>(c, c.chi_cap, L, B, G1, CD, fid_out);
+  const size_t sm = work_small_bytes(c.chi_cap, true, c.use_tc != 0);
+  if (c.use_tc) {
+    cudaFuncSetAttribute(k_compress_big<BIG_NT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_compress_big<BIG_NT, true><<<c.n_slots, BIG_NT, sm, s>>>(c, c.chi_cap, L, B, G1, CD, fid_out);
+  } else {
+    cudaFuncSetAttribute(k_compress_big<BIG_NT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_compress_big<BIG_NT, false><<<c.n_slots, BIG_NT, sm, s>>>(c, c.chi_cap, L, B, G1, CD, fid_out);
+  }
 }
 
 template <int NT, bool BIG>

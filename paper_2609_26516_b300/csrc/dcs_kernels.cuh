@@ -83,6 +83,7 @@ struct DevCtx {
   int32_t* status;           // context-wide error bits
   int32_t* plan;             // branch plan scratch
   float2* work;              // per-slot work area of the large-tile kernels (nullptr: small)
+  int32_t use_tc;            // large-tile contractions on the tensor cores (3xTF32)
   size_t work_stride;        // complex elements per slot of `work`
   uint64_t seed;
   int32_t chi_max;

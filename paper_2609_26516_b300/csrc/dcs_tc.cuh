@@ -1,0 +1,294 @@
+// Tensor-core complex GEMM for sm_103a: tcgen05.mma (kind::tf32) with the accumulators in
+// tensor memory (TMEM), issued by one thread of the CTA, completion signalled on mbarriers.
+//
+// C[m, n] = sum_k opA(m, k) opB(k, n) in complex64 with FP32 accuracy:
+//  * real embedding: A_r[m][2k] = Re a, A_r[m][2k+1] = Im a;
+//    B_r[2k][2n] = Re b, B_r[2k+1][2n] = -Im b, B_r[2k][2n+1] = Im b, B_r[2k+1][2n+1] = Re b,
+//    so that (A_r B_r)[m][2n] = Re c and [m][2n+1] = Im c;
+//  * 3xTF32: every operand x = hi + lo with hi = x with the low 13 mantissa bits cleared and
+//    lo = x - hi; A B ~ hi_A hi_B + hi_A lo_B + lo_A hi_B (the dropped lo lo term is
+//    ~2^-22 relative).
+// Tile: 128 complex rows x 128 complex columns (MMA M = 128, N = 256 real), K in steps of 8
+// complex (16 real = two MMAs of K = 8).  Operands are staged by all threads in the
+// canonical K-major layout without swizzle: 8-row x 16-byte core matrices, core matrices
+// along K 128 bytes apart (leading-dimension offset), 8-row groups 512 bytes apart (stride
+// offset).  Two staging buffers alternate; the MMAs of one stage run while the other is
+// filled.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "dcs_device.cuh"
+
+namespace dcs {
+
+constexpr int TC_M = 128;   // complex rows per tile (= MMA M)
+constexpr int TC_N = 128;   // complex columns per tile (MMA N = 256 real)
+constexpr int TC_K = 8;     // complex K per stage (16 real)
+constexpr int TC_A_FLOATS = TC_M * 2 * TC_K;        // one A copy (hi or lo): 128 x 16
+constexpr int TC_B_FLOATS = 2 * TC_N * 2 * TC_K;    // one B copy: 256 x 16
+constexpr int TC_STAGE_FLOATS = 2 * (TC_A_FLOATS + TC_B_FLOATS);
+constexpr int TC_SMEM_FLOATS = 2 * TC_STAGE_FLOATS;  // two stages: 96 KB
+constexpr int TC_TMEM_COLS = 256;
+constexpr long long TC_WAIT_LIMIT = 1ll << 26;      // bounded mbarrier spins
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor: start >> 4 (bits 0-13), leading-dimension byte offset
+// >> 4 (16-29), stride byte offset >> 4 (32-45), version 1 (bit 46), no swizzle (61-63 = 0).
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::tf32: D = F32 (bits 4-5 = 1), A = B = TF32 (bits 7-9,
+// 10-12 = 2), both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+__host__ __device__ constexpr uint32_t tc_idesc(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                       uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+      :
+      : "r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t* mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+               :
+               : "r"(smem_addr(mbar))
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" : : "r"(smem_addr(mbar)), "r"(count) : "memory");
+}
+
+// Wait for the completion of the phase with parity `parity`; false if the bounded spin ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
+  for (long long it = 0; it < TC_WAIT_LIMIT; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(mbar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// TMEM allocation / release by one whole warp.
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+               :
+               : "r"(smem_addr(dst_smem)), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" : : "r"(taddr), "r"(ncols) : "memory");
+}
+
+// 32 lanes x 32 consecutive columns of 32-bit data into v[0..31] (this warp's lane quadrant).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tf32_split(float x, float& hi, float& lo) {
+  hi = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+  lo = x - hi;
+}
+
+// float index of element (row, kr) of a K-major 16-column operand in the canonical layout
+__device__ __forceinline__ int tc_off(int row, int kr) {
+  return (((row >> 3) * 4 + (kr >> 2)) * 32) + (row & 7) * 4 + (kr & 3);
+}
+
+// Per-CTA state of the tensor-core GEMM (in shared memory).
+struct TcState {
+  float* stage;        // TC_SMEM_FLOATS, 16-byte aligned
+  uint64_t* mbar;      // 2 mbarriers
+  int* uses;           // 2 commit counters
+  uint32_t* tmem;      // TMEM base address (written by tmem_alloc)
+  int* err;            // set to 1 if a bounded wait gave up
+};
+
+// One thread initialises the barriers; warp 0 allocates TMEM.  All threads call.
+__device__ __forceinline__ void tc_setup(TcState& t) {
+  if (threadIdx.x == 0) {
+    mbar_init(&t.mbar[0], 1);
+    mbar_init(&t.mbar[1], 1);
+    t.uses[0] = t.uses[1] = 0;
+    *t.err = 0;
+  }
+  if (threadIdx.x < 32) tmem_alloc(t.tmem, TC_TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+}
+
+__device__ __forceinline__ void tc_teardown(TcState& t) {
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (threadIdx.x < 32) tmem_dealloc(*t.tmem, TC_TMEM_COLS);
+}
+
+template <int NT>
+__device__ void cta_cgemm_tc(int M, int N, int K, const float2* A, int sam, int sak, bool conjA,
+                             const float2* B, int sbk, int sbn, bool conjB, float2* Cm, int scm,
+                             int scn, TcState& t) {
+  static_assert(NT % 128 == 0, "the epilogue needs whole warp quadrants");
+  constexpr uint32_t IDESC = tc_idesc(128, 256);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t tbase = *t.tmem;
+  const int ksteps = (K + TC_K - 1) / TC_K;
+  for (int m0 = 0; m0 < M; m0 += TC_M)
+    for (int n0 = 0; n0 < N; n0 += TC_N) {
+      for (int s = 0; s < ksteps; ++s) {
+        const int b = s & 1;
+        float* st = t.stage + b * TC_STAGE_FLOATS;
+        float* Ahi = st;
+        float* Alo = Ahi + TC_A_FLOATS;
+        float* Bhi = Alo + TC_A_FLOATS;
+        float* Blo = Bhi + TC_B_FLOATS;
+        // the MMAs that last read this buffer must be done before it is overwritten
+        if (tid == 0 && t.uses[b] > 0) {
+          if (!mbar_wait(&t.mbar[b], (uint32_t)((t.uses[b] - 1) & 1))) *t.err = 1;
+        }
+        __syncthreads();
+        const int k0 = s * TC_K;
+        for (int idx = tid; idx < TC_M * TC_K; idx += NT) {
+          int mm, kk;
+          if (sak == 1) {
+            mm = idx / TC_K;
+            kk = idx % TC_K;
+          } else {
+            kk = idx / TC_M;
+            mm = idx % TC_M;
+          }
+          const int gm = m0 + mm, gk = k0 + kk;
+          float2 v = cz();
+          if (gm < M && gk < K) {
+            v = A[(size_t)gm * sam + (size_t)gk * sak];
+            if (conjA) v.y = -v.y;
+          }
+          float h, l;
+          tf32_split(v.x, h, l);
+          Ahi[tc_off(mm, 2 * kk)] = h;
+          Alo[tc_off(mm, 2 * kk)] = l;
+          tf32_split(v.y, h, l);
+          Ahi[tc_off(mm, 2 * kk + 1)] = h;
+          Alo[tc_off(mm, 2 * kk + 1)] = l;
+        }
+        for (int idx = tid; idx < TC_K * TC_N; idx += NT) {
+          int kk, nn;
+          if (sbn == 1) {
+            kk = idx / TC_N;
+            nn = idx % TC_N;
+          } else {
+            nn = idx / TC_K;
+            kk = idx % TC_K;
+          }
+          const int gk = k0 + kk, gn = n0 + nn;
+          float2 v = cz();
+          if (gk < K && gn < N) {
+            v = B[(size_t)gk * sbk + (size_t)gn * sbn];
+            if (conjB) v.y = -v.y;
+          }
+          float rh, rl, ih, il;
+          tf32_split(v.x, rh, rl);
+          tf32_split(v.y, ih, il);
+          // rows of the K-major B_r^T: real column nr = 2n (Re c), 2n+1 (Im c)
+          Bhi[tc_off(2 * nn, 2 * kk)] = rh;
+          Blo[tc_off(2 * nn, 2 * kk)] = rl;
+          Bhi[tc_off(2 * nn, 2 * kk + 1)] = -ih;
+          Blo[tc_off(2 * nn, 2 * kk + 1)] = -il;
+          Bhi[tc_off(2 * nn + 1, 2 * kk)] = ih;
+          Blo[tc_off(2 * nn + 1, 2 * kk)] = il;
+          Bhi[tc_off(2 * nn + 1, 2 * kk + 1)] = rh;
+          Blo[tc_off(2 * nn + 1, 2 * kk + 1)] = rl;
+        }
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+          tc_fence_after();
+          const float* As[3] = {Ahi, Ahi, Alo};
+          const float* Bs[3] = {Bhi, Blo, Bhi};
+#pragma unroll
+          for (int p = 0; p < 3; ++p)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              // K-chunks 2h, 2h+1 of this stage: start two core matrices (256 B) further
+              const uint64_t ad = tc_desc(smem_addr(As[p]) + h * 256, 128, 512);
+              const uint64_t bd = tc_desc(smem_addr(Bs[p]) + h * 256, 128, 512);
+              tc_mma(tbase, ad, bd, IDESC, (s > 0 || p > 0 || h > 0) ? 1u : 0u);
+            }
+          tc_commit(&t.mbar[b]);
+          t.uses[b] += 1;
+        }
+      }
+      // epilogue: wait for the last stage (and the one before), read TMEM, write C
+      if (tid == 0) {
+        for (int b = 0; b < 2; ++b)
+          if (t.uses[b] > 0 && !mbar_wait(&t.mbar[b], (uint32_t)((t.uses[b] - 1) & 1))) *t.err = 1;
+      }
+      tc_fence_before();
+      __syncthreads();
+      tc_fence_after();
+      for (int wq = warp; wq < 16; wq += NT / 32) {
+        const int quad = wq & 3, cg = wq >> 2;  // lanes 32 quad.., real columns 64 cg..
+        const int row = quad * 32 + lane;
+        for (int half = 0; half < 2; ++half) {
+          float v[32];
+          tmem_ld32(tbase + ((uint32_t)(quad * 32) << 16) + (uint32_t)(cg * 64 + half * 32), v);
+          const int gm = m0 + row;
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int gn = n0 + cg * 32 + half * 16 + j;
+            if (gm < M && gn < N) Cm[(size_t)gm * scm + (size_t)gn * scn] = make_float2(v[2 * j], v[2 * j + 1]);
+          }
+        }
+      }
+      tc_fence_before();
+      __syncthreads();
+      tc_fence_after();
+    }
+}
+
+}  // namespace dcs

@@ -1,0 +1,61 @@
+"""dcs_cgemm (the contraction primitive of the large-bond kernels) against PyTorch complex128
+matmul: FP32 SIMT and tcgen05 tensor-core (3xTF32) modes, ragged sizes, strided and
+conjugated operands.  Bar: relative Frobenius error <= 1e-5 (FP32 accuracy)."""
+import ctypes
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _run(mode, batch, M, N, K, transA=False, transB=False, conjA=False, conjB=False, seed=0):
+    from paper_2609_26516_b300 import _native as N_
+    lib = N_.load()
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    # stored A is M x K (row-major) or K x M when transA; likewise B
+    a_shape = (batch, K, M) if transA else (batch, M, K)
+    b_shape = (batch, N, K) if transB else (batch, K, N)
+    A = torch.complex(torch.randn(a_shape, generator=g), torch.randn(a_shape, generator=g)).to(torch.complex64).cuda()
+    B = torch.complex(torch.randn(b_shape, generator=g), torch.randn(b_shape, generator=g)).to(torch.complex64).cuda()
+    C = torch.zeros((batch, M, N), dtype=torch.complex64, device="cuda")
+    sam, sak = (1, M) if transA else (K, 1)
+    sbk, sbn = (1, K) if transB else (N, 1)
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    st = lib.dcs_cgemm(mode, batch, M, N, K,
+                       ctypes.c_void_p(A.data_ptr()), sam, sak, A[0].numel(), int(conjA),
+                       ctypes.c_void_p(B.data_ptr()), sbk, sbn, B[0].numel(), int(conjB),
+                       ctypes.c_void_p(C.data_ptr()), N, 1, M * N,
+                       ctypes.c_void_p(err.data_ptr()),
+                       ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == 0
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    a = A.to(torch.complex128)
+    b = B.to(torch.complex128)
+    if transA:
+        a = a.transpose(1, 2)
+    if transB:
+        b = b.transpose(1, 2)
+    if conjA:
+        a = a.conj()
+    if conjB:
+        b = b.conj()
+    ref = a @ b
+    rel = (C.to(torch.complex128) - ref).norm() / ref.norm()
+    return float(rel)
+
+
+@pytest.mark.parametrize("mode", [0, 1], ids=["simt", "tensor"])
+@pytest.mark.parametrize("shape", [(1, 128, 128, 8), (2, 128, 128, 64), (3, 200, 130, 37),
+                                   (1, 64, 300, 500), (1, 7, 5, 3)])
+def test_cgemm_plain(mode, shape):
+    assert _run(mode, *shape) <= 1e-5
+
+
+@pytest.mark.parametrize("mode", [0, 1], ids=["simt", "tensor"])
+def test_cgemm_strided_and_conjugated(mode):
+    assert _run(mode, 2, 150, 90, 70, transA=True, conjA=True) <= 1e-5
+    assert _run(mode, 2, 150, 90, 70, transB=True, conjB=True) <= 1e-5
+    assert _run(mode, 1, 260, 140, 96, transA=True, transB=True, conjA=True, conjB=True) <= 1e-5

@@ -25,10 +25,10 @@ def f_tol(n_sites, n_compressions):
     return 1e-5 + 8 * U32 * n_sites * max(1, n_compressions)
 
 
-def _sim(n, chi, slots, ncb, tol=1e-10, sweeps=2, seed=1, path=0):
+def _sim(n, chi, slots, ncb, tol=1e-10, sweeps=2, seed=1, path=0, prec=0):
     from paper_2609_26516_b300 import Simulator
     return Simulator(n, chi, slots, max(ncb, 1), tol=tol, sweeps=sweeps, seed=seed,
-                     kernel_path=path)
+                     kernel_path=path, precision=prec)
 
 
 def _overlap(A, B):
@@ -49,8 +49,8 @@ def _state_fid(sim, pos, ref_mps):
 
 
 def _single_path_parity(circ, chi, shots, check_shots, seed=1, tol=1e-10, sweeps=2,
-                        state_check=True, path=0):
-    sim = _sim(circ.n_qubits, chi, shots, circ.n_cbits, tol, sweeps, seed, path)
+                        state_check=True, path=0, prec=0):
+    sim = _sim(circ.n_qubits, chi, shots, circ.n_cbits, tol, sweeps, seed, path, prec)
     sim.init_state(shots)
     sim.run_circuit(circ)
     res = sim.results()
@@ -238,10 +238,18 @@ def test_global_tiles_ghz_and_teleport():
     _single_path_parity(C.teleport(4), 4, 64, list(range(0, 64, 13)), path=2)
 
 
-def test_global_tiles_ragged_chi_above_shared_limit():
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp32", "tf32x3"])
+def test_global_tiles_ragged_chi_above_shared_limit(prec):
     # chi_max = 40 is above the shared-memory tiles and not a multiple of the GEMM tile
     circ = C.brickwork(14, 16, 0.02, 9)  # the middle bonds reach 40 and are truncated
-    _single_path_parity(circ, 40, 3, [0, 1, 2])
+    _single_path_parity(circ, 40, 3, [0, 1, 2], prec=prec)
+
+
+def test_global_tiles_tensor_cores_at_chi_96():
+    # bonds up to 96: the environment and site products are large enough for the tensor
+    # cores (M, N >= 64) on the TF32x3 path
+    circ = C.brickwork(16, 14, 0.0, 21)
+    _single_path_parity(circ, 96, 2, [0, 1], prec=1)
 
 
 def test_global_tiles_multi_path():
