@@ -101,45 +101,9 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def sweeps_per_shot(bits: np.ndarray) -> np.ndarray:
-    """Compression sweeps each shot ran: 2 unconditional chunks, plus the data feed-forward
-    chunk unless no prefix parity is 1, plus the reset chunk unless every ancilla read 0
-    (a chunk whose gates are all skipped is not compressed); s sweeps each."""
-    n_anc = N_QUBITS // 2
-    meas = bits[:, :n_anc - 1]  # ancilla outcomes that enter the prefix parities
-    ff = np.any(np.cumsum(meas, axis=1) % 2 == 1, axis=1)
-    rst = np.any(bits[:, n_anc:2 * n_anc] == 1, axis=1)
-    return SWEEPS * (2 + ff.astype(np.int64) + rst.astype(np.int64))
-
-
-def algorithmic_flops_per_shot() -> float:
-    """Algorithmic real flops of the compression sweeps of one GHZ shot (contractions only):
-    per one-site update 8 (2 b_l D_l a_l a_r + 4 b_l b_r D_r a_r + 4 b_l a_r D_l D_r) with the
-    bond dimensions this circuit has (all internal bonds 2 after the first layer; the CNOT
-    MPO bond is 2, the single-qubit layers 1)."""
-    n = N_QUBITS
-    total = 0.0
-    # chunk 1 (H + CNOT pairs (2i, 2i+1)): bonds after guess 2 on odd bonds, 1 on even bonds
-    # chunk 2 (CNOT pairs (2i+1, 2i+2)): all internal bonds 2 except the idle last ancilla
-    # chunks 3, 4 (conditional X): bonds 2, D = 1
-    def upd(bl, br, al, ar, dl, dr):
-        return 8.0 * (2 * bl * dl * al * ar + 4 * bl * br * dr * ar + 4 * bl * ar * dl * dr)
-
-    def chunk(bonds_b, bonds_a, D):
-        f = 0.0
-        for j in range(n):
-            f += upd(bonds_b[j], bonds_b[j + 1], bonds_a[j], bonds_a[j + 1], D[j], D[j + 1])
-        return f
-
-    one = [1] * (n + 1)
-    b1 = [1] + [2 if (b % 2 == 1) else 1 for b in range(1, n)] + [1]
-    b2 = [1] + [2] * (n - 2) + [1, 1]
-    D1 = [1] + [2 if b % 2 == 1 else 1 for b in range(1, n)] + [1]
-    D2 = [1] + [2 if (b % 2 == 0 and b < n - 1) else 1 for b in range(1, n)] + [1]
-    total += SWEEPS * chunk(b1, one, D1)
-    total += SWEEPS * chunk(b2, b1, D2)
-    total += 2 * SWEEPS * chunk(b2, b2, one)
-    return total
+def mps_bytes(bonds) -> int:
+    """complex64 bytes of an MPS with the given bond dimensions."""
+    return sum(8 * 2 * int(bonds[j]) * int(bonds[j + 1]) for j in range(len(bonds) - 1))
 
 
 def cpu_oracle_sample(seconds: float = 15.0, max_shots: int = 200):
@@ -268,15 +232,16 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         t_step = float(t.item())
     res = sim.results()
-    sps = sweeps_per_shot(res["bits"])
+    n_comp, n_sweeps = sim.counters()  # of the last step (counters restart at init_state)
     value = world * args.shots / t_step
-    sweeps_s = world * float(sps.sum()) / t_step
+    sweeps_s = world * n_sweeps / t_step
+    comp_s = world * n_comp / t_step
 
-    # ---- dominant kernel: the compression kernel timed alone on the same stream
-    from paper_2609_26516_b300.sim import encode_ops as enc
-    layer_ops = [o for o in circ.ops[: N_QUBITS // 2 + (N_QUBITS // 2 - 1)]]  # H + CNOT layer
+    # ---- dominant kernel: the compression launch of the first chunk (H + CNOT layer),
+    # timed alone on the library's stream, L2 flushed before it
+    layer_ops = circ.ops[: N_QUBITS // 2 + (N_QUBITS // 2 - 1)]
+    gl = encode_ops(layer_ops)
     k_ms = []
-    gl = enc(layer_ops)
     for i in range(6):
         sim.init_state(args.shots, shot0=shot0)
         flush.fill_(1)
@@ -289,20 +254,14 @@ def main():
         if i >= 2:
             k_ms.append(a.elapsed_time(b))
     comp_ms = statistics.median(k_ms)
-    # algorithmic flops of that launch: chunk 1 with bra bonds (1,2,1,2,...) and s sweeps
-    peaks, peak_kind = measured_peaks()
-    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
-    fp32_peak_tflops = sm_count * 128 * 2 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+    # algorithmic bytes of that launch per shot: read the ket (|0...0>, bonds 1) and write the
+    # bra (bonds 2 across each H+CNOT pair); the guess is exact, so no environment traffic
     n = N_QUBITS
-    one = [1] * (n + 1)
-    b1 = [1] + [2 if (b % 2 == 1) else 1 for b in range(1, n)] + [1]
-    D1 = [1] + [2 if b % 2 == 1 else 1 for b in range(1, n)] + [1]
-    f_launch = 0.0
-    for j in range(n):
-        bl, br, al, ar, dl, dr = b1[j], b1[j + 1], one[j], one[j + 1], D1[j], D1[j + 1]
-        f_launch += 8.0 * (2 * bl * dl * al * ar + 4 * bl * br * dr * ar + 4 * bl * ar * dl * dr)
-    f_launch *= SWEEPS * args.shots
-    achieved = f_launch / (comp_ms / 1000.0) / 1e12
+    ket = [1] * (n + 1)
+    bra = [1] + [2 if (b_ % 2 == 1) else 1 for b_ in range(1, n)] + [1]
+    bytes_launch = args.shots * (mps_bytes(ket) + mps_bytes(bra))
+    achieved = bytes_launch / (comp_ms / 1000.0) / 1e9
+    peaks, peak_kind = measured_peaks()
 
     # ---- end to end through the C ABI with host buffers (tables up, results down)
     e2e_t = []
@@ -338,11 +297,12 @@ def main():
                    "l2": "flushed between timed steps (256 MB write outside the events)",
                    "parallelism": f"shots sharded over {world} GPU(s), no collective"},
         "sweeps_per_s": sweeps_s,
-        "roofline": {"bound": "alu", "kernel": "k_compress<8,32> (H+CNOT chunk, all shots)",
-                     "achieved": achieved, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
-                     "frac": achieved / fp32_peak_tflops, "traffic": None,
-                     "peak_source": f"FP32 SIMT: {sm_count} SMs x 128 lanes x 2 x "
-                                    f"{peaks.get('sm_max_mhz', 2032.0)} MHz ({peak_kind} clock)",
+        "compression_steps_per_s": comp_s,
+        "roofline": {"bound": "hbm", "kernel": "k_compress<32> (H+CNOT chunk, all shots)",
+                     "achieved": achieved, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+                     "frac": achieved / float(peaks["hbm_gbs"]), "traffic": None,
+                     "peak_source": f"hbm_gbs of MEASURED_PEAKS.json ({peak_kind})",
+                     "note": "latency-bound: a dependent chain of bond-2 operations per shot",
                      "launch_ms": comp_ms},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "shots/s", "h2d_bytes_per_step": int(h2d),

@@ -215,6 +215,12 @@ uint64_t dcs_kernel_launches(dcs_ctx_t ctx);
  * created. */
 uint64_t dcs_bytes_uploaded(dcs_ctx_t ctx);
 
+/* Synchronises and reads the device counters since the last dcs_init_state: compression
+ * steps run (summed over slots) and one-site sweeps run.  A compression step whose initial
+ * guess is exact (no truncation beyond tol) runs no sweep: the guess is then the target
+ * W|A> itself, which every one-site update would return unchanged. */
+dcs_status_t dcs_get_counters(dcs_ctx_t ctx, uint64_t* compressions, uint64_t* sweeps);
+
 /* Complex GEMM, the contraction primitive of the large-bond compression kernels (every
  * environment and site product of the compression step is one): for each of `batch`
  * problems b, C_b[m, n] = sum_k opA(m, k) opB(k, n), m < M, n < N, k < K, with

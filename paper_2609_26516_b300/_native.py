@@ -65,6 +65,7 @@ SIGNATURES = {
     "dcs_run_circuit": (_c.c_int, [_P, _c.POINTER(dcs_op), _c.c_int, _c.c_uint64, _c.c_int]),
     "dcs_kernel_launches": (_c.c_uint64, [_P]),
     "dcs_bytes_uploaded": (_c.c_uint64, [_P]),
+    "dcs_get_counters": (_c.c_int, [_P, _c.POINTER(_c.c_uint64), _c.POINTER(_c.c_uint64)]),
     "dcs_cgemm": (_c.c_int, [_c.c_int32, _c.c_int32, _c.c_int32, _c.c_int32, _c.c_int32,
                              _P, _c.c_int64, _c.c_int64, _c.c_int64, _c.c_int32,
                              _P, _c.c_int64, _c.c_int64, _c.c_int64, _c.c_int32,

@@ -26,7 +26,7 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
   size_t mps0, mps1, lc, rc, bonds, centre, ketbuf, p, F, rr, creg, flags, shot, order, count,
-      status, plan, prog, work, total;
+      status, plan, counters, prog, work, total;
   bool big;
   size_t work_stride;
   int chi_cap, site_stride, env_stride;
@@ -85,6 +85,7 @@ Layout make_layout(const dcs_config* c) {
   L.count = take(sizeof(int32_t));
   L.status = take(sizeof(int32_t));
   L.plan = take((PLAN_HDR + 4 * S) * sizeof(int32_t));
+  L.counters = take(2 * sizeof(unsigned long long));
   L.prog = take(kProgBytes);
   L.work = take(S * L.work_stride * sizeof(float2));
   L.total = off;
@@ -342,6 +343,7 @@ dcs_status_t dcs_create(dcs_ctx_t* out, const dcs_config* cfg, void* dev_arena, 
   d.count = reinterpret_cast<int32_t*>(a + lay.count);
   d.status = reinterpret_cast<int32_t*>(a + lay.status);
   d.plan = reinterpret_cast<int32_t*>(a + lay.plan);
+  d.counters = reinterpret_cast<unsigned long long*>(a + lay.counters);
   d.work = lay.big ? reinterpret_cast<float2*>(a + lay.work) : nullptr;
   d.use_tc = (lay.big && cfg->precision == DCS_PREC_TF32X3) ? 1 : 0;
   d.work_stride = lay.work_stride;
@@ -372,6 +374,17 @@ const char* dcs_last_error(dcs_ctx_t c) { return c ? c->err.c_str() : "null cont
 uint64_t dcs_kernel_launches(dcs_ctx_t c) { return c ? c->launches : 0; }
 
 uint64_t dcs_bytes_uploaded(dcs_ctx_t c) { return c ? c->uploaded : 0; }
+
+dcs_status_t dcs_get_counters(dcs_ctx_t c, uint64_t* compressions, uint64_t* sweeps) {
+  if (!c) return DCS_ERR_INVALID;
+  dcs_status_t st = cuda_check(c, cudaStreamSynchronize(c->stream), "synchronize");
+  if (st != DCS_OK) return st;
+  unsigned long long v[2] = {0, 0};
+  cudaMemcpy(v, c->dev.counters, sizeof(v), cudaMemcpyDeviceToHost);
+  if (compressions) *compressions = v[0];
+  if (sweeps) *sweeps = v[1];
+  return cuda_check(c, cudaGetLastError(), "counters");
+}
 
 dcs_status_t dcs_init_state(dcs_ctx_t c, int n_active, int multipath, uint64_t shot0) {
   if (!c) return DCS_ERR_INVALID;

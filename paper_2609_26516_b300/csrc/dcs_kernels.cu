@@ -488,6 +488,10 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_compress(DevCtx c,
   }
   __syncthreads();
   int centre = c.centre[slot];
+  if (threadIdx.x == 0) {
+    sm.iv[7] = 1;    // the guess is exact (no truncation beyond the tolerance) so far
+    sm.dv[1] = 1.0;  // product of the kept weight fractions
+  }
   // ---- initial guess: copy the ket, then apply the chunk block by block
   for (int j = 0; j < n; ++j)
     gcopy<NT>(site_ptr(c, bb, slot, j), site_ptr(c, kb, slot, j), sm.abnd[j] * 2 * sm.abnd[j + 1]);
@@ -555,10 +559,14 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_compress(DevCtx c,
     cta_jacobi_svd<NT>(X, m, nn, m, V, nn, sm.sig2, sm.perm, &sm.iv[5], sm.red);
     if (threadIdx.x == 0) {
       const int k = trunc_rank(sm.sig2, sm.perm, nn, c.chi_max, c.tol);
-      double w = 0.0;
+      double w = 0.0, tot = 0.0;
+      for (int i = 0; i < nn; ++i) tot += sm.sig2[i];
       for (int i = 0; i < k; ++i) w += sm.sig2[sm.perm[i]];
       sm.iv[6] = k;
       sm.dv[0] = w;
+      // exact unless the rank was capped by chi_max above the tolerance
+      if (tot - w > c.tol * tot) sm.iv[7] = 0;
+      if (tot > 0.0) sm.dv[1] *= w / tot;
     }
     __syncthreads();
     const int k = sm.iv[6];
@@ -579,9 +587,16 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_compress(DevCtx c,
     __syncthreads();
   }
   move_centre<NT>(c, sm, bb, slot, centre, 0);
-  // ---- right environments of the guess: R_j for j = n-1 .. 1 (mirrored env updates)
   int* bt = sm.bnd;
   int* at = sm.abnd;
+  double fval = 0.0;
+  // An exact guess is the target W|A> itself, already the optimum of every one-site update:
+  // the sweeps would return it unchanged (f = 1 up to the tolerance), so they are skipped.
+  const bool exact = sm.iv[7] != 0;
+  if (exact) {
+    fval = sm.dv[1];
+  } else {
+  // ---- right environments of the guess: R_j for j = n-1 .. 1 (mirrored env updates)
   if (threadIdx.x == 0) sm.E[0] = make_float2(1.f, 0.f);
   __syncthreads();
   for (int j = n - 1; j >= 1; --j) {
@@ -613,7 +628,6 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_compress(DevCtx c,
     __syncthreads();
   }
   // ---- one-site sweeps
-  double fval = 0.0;
   for (int sw = 0; sw < c.sweeps; ++sw) {
     if (threadIdx.x == 0) sm.E[0] = make_float2(1.f, 0.f);
     __syncthreads();
@@ -705,6 +719,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_compress(DevCtx c,
       centre = 0;
     }
   }
+  }  // not exact
   // ---- the bra becomes the ket
   int* obonds = bonds_ptr(c, slot, bb);
   for (int i = threadIdx.x; i <= n; i += NT) obonds[i] = bt[i];
@@ -714,6 +729,10 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_compress(DevCtx c,
     if (!(fval == fval) || fval > 1e300) c.flags[slot] |= DCS_FLAG_NUMERICAL;
     c.F[slot] *= fval;
     if (fid_out) fid_out[slot] = fval;
+    if (c.counters) {
+      atomicAdd(&c.counters[0], 1ull);
+      atomicAdd(&c.counters[1], exact ? 0ull : (unsigned long long)c.sweeps);
+    }
   }
 }
 
@@ -815,6 +834,10 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
   int centre = c.centre[slot];
   int* bt = sm.bnd;
   int* at = sm.abnd;
+  if (threadIdx.x == 0) {
+    sm.iv[7] = 1;
+    sm.dv[1] = 1.0;
+  }
   PHASE_START();
   // ---- initial guess: the chunk applied block by block to a copy of the ket
   for (int j = 0; j < n; ++j)
@@ -878,10 +901,13 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
     PHASE_MARK(3);
     if (threadIdx.x == 0) {
       const int kk = trunc_rank(sm.sig2, sm.perm, nn, c.chi_max, c.tol);
-      double w = 0.0;
+      double w = 0.0, tot = 0.0;
+      for (int i = 0; i < nn; ++i) tot += sm.sig2[i];
       for (int i = 0; i < kk; ++i) w += sm.sig2[sm.perm[i]];
       sm.iv[6] = kk;
       sm.dv[0] = w;
+      if (tot - w > c.tol * tot) sm.iv[7] = 0;
+      if (tot > 0.0) sm.dv[1] *= w / tot;
     }
     __syncthreads();
     const int kk = sm.iv[6];
@@ -904,6 +930,11 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
   }
   move_centre<NT>(c, sm, bb, slot, centre, 0);
   PHASE_MARK(5);
+  double fval = 0.0;
+  const bool exact = sm.iv[7] != 0;  // exact guess: the sweeps are skipped (see k_compress)
+  if (exact) {
+    fval = sm.dv[1];
+  } else {
   // ---- right environments of the guess (mirrored env updates with B given)
   if (threadIdx.x == 0) sm.E[0] = make_float2(1.f, 0.f);
   __syncthreads();
@@ -932,7 +963,6 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
   }
   PHASE_MARK(6);
   // ---- one-site sweeps
-  double fval = 0.0;
   for (int sw = 0; sw < c.sweeps; ++sw) {
     // reduced-precision contractions, then the last sweep in FP32 as refinement (its f is
     // the reported fidelity)
@@ -1028,6 +1058,7 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
       centre = 0;
     }
   }
+  }  // not exact
   if (TC) {
     if (threadIdx.x == 0 && *sm.tc.err) atomicOr(c.status, 1 << DCS_ERR_TIMEOUT);
     tc_teardown(sm.tc);
@@ -1040,6 +1071,10 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
     if (!(fval == fval) || fval > 1e300) c.flags[slot] |= DCS_FLAG_NUMERICAL;
     c.F[slot] *= fval;
     if (fid_out) fid_out[slot] = fval;
+    if (c.counters) {
+      atomicAdd(&c.counters[0], 1ull);
+      atomicAdd(&c.counters[1], exact ? 0ull : (unsigned long long)c.sweeps);
+    }
   }
 }
 
@@ -1131,6 +1166,7 @@ __global__ void k_init(DevCtx c, int n_active, int multipath, uint64_t shot0) {
   if (slot == 0 && threadIdx.x == 0) {
     *c.count = multipath ? 1 : n_active;
     *c.status = 0;
+    if (c.counters) c.counters[0] = c.counters[1] = 0ull;
   }
   if (threadIdx.x == 0) c.order[slot] = slot;
   const bool active = multipath ? (slot == 0) : (slot < n_active);

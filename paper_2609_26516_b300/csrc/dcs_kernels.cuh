@@ -82,6 +82,7 @@ struct DevCtx {
   int32_t* count;            // number of active slots
   int32_t* status;           // context-wide error bits
   int32_t* plan;             // branch plan scratch
+  unsigned long long* counters;  // [0] compression steps run, [1] sweeps run (since init)
   float2* work;              // per-slot work area of the large-tile kernels (nullptr: small)
   int32_t use_tc;            // large-tile contractions on the tensor cores (3xTF32)
   size_t work_stride;        // complex elements per slot of `work`

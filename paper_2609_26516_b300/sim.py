@@ -122,6 +122,12 @@ class Simulator:
     def bytes_uploaded(self) -> int:
         return int(self.lib.dcs_bytes_uploaded(self.ctx))
 
+    def counters(self):
+        """(compression steps run, one-site sweeps run) since the last init_state."""
+        a, b = ctypes.c_uint64(0), ctypes.c_uint64(0)
+        self._check(self.lib.dcs_get_counters(self.ctx, ctypes.byref(a), ctypes.byref(b)))
+        return int(a.value), int(b.value)
+
     # ------------------------------------------------------------------ calls
     def init_state(self, n_active: int, multipath: bool = False, shot0: int = 0):
         self._check(self.lib.dcs_init_state(self.ctx, n_active, int(multipath), shot0))
