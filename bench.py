@@ -156,6 +156,94 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_brick(args):
+    """Random dynamic brickwork at a bounded depth and shot count: the time of each gate run
+    (compression launches) and of the measurement runs, shots/s and one-site sweeps/s."""
+    import torch
+    import circuits as C
+    from paper_2609_26516_b300 import Simulator
+    shots = args.shots if args.shots != SHOTS else 148
+    circ = C.brickwork(args.n, args.depth, args.p, 3)
+    sim = Simulator(args.n, args.chi, shots, circ.n_cbits, tol=TOL, sweeps=args.sweeps, seed=SEED,
+                    precision=args.precision)
+    runs, run = [], []
+    for o in circ.ops:  # gate runs between measurement groups (each run is one chunk)
+        if isinstance(o, C.Measure):
+            if run:
+                runs.append(run)
+                run = []
+            if runs and isinstance(runs[-1][0], C.Measure):
+                runs[-1].append(o)
+            else:
+                runs.append([o])
+        else:
+            run.append(o)
+    if run:
+        runs.append(run)
+    sim.init_state(shots)
+    layer_ms, meas_ms = [], []
+    n_meas = 0
+    for grp in runs:
+        a = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        a.record(sim.stream)
+        sim.run_circuit(grp, meas_idx0=n_meas)
+        e.record(sim.stream)
+        n_meas += sum(isinstance(o, C.Measure) for o in grp)
+        torch.cuda.synchronize()
+        (meas_ms if isinstance(grp[0], C.Measure) else layer_ms).append(a.elapsed_time(e))
+    n_comp, n_sweeps = sim.counters()
+    total_s = (sum(layer_ms) + sum(meas_ms)) / 1000.0
+    bonds, _, _ = sim.export_mps(0)
+    print(json.dumps({
+        "workload": f"brickwork n={args.n} depth={args.depth} p={args.p} chi_max={args.chi} "
+                    f"s={args.sweeps} shots={shots} precision={'tf32x3' if args.precision else 'fp32'}",
+        "shots_per_s": shots / total_s, "sweeps_per_s": n_sweeps / total_s,
+        "layer_ms": [round(x, 2) for x in layer_ms], "measure_ms_total": round(sum(meas_ms), 2),
+        "max_bond": int(max(bonds)), "F_shot0": float(sim.results()["F"][0])}), flush=True)
+
+
+def run_cgemm(args):
+    """The contraction primitive alone at the site-contraction shape of chi_max: M = 2 chi,
+    N = chi, K = 4 chi complex (the F = T2 R^T product with an MPO bond of 4), one problem
+    per SM, SIMT vs tensor cores."""
+    import ctypes
+    import torch
+    from paper_2609_26516_b300 import _native as N_
+    lib = N_.load()
+    chi = args.chi
+    M, Nn, K = 2 * chi, chi, 4 * chi
+    batch = args.shots if args.shots != SHOTS else 148
+    g = torch.Generator(device="cuda").manual_seed(0)
+    A = torch.randn((batch, M, K), dtype=torch.complex64, device="cuda", generator=g)
+    B = torch.randn((batch, Nn, K), dtype=torch.complex64, device="cuda", generator=g)
+    Cm = torch.zeros((batch, M, Nn), dtype=torch.complex64, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    st = torch.cuda.current_stream()
+    out = {"workload": f"complex GEMM M={M} N={Nn} K={K} batch={batch} (B transposed)",
+           "flops_per_call": 8.0 * M * Nn * K * batch}
+    for mode, name in ((1, "tensor_tf32x3"), (0, "simt_fp32")):
+        times = []
+        for i in range(5):
+            a = torch.cuda.Event(enable_timing=True)
+            e = torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            rc = lib.dcs_cgemm(mode, batch, M, Nn, K, ctypes.c_void_p(A.data_ptr()), K, 1, M * K, 0,
+                               ctypes.c_void_p(B.data_ptr()), 1, K, Nn * K, 0,
+                               ctypes.c_void_p(Cm.data_ptr()), Nn, 1, M * Nn,
+                               ctypes.c_void_p(err.data_ptr()), ctypes.c_void_p(st.cuda_stream))
+            e.record(st)
+            torch.cuda.synchronize()
+            assert rc == 0 and int(err.item()) == 0
+            if i >= 2:
+                times.append(a.elapsed_time(e))
+        ms = statistics.median(times)
+        out[name] = {"ms": ms, "tflops": out["flops_per_call"] / (ms / 1000.0) / 1e12}
+    ref = (A[:2].to(torch.complex128) @ B[:2].to(torch.complex128).transpose(1, 2))
+    out["rel_err_simt_last"] = float((Cm[:2].to(torch.complex128) - ref).norm() / ref.norm())
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -164,9 +252,23 @@ def main():
     ap.add_argument("--impl", default="dcs", choices=["dcs", "reference"])
     ap.add_argument("--shots", type=int, default=SHOTS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="ghz64", choices=["ghz64", "brick", "cgemm"],
+                    help="ghz64: the benchmark line; brick / cgemm: extra measurements")
+    ap.add_argument("--n", type=int, default=40)
+    ap.add_argument("--depth", type=int, default=40)
+    ap.add_argument("--p", type=float, default=0.1)
+    ap.add_argument("--chi", type=int, default=256)
+    ap.add_argument("--sweeps", type=int, default=2)
+    ap.add_argument("--precision", type=int, default=0, help="0 FP32, 1 TF32x3 (large chi)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "brick":
+        run_brick(args)
+        return
+    if args.workload == "cgemm":
+        run_cgemm(args)
         return
     args.warmup = max(args.warmup, 3)
 
