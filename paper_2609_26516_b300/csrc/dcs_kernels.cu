@@ -446,6 +446,25 @@ __device__ void move_centre(const DevCtx& c, Work& sm, int buf, int slot, int& c
 }
 
 // ----------------------------------------------------------------------------- compression
+// The sites the initial guess reads or writes form one interval [lo, hi]: the centre's path
+// from where it stands through every block (q, q+1) of the chunk, plus every site a lone
+// single-qubit gate acts on.  Only these sites are copied into the bra buffer up front; when
+// the guess turns out exact they are copied back in place and the buffers are not swapped.
+__device__ __forceinline__ void guess_range(const DLayer* L, const DBlock* BK, int n, int centre,
+                                            int& lo, int& hi) {
+  lo = hi = centre;
+  for (int j = 0; j < n; ++j)
+    if (L->site[j].kind == 1) {
+      lo = j < lo ? j : lo;
+      hi = j > hi ? j : hi;
+    }
+  for (int ib = 0; ib < L->n_blocks; ++ib) {
+    const int q = BK[L->blk_off + ib].q;
+    lo = q < lo ? q : lo;
+    hi = q + 1 > hi ? q + 1 : hi;
+  }
+}
+
 // one warp per CTA for the small tiles: at most 64 registers so 32 CTAs fit an SM
 template <int NT>
 struct MinBlocks {
@@ -492,8 +511,10 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_compress(DevCtx c,
     sm.iv[7] = 1;    // the guess is exact (no truncation beyond the tolerance) so far
     sm.dv[1] = 1.0;  // product of the kept weight fractions
   }
-  // ---- initial guess: copy the ket, then apply the chunk block by block
-  for (int j = 0; j < n; ++j)
+  // ---- initial guess: copy the sites it touches, then apply the chunk block by block
+  int lo, hi;
+  guess_range(L, BK, n, centre, lo, hi);
+  for (int j = lo; j <= hi; ++j)
     gcopy<NT>(site_ptr(c, bb, slot, j), site_ptr(c, kb, slot, j), sm.abnd[j] * 2 * sm.abnd[j + 1]);
   __syncthreads();
   for (int j = 0; j < n; ++j) {
@@ -586,16 +607,22 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_compress(DevCtx c,
     centre = q;
     __syncthreads();
   }
-  move_centre<NT>(c, sm, bb, slot, centre, 0);
   int* bt = sm.bnd;
   int* at = sm.abnd;
   double fval = 0.0;
   // An exact guess is the target W|A> itself, already the optimum of every one-site update:
-  // the sweeps would return it unchanged (f = 1 up to the tolerance), so they are skipped.
+  // the sweeps would return it unchanged (f = 1 up to the tolerance), so they are skipped and
+  // the touched sites go back into the ket buffer, the centre staying where the guess left it.
   const bool exact = sm.iv[7] != 0;
   if (exact) {
+    for (int j = lo; j <= hi; ++j)
+      gcopy<NT>(site_ptr(c, kb, slot, j), site_ptr(c, bb, slot, j), bt[j] * 2 * bt[j + 1]);
     fval = sm.dv[1];
   } else {
+  for (int j = 0; j < n; ++j)
+    if (j < lo || j > hi) gcopy<NT>(site_ptr(c, bb, slot, j), site_ptr(c, kb, slot, j), at[j] * 2 * at[j + 1]);
+  __syncthreads();
+  move_centre<NT>(c, sm, bb, slot, centre, 0);
   // ---- right environments of the guess: R_j for j = n-1 .. 1 (mirrored env updates)
   if (threadIdx.x == 0) sm.E[0] = make_float2(1.f, 0.f);
   __syncthreads();
@@ -720,12 +747,13 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_compress(DevCtx c,
     }
   }
   }  // not exact
-  // ---- the bra becomes the ket
-  int* obonds = bonds_ptr(c, slot, bb);
+  // ---- the bra becomes the ket (an exact guess was written back into the ket buffer)
+  const int nb_ = exact ? kb : bb;
+  int* obonds = bonds_ptr(c, slot, nb_);
   for (int i = threadIdx.x; i <= n; i += NT) obonds[i] = bt[i];
   if (threadIdx.x == 0) {
     c.centre[slot] = centre;
-    c.ketbuf[slot] = bb;
+    c.ketbuf[slot] = nb_;
     if (!(fval == fval) || fval > 1e300) c.flags[slot] |= DCS_FLAG_NUMERICAL;
     c.F[slot] *= fval;
     if (fid_out) fid_out[slot] = fval;
@@ -839,8 +867,10 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
     sm.dv[1] = 1.0;
   }
   PHASE_START();
-  // ---- initial guess: the chunk applied block by block to a copy of the ket
-  for (int j = 0; j < n; ++j)
+  // ---- initial guess: the chunk applied block by block to a copy of the sites it touches
+  int lo, hi;
+  guess_range(L, BK, n, centre, lo, hi);
+  for (int j = lo; j <= hi; ++j)
     gcopy<NT>(site_ptr(c, bb, slot, j), site_ptr(c, kb, slot, j), at[j] * 2 * at[j + 1]);
   __syncthreads();
   for (int j = 0; j < n; ++j) {
@@ -928,13 +958,18 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
     __syncthreads();
     PHASE_MARK(4);
   }
-  move_centre<NT>(c, sm, bb, slot, centre, 0);
-  PHASE_MARK(5);
   double fval = 0.0;
   const bool exact = sm.iv[7] != 0;  // exact guess: the sweeps are skipped (see k_compress)
   if (exact) {
+    for (int j = lo; j <= hi; ++j)
+      gcopy<NT>(site_ptr(c, kb, slot, j), site_ptr(c, bb, slot, j), bt[j] * 2 * bt[j + 1]);
     fval = sm.dv[1];
   } else {
+  for (int j = 0; j < n; ++j)
+    if (j < lo || j > hi) gcopy<NT>(site_ptr(c, bb, slot, j), site_ptr(c, kb, slot, j), at[j] * 2 * at[j + 1]);
+  __syncthreads();
+  move_centre<NT>(c, sm, bb, slot, centre, 0);
+  PHASE_MARK(5);
   // ---- right environments of the guess (mirrored env updates with B given)
   if (threadIdx.x == 0) sm.E[0] = make_float2(1.f, 0.f);
   __syncthreads();
@@ -1063,11 +1098,12 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
     if (threadIdx.x == 0 && *sm.tc.err) atomicOr(c.status, 1 << DCS_ERR_TIMEOUT);
     tc_teardown(sm.tc);
   }
-  int* obonds = bonds_ptr(c, slot, bb);
+  const int nb_ = exact ? kb : bb;
+  int* obonds = bonds_ptr(c, slot, nb_);
   for (int i = threadIdx.x; i <= n; i += NT) obonds[i] = bt[i];
   if (threadIdx.x == 0) {
     c.centre[slot] = centre;
-    c.ketbuf[slot] = bb;
+    c.ketbuf[slot] = nb_;
     if (!(fval == fval) || fval > 1e300) c.flags[slot] |= DCS_FLAG_NUMERICAL;
     c.F[slot] *= fval;
     if (fid_out) fid_out[slot] = fval;

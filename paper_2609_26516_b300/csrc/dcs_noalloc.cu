@@ -56,7 +56,7 @@ FixedProg g_prog;
 size_t up(size_t x) { return (x + 255) / 256 * 256; }
 
 struct Carve {
-  size_t lc, rc, bonds, ints, dbl, creg, flags, shot, plan, layer, blocks, g1, conds, total;
+  size_t mps, lc, rc, bonds, ints, dbl, creg, flags, shot, plan, layer, blocks, g1, conds, total;
 };
 
 Carve carve(int n, int C) {
@@ -68,6 +68,7 @@ Carve carve(int n, int C) {
     return r;
   };
   const size_t env = (size_t)(n + 1) * 4 * C * C * sizeof(float2);
+  k.mps = take((size_t)n * 2 * C * C * sizeof(float2));  // the second MPS buffer
   k.lc = take(env);
   k.rc = take(env);
   k.bonds = take(2 * (size_t)(n + 1) * sizeof(int32_t));
@@ -89,12 +90,22 @@ struct Creg {
   uint64_t w[DCS_CWORDS];
 };
 
-// Per-call state of the single slot: nothing carries over from the previous call.
-__global__ void k_noalloc_prepare(DevCtx c, const int32_t* ket_bonds, int centre, Creg creg) {
+// Per-call state of the single slot: nothing carries over from the previous call.  The
+// caller's ket is read only: it is copied into the caller's bra buffer, which serves as the
+// slot's first MPS buffer (an exact step updates it in place; otherwise the result lands in
+// the scratch MPS buffer and k_noalloc_finish copies it over).
+__global__ void k_noalloc_prepare(DevCtx c, const int32_t* ket_bonds, int centre, Creg creg,
+                                  const float2* ket) {
   const int n = c.n;
   for (int i = threadIdx.x; i <= n; i += blockDim.x) {
     c.bonds[i] = ket_bonds[i];
     c.bonds[n + 1 + i] = ket_bonds[i];
+  }
+  for (int j = 0; j < n; ++j) {
+    long long len = (long long)ket_bonds[j] * 2 * ket_bonds[j + 1];
+    len = len < 0 ? 0 : (len > (long long)c.site_stride ? (long long)c.site_stride : len);
+    for (int e = threadIdx.x; e < (int)len; e += blockDim.x)
+      c.mps[0][(size_t)j * c.site_stride + e] = ket[(size_t)j * c.site_stride + e];
   }
   if (threadIdx.x < DCS_CWORDS) c.creg[threadIdx.x] = creg.w[threadIdx.x];
   if (threadIdx.x == 0) {
@@ -112,18 +123,20 @@ __global__ void k_noalloc_prepare(DevCtx c, const int32_t* ket_bonds, int centre
   }
 }
 
-// Bond dimensions and centre of the result; a slot left unchanged (every gate skipped by
-// its condition) hands back the input.
+// Bond dimensions and centre of the result.  The bra buffer already holds it unless the
+// step swapped buffers (the sweeps ran): then it is copied over from the scratch buffer.  A
+// slot left unchanged (every gate skipped by its condition) hands back the input.
 __global__ void k_noalloc_finish(DevCtx c, int32_t* bra_bonds, int32_t* bra_centre,
-                                 float2* bra, const float2* ket) {
+                                 float2* bra) {
   const int n = c.n;
   const int buf = c.ketbuf[0];
-  for (int i = threadIdx.x; i <= n; i += blockDim.x) bra_bonds[i] = c.bonds[buf * (n + 1) + i];
-  if (buf == 0) {  // not compressed: copy the ket through
+  const int* bd = c.bonds + buf * (n + 1);
+  for (int i = threadIdx.x; i <= n; i += blockDim.x) bra_bonds[i] = bd[i];
+  if (buf == 1) {
     for (int j = 0; j < n; ++j) {
-      const int len = c.bonds[j] * 2 * c.bonds[j + 1];
+      const int len = bd[j] * 2 * bd[j + 1];
       for (int e = threadIdx.x; e < len; e += blockDim.x)
-        bra[(size_t)j * c.site_stride + e] = ket[(size_t)j * c.site_stride + e];
+        bra[(size_t)j * c.site_stride + e] = c.mps[1][(size_t)j * c.site_stride + e];
     }
   }
   if (threadIdx.x == 0 && bra_centre) *bra_centre = c.centre[0];
@@ -181,8 +194,8 @@ extern "C" dcs_status_t dcs_compress_noalloc(int32_t n_qubits, int32_t chi_max, 
   d.env_stride = 4 * C * C;
   d.mps_slot_stride = (size_t)n_qubits * d.site_stride;
   d.env_slot_stride = (size_t)(n_qubits + 1) * d.env_stride;
-  d.mps[0] = const_cast<float2*>(static_cast<const float2*>(ket));  // read only
-  d.mps[1] = static_cast<float2*>(bra);
+  d.mps[0] = static_cast<float2*>(bra);
+  d.mps[1] = reinterpret_cast<float2*>(base + k.mps);
   d.Lc = reinterpret_cast<float2*>(base + k.lc);
   d.Rc = reinterpret_cast<float2*>(base + k.rc);
   d.bonds = reinterpret_cast<int32_t*>(base + k.bonds);
@@ -207,7 +220,7 @@ extern "C" dcs_status_t dcs_compress_noalloc(int32_t n_qubits, int32_t chi_max, 
 
   Creg cr{};
   if (creg) std::memcpy(cr.w, creg, sizeof(cr.w));
-  k_noalloc_prepare<<<1, 128, 0, s>>>(d, ket_bonds, ket_centre, cr);
+  k_noalloc_prepare<<<1, 128, 0, s>>>(d, ket_bonds, ket_centre, cr, static_cast<const float2*>(ket));
   if (cudaGetLastError() != cudaSuccess) return DCS_ERR_CUDA;
   if (n_gates > 0) {
     // the tables travel from static host storage; a copy from pageable memory returns once
@@ -235,8 +248,7 @@ extern "C" dcs_status_t dcs_compress_noalloc(int32_t n_qubits, int32_t chi_max, 
     if (cudaMemcpyAsync(f, &one, sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess)
       return DCS_ERR_CUDA;
   }
-  k_noalloc_finish<<<1, 128, 0, s>>>(d, bra_bonds, bra_centre, static_cast<float2*>(bra),
-                                     static_cast<const float2*>(ket));
+  k_noalloc_finish<<<1, 128, 0, s>>>(d, bra_bonds, bra_centre, static_cast<float2*>(bra));
   if (cudaGetLastError() != cudaSuccess) return DCS_ERR_CUDA;
   return DCS_OK;
 }
