@@ -256,6 +256,108 @@ __device__ int cta_qr(float2* X, int m, int n, int ld, float2* Q, int ldq, float
   return r;
 }
 
+// ----------------------------------------------------------------------------- warp QR
+// Bond dimensions <= 4: the (m x n) matrix of a centre move (m <= 8 rows, n <= 4 columns)
+// lives in one warp's registers, one complex entry per lane at lane = col * 8 + row and
+// zero outside the matrix; a column sum is a butterfly over the three row bits.
+constexpr unsigned FULL_MASK = 0xffffffffu;
+
+__device__ __forceinline__ float2 shfl2(float2 v, int src) {
+  return make_float2(__shfl_sync(FULL_MASK, v.x, src), __shfl_sync(FULL_MASK, v.y, src));
+}
+__device__ __forceinline__ float colsum8(float v) {
+  v += __shfl_xor_sync(FULL_MASK, v, 1);
+  v += __shfl_xor_sync(FULL_MASK, v, 2);
+  v += __shfl_xor_sync(FULL_MASK, v, 4);
+  return v;
+}
+__device__ __forceinline__ double colsum8d(double v) {
+  v += __shfl_xor_sync(FULL_MASK, v, 1);
+  v += __shfl_xor_sync(FULL_MASK, v, 2);
+  v += __shfl_xor_sync(FULL_MASK, v, 4);
+  return v;
+}
+__device__ __forceinline__ float2 colsum8c(float2 v) {
+  return make_float2(colsum8(v.x), colsum8(v.y));
+}
+
+// Householder QR of the warp matrix x (m x n, m <= 8, n <= 4): the same reflectors as
+// cta_qr (unit vectors u_k = (x - alpha_k e_k) / ||x - alpha_k e_k||, alpha_k of modulus
+// ||x|| and phase opposite to x_k; FP32 norms, redone in FP64 below 1e-30; a zero column
+// gets H_k = I).  On return x holds R (r x n, upper triangular, rows >= r zero) and q holds
+// the explicit Q = H_0 ... H_{r-1} [I_r; 0] (m x r), r = min(m, n), both in the warp layout.
+// Every lane of the warp must call it with the same m and n.
+__device__ __forceinline__ int warp_qr8x4(float2& x, int m, int n, float2& q) {
+  const int lane = threadIdx.x & 31, row = lane & 7, col = lane >> 3;
+  const int r = m < n ? m : n;
+  float2 U = cz();  // reflector `col` at this lane's row
+  for (int k = 0; k < r; ++k) {
+    const bool in_k = col == k && row >= k && row < m;
+    const float s32 = __shfl_sync(FULL_MASK, colsum8(in_k ? cabs2(x) : 0.f), k * 8);
+    const float2 x0 = shfl2(x, k * 8 + k);
+    const float2 xk = shfl2(x, k * 8 + row);  // X[row][k]
+    float2 u = cz(), alpha = cz();
+    bool skip = false;
+    if (s32 > 1e-30f) {
+      const float nrm = sqrtf(s32);
+      const float a0 = hypotf(x0.x, x0.y);
+      const float inv = 1.f / sqrtf(2.f * nrm * (nrm + a0));
+      alpha = a0 > 0.f ? make_float2(-x0.x / a0 * nrm, -x0.y / a0 * nrm) : make_float2(-nrm, 0.f);
+      if (row >= k && row < m) {
+        u = xk;
+        if (row == k) u = csub(u, alpha);
+        u = cscale(u, inv);
+      }
+    } else {
+      const double sd = __shfl_sync(FULL_MASK, colsum8d(in_k ? cabs2d(x) : 0.0), k * 8);
+      const double nrm = sqrt(sd);
+      const double a0 = sqrt(cabs2d(x0));
+      const double vn = sqrt(2.0 * nrm * (nrm + a0));
+      skip = !(vn > 0.0);
+      if (!skip) {
+        double ar = -nrm, ai = 0.0;
+        if (a0 > 0.0) {
+          ar = -(double)x0.x / a0 * nrm;
+          ai = -(double)x0.y / a0 * nrm;
+        }
+        alpha = make_float2((float)ar, (float)ai);
+        if (row >= k && row < m) {
+          double vr = xk.x, vi = xk.y;
+          if (row == k) {
+            vr -= ar;
+            vi -= ai;
+          }
+          u = make_float2((float)(vr / vn), (float)(vi / vn));
+        }
+      }
+    }
+    if (!skip) {
+      float2 d = cz();
+      if (col > k && col < n) cfmac(d, u, x);
+      d = colsum8c(d);
+      if (col > k && col < n) {
+        x.x -= 2.f * (u.x * d.x - u.y * d.y);
+        x.y -= 2.f * (u.x * d.y + u.y * d.x);
+      }
+      if (col == k && row >= k) x = row == k ? alpha : cz();
+    }
+    if (col == k) U = u;
+  }
+  float2 qv = make_float2(row == col && col < r ? 1.f : 0.f, 0.f);
+  for (int k = r - 1; k >= 0; --k) {
+    const float2 uk = shfl2(U, k * 8 + row);
+    float2 d = cz();
+    if (col < r) cfmac(d, uk, qv);
+    d = colsum8c(d);
+    if (col < r) {
+      qv.x -= 2.f * (uk.x * d.x - uk.y * d.y);
+      qv.y -= 2.f * (uk.x * d.y + uk.y * d.x);
+    }
+  }
+  q = qv;
+  return r;
+}
+
 // ----------------------------------------------------------------------------- SVD
 // One-sided (Hestenes) Jacobi SVD of X (m x n, column-major, ld): rotates pairs of columns
 // until they are mutually orthogonal, X V = U Sigma, accumulating the unitary V (n x n,

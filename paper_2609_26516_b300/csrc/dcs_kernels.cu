@@ -23,6 +23,27 @@ namespace dcs {
 
 // ----------------------------------------------------------------------------- helpers
 
+// Optional per-phase cycle counters of the compression and measurement kernels (built with
+// -DDCS_PHASE_TIMERS; read back with dcs_debug_phase_cycles).  Off in normal builds.
+// Slots 0-9: large-tile compression; 10-15: small-tile compression; 16-17: measurement.
+#ifdef DCS_PHASE_TIMERS
+__device__ unsigned long long g_phase_cycles[24];
+#define PHASE_START() long long _pt = clock64()
+#define PHASE_MARK(i)                                                                     \
+  do {                                                                                    \
+    __syncthreads();                                                                      \
+    if (threadIdx.x == 0) {                                                               \
+      const long long _n = clock64();                                                     \
+      atomicAdd(&g_phase_cycles[i], (unsigned long long)(_n - _pt));                      \
+      _pt = _n;                                                                           \
+    }                                                                                     \
+  } while (0)
+#else
+#define PHASE_START()
+#define PHASE_MARK(i)
+#endif
+
+
 __device__ __forceinline__ bool cond_holds(const DCond& cd, const uint64_t* c) {
   if (cd.op == DCS_COND_NONE) return true;
   if (cd.op == DCS_COND_XOR) {
@@ -111,6 +132,10 @@ __device__ __noinline__ void build_W(int j, const DLayer* L, const DBlock* BK, c
 
 // G_blk = (Post_q x Post_{q+1}) G2 (Pre_q x Pre_{q+1}), row-major 4x4.  One thread.
 __device__ __noinline__ void build_block(const DBlock& b, const DGate1* G1, const uint64_t* c, float2* G) {
+  if (b.composed) {
+    for (int i = 0; i < 16; ++i) G[i] = b.Gc[i];
+    return;
+  }
   float2 Pre0[4], Post0[4], Pre1[4], Post1[4];
   prod1q(G1, b.pre_off[0], b.pre_n[0], c, Pre0);
   prod1q(G1, b.post_off[0], b.post_n[0], c, Post0);
@@ -432,9 +457,89 @@ __device__ void hop_left(const DevCtx& c, Work& sm, int buf, int slot, int j) {
   __syncthreads();
 }
 
+// Every bond <= 4, one warp per slot: a run of centre moves with the moving centre tensor
+// kept in registers (warp layout of warp_qr8x4).  Each hop is the same gauge move as
+// hop_right / hop_left; only the hop's Q goes to memory, and the centre tensor once at the
+// end of the run.
+__device__ void warp_move_centre4(const DevCtx& c, Work& sm, int buf, int slot, int& centre,
+                                  int target) {
+  if (centre == target) return;
+  const int lane = threadIdx.x & 31, row = lane & 7, col = lane >> 3;
+  int* b = sm.bnd;
+  int j = centre;
+  float2 x = cz();
+  if (target > centre) {
+    // X_j: rows (a s) = a * 2 + s, columns x; T_j[a][s][x] at (a * 2 + s) * br + x
+    int bl = b[j];
+    {
+      const int br = b[j + 1];
+      if (row < 2 * bl && col < br) x = site_ptr(c, buf, slot, j)[row * br + col];
+    }
+    while (j < target) {
+      const int br = b[j + 1], bn = b[j + 2];
+      float2 q;
+      const int r = warp_qr8x4(x, 2 * bl, br, q);
+      if (row < 2 * bl && col < r) site_ptr(c, buf, slot, j)[row * r + col] = q;
+      // T_{j+1} := R T_{j+1}, produced directly in the layout of the next hop
+      const float2* nx = site_ptr(c, buf, slot, j + 1);
+      const int k = row >> 1, sp = row & 1;
+      const bool live = k < r && col < bn;
+      float2 acc = cz();
+      for (int y = 0; y < br; ++y) {
+        const float2 ry = shfl2(x, y * 8 + k);
+        if (live) cfma(acc, ry, nx[(y * 2 + sp) * bn + col]);
+      }
+      x = live ? acc : cz();
+      if (lane == 0) b[j + 1] = r;
+      bl = r;
+      ++j;
+    }
+    const int br = b[j + 1];
+    if (row < 2 * bl && col < br) site_ptr(c, buf, slot, j)[row * br + col] = x;
+  } else {
+    // mirrored: X'_j rows (x t) = x * 2 + t, columns a; T_j[a][t][x] at (a * 2 + t) * br + x
+    int br = b[j + 1];
+    {
+      const int bl = b[j];
+      if (row < 2 * br && col < bl) x = site_ptr(c, buf, slot, j)[(col * 2 + (row & 1)) * br + (row >> 1)];
+    }
+    while (j > target) {
+      const int bl = b[j], bp = b[j - 1];
+      float2 q;
+      const int r = warp_qr8x4(x, 2 * br, bl, q);
+      // T_j[k][t][x] := Q'[(x t)][k]
+      if (row < 2 * br && col < r) site_ptr(c, buf, slot, j)[(col * 2 + (row & 1)) * br + (row >> 1)] = q;
+      // T_{j-1}[a'][s][k] := sum_a T_{j-1}[a'][s][a] R'[k][a], in the mirrored layout of the
+      // next hop: lane (a', k * 2 + s)
+      const float2* pv = site_ptr(c, buf, slot, j - 1);
+      const int k = row >> 1, sp = row & 1;
+      const bool live = k < r && col < bp;
+      float2 acc = cz();
+      for (int a = 0; a < bl; ++a) {
+        const float2 ra = shfl2(x, a * 8 + k);
+        if (live) cfma(acc, pv[(col * 2 + sp) * bl + a], ra);
+      }
+      x = live ? acc : cz();
+      if (lane == 0) b[j] = r;
+      br = r;
+      --j;
+    }
+    const int bl = b[j];
+    if (row < 2 * br && col < bl) site_ptr(c, buf, slot, j)[(col * 2 + (row & 1)) * br + (row >> 1)] = x;
+  }
+  centre = target;
+  __syncwarp();
+}
+
 template <int NT>
 __device__ void move_centre(const DevCtx& c, Work& sm, int buf, int slot, int& centre,
                             int target) {
+  if constexpr (NT == 32) {
+    if (sm.C == 4) {
+      warp_move_centre4(c, sm, buf, slot, centre, target);
+      return;
+    }
+  }
   while (centre < target) {
     hop_right<NT>(c, sm, buf, slot, centre);
     ++centre;
@@ -511,6 +616,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_compress(DevCtx c,
     sm.iv[7] = 1;    // the guess is exact (no truncation beyond the tolerance) so far
     sm.dv[1] = 1.0;  // product of the kept weight fractions
   }
+  PHASE_START();
   // ---- initial guess: copy the sites it touches, then apply the chunk block by block
   int lo, hi;
   guess_range(L, BK, n, centre, lo, hi);
@@ -539,7 +645,9 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_compress(DevCtx c,
   for (int ib = 0; ib < L->n_blocks; ++ib) {
     const DBlock& blk = BK[L->blk_off + ib];
     const int q = blk.q;
+    PHASE_MARK(10);
     move_centre<NT>(c, sm, bb, slot, centre, q + 1);
+    PHASE_MARK(11);
     const int b0 = sm.bnd[q], b1 = sm.bnd[q + 1], b2 = sm.bnd[q + 2];
     gcopy<NT>(sm.S, site_ptr(c, bb, slot, q), b0 * 2 * b1);
     gcopy<NT>(sm.F, site_ptr(c, bb, slot, q + 1), b1 * 2 * b2);
@@ -577,7 +685,9 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_compress(DevCtx c,
         for (int u = 0; u < 2; ++u) X[(a * 2 + s) + (u * b2 + bcol) * m] = out[s * 2 + u];
     }
     __syncthreads();
+    PHASE_MARK(12);
     cta_jacobi_svd<NT>(X, m, nn, m, V, nn, sm.sig2, sm.perm, &sm.iv[5], sm.red);
+    PHASE_MARK(13);
     if (threadIdx.x == 0) {
       const int k = trunc_rank(sm.sig2, sm.perm, nn, c.chi_max, c.tol);
       double w = 0.0, tot = 0.0;
@@ -606,7 +716,9 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_compress(DevCtx c,
     if (threadIdx.x == 0) sm.bnd[q + 1] = k;
     centre = q;
     __syncthreads();
+    PHASE_MARK(14);
   }
+  PHASE_MARK(10);
   int* bt = sm.bnd;
   int* at = sm.abnd;
   double fval = 0.0;
@@ -747,6 +859,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_compress(DevCtx c,
     }
   }
   }  // not exact
+  PHASE_MARK(15);
   // ---- the bra becomes the ket (an exact guess was written back into the ket buffer)
   const int nb_ = exact ? kb : bb;
   int* obonds = bonds_ptr(c, slot, nb_);
@@ -767,24 +880,6 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_compress(DevCtx c,
 // ----------------------------------------------------------------------------- large tiles
 constexpr int BIG_NT = 512;
 
-// Optional per-phase cycle counters of the large-tile kernel (built with
-// -DDCS_PHASE_TIMERS; read back with dcs_debug_phase_cycles).  Off in normal builds.
-#ifdef DCS_PHASE_TIMERS
-__device__ unsigned long long g_phase_cycles[16];
-#define PHASE_START() long long _pt = clock64()
-#define PHASE_MARK(i)                                                                     \
-  do {                                                                                    \
-    __syncthreads();                                                                      \
-    if (threadIdx.x == 0) {                                                               \
-      const long long _n = clock64();                                                     \
-      atomicAdd(&g_phase_cycles[i], (unsigned long long)(_n - _pt));                      \
-      _pt = _n;                                                                           \
-    }                                                                                     \
-  } while (0)
-#else
-#define PHASE_START()
-#define PHASE_MARK(i)
-#endif
 
 // T2[b][s][e][x] = sum_{d,t} T1(b, d, t, x) W(d, s, t, e) with T1 at
 // b*ib + d*id + t*it + x*ix and T2 natural (b-stride 2 ne nx); mirrored: the coefficient is
@@ -1138,9 +1233,12 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_measure(DevCtx c, 
   for (int i = threadIdx.x; i <= n; i += NT) sm.bnd[i] = kbonds[i];
   __syncthreads();
   int centre = c.centre[slot];
+  PHASE_START();
   for (int im = 0; im < n_meas; ++im) {
     const int q = meas[im].q;
+    PHASE_MARK(17);
     move_centre<NT>(c, sm, kb, slot, centre, q);
+    PHASE_MARK(16);
     const int bl = sm.bnd[q], br = sm.bnd[q + 1];
     float2* A = site_ptr(c, kb, slot, q);
     double s0 = 0.0, s1 = 0.0;
@@ -1542,12 +1640,12 @@ void launch_branch_topk(const DevCtx& c, int M, cudaStream_t s) {
 }  // namespace dcs
 
 #ifdef DCS_PHASE_TIMERS
-// Debug builds only: the large-tile kernel's per-phase cycle sums (not part of the ABI).
+// Debug builds only: the kernels' per-phase cycle sums, 24 slots (not part of the ABI).
 extern "C" int dcs_debug_phase_cycles(unsigned long long* out, int reset) {
-  if (cudaMemcpyFromSymbol(out, dcs::g_phase_cycles, sizeof(unsigned long long) * 16) != cudaSuccess)
+  if (cudaMemcpyFromSymbol(out, dcs::g_phase_cycles, sizeof(unsigned long long) * 24) != cudaSuccess)
     return 1;
   if (reset) {
-    unsigned long long z[16] = {0};
+    unsigned long long z[24] = {0};
     cudaMemcpyToSymbol(dcs::g_phase_cycles, z, sizeof(z));
   }
   return 0;

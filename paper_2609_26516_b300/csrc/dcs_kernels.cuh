@@ -31,6 +31,8 @@ struct DBlock {
   float2 WR[16];    // WR[(d*2+u)*2 + v]: right factor
   DCond cond;       // condition of G2 (op NONE: unconditional)
   int32_t pre_off[2], pre_n[2], post_off[2], post_n[2];  // into the DGate1 array
+  int32_t composed;  // 1: no gate of the block is conditional and Gc holds the whole block
+  float2 Gc[16];     // (Post_q x Post_{q+1}) G2 (Pre_q x Pre_{q+1}), composed in FP64
 };
 
 // Per-site description of a chunk.

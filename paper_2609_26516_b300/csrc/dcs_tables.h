@@ -197,6 +197,47 @@ const char* build_layer(Prog& P, int n, const dcs_op* gates, int n_gates) {
         }
       B.post_n[side] = (int)P.g1.size() - B.post_off[side];
     }
+    // a block without conditional gates is the same on every slot: compose it here
+    bool fixed = o2.cond.op == DCS_COND_NONE;
+    for (int i = 0; i < n_gates && fixed; ++i)
+      if (gates[i].kind == DCS_OP_GATE1 && (gates[i].q0 == q || gates[i].q0 == q + 1) &&
+          gates[i].cond.op != DCS_COND_NONE)
+        fixed = false;
+    B.composed = fixed ? 1 : 0;
+    if (fixed) {
+      // one-qubit products, later gates on the left: pre[side], post[side]
+      cd pre[2][4], post[2][4];
+      for (int side = 0; side < 2; ++side) {
+        const int qq = q + side;
+        for (int part = 0; part < 2; ++part) {
+          cd* U = part == 0 ? pre[side] : post[side];
+          U[0] = 1.0; U[1] = 0.0; U[2] = 0.0; U[3] = 1.0;
+          const int i0 = part == 0 ? 0 : two_pos[q] + 1, i1 = part == 0 ? two_pos[q] : n_gates;
+          for (int i = i0; i < i1; ++i) {
+            if (gates[i].kind != DCS_OP_GATE1 || gates[i].q0 != qq) continue;
+            cd m[4], o[4];
+            int l2;
+            gate_matrix(gates[i], m, l2);
+            for (int r = 0; r < 2; ++r)
+              for (int k = 0; k < 2; ++k) o[r * 2 + k] = m[r * 2 + 0] * U[0 * 2 + k] + m[r * 2 + 1] * U[1 * 2 + k];
+            for (int e = 0; e < 4; ++e) U[e] = o[e];
+          }
+        }
+      }
+      cd Mx[16];
+      for (int oi = 0; oi < 4; ++oi)  // Mx = G2 (pre_q x pre_{q+1})
+        for (int ii = 0; ii < 4; ++ii) {
+          cd acc = 0.0;
+          for (int k = 0; k < 4; ++k) acc += G[oi * 4 + k] * pre[0][(k >> 1) * 2 + (ii >> 1)] * pre[1][(k & 1) * 2 + (ii & 1)];
+          Mx[oi * 4 + ii] = acc;
+        }
+      for (int oi = 0; oi < 4; ++oi)  // Gc = (post_q x post_{q+1}) Mx
+        for (int ii = 0; ii < 4; ++ii) {
+          cd acc = 0.0;
+          for (int k = 0; k < 4; ++k) acc += post[0][(oi >> 1) * 2 + (k >> 1)] * post[1][(oi & 1) * 2 + (k & 1)] * Mx[k * 4 + ii];
+          B.Gc[oi * 4 + ii] = make_float2((float)acc.real(), (float)acc.imag());
+        }
+    }
     L.site[q].kind = 2;
     L.site[q].blk = (int)bi;
     L.site[q + 1].kind = 3;
