@@ -20,14 +20,23 @@ The paper states only the one-site update.  Readings used for what it leaves ope
    disjoint blocks; the initial bra is A with every block applied gate-by-gate in
    canonical form, two-qubit blocks followed by a truncated SVD of the two-site tensor
    (keep the smallest rank k <= chi_max whose discarded weight sum_{i>=k} s_i^2 is
-   <= tol * sum_i s_i^2).  Without truncation this guess is the exact W|A>.
-2. Then s one-site sweeps against the exact target W|A> (W the chunk's MPO): left to
+   <= tol * sum_i s_i^2).  Without truncation this guess is the exact W|A>.  The two-qubit
+   blocks are taken in order of q starting from the end of the layer nearest to the
+   orthogonality centre (ascending when |c - q_min| <= |c - (q_max + 1)|), the centre
+   moved to the nearer site of each block, and the singular values put on the site facing
+   the next block (B_q = U, B_{q+1} = S Vh ascending; B_q = U S, B_{q+1} = Vh descending),
+   so the centre crosses the layer once.
+2. If no block discarded more than the tolerance (sum_{i>=k} s_i^2 <= tol * sum_i s_i^2
+   for every block), the guess is W|A> up to that tolerance and is itself the optimum the
+   sweeps converge to (f = 1 up to rounding): the sweeps are skipped, f is the product of
+   the kept weight fractions and the centre stays where the guess left it.
+3. Otherwise s one-site sweeps against the exact target W|A> (W the chunk's MPO): left to
    right first, alternating; each site takes F / ||F|| re-orthonormalised by QR (LQ when
    moving right to left), the triangular factor being dropped because the next site's
    update is recomputed from the environments.  One direction is one sweep; with s even
    the centre ends at site 0, with s odd at site n-1.  Bond dimensions do not change in
    the sweeps.
-3. f is ||F||^2 at the last update of the last sweep: B is normalised with every other
+4. f is ||F||^2 at the last update of the last sweep: B is normalised with every other
    site orthonormal, W unitary and A normalised, so ||F|| = |<B|W A>|.
 """
 from __future__ import annotations
@@ -165,40 +174,62 @@ class CompressInfo:
 
 
 def initial_guess(A: MPS, blocks, chi_max: int, tol: float):
-    """Initial bra: the chunk applied block by block to a copy of A, right to left, in
-    canonical form (the usual gate-by-gate update).  A two-qubit block G on (q, q+1):
-    move the centre to q+1, Theta[a,s,u,b] = sum G[s,u,t,v] A_q[a,t,x] A_{q+1}[x,v,b],
-    truncated SVD of Theta as (2 chi_q) x (2 chi_{q+2}) with rank ``trunc_rank(s, chi_max,
-    tol)``, B_q := U S / ||S||, B_{q+1} := Vh (centre q).  A single-qubit block U on q:
-    B_q[a,s,b] = sum_t U[s,t] A_q[a,t,b].  Returns (B, kept weights)."""
+    """Initial bra: the chunk applied block by block to a copy of A in canonical form (the
+    usual gate-by-gate update), blocks ordered as in reading 1 of the module header.  A
+    two-qubit block G on (q, q+1): move the centre to the nearer of q, q+1,
+    Theta[a,s,u,b] = sum G[s,u,t,v] A_q[a,t,x] A_{q+1}[x,v,b], truncated SVD of Theta as
+    (2 chi_q) x (2 chi_{q+2}) with rank ``trunc_rank(s, chi_max, tol)``; S / ||S|| goes to
+    q+1 (ascending order, centre q+1) or to q (descending, centre q).  A single-qubit block
+    U on q: B_q[a,s,b] = sum_t U[s,t] A_q[a,t,b].  Returns (B, kept weight fractions,
+    exact), exact meaning no block discarded more than tol of its weight."""
     B = A.copy()
     kept = []
-    for q, G in sorted(blocks, key=lambda x: -x[0]):
+    exact = True
+    two = sorted((q, G) for q, G in blocks if G.shape == (4, 4))
+    for q, G in blocks:
         if G.shape == (2, 2):
             B.T[q] = np.einsum("st,atb->asb", G, B.T[q])
-            continue
-        move_centre(B, q + 1)
+    if two:
+        c = B.centre
+        ascending = abs(c - two[0][0]) <= abs(c - (two[-1][0] + 1))
+        if not ascending:
+            two = two[::-1]
+    for q, G in two:
+        move_centre(B, q if B.centre <= q else q + 1)
         th = np.einsum("asx,xtb->astb", B.T[q], B.T[q + 1])
         th = np.einsum("uvst,astb->auvb", G.reshape(2, 2, 2, 2), th)
         al, br = th.shape[0], th.shape[3]
         U, s, Vh = np.linalg.svd(th.reshape(al * 2, 2 * br), full_matrices=False)
         k = trunc_rank(s, chi_max, tol)
         w = float(np.sum(s[:k] ** 2))
-        kept.append(w / float(np.sum(s ** 2)))
-        B.T[q] = (U[:, :k] * (s[None, :k] / np.sqrt(w))).reshape(al, 2, k)
-        B.T[q + 1] = Vh[:k].reshape(k, 2, br)
-        B.centre = q
-    return B, kept
+        tot = float(np.sum(s ** 2))
+        kept.append(w / tot)
+        if tot - w > tol * tot:
+            exact = False
+        sk = s[:k] / np.sqrt(w)
+        if ascending:
+            B.T[q] = U[:, :k].reshape(al, 2, k)
+            B.T[q + 1] = (sk[:, None] * Vh[:k]).reshape(k, 2, br)
+            B.centre = q + 1
+        else:
+            B.T[q] = (U[:, :k] * sk[None, :]).reshape(al, 2, k)
+            B.T[q + 1] = Vh[:k].reshape(k, 2, br)
+            B.centre = q
+    return B, kept, exact
 
 
-def compress(A: MPS, blocks, W, chi_max: int, tol: float, sweeps: int):
+def compress(A: MPS, blocks, W, chi_max: int, tol: float, sweeps: int, skip_exact: bool = True):
     """CompressionStep (Sec. "Simulating unitary quantum circuits with DMRG") with the
     readings in the module header.  ``blocks`` is the chunk as [(q, 4x4 or 2x2 matrix)],
-    W its MPO.  A is not modified.  Returns (B, info), B normalised with centre 0 (sweeps
-    even) or n-1 (odd)."""
+    W its MPO.  A is not modified.  Returns (B, info), B normalised; after the sweeps its
+    centre is 0 (sweeps even) or n-1 (odd); an exact guess (reading 2) is returned as it is
+    unless ``skip_exact`` is False, which runs the sweeps on it all the same."""
     assert sweeps >= 1
     n = A.n
-    B0, kept = initial_guess(A, blocks, chi_max, tol)
+    B0, kept, exact = initial_guess(A, blocks, chi_max, tol)
+    if exact and skip_exact:
+        f = float(np.prod(kept)) if kept else 1.0
+        return B0, CompressInfo(f, [], kept)
     move_centre(B0, 0)
     B = B0.T
     one = np.ones((1, 1, 1), dtype=np.complex128)

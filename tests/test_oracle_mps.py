@@ -123,11 +123,43 @@ def test_compress_exact_regime_equals_statevector(n):
     blocks = _layer_blocks(rng, n, 1) + [(0, C.haar_unitary(rng, 2))]
     W = LY.blocks_mpo(n, blocks)
     want = LY.chunk_unitary_dense(n, W) @ dense(A)
+    # the guess is exact: returned as it is (the sweeps are skipped)
+    B, info = M.compress(A.copy(), blocks, W, 64, 0.0, 2)
+    assert info.fidelities_per_sweep == []
+    assert abs(info.f - 1.0) < 1e-12
+    assert abs(abs(np.vdot(dense(B), want)) - 1.0) < 1e-12
+    # ... and sweeping it all the same returns the same state: the shortcut loses nothing
     for s in (1, 2, 3):
-        B, info = M.compress(A.copy(), blocks, W, 64, 0.0, s)
+        B2, info = M.compress(A.copy(), blocks, W, 64, 0.0, s, skip_exact=False)
         assert abs(info.f - 1.0) < 1e-12
-        assert abs(abs(np.vdot(dense(B), want)) - 1.0) < 1e-12
-        assert B.centre == (0 if s % 2 == 0 else n - 1)
+        assert abs(abs(np.vdot(dense(B2), dense(B))) - 1.0) < 1e-12
+        assert B2.centre == (0 if s % 2 == 0 else n - 1)
+
+
+@pytest.mark.parametrize("centre", [0, 3, 8])
+def test_guess_block_order_starts_nearest_the_centre(centre):
+    # n = 9, blocks on (1,2), (3,4), (5,6): from the left end the guess runs ascending and
+    # leaves the centre at q_max + 1 = 6; from the right end descending, centre q_min = 1.
+    rng = np.random.default_rng(5)
+    n = 9
+    A = random_mps(rng, n, 2)
+    M.move_centre(A, centre)
+    blocks = [(q, C.haar_su4(rng)) for q in (1, 3, 5)]
+    W = LY.blocks_mpo(n, blocks)
+    want = LY.chunk_unitary_dense(n, W) @ dense(A)
+    B, kept, exact = M.initial_guess(A, blocks, 64, 0.0)
+    assert exact and all(abs(x - 1.0) < 1e-12 for x in kept)
+    assert B.centre == (6 if centre <= 4 else 1)
+    assert abs(abs(np.vdot(dense(B), want)) - 1.0) < 1e-12
+    # canonical form around the centre: left sites left-orthonormal, right sites right-
+    for j, t in enumerate(B.T):
+        al, _, ar = t.shape
+        if j < B.centre:
+            m = t.reshape(al * 2, ar)
+            np.testing.assert_allclose(m.conj().T @ m, np.eye(ar), atol=1e-12)
+        elif j > B.centre:
+            m = t.reshape(al, 2 * ar)
+            np.testing.assert_allclose(m @ m.conj().T, np.eye(al), atol=1e-12)
 
 
 @pytest.mark.parametrize("seed", [1, 2, 3])
