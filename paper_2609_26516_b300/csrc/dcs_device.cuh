@@ -308,6 +308,8 @@ __device__ __forceinline__ int warp_qr8x4(float2& x, int m, int n, float2& q) {
         if (row == k) u = csub(u, alpha);
         u = cscale(u, inv);
       }
+    } else if (!__any_sync(FULL_MASK, in_k && (x.x != 0.f || x.y != 0.f))) {
+      skip = true;  // an exactly zero column (common after a collapse): H_k = I, no FP64
     } else {
       const double sd = __shfl_sync(FULL_MASK, colsum8d(in_k ? cabs2d(x) : 0.0), k * 8);
       const double nrm = sqrt(sd);
@@ -366,11 +368,11 @@ __device__ __forceinline__ int warp_qr8x4(float2& x, int m, int n, float2& q) {
 // Gram [[a, g], [conj g, b]] is rotated when |g| > 2 sqrt(m) eps sqrt(a b):
 // zeta = (b - a) / (2|g|), t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1+t^2),
 // s = c t, x_i' = c x_i - s e^{-i phi} x_j, x_j' = s x_i + c e^{-i phi} x_j, g = |g| e^{i phi}.
-// Afterwards sig2[j] = ||x_j||^2 and perm[0..n) lists columns by decreasing norm
-// (ties: lower index first).  Scratch: red[NT/32], flag (int).
+// Afterwards sig2[j] = sigf[j] = ||x_j||^2 (FP32 sum) and perm[0..n) lists columns by
+// decreasing norm (ties: lower index first).  Scratch: red[NT/32], flag (int).
 template <int NT>
 __device__ void cta_jacobi_svd(float2* X, int m, int n, int ld, float2* V, int ldv,
-                               double* sig2, int* perm, int* flag, double* red) {
+                               double* sig2, float* sigf, int* perm, int* flag, double* red) {
   for (int idx = threadIdx.x; idx < n * n; idx += NT) {
     const int i = idx % n, j = idx / n;
     V[i + j * ldv] = make_float2(i == j ? 1.f : 0.f, 0.f);
@@ -451,23 +453,83 @@ __device__ void cta_jacobi_svd(float2* X, int m, int n, int ld, float2* V, int l
     if (*flag == 0) break;
     __syncthreads();
   }
-  // column norms (FP64) and ordering
+  // column norms (FP32 sums, also handed out in FP64) and their ordering
   for (int j = threadIdx.x; j < n; j += NT) {
     float s = 0.f;
     for (int i = 0; i < m; ++i) s += cabs2(X[i + j * ld]);
+    sigf[j] = s;
     sig2[j] = (double)s;
   }
   __syncthreads();
   for (int j = threadIdx.x; j < n; j += NT) {
     int rank = 0;
-    const double sj = sig2[j];
+    const float sj = sigf[j];
     for (int i = 0; i < n; ++i) {
-      const double si = sig2[i];
+      const float si = sigf[i];
       rank += (si > sj) || (si == sj && i < j);
     }
     perm[rank] = j;
   }
   __syncthreads();
+}
+
+// ----------------------------------------------------------------------------- float-float
+// Sums of squares to about FP64 accuracy on the FP32 pipe (an FP64 instruction costs a
+// whole warp dozens of cycles on this part): a value is an unevaluated sum hi + lo, squares
+// are split exactly with an FMA, additions use Knuth's TwoSum.  The _rn intrinsics keep
+// the compiler from contracting the error terms.
+struct ffloat {
+  float hi, lo;
+};
+__device__ __forceinline__ ffloat ff_add(ffloat a, ffloat b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bb = __fsub_rn(s, a.hi);
+  const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  const float t = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  const float hi = __fadd_rn(s, t);
+  return {hi, __fsub_rn(t, __fsub_rn(hi, s))};
+}
+__device__ __forceinline__ ffloat ff_abs2(float2 x) {
+  const float p = __fmul_rn(x.x, x.x), q = __fmul_rn(x.y, x.y);
+  const ffloat a{p, fmaf(x.x, x.x, -p)}, b{q, fmaf(x.y, x.y, -q)};
+  return ff_add(a, b);
+}
+__device__ __forceinline__ ffloat ff_warp_sum(ffloat a) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const ffloat b{__shfl_xor_sync(FULL_MASK, a.hi, o), __shfl_xor_sync(FULL_MASK, a.lo, o)};
+    a = ff_add(a, b);
+  }
+  return a;
+}
+__device__ __forceinline__ double ff_to_double(ffloat a) { return (double)a.hi + (double)a.lo; }
+
+// Warp version of trunc_rank for n <= 32 values, FP32: lane i takes the i-th largest value
+// w_(i) = sigf[perm[i]]; returns k and sets kept = sum_{i<k} w_(i), disc = sum_{i>=k} w_(i).
+__device__ __forceinline__ int warp_trunc_rank(const float* sigf, const int* perm, int n, int cap,
+                                               double tol, float& kept, float& disc) {
+  const int lane = threadIdx.x & 31;
+  const float v = lane < n ? sigf[perm[lane]] : 0.f;
+  float S = v;  // suffix sums S_i = sum_{j >= i} w_(j)
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float t = __shfl_down_sync(FULL_MASK, S, o);
+    if (lane + o < 32) S += t;
+  }
+  const float tot = __shfl_sync(FULL_MASK, S, 0);
+  const float lim = (float)tol * tot;
+  const unsigned keep = __ballot_sync(FULL_MASK, lane >= 1 && lane < n && S > lim);
+  int k = keep ? 32 - __clz(keep) : 1;
+  if (k > cap) k = cap;
+  if (k > n) k = n;
+  if (k < 1) k = 1;
+  disc = k < 32 ? __shfl_sync(FULL_MASK, S, k & 31) : 0.f;
+  if (k >= n) disc = 0.f;
+  float w = lane < k ? v : 0.f;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(FULL_MASK, w, o);
+  kept = w;
+  return k;
 }
 
 // Smallest k >= 1 with sum_{i >= k} w_(i) <= tol * sum_i w_i, w_(i) the values in

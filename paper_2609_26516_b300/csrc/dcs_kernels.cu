@@ -297,6 +297,7 @@ struct Work {
   double* sig2;
   double* dv;  // scalar broadcast
   float* tau;
+  float* sigf;  // singular values squared, FP32 (2C)
   int* perm;
   int* bnd;    // bonds being modified [n+1]
   int* abnd;   // bonds of the ket [n+1]
@@ -309,7 +310,7 @@ struct Work {
 __host__ __device__ inline size_t work_small_bytes(int C, bool big, bool tc = false) {
   return (tc ? sizeof(float) * TC_SMEM_FLOATS + 64 : 0) +
          sizeof(float2) * (64 + 64 + 16 + 2 * C + (big ? (GBM + GBN) * GBK : 0)) +
-         sizeof(double) * (32 + 2 * C + 8) + sizeof(float) * 2 * C +
+         sizeof(double) * (32 + 2 * C + 8) + sizeof(float) * 4 * C +
          sizeof(int) * (2 * C + 2 * (DCS_MAX_QUBITS + 1) + 16) + sizeof(uint64_t) * DCS_CWORDS + 64;
 }
 __host__ __device__ inline size_t work_tile_elems(int C, bool big) {
@@ -356,7 +357,8 @@ __device__ void carve(Work& w, unsigned char* raw, int C, float2* big_area, bool
   w.T2 = big_area ? w.F + 2 * C * C : nullptr;
   float2* after = big_area ? tiles : w.F + 2 * C * C;
   w.tau = reinterpret_cast<float*>(after);
-  w.perm = reinterpret_cast<int*>(w.tau + 2 * C);
+  w.sigf = w.tau + 2 * C;
+  w.perm = reinterpret_cast<int*>(w.sigf + 2 * C);
   w.bnd = w.perm + 2 * C;
   w.abnd = w.bnd + DCS_MAX_QUBITS + 1;
   w.iv = w.abnd + DCS_MAX_QUBITS + 1;
@@ -686,22 +688,36 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_compress(DevCtx c,
     }
     __syncthreads();
     PHASE_MARK(12);
-    cta_jacobi_svd<NT>(X, m, nn, m, V, nn, sm.sig2, sm.perm, &sm.iv[5], sm.red);
+    cta_jacobi_svd<NT>(X, m, nn, m, V, nn, sm.sig2, sm.sigf, sm.perm, &sm.iv[5], sm.red);
     PHASE_MARK(13);
-    if (threadIdx.x == 0) {
-      const int k = trunc_rank(sm.sig2, sm.perm, nn, c.chi_max, c.tol);
-      double w = 0.0, tot = 0.0;
-      for (int i = 0; i < nn; ++i) tot += sm.sig2[i];
-      for (int i = 0; i < k; ++i) w += sm.sig2[sm.perm[i]];
-      sm.iv[6] = k;
-      sm.dv[0] = w;
-      // exact unless the rank was capped by chi_max above the tolerance
-      if (tot - w > c.tol * tot) sm.iv[7] = 0;
-      if (tot > 0.0) sm.dv[1] *= w / tot;
+    int k;
+    float inv;
+    if constexpr (NT == 32) {  // one warp: lane-parallel rank decision, FP32
+      float kept, disc;
+      k = warp_trunc_rank(sm.sigf, sm.perm, nn, c.chi_max, c.tol, kept, disc);
+      const float tot = kept + disc;
+      inv = 1.f / sqrtf(kept);
+      if (threadIdx.x == 0) {
+        // exact unless the rank was capped by chi_max above the tolerance
+        if (disc > (float)c.tol * tot) sm.iv[7] = 0;
+        if (tot > 0.f && disc > 0.f) sm.dv[1] *= 1.0 - (double)(disc / tot);
+      }
+    } else {
+      if (threadIdx.x == 0) {
+        const int kk = trunc_rank(sm.sig2, sm.perm, nn, c.chi_max, c.tol);
+        double w = 0.0, tot = 0.0;
+        for (int i = 0; i < nn; ++i) tot += sm.sig2[i];
+        for (int i = 0; i < kk; ++i) w += sm.sig2[sm.perm[i]];
+        sm.iv[6] = kk;
+        sm.dv[0] = w;
+        // exact unless the rank was capped by chi_max above the tolerance
+        if (tot - w > c.tol * tot) sm.iv[7] = 0;
+        if (tot > 0.0) sm.dv[1] *= w / tot;
+      }
+      __syncthreads();
+      k = sm.iv[6];
+      inv = (float)(1.0 / sqrt(sm.dv[0]));
     }
-    __syncthreads();
-    const int k = sm.iv[6];
-    const float inv = (float)(1.0 / sqrt(sm.dv[0]));
     float2* pq = site_ptr(c, bb, slot, q);
     for (int idx = threadIdx.x; idx < m * k; idx += NT) {
       const int row = idx / k, kk = idx % k;
@@ -1022,7 +1038,7 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
     }
     __syncthreads();
     PHASE_MARK(2);
-    cta_jacobi_svd<NT>(X, m, nn, m, V, nn, sm.sig2, sm.perm, &sm.iv[5], sm.red);
+    cta_jacobi_svd<NT>(X, m, nn, m, V, nn, sm.sig2, sm.sigf, sm.perm, &sm.iv[5], sm.red);
     PHASE_MARK(3);
     if (threadIdx.x == 0) {
       const int kk = trunc_rank(sm.sig2, sm.perm, nn, c.chi_max, c.tol);
@@ -1242,13 +1258,24 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_measure(DevCtx c, 
     const int bl = sm.bnd[q], br = sm.bnd[q + 1];
     float2* A = site_ptr(c, kb, slot, q);
     double s0 = 0.0, s1 = 0.0;
-    for (int idx = threadIdx.x; idx < bl * 2 * br; idx += NT) {
-      const double w = cabs2d(A[idx]);
-      if ((idx / br) & 1) s1 += w;
-      else s0 += w;
+    if constexpr (NT == 32) {  // one warp: float-float sums (FP64 accuracy, FP32 pipe)
+      ffloat a0{0.f, 0.f}, a1{0.f, 0.f};
+      for (int idx = threadIdx.x; idx < bl * 2 * br; idx += NT) {
+        const ffloat w = ff_abs2(A[idx]);
+        if ((idx / br) & 1) a1 = ff_add(a1, w);
+        else a0 = ff_add(a0, w);
+      }
+      s0 = ff_to_double(ff_warp_sum(a0));
+      s1 = ff_to_double(ff_warp_sum(a1));
+    } else {
+      for (int idx = threadIdx.x; idx < bl * 2 * br; idx += NT) {
+        const double w = cabs2d(A[idx]);
+        if ((idx / br) & 1) s1 += w;
+        else s0 += w;
+      }
+      s0 = block_sum<NT>(s0, sm.red);
+      s1 = block_sum<NT>(s1, sm.red);
     }
-    s0 = block_sum<NT>(s0, sm.red);
-    s1 = block_sum<NT>(s1, sm.red);
     const double tot = s0 + s1;
     const double p0 = s0 / tot;
     if (mode == MEAS_PROB) {
@@ -1275,7 +1302,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_measure(DevCtx c, 
       __syncthreads();
       continue;
     }
-    const float sc = (float)(1.0 / sqrt(rm));
+    const float sc = NT == 32 ? 1.f / sqrtf((float)rm) : (float)(1.0 / sqrt(rm));
     for (int idx = threadIdx.x; idx < bl * 2 * br; idx += NT) {
       const int s = (idx / br) & 1;
       A[idx] = (s == m) ? cscale(A[idx], sc) : cz();
