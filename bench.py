@@ -48,57 +48,101 @@ def measured_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    """SM clock and clock-event (throttle) reasons sampled during the timed region.
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NVML is polled every 5 ms from a thread (the timed region of a step is milliseconds long),
+    the GPU found by its UUID; nvidia-smi at 200 ms is the fallback.  Read-only queries."""
 
-    def __init__(self, gpu_index: int):
-        self.gpu = gpu_index
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown"}
+
+    def __init__(self, cuda_index: int):
+        self.cuda_index = cuda_index
+        self.samples = []  # (sm_mhz, max_mhz, reason bits)
+        self.stop_flag = threading.Event()
+        self.t = None
         self.proc = None
-        self.lines = []
+        self.ready = threading.Event()
+
+    def _uuid(self):
+        try:
+            import torch
+            return "GPU-" + str(torch.cuda.get_device_properties(self.cuda_index).uuid)
+        except Exception:
+            return None
+
+    def _nvml_loop(self, nv, h):
+        try:
+            get_reasons = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                nv.nvmlDeviceGetCurrentClocksThrottleReasons
+            smax = nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM)
+            while not self.stop_flag.is_set():
+                self.samples.append((nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM), smax,
+                                     int(get_reasons(h))))
+                self.ready.set()
+                time.sleep(0.005)
+        finally:
+            self.ready.set()
 
     def start(self):
+        uuid = self._uuid()
+        try:
+            import pynvml as nv
+            nv.nvmlInit()
+            try:
+                h = nv.nvmlDeviceGetHandleByUUID(uuid)
+            except Exception:
+                h = nv.nvmlDeviceGetHandleByIndex(self.cuda_index)
+            self.t = threading.Thread(target=self._nvml_loop, args=(nv, h), daemon=True)
+            self.t.start()
+            self.ready.wait(2.0)
+            return
+        except Exception:
+            self.t = None
+        fields = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+                  "clocks_event_reasons.hw_thermal_slowdown,"
+                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                ["nvidia-smi", "-i", uuid or str(self.cuda_index), f"--query-gpu={fields}",
                  "--format=csv,noheader,nounits", "-lms", "200"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t = threading.Thread(target=self._smi_read, daemon=True)
             self.t.start()
         except OSError:
             self.proc = None
 
-    def _read(self):
+    def _smi_read(self):
+        bits = (0x8, 0x40, 0x20, 0x4)
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            parts = [x.strip() for x in line.split(",")]
+            try:
+                r = sum(b for b, v in zip(bits, parts[2:6]) if v.lower().startswith("active"))
+                self.samples.append((float(parts[0]), float(parts[1]), r))
+            except (ValueError, IndexError):
+                continue
 
     def stop(self):
-        if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except subprocess.TimeoutExpired:
-            self.proc.kill()
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            parts = [x.strip() for x in ln.split(",")]
-            if len(parts) < 9:
-                continue
+        self.stop_flag.set()
+        if self.proc is not None:
+            self.proc.terminate()
             try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower().startswith("active"):
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.t is not None:
+            self.t.join(timeout=5)
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        reasons = set()
+        for _, _, r in self.samples:
+            for bit, nm in self.REASONS.items():
+                if r & bit:
                     reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        return {"sm_mhz": statistics.median(x[0] for x in self.samples),
+                "sm_max_mhz": max(x[1] for x in self.samples),
+                "reasons": sorted(reasons), "samples": len(self.samples),
+                "source": "nvml 5 ms" if self.proc is None else "nvidia-smi 200 ms"}
 
 
 def mps_bytes(bonds) -> int:
@@ -247,7 +291,7 @@ def run_cgemm(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="dcs", choices=["dcs", "reference"])
     ap.add_argument("--shots", type=int, default=SHOTS)
@@ -325,7 +369,7 @@ def main():
             durs.append((e0, e1))
     torch.cuda.synchronize()
     barrier()
-    launches = (sim.launches - l0) // args.steps
+    launches = sim.launches - l0
     ms = [a.elapsed_time(b) for a, b in durs]
     clk = clocks.stop()
     t_step = sum(ms) / len(ms) / 1000.0
@@ -410,6 +454,7 @@ def main():
         "e2e": {"value": e2e_value, "unit": "shots/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
+        "gpu_launches_per_step": int(launches) // args.steps,
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)

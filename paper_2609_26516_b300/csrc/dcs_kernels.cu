@@ -5,9 +5,12 @@
 // Compression step (Sec. "Simulating unitary quantum circuits with DMRG"): the bra starts
 // as the chunk applied block by block to the ket in canonical form, each two-qubit block
 // followed by a truncated SVD (keep the smallest rank whose discarded weight is
-// <= tol * total, at most chi_max); then `sweeps` one-site sweeps against the exact target
-// W|A>: each site takes F / ||F|| (Sec. above: the optimum of max <T|F>), made orthonormal
-// by Householder QR, and the last site gives f = ||F||^2 = |<B|W A>|^2.
+// <= tol * total, at most chi_max), the blocks taken from the end of the layer nearest the
+// orthogonality centre so the centre crosses the layer once.  If no block discarded more
+// than the tolerance the guess is the result (f = product of the kept weight fractions);
+// otherwise `sweeps` one-site sweeps against the exact target W|A> follow: each site takes
+// F / ||F|| (Sec. above: the optimum of max <T|F>), made orthonormal by Householder QR, and
+// the last site gives f = ||F||^2 = |<B|W A>|^2.
 //
 // Right-to-left steps reuse the left-to-right code on the mirrored chain: a site tensor
 // A[a][t][x] is read as A'[x][t][a], an MPO tensor W[d][s][t][e] as W'[e][s][t][d], and the
@@ -459,78 +462,221 @@ __device__ void hop_left(const DevCtx& c, Work& sm, int buf, int slot, int j) {
   __syncthreads();
 }
 
-// Every bond <= 4, one warp per slot: a run of centre moves with the moving centre tensor
-// kept in registers (warp layout of warp_qr8x4).  Each hop is the same gauge move as
-// hop_right / hop_left; only the hop's Q goes to memory, and the centre tensor once at the
-// end of the run.
+// Every bond <= 4, one warp per slot: the orthogonality-centre tensor T_j rides in
+// registers (warp layout of warp_qr8x4) through runs of centre moves and measurements.  In
+// the right layout its matrix is rows (a s) = a * 2 + s, columns x; in the left layout rows
+// (x s) = x * 2 + s, columns a.  Each hop is the same gauge move as hop_right / hop_left;
+// only the hop's Q goes to memory, and the centre tensor when the run ends.
+struct Roll {
+  float2 x;    // T_j[a][s][x] in the current layout, zero outside
+  int j;       // site
+  int bl, br;  // its bonds
+  bool right;  // layout
+};
+
+__device__ __forceinline__ int roll_lane_row() { return threadIdx.x & 7; }
+__device__ __forceinline__ int roll_lane_col() { return (threadIdx.x & 31) >> 3; }
+
+// element offset of this lane's entry inside the packed site [bl][2][br], or -1
+__device__ __forceinline__ int roll_offset(const Roll& R) {
+  const int row = roll_lane_row(), col = roll_lane_col();
+  if (R.right) return (row < 2 * R.bl && col < R.br) ? row * R.br + col : -1;
+  return (row < 2 * R.br && col < R.bl) ? (col * 2 + (row & 1)) * R.br + (row >> 1) : -1;
+}
+
+__device__ __forceinline__ void roll_load(const DevCtx& c, const Work& sm, int buf, int slot,
+                                          int j, bool right, Roll& R) {
+  R.j = j;
+  R.bl = sm.bnd[j];
+  R.br = sm.bnd[j + 1];
+  R.right = right;
+  const int off = roll_offset(R);
+  R.x = off >= 0 ? site_ptr(c, buf, slot, j)[off] : cz();
+}
+
+__device__ __forceinline__ void roll_store(const DevCtx& c, int buf, int slot, const Roll& R) {
+  const int off = roll_offset(R);
+  if (off >= 0) site_ptr(c, buf, slot, R.j)[off] = R.x;
+}
+
+// switch layouts: lane (col u, row v * 2 + s) takes lane (col v, row u * 2 + s)
+__device__ __forceinline__ void roll_flip(Roll& R) {
+  const int row = roll_lane_row(), col = roll_lane_col();
+  const float2 v = shfl2(R.x, (row >> 1) * 8 + col * 2 + (row & 1));
+  const bool ok = R.right ? (col < R.bl && (row >> 1) < R.br) : (col < R.br && (row >> 1) < R.bl);
+  R.x = ok ? v : cz();
+  R.right = !R.right;
+}
+
+// centre j -> j+1 (right layout): T_j = Q R, T_j := Q, T_{j+1} := R T_{j+1}
+__device__ __forceinline__ void roll_hop_right(const DevCtx& c, Work& sm, int buf, int slot, Roll& R) {
+  const int lane = threadIdx.x & 31, row = roll_lane_row(), col = roll_lane_col();
+  const int j = R.j, bl = R.bl, br = R.br, bn = sm.bnd[j + 2];
+  float2 q;
+  const int r = warp_qr8x4(R.x, 2 * bl, br, q);
+  if (row < 2 * bl && col < r) site_ptr(c, buf, slot, j)[row * r + col] = q;
+  const float2* nx = site_ptr(c, buf, slot, j + 1);
+  const int k = row >> 1, sp = row & 1;
+  const bool live = k < r && col < bn;
+  float2 acc = cz();
+  for (int y = 0; y < br; ++y) {
+    const float2 ry = shfl2(R.x, y * 8 + k);
+    if (live) cfma(acc, ry, nx[(y * 2 + sp) * bn + col]);
+  }
+  R.x = live ? acc : cz();
+  if (lane == 0) sm.bnd[j + 1] = r;
+  __syncwarp();
+  R.j = j + 1;
+  R.bl = r;
+  R.br = bn;
+}
+
+// centre j -> j-1 (left layout): T_j read as (x t) x a = Q' R', T_j[k][t][x] := Q'[(x t)][k],
+// T_{j-1}[a'][s][k] := sum_a T_{j-1}[a'][s][a] R'[k][a]
+__device__ __forceinline__ void roll_hop_left(const DevCtx& c, Work& sm, int buf, int slot, Roll& R) {
+  const int lane = threadIdx.x & 31, row = roll_lane_row(), col = roll_lane_col();
+  const int j = R.j, bl = R.bl, br = R.br, bp = sm.bnd[j - 1];
+  float2 q;
+  const int r = warp_qr8x4(R.x, 2 * br, bl, q);
+  if (row < 2 * br && col < r) site_ptr(c, buf, slot, j)[(col * 2 + (row & 1)) * br + (row >> 1)] = q;
+  const float2* pv = site_ptr(c, buf, slot, j - 1);
+  const int k = row >> 1, sp = row & 1;
+  const bool live = k < r && col < bp;
+  float2 acc = cz();
+  for (int a = 0; a < bl; ++a) {
+    const float2 ra = shfl2(R.x, a * 8 + k);
+    if (live) cfma(acc, pv[(col * 2 + sp) * bl + a], ra);
+  }
+  R.x = live ? acc : cz();
+  if (lane == 0) sm.bnd[j] = r;
+  __syncwarp();
+  R.j = j - 1;
+  R.br = r;
+  R.bl = bp;
+}
+
+__device__ __forceinline__ void roll_move(const DevCtx& c, Work& sm, int buf, int slot, Roll& R,
+                                          int target) {
+  if (target > R.j) {
+    if (!R.right) roll_flip(R);
+    while (R.j < target) roll_hop_right(c, sm, buf, slot, R);
+  } else if (target < R.j) {
+    if (R.right) roll_flip(R);
+    while (R.j > target) roll_hop_left(c, sm, buf, slot, R);
+  }
+}
+
 __device__ void warp_move_centre4(const DevCtx& c, Work& sm, int buf, int slot, int& centre,
                                   int target) {
   if (centre == target) return;
-  const int lane = threadIdx.x & 31, row = lane & 7, col = lane >> 3;
-  int* b = sm.bnd;
-  int j = centre;
-  float2 x = cz();
-  if (target > centre) {
-    // X_j: rows (a s) = a * 2 + s, columns x; T_j[a][s][x] at (a * 2 + s) * br + x
-    int bl = b[j];
-    {
-      const int br = b[j + 1];
-      if (row < 2 * bl && col < br) x = site_ptr(c, buf, slot, j)[row * br + col];
-    }
-    while (j < target) {
-      const int br = b[j + 1], bn = b[j + 2];
-      float2 q;
-      const int r = warp_qr8x4(x, 2 * bl, br, q);
-      if (row < 2 * bl && col < r) site_ptr(c, buf, slot, j)[row * r + col] = q;
-      // T_{j+1} := R T_{j+1}, produced directly in the layout of the next hop
-      const float2* nx = site_ptr(c, buf, slot, j + 1);
-      const int k = row >> 1, sp = row & 1;
-      const bool live = k < r && col < bn;
-      float2 acc = cz();
-      for (int y = 0; y < br; ++y) {
-        const float2 ry = shfl2(x, y * 8 + k);
-        if (live) cfma(acc, ry, nx[(y * 2 + sp) * bn + col]);
-      }
-      x = live ? acc : cz();
-      if (lane == 0) b[j + 1] = r;
-      bl = r;
-      ++j;
-    }
-    const int br = b[j + 1];
-    if (row < 2 * bl && col < br) site_ptr(c, buf, slot, j)[row * br + col] = x;
-  } else {
-    // mirrored: X'_j rows (x t) = x * 2 + t, columns a; T_j[a][t][x] at (a * 2 + t) * br + x
-    int br = b[j + 1];
-    {
-      const int bl = b[j];
-      if (row < 2 * br && col < bl) x = site_ptr(c, buf, slot, j)[(col * 2 + (row & 1)) * br + (row >> 1)];
-    }
-    while (j > target) {
-      const int bl = b[j], bp = b[j - 1];
-      float2 q;
-      const int r = warp_qr8x4(x, 2 * br, bl, q);
-      // T_j[k][t][x] := Q'[(x t)][k]
-      if (row < 2 * br && col < r) site_ptr(c, buf, slot, j)[(col * 2 + (row & 1)) * br + (row >> 1)] = q;
-      // T_{j-1}[a'][s][k] := sum_a T_{j-1}[a'][s][a] R'[k][a], in the mirrored layout of the
-      // next hop: lane (a', k * 2 + s)
-      const float2* pv = site_ptr(c, buf, slot, j - 1);
-      const int k = row >> 1, sp = row & 1;
-      const bool live = k < r && col < bp;
-      float2 acc = cz();
-      for (int a = 0; a < bl; ++a) {
-        const float2 ra = shfl2(x, a * 8 + k);
-        if (live) cfma(acc, pv[(col * 2 + sp) * bl + a], ra);
-      }
-      x = live ? acc : cz();
-      if (lane == 0) b[j] = r;
-      br = r;
-      --j;
-    }
-    const int bl = b[j];
-    if (row < 2 * br && col < bl) site_ptr(c, buf, slot, j)[(col * 2 + (row & 1)) * br + (row >> 1)] = x;
-  }
+  Roll R;
+  roll_load(c, sm, buf, slot, centre, target > centre, R);
+  roll_move(c, sm, buf, slot, R, target);
+  roll_store(c, buf, slot, R);
   centre = target;
   __syncwarp();
+}
+
+// A run of measurements (Alg. 1 Measure / MeasureProb) with the centre tensor in registers:
+// the same steps as the general path of k_measure, for every bond <= 4.
+__device__ void warp_measure_run4(const DevCtx& c, Work& sm, int kb, int slot, int centre,
+                                  const DMeas* meas, int n_meas, int mode,
+                                  const uint8_t* forced, double* p0_out) {
+  const int lane = threadIdx.x & 31, row = lane & 7;
+  Roll R;
+  roll_load(c, sm, kb, slot, centre, n_meas == 0 || meas[0].q >= centre, R);
+  for (int im = 0; im < n_meas; ++im) {
+    const int q = meas[im].q;
+    roll_move(c, sm, kb, slot, R, q);
+    // slice weights r_s = sum |T_q[:, s, :]|^2, float-float; the slice is the row's low bit
+    const ffloat w = ff_abs2(R.x);
+    const ffloat z{0.f, 0.f};
+    const double s0 = ff_to_double(ff_warp_sum((row & 1) ? z : w));
+    const double s1 = ff_to_double(ff_warp_sum((row & 1) ? w : z));
+    const double p0 = s0 / (s0 + s1);
+    if (mode == MEAS_PROB) {
+      if (lane == 0) {
+        if (p0_out) p0_out[slot] = p0;
+        c.rr[2 * (size_t)slot] = s0;
+        c.rr[2 * (size_t)slot + 1] = s1;
+        if (!(p0 == p0)) c.flags[slot] |= DCS_FLAG_NUMERICAL;
+      }
+      continue;
+    }
+    int m;
+    if (mode == MEAS_SAMPLE) {
+      const double u = philox_uniform(c.seed, c.shot[slot], meas[im].ordinal);
+      m = (u < p0) ? 0 : 1;
+      if (lane == 0 && fabs(u - p0) < 1e-6) c.flags[slot] |= DCS_FLAG_DRAW_NEAR_THRESHOLD;
+    } else {
+      m = forced[slot] ? 1 : 0;
+    }
+    const double pm = m ? (1.0 - p0) : p0;
+    const double rm = m ? s1 : s0;
+    if (!(pm > 1e-12)) {
+      if (lane == 0) c.flags[slot] |= (pm == pm) ? DCS_FLAG_ZERO_PROB : DCS_FLAG_NUMERICAL;
+      continue;
+    }
+    const float sc = 1.f / sqrtf((float)rm);
+    R.x = (row & 1) == m ? cscale(R.x, sc) : cz();
+    if (lane == 0) {
+      c.p[slot] *= pm;
+      const int cb = meas[im].cbit;
+      uint64_t& wd = c.creg[(size_t)slot * DCS_CWORDS + (cb >> 6)];
+      wd = (wd & ~(1ull << (cb & 63))) | ((uint64_t)m << (cb & 63));
+    }
+  }
+  roll_store(c, kb, slot, R);
+  __syncwarp();
+  int* kbonds = bonds_ptr(c, slot, kb);
+  for (int i = lane; i <= c.n; i += 32) kbonds[i] = sm.bnd[i];
+  if (lane == 0) c.centre[slot] = R.j;
+}
+
+// Sites [lo, hi] of buffer `from` copied to buffer `to`, bond dimensions `bd`; every bond
+// <= 4: one thread per site.  16-byte accesses when both sites start on a 16-byte boundary
+// (the site stride, 2 C^2 complex, is even, so the pair read past an odd end stays inside
+// the site); 8-byte ones otherwise (a caller's buffer in dcs_compress_noalloc).
+template <int NT>
+__device__ __forceinline__ void copy_sites4(const DevCtx& c, int to, int from, int slot, int lo,
+                                            int hi, const int* bd) {
+  for (int j = lo + (int)threadIdx.x; j <= hi; j += NT) {
+    const int len = bd[j] * 2 * bd[j + 1];
+    const float2* s2 = site_ptr(c, from, slot, j);
+    float2* d2 = site_ptr(c, to, slot, j);
+    if (((reinterpret_cast<uintptr_t>(s2) | reinterpret_cast<uintptr_t>(d2)) & 15) == 0) {
+      const float4* s = reinterpret_cast<const float4*>(s2);
+      float4* d = reinterpret_cast<float4*>(d2);
+      for (int e = 0; e < (len + 1) / 2; ++e) d[e] = s[e];
+    } else {
+      for (int e = 0; e < len; ++e) d2[e] = s2[e];
+    }
+  }
+}
+
+// The chunk's lone single-qubit gates (sites of kind 1), one thread per site.
+template <int NT>
+__device__ __forceinline__ void apply_lone_1q_threads(const DevCtx& c, Work& sm, int buf,
+                                                      int slot, const DLayer* L,
+                                                      const DGate1* G1) {
+  for (int j = threadIdx.x; j < c.n; j += NT) {
+    if (L->site[j].kind != 1) continue;
+    float2 U[4];
+    prod1q(G1, L->site[j].g_off, L->site[j].g_n, sm.creg, U);
+    float2* p = site_ptr(c, buf, slot, j);
+    const int bl = sm.bnd[j], br = sm.bnd[j + 1];
+    for (int a = 0; a < bl; ++a)
+      for (int x = 0; x < br; ++x) {
+        const float2 v0 = p[(a * 2 + 0) * br + x], v1 = p[(a * 2 + 1) * br + x];
+        float2 o0 = cz(), o1 = cz();
+        cfma(o0, U[0], v0);
+        cfma(o0, U[1], v1);
+        cfma(o1, U[2], v0);
+        cfma(o1, U[3], v1);
+        p[(a * 2 + 0) * br + x] = o0;
+        p[(a * 2 + 1) * br + x] = o1;
+      }
+  }
 }
 
 template <int NT>
@@ -570,6 +716,16 @@ __device__ __forceinline__ void guess_range(const DLayer* L, const DBlock* BK, i
     lo = q < lo ? q : lo;
     hi = q + 1 > hi ? q + 1 : hi;
   }
+}
+
+// Blocks (stored by decreasing q) are taken from the end of the layer nearest the centre:
+// ascending when |centre - q_min| <= |centre - (q_max + 1)|.
+__device__ __forceinline__ bool guess_ascending(const DLayer* L, const DBlock* BK, int centre) {
+  const int nb = L->n_blocks;
+  if (nb == 0) return true;
+  const int qmin = BK[L->blk_off + nb - 1].q, qmax = BK[L->blk_off].q;
+  const int dl = centre - qmin, dr = centre - (qmax + 1);
+  return (dl < 0 ? -dl : dl) <= (dr < 0 ? -dr : dr);
 }
 
 // one warp per CTA for the small tiles: at most 64 registers so 32 CTAs fit an SM
@@ -622,10 +778,16 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_compress(DevCtx c,
   // ---- initial guess: copy the sites it touches, then apply the chunk block by block
   int lo, hi;
   guess_range(L, BK, n, centre, lo, hi);
-  for (int j = lo; j <= hi; ++j)
-    gcopy<NT>(site_ptr(c, bb, slot, j), site_ptr(c, kb, slot, j), sm.abnd[j] * 2 * sm.abnd[j + 1]);
+  if (C == 4) {
+    copy_sites4<NT>(c, bb, kb, slot, lo, hi, sm.abnd);
+    __syncthreads();
+    apply_lone_1q_threads<NT>(c, sm, bb, slot, L, G1);
+  } else {
+    for (int j = lo; j <= hi; ++j)
+      gcopy<NT>(site_ptr(c, bb, slot, j), site_ptr(c, kb, slot, j), sm.abnd[j] * 2 * sm.abnd[j + 1]);
+  }
   __syncthreads();
-  for (int j = 0; j < n; ++j) {
+  for (int j = 0; j < n && C != 4; ++j) {
     if (L->site[j].kind != 1) continue;
     if (threadIdx.x == 0) prod1q(G1, L->site[j].g_off, L->site[j].g_n, sm.creg, sm.G);
     __syncthreads();
@@ -644,11 +806,12 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_compress(DevCtx c,
     }
     __syncthreads();
   }
-  for (int ib = 0; ib < L->n_blocks; ++ib) {
-    const DBlock& blk = BK[L->blk_off + ib];
+  const bool asc = guess_ascending(L, BK, centre);
+  for (int t = 0; t < L->n_blocks; ++t) {
+    const DBlock& blk = BK[L->blk_off + (asc ? L->n_blocks - 1 - t : t)];
     const int q = blk.q;
     PHASE_MARK(10);
-    move_centre<NT>(c, sm, bb, slot, centre, q + 1);
+    move_centre<NT>(c, sm, bb, slot, centre, centre <= q ? q : q + 1);
     PHASE_MARK(11);
     const int b0 = sm.bnd[q], b1 = sm.bnd[q + 1], b2 = sm.bnd[q + 2];
     gcopy<NT>(sm.S, site_ptr(c, bb, slot, q), b0 * 2 * b1);
@@ -718,19 +881,24 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_compress(DevCtx c,
       k = sm.iv[6];
       inv = (float)(1.0 / sqrt(sm.dv[0]));
     }
+    // the singular values go to the site facing the next block: B_q = U S, B_{q+1} = Vh
+    // (descending, centre q) or B_q = U, B_{q+1} = S Vh (ascending, centre q+1); X = U S
     float2* pq = site_ptr(c, bb, slot, q);
     for (int idx = threadIdx.x; idx < m * k; idx += NT) {
       const int row = idx / k, kk = idx % k;
-      pq[idx] = cscale(X[row + sm.perm[kk] * m], inv);
+      const float sg = sm.sigf[sm.perm[kk]];
+      const float sc = asc ? (sg > 0.f ? 1.f / sqrtf(sg) : 0.f) : inv;
+      pq[idx] = cscale(X[row + sm.perm[kk] * m], sc);
     }
     float2* pq1 = site_ptr(c, bb, slot, q + 1);
     for (int idx = threadIdx.x; idx < k * nn; idx += NT) {
       const int kk = idx / nn, col = idx % nn;
-      pq1[idx] = cconj(V[col + sm.perm[kk] * nn]);
+      const float2 v = cconj(V[col + sm.perm[kk] * nn]);
+      pq1[idx] = asc ? cscale(v, sqrtf(sm.sigf[sm.perm[kk]]) * inv) : v;
     }
     __syncthreads();
     if (threadIdx.x == 0) sm.bnd[q + 1] = k;
-    centre = q;
+    centre = asc ? q + 1 : q;
     __syncthreads();
     PHASE_MARK(14);
   }
@@ -743,8 +911,12 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_compress(DevCtx c,
   // the touched sites go back into the ket buffer, the centre staying where the guess left it.
   const bool exact = sm.iv[7] != 0;
   if (exact) {
-    for (int j = lo; j <= hi; ++j)
-      gcopy<NT>(site_ptr(c, kb, slot, j), site_ptr(c, bb, slot, j), bt[j] * 2 * bt[j + 1]);
+    if (C == 4) {
+      copy_sites4<NT>(c, kb, bb, slot, lo, hi, bt);
+    } else {
+      for (int j = lo; j <= hi; ++j)
+        gcopy<NT>(site_ptr(c, kb, slot, j), site_ptr(c, bb, slot, j), bt[j] * 2 * bt[j + 1]);
+    }
     fval = sm.dv[1];
   } else {
   for (int j = 0; j < n; ++j)
@@ -1004,10 +1176,11 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
     __syncthreads();
   }
   PHASE_MARK(0);
-  for (int ib = 0; ib < L->n_blocks; ++ib) {
-    const DBlock& blk = BK[L->blk_off + ib];
+  const bool asc = guess_ascending(L, BK, centre);
+  for (int t = 0; t < L->n_blocks; ++t) {
+    const DBlock& blk = BK[L->blk_off + (asc ? L->n_blocks - 1 - t : t)];
     const int q = blk.q;
-    move_centre<NT>(c, sm, bb, slot, centre, q + 1);
+    move_centre<NT>(c, sm, bb, slot, centre, centre <= q ? q : q + 1);
     PHASE_MARK(1);
     const int b0 = bt[q], b1 = bt[q + 1], b2 = bt[q + 2];
     if (threadIdx.x == 0) build_block(blk, G1, sm.creg, sm.G);
@@ -1053,19 +1226,22 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
     __syncthreads();
     const int kk = sm.iv[6];
     const float inv = (float)(1.0 / sqrt(sm.dv[0]));
-    float2* pq = site_ptr(c, bb, slot, q);
+    float2* pq = site_ptr(c, bb, slot, q);  // singular values placed as in k_compress
     for (int idx = threadIdx.x; idx < m * kk; idx += NT) {
       const int row = idx / kk, k2 = idx % kk;
-      pq[idx] = cscale(X[row + (size_t)sm.perm[k2] * m], inv);
+      const float sg = sm.sigf[sm.perm[k2]];
+      const float sc = asc ? (sg > 0.f ? 1.f / sqrtf(sg) : 0.f) : inv;
+      pq[idx] = cscale(X[row + (size_t)sm.perm[k2] * m], sc);
     }
     float2* pq1 = site_ptr(c, bb, slot, q + 1);
     for (int idx = threadIdx.x; idx < kk * nn; idx += NT) {
       const int k2 = idx / nn, col = idx % nn;
-      pq1[idx] = cconj(V[col + (size_t)sm.perm[k2] * nn]);
+      const float2 v = cconj(V[col + (size_t)sm.perm[k2] * nn]);
+      pq1[idx] = asc ? cscale(v, sqrtf(sm.sigf[sm.perm[k2]]) * inv) : v;
     }
     __syncthreads();
     if (threadIdx.x == 0) bt[q + 1] = kk;
-    centre = q;
+    centre = asc ? q + 1 : q;
     __syncthreads();
     PHASE_MARK(4);
   }
@@ -1249,6 +1425,12 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_measure(DevCtx c, 
   for (int i = threadIdx.x; i <= n; i += NT) sm.bnd[i] = kbonds[i];
   __syncthreads();
   int centre = c.centre[slot];
+  if constexpr (NT == 32 && !BIG) {
+    if (C == 4) {
+      warp_measure_run4(c, sm, kb, slot, centre, meas, n_meas, mode, forced, p0_out);
+      return;
+    }
+  }
   PHASE_START();
   for (int im = 0; im < n_meas; ++im) {
     const int q = meas[im].q;
