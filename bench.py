@@ -39,6 +39,12 @@ WORKLOAD = "dynamic GHZ n=64 (32 data + 32 ancilla), chi_max=8, s=2, tol=1e-10, 
 METRIC = "shots/s (single-path dynamic GHZ n=64, chi_max=8)"
 
 
+# DRAM bytes (read + write) per shot of the H + CNOT compression launch, from the ncu
+# capture summarised in profiles/k_compress_ghz64_hcnot.md (2,000 shots: 31.78 MB read,
+# 2.01 MB written).  Valid for the kernel build that capture measured.
+HCNOT_TRAFFIC_PER_SHOT = (31.78496e6 + 2.006272e6) / 2000
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -51,7 +57,7 @@ class ClockSampler:
     """SM clock and clock-event (throttle) reasons sampled during the timed region.
 
     NVML is polled every 5 ms from a thread (the timed region of a step is milliseconds long),
-    the GPU found by its UUID; nvidia-smi at 200 ms is the fallback.  Read-only queries."""
+    the GPU found by its UUID; nvidia-smi at 50 ms is the fallback.  Read-only queries."""
 
     REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
                0x40: "hw_thermal_slowdown"}
@@ -71,33 +77,56 @@ class ClockSampler:
         except Exception:
             return None
 
-    def _nvml_loop(self, nv, h):
+    def _nvml_open(self, uuid):
+        """libnvidia-ml through ctypes (read-only queries); returns (lib, handle) or None."""
+        import ctypes
         try:
-            get_reasons = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            nv = ctypes.CDLL("libnvidia-ml.so.1")
+        except OSError:
+            return None
+        if nv.nvmlInit_v2() != 0:
+            return None
+        h = ctypes.c_void_p()
+        if uuid and nv.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(h)) == 0:
+            return nv, h
+        cnt = ctypes.c_uint(0)
+        nv.nvmlDeviceGetCount_v2(ctypes.byref(cnt))
+        idx = 0 if cnt.value == 1 else self.cuda_index
+        if nv.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(idx), ctypes.byref(h)) == 0:
+            return nv, h
+        return None
+
+    def _nvml_loop(self, nv, h):
+        import ctypes
+        try:
+            reasons_fn = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
                 nv.nvmlDeviceGetCurrentClocksThrottleReasons
-            smax = nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM)
+            smax = ctypes.c_uint(0)
+            nv.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(smax))  # NVML_CLOCK_SM = 1
+            clk = ctypes.c_uint(0)
+            rs = ctypes.c_ulonglong(0)
             while not self.stop_flag.is_set():
-                self.samples.append((nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM), smax,
-                                     int(get_reasons(h))))
-                self.ready.set()
+                ok = nv.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(clk)) == 0
+                ok = ok and reasons_fn(h, ctypes.byref(rs)) == 0
+                if ok:
+                    self.samples.append((float(clk.value), float(smax.value), int(rs.value)))
+                    self.ready.set()
                 time.sleep(0.005)
         finally:
             self.ready.set()
 
     def start(self):
         uuid = self._uuid()
-        try:
-            import pynvml as nv
-            nv.nvmlInit()
-            try:
-                h = nv.nvmlDeviceGetHandleByUUID(uuid)
-            except Exception:
-                h = nv.nvmlDeviceGetHandleByIndex(self.cuda_index)
-            self.t = threading.Thread(target=self._nvml_loop, args=(nv, h), daemon=True)
+        opened = self._nvml_open(uuid)
+        if opened is not None:
+            self.t = threading.Thread(target=self._nvml_loop, args=opened, daemon=True)
             self.t.start()
             self.ready.wait(2.0)
-            return
-        except Exception:
+            if self.samples:
+                return
+            self.stop_flag.set()
+            self.t.join(timeout=2)
+            self.stop_flag.clear()
             self.t = None
         fields = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
                   "clocks_event_reasons.hw_thermal_slowdown,"
@@ -105,10 +134,11 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", uuid or str(self.cuda_index), f"--query-gpu={fields}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._smi_read, daemon=True)
             self.t.start()
+            self.ready.wait(3.0)
         except OSError:
             self.proc = None
 
@@ -119,6 +149,7 @@ class ClockSampler:
             try:
                 r = sum(b for b, v in zip(bits, parts[2:6]) if v.lower().startswith("active"))
                 self.samples.append((float(parts[0]), float(parts[1]), r))
+                self.ready.set()
             except (ValueError, IndexError):
                 continue
 
@@ -142,7 +173,7 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(x[0] for x in self.samples),
                 "sm_max_mhz": max(x[1] for x in self.samples),
                 "reasons": sorted(reasons), "samples": len(self.samples),
-                "source": "nvml 5 ms" if self.proc is None else "nvidia-smi 200 ms"}
+                "source": "nvml 5 ms" if self.proc is None else "nvidia-smi 50 ms"}
 
 
 def mps_bytes(bonds) -> int:
@@ -446,9 +477,13 @@ def main():
         "compression_steps_per_s": comp_s,
         "roofline": {"bound": "hbm", "kernel": "k_compress<32> (H+CNOT chunk, all shots)",
                      "achieved": achieved, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
-                     "frac": achieved / float(peaks["hbm_gbs"]), "traffic": None,
+                     "frac": achieved / float(peaks["hbm_gbs"]),
+                     "traffic": HCNOT_TRAFFIC_PER_SHOT * args.shots,
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, "
+                                       "2,000-shot capture scaled by shots",
                      "peak_source": f"hbm_gbs of MEASURED_PEAKS.json ({peak_kind})",
-                     "note": "latency-bound: a dependent chain of bond-2 operations per shot",
+                     "note": "issue/latency-bound: a dependent chain of bond-2 operations "
+                             "per shot (neither roof binds; see profiles/)",
                      "launch_ms": comp_ms},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "shots/s", "h2d_bytes_per_step": int(h2d),
