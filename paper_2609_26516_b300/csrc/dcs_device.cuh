@@ -48,7 +48,9 @@ __device__ __forceinline__ void cfmac(float2& acc, float2 a, float2 b) {
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): multipliers 0xD2511F53, 0xCD9E8D57,
 // Weyl increments 0x9E3779B9, 0xBB67AE85.  Counter (ordinal, 0, shot lo, shot hi), key
 // (seed lo, seed hi); the uniform is ((w0 >> 5) * 2^26 + (w1 >> 6)) * 2^-53.
-__device__ __forceinline__ double philox_uniform(uint64_t seed, uint64_t shot, uint64_t ordinal) {
+// The two words that make the uniform: hi27 = w0 >> 5, lo26 = w1 >> 6.
+__device__ __forceinline__ void philox_words(uint64_t seed, uint64_t shot, uint64_t ordinal,
+                                             uint32_t& hi27, uint32_t& lo26) {
   uint32_t c0 = (uint32_t)ordinal, c1 = 0u, c2 = (uint32_t)shot, c3 = (uint32_t)(shot >> 32);
   uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
 #pragma unroll
@@ -65,8 +67,13 @@ __device__ __forceinline__ double philox_uniform(uint64_t seed, uint64_t shot, u
     c2 = n2;
     c3 = lo0;
   }
-  const uint64_t hi = (uint64_t)(c0 >> 5), lo = (uint64_t)(c1 >> 6);
-  return (double)(hi * 67108864ull + lo) * (1.0 / 9007199254740992.0);
+  hi27 = c0 >> 5;
+  lo26 = c1 >> 6;
+}
+__device__ __forceinline__ double philox_uniform(uint64_t seed, uint64_t shot, uint64_t ordinal) {
+  uint32_t hi, lo;
+  philox_words(seed, shot, ordinal, hi, lo);
+  return (double)((uint64_t)hi * 67108864ull + lo) * (1.0 / 9007199254740992.0);
 }
 
 // ----------------------------------------------------------------------------- reductions
@@ -503,6 +510,29 @@ __device__ __forceinline__ ffloat ff_warp_sum(ffloat a) {
   return a;
 }
 __device__ __forceinline__ double ff_to_double(ffloat a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ ffloat ff_neg(ffloat a) { return {-a.hi, -a.lo}; }
+// a / b to about 2^-44 relative (one correction step of the FP32 quotient)
+__device__ __forceinline__ ffloat ff_div(ffloat a, ffloat b) {
+  const float q1 = __fdiv_rn(a.hi, b.hi);
+  const float ph = __fmul_rn(q1, b.hi);
+  const float pl = fmaf(q1, b.hi, -ph);
+  const float r = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, ph), pl), __fsub_rn(a.lo, __fmul_rn(q1, b.lo)));
+  const float q2 = __fdiv_rn(r, b.hi);
+  const float hi = __fadd_rn(q1, q2);
+  return {hi, __fsub_rn(q2, __fsub_rn(hi, q1))};
+}
+// sign of a - b: -1, 0, +1
+__device__ __forceinline__ int ff_cmp(ffloat a, ffloat b) {
+  const ffloat d = ff_add(a, ff_neg(b));
+  return d.hi < 0.f ? -1 : (d.hi > 0.f ? 1 : (d.lo < 0.f ? -1 : (d.lo > 0.f ? 1 : 0)));
+}
+// The uniform u = hi27 2^-27 + lo26 2^-53 as a float-float, within 2^-48 of u.
+__device__ __forceinline__ ffloat ff_uniform(uint32_t hi27, uint32_t lo26) {
+  const float a = __fmul_rn((float)(hi27 >> 3), 5.9604644775390625e-08f);          // 2^-24
+  const float b = __fmul_rn((float)(((hi27 & 7u) << 26) | lo26), 1.1102230246251565e-16f);  // 2^-53
+  const float hi = __fadd_rn(a, b);
+  return {hi, __fsub_rn(b, __fsub_rn(hi, a))};
+}
 
 // Warp version of trunc_rank for n <= 32 values, FP32: lane i takes the i-th largest value
 // w_(i) = sigf[perm[i]]; returns k and sets kept = sum_{i<k} w_(i), disc = sum_{i>=k} w_(i).

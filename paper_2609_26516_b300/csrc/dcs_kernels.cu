@@ -588,39 +588,47 @@ __device__ void warp_measure_run4(const DevCtx& c, Work& sm, int kb, int slot, i
   for (int im = 0; im < n_meas; ++im) {
     const int q = meas[im].q;
     roll_move(c, sm, kb, slot, R, q);
-    // slice weights r_s = sum |T_q[:, s, :]|^2, float-float; the slice is the row's low bit
+    // slice weights r_s = sum |T_q[:, s, :]|^2 and p_0 = r_0 / (r_0 + r_1), all in float-float
+    // (about 2^-44 relative, FP32 pipe); the slice is the row's low bit
     const ffloat w = ff_abs2(R.x);
     const ffloat z{0.f, 0.f};
-    const double s0 = ff_to_double(ff_warp_sum((row & 1) ? z : w));
-    const double s1 = ff_to_double(ff_warp_sum((row & 1) ? w : z));
-    const double p0 = s0 / (s0 + s1);
+    const ffloat r0 = ff_warp_sum((row & 1) ? z : w);
+    const ffloat r1 = ff_warp_sum((row & 1) ? w : z);
+    const ffloat p0 = ff_div(r0, ff_add(r0, r1));
     if (mode == MEAS_PROB) {
       if (lane == 0) {
-        if (p0_out) p0_out[slot] = p0;
-        c.rr[2 * (size_t)slot] = s0;
-        c.rr[2 * (size_t)slot + 1] = s1;
-        if (!(p0 == p0)) c.flags[slot] |= DCS_FLAG_NUMERICAL;
+        const double p0d = ff_to_double(p0);
+        if (p0_out) p0_out[slot] = p0d;
+        c.rr[2 * (size_t)slot] = ff_to_double(r0);
+        c.rr[2 * (size_t)slot + 1] = ff_to_double(r1);
+        if (!(p0d == p0d)) c.flags[slot] |= DCS_FLAG_NUMERICAL;
       }
       continue;
     }
     int m;
     if (mode == MEAS_SAMPLE) {
-      const double u = philox_uniform(c.seed, c.shot[slot], meas[im].ordinal);
-      m = (u < p0) ? 0 : 1;
-      if (lane == 0 && fabs(u - p0) < 1e-6) c.flags[slot] |= DCS_FLAG_DRAW_NEAR_THRESHOLD;
+      // m = 0 iff u < p_0; u within 2^-48 of the FP64 uniform, so only draws far inside
+      // the flagged window |u - p_0| < 1e-6 could be decided differently
+      uint32_t hi27, lo26;
+      philox_words(c.seed, c.shot[slot], meas[im].ordinal, hi27, lo26);
+      const ffloat u = ff_uniform(hi27, lo26);
+      m = ff_cmp(u, p0) < 0 ? 0 : 1;
+      const ffloat d = ff_add(u, ff_neg(p0));
+      if (lane == 0 && fabsf(d.hi) < 1e-6f) c.flags[slot] |= DCS_FLAG_DRAW_NEAR_THRESHOLD;
     } else {
       m = forced[slot] ? 1 : 0;
     }
-    const double pm = m ? (1.0 - p0) : p0;
-    const double rm = m ? s1 : s0;
-    if (!(pm > 1e-12)) {
-      if (lane == 0) c.flags[slot] |= (pm == pm) ? DCS_FLAG_ZERO_PROB : DCS_FLAG_NUMERICAL;
+    const ffloat one{1.f, 0.f};
+    const ffloat pm = m ? ff_add(one, ff_neg(p0)) : p0;
+    const ffloat rm = m ? r1 : r0;
+    if (!(pm.hi > 1e-12f)) {
+      if (lane == 0) c.flags[slot] |= (pm.hi == pm.hi) ? DCS_FLAG_ZERO_PROB : DCS_FLAG_NUMERICAL;
       continue;
     }
-    const float sc = 1.f / sqrtf((float)rm);
+    const float sc = 1.f / sqrtf(rm.hi);
     R.x = (row & 1) == m ? cscale(R.x, sc) : cz();
     if (lane == 0) {
-      c.p[slot] *= pm;
+      c.p[slot] *= ff_to_double(pm);
       const int cb = meas[im].cbit;
       uint64_t& wd = c.creg[(size_t)slot * DCS_CWORDS + (cb >> 6)];
       wd = (wd & ~(1ull << (cb & 63))) | ((uint64_t)m << (cb & 63));
