@@ -378,6 +378,10 @@ __device__ __forceinline__ int warp_qr8x4(float2& x, int m, int n, float2& q) {
 // Afterwards sig2[j] = sigf[j] = ||x_j||^2 (FP32 sum) and perm[0..n) lists columns by
 // decreasing norm (ties: lower index first).  Scratch: red[NT/32], flag (int).
 template <int NT>
+__device__ void svd_finish(const float2* X, int m, int n, int ld, double* sig2, float* sigf,
+                           int* perm);
+
+template <int NT>
 __device__ void cta_jacobi_svd(float2* X, int m, int n, int ld, float2* V, int ldv,
                                double* sig2, float* sigf, int* perm, int* flag, double* red) {
   for (int idx = threadIdx.x; idx < n * n; idx += NT) {
@@ -460,7 +464,13 @@ __device__ void cta_jacobi_svd(float2* X, int m, int n, int ld, float2* V, int l
     if (*flag == 0) break;
     __syncthreads();
   }
-  // column norms (FP32 sums, also handed out in FP64) and their ordering
+  svd_finish<NT>(X, m, n, ld, sig2, sigf, perm);
+}
+
+// Column norms of the rotated X (FP32 sums, also handed out in FP64) and their ordering.
+template <int NT>
+__device__ void svd_finish(const float2* X, int m, int n, int ld, double* sig2, float* sigf,
+                           int* perm) {
   for (int j = threadIdx.x; j < n; j += NT) {
     float s = 0.f;
     for (int i = 0; i < m; ++i) s += cabs2(X[i + j * ld]);
@@ -478,6 +488,146 @@ __device__ void cta_jacobi_svd(float2* X, int m, int n, int ld, float2* V, int l
     perm[rank] = j;
   }
   __syncthreads();
+}
+
+// One pair rotation of the one-sided Jacobi method on two staged columns ci, cj of length
+// cs, whose first m entries are X and the rest V, by one warp (same rotation and threshold
+// as cta_jacobi_svd).  Returns whether it rotated.
+__device__ __forceinline__ bool warp_jacobi_pair(float2* ci, float2* cj, int m, int cs, float thr) {
+  const int lane = threadIdx.x & 31;
+  float a = 0.f, b = 0.f;
+  float2 g = cz();
+  for (int i = lane; i < m; i += 32) {
+    const float2 xi = ci[i], xj = cj[i];
+    a += cabs2(xi);
+    b += cabs2(xj);
+    cfmac(g, xi, xj);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(FULL_MASK, a, o);
+    b += __shfl_xor_sync(FULL_MASK, b, o);
+    g.x += __shfl_xor_sync(FULL_MASK, g.x, o);
+    g.y += __shfl_xor_sync(FULL_MASK, g.y, o);
+  }
+  const float ag = hypotf(g.x, g.y);
+  if (!(ag > thr * sqrtf(a * b) && ag > 0.f)) return false;
+  const float zeta = (b - a) / (2.f * ag);
+  const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+  const float c = rsqrtf(1.f + t * t);
+  const float s = c * t;
+  const float2 ph = make_float2(g.x / ag, -g.y / ag);  // e^{-i phi}
+  for (int i = lane; i < cs; i += 32) {
+    const float2 xi = ci[i];
+    const float2 xj = cmul(ph, cj[i]);
+    ci[i] = make_float2(c * xi.x - s * xj.x, c * xi.y - s * xj.y);
+    cj[i] = make_float2(s * xi.x + c * xj.x, s * xi.y + c * xj.y);
+  }
+  return true;
+}
+
+// Columns [c0, c0 + w) of X (m rows) and V (n rows) to or from the staging area, one staged
+// column of m + n entries each.
+template <int NT>
+__device__ __forceinline__ void stage_cols(float2* S, float2* X, int m, int ld, float2* V,
+                                           int n, int ldv, int c0, int w, bool in) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cs = m + n;
+  for (int col = warp; col < w; col += NT / 32) {
+    float2* sc = S + (size_t)col * cs;
+    float2* xc = X + (size_t)(c0 + col) * ld;
+    float2* vc = V + (size_t)(c0 + col) * ldv;
+    for (int i = lane; i < m; i += 32) {
+      if (in) sc[i] = xc[i];
+      else xc[i] = sc[i];
+    }
+    for (int i = lane; i < n; i += 32) {
+      if (in) sc[m + i] = vc[i];
+      else vc[i] = sc[m + i];
+    }
+  }
+}
+
+// Blocked one-sided Jacobi SVD for matrices too large for shared memory, with the rotations,
+// threshold and outputs of cta_jacobi_svd.  The n columns are cut into blocks of w.  Each
+// sweep rotates every pair of columns once, with both columns staged in shared memory
+// together with the matching columns of V.  Block I stays staged while the blocks J > I pass
+// through.  The pairs inside I come first (circle method on its columns), then for each J
+// its cross pairs in w rounds of disjoint pairs (a, (a + r) mod w).  Per sweep X and V
+// cross HBM about n / w times instead of about n times.
+template <int NT>
+__device__ void cta_jacobi_svd_staged(float2* X, int m, int n, int ld, float2* V, int ldv,
+                                      double* sig2, float* sigf, int* perm, int* flag,
+                                      double* red, float2* stage, size_t stage_elems) {
+  const int cs = m + n;
+  int w = (int)(stage_elems / (2 * (size_t)cs));
+  if (w > n) w = n;
+  if (w < 2) {
+    cta_jacobi_svd<NT>(X, m, n, ld, V, ldv, sig2, sigf, perm, flag, red);
+    return;
+  }
+  constexpr int NW = NT / 32;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int idx = threadIdx.x; idx < n * n; idx += NT) {
+    const int i = idx % n, j = idx / n;
+    V[i + (size_t)j * ldv] = make_float2(i == j ? 1.f : 0.f, 0.f);
+  }
+  __syncthreads();
+  const int nb = (n + w - 1) / w;
+  const float thr = 2.f * sqrtf((float)m) * 5.96e-8f;
+  float2* SI = stage;
+  float2* SJ = stage + (size_t)w * cs;
+  if (threadIdx.x == 0) *flag = 0;
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    int rotated = 0;
+    for (int I = 0; I < nb; ++I) {
+      const int i0 = I * w, wi = (n - i0) < w ? (n - i0) : w;
+      __syncthreads();
+      stage_cols<NT>(SI, X, m, ld, V, n, ldv, i0, wi, true);
+      __syncthreads();
+      // pairs inside block I: circle method
+      const int N = (wi + 1) & ~1;
+      for (int rnd = 0; rnd < N - 1; ++rnd) {
+        for (int p = warp; p < N / 2; p += NW) {
+          int ci, cj;
+          if (p == 0) {
+            ci = rnd;
+            cj = N - 1;
+          } else {
+            ci = (rnd + p) % (N - 1);
+            cj = (rnd - p + (N - 1)) % (N - 1);
+          }
+          if (ci < wi && cj < wi && ci != cj)
+            rotated |= warp_jacobi_pair(SI + (size_t)ci * cs, SI + (size_t)cj * cs, m, cs, thr);
+        }
+        __syncthreads();
+      }
+      for (int J = I + 1; J < nb; ++J) {
+        const int j0 = J * w, wj = (n - j0) < w ? (n - j0) : w;
+        stage_cols<NT>(SJ, X, m, ld, V, n, ldv, j0, wj, true);
+        __syncthreads();
+        for (int r = 0; r < w; ++r) {
+          for (int a = warp; a < wi; a += NW) {
+            const int bcol = (a + r) % w;
+            if (bcol < wj)
+              rotated |= warp_jacobi_pair(SI + (size_t)a * cs, SJ + (size_t)bcol * cs, m, cs, thr);
+          }
+          __syncthreads();
+        }
+        stage_cols<NT>(SJ, X, m, ld, V, n, ldv, j0, wj, false);
+        __syncthreads();
+      }
+      stage_cols<NT>(SI, X, m, ld, V, n, ldv, i0, wi, false);
+    }
+    if (lane == 0 && rotated) *flag = 1;
+    __syncthreads();
+    const int any = *flag;
+    __syncthreads();
+    if (threadIdx.x == 0) *flag = 0;
+    if (!any) break;
+  }
+  __syncthreads();
+  svd_finish<NT>(X, m, n, ld, sig2, sigf, perm);
 }
 
 // ----------------------------------------------------------------------------- float-float

@@ -296,6 +296,8 @@ struct Work {
   float2* gB;
   TcState tc;  // tensor-core GEMM state (large path with precision TF32X3)
   bool use_tc;
+  float2* stage;       // large path: shared staging of the blocked SVD (aliases tc.stage)
+  size_t stage_elems;  // its size in complex elements
   double* red;
   double* sig2;
   double* dv;  // scalar broadcast
@@ -310,11 +312,23 @@ struct Work {
 };
 
 
-__host__ __device__ inline size_t work_small_bytes(int C, bool big, bool tc = false) {
-  return (tc ? sizeof(float) * TC_SMEM_FLOATS + 64 : 0) +
-         sizeof(float2) * (64 + 64 + 16 + 2 * C + (big ? (GBM + GBN) * GBK : 0)) +
+__host__ __device__ inline size_t work_arrays_bytes(int C, bool big) {
+  return sizeof(float2) * (64 + 64 + 16 + 2 * C + (big ? (GBM + GBN) * GBK : 0)) +
          sizeof(double) * (32 + 2 * C + 8) + sizeof(float) * 4 * C +
          sizeof(int) * (2 * C + 2 * (DCS_MAX_QUBITS + 1) + 16) + sizeof(uint64_t) * DCS_CWORDS + 64;
+}
+// Large path: a 128-byte head (tensor-core barriers and counters) and a staging region that
+// serves the tensor-core GEMM tiles and the blocked SVD in turn, filling the CTA's shared
+// memory up to 224 KB.
+constexpr size_t BIG_SMEM_BYTES = 224 * 1024;
+constexpr size_t BIG_HEAD_BYTES = 128;
+__host__ __device__ inline size_t big_stage_bytes(int C) {
+  const size_t rest = work_arrays_bytes(C, true) + BIG_HEAD_BYTES;
+  return rest < BIG_SMEM_BYTES ? ((BIG_SMEM_BYTES - rest) & ~(size_t)127) : 0;
+}
+__host__ __device__ inline size_t work_small_bytes(int C, bool big, bool tc = false) {
+  (void)tc;
+  return work_arrays_bytes(C, big) + (big ? BIG_HEAD_BYTES + big_stage_bytes(C) : 0);
 }
 __host__ __device__ inline size_t work_tile_elems(int C, bool big) {
   return (size_t)(big ? 28 : 20) * C * C;
@@ -323,14 +337,19 @@ __host__ __device__ inline size_t work_tile_elems(int C, bool big) {
 __device__ void carve(Work& w, unsigned char* raw, int C, float2* big_area, bool tc = false) {
   w.C = C;
   w.use_tc = tc;
-  if (tc) {  // tensor-core staging first (16-byte aligned), then its barriers and counters
-    w.tc.stage = reinterpret_cast<float*>(raw);
-    uint64_t* tail = reinterpret_cast<uint64_t*>(w.tc.stage + TC_SMEM_FLOATS);
-    w.tc.mbar = tail;
-    w.tc.uses = reinterpret_cast<int*>(tail + 2);
+  w.stage = nullptr;
+  w.stage_elems = 0;
+  if (big_area) {  // head (barriers, counters), then the 128-byte aligned staging region
+    uint64_t* head = reinterpret_cast<uint64_t*>(raw);
+    w.tc.mbar = head;
+    w.tc.uses = reinterpret_cast<int*>(head + 2);
     w.tc.tmem = reinterpret_cast<uint32_t*>(w.tc.uses + 2);
     w.tc.err = reinterpret_cast<int*>(w.tc.tmem + 1);
-    raw += sizeof(float) * TC_SMEM_FLOATS + 64;
+    raw += BIG_HEAD_BYTES;
+    w.stage = reinterpret_cast<float2*>(raw);
+    w.stage_elems = big_stage_bytes(C) / sizeof(float2);
+    w.tc.stage = reinterpret_cast<float*>(raw);
+    raw += big_stage_bytes(C);
   }
   uint64_t* c64 = reinterpret_cast<uint64_t*>(raw);
   w.creg = c64;
@@ -1219,7 +1238,8 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
     }
     __syncthreads();
     PHASE_MARK(2);
-    cta_jacobi_svd<NT>(X, m, nn, m, V, nn, sm.sig2, sm.sigf, sm.perm, &sm.iv[5], sm.red);
+    cta_jacobi_svd_staged<NT>(X, m, nn, m, V, nn, sm.sig2, sm.sigf, sm.perm, &sm.iv[5], sm.red,
+                              sm.stage, sm.stage_elems);
     PHASE_MARK(3);
     if (threadIdx.x == 0) {
       const int kk = trunc_rank(sm.sig2, sm.perm, nn, c.chi_max, c.tol);
@@ -1791,7 +1811,8 @@ static void compress_c(const DevCtx& c, int C, const DLayer* L, const DBlock* B,
 static void compress_big(const DevCtx& c, const DLayer* L, const DBlock* B, const DGate1* G1,
                          const DCond* CD, double* fid_out, cudaStream_t s) {
   const size_t sm = work_small_bytes(c.chi_cap, true, c.use_tc != 0);
-  if (c.use_tc) {
+  // the tensor-core tiles live in the staging region; the bond cap keeps it large enough
+  if (c.use_tc && big_stage_bytes(c.chi_cap) >= sizeof(float) * TC_SMEM_FLOATS) {
     cudaFuncSetAttribute(k_compress_big<BIG_NT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_compress_big<BIG_NT, true><<<c.n_slots, BIG_NT, sm, s>>>(c, c.chi_cap, L, B, G1, CD, fid_out);
   } else {
