@@ -368,6 +368,16 @@ __device__ __forceinline__ int warp_qr8x4(float2& x, int m, int n, float2& q) {
 }
 
 // ----------------------------------------------------------------------------- SVD
+// Absolute rotation floor of the Jacobi SVDs: 2^-40 ||X||_F^2 (FP32 sum, block reduction).
+template <int NT>
+__device__ float jacobi_floor(const float2* X, int m, int n, int ld, double* red) {
+  float s = 0.f;
+  for (int j = 0; j < n; ++j)
+    for (int i = threadIdx.x; i < m; i += NT) s += cabs2(X[i + (size_t)j * ld]);
+  s = block_sumf<NT>(s, reinterpret_cast<float*>(red));
+  return s * 9.09494702e-13f;
+}
+
 // One-sided (Hestenes) Jacobi SVD of X (m x n, column-major, ld): rotates pairs of columns
 // until they are mutually orthogonal, X V = U Sigma, accumulating the unitary V (n x n,
 // column-major, ldv).  Pairs follow the circle-method tournament so each round rotates
@@ -382,8 +392,8 @@ __device__ void svd_finish(const float2* X, int m, int n, int ld, double* sig2, 
                            int* perm);
 
 template <int NT>
-__device__ void cta_jacobi_svd(float2* X, int m, int n, int ld, float2* V, int ldv,
-                               double* sig2, float* sigf, int* perm, int* flag, double* red) {
+__device__ int cta_jacobi_svd(float2* X, int m, int n, int ld, float2* V, int ldv,
+                              double* sig2, float* sigf, int* perm, int* flag, double* red) {
   for (int idx = threadIdx.x; idx < n * n; idx += NT) {
     const int i = idx % n, j = idx / n;
     V[i + j * ldv] = make_float2(i == j ? 1.f : 0.f, 0.f);
@@ -396,9 +406,14 @@ __device__ void cta_jacobi_svd(float2* X, int m, int n, int ld, float2* V, int l
   const int ngroups = NT / G;
   const int grp = threadIdx.x / G, gl = threadIdx.x % G;
   // convergence: |g| <= 2 sqrt(m) eps32 sqrt(a b), the FP32 rounding level of the computed
-  // inner product (the column-orthogonality test of one-sided Jacobi codes)
+  // inner product (the column-orthogonality test of one-sided Jacobi codes), or |g| below
+  // 2^-40 of the squared Frobenius norm: pairs of columns at the FP32 noise level, which
+  // rounding otherwise keeps rotating up to the sweep cap.  The floor sits two orders of
+  // magnitude under the truncation tolerances used (1e-10 of the weight)
   const float thr = 2.f * sqrtf((float)m) * 5.96e-8f;
-  for (int sweep = 0; sweep < 30 && N >= 2; ++sweep) {
+  const float floor_g = jacobi_floor<NT>(X, m, n, ld, red);
+  int sweep = 0;
+  for (; sweep < 30 && N >= 2; ++sweep) {
     if (threadIdx.x == 0) *flag = 0;
     __syncthreads();
     for (int rnd = 0; rnd < N - 1; ++rnd) {
@@ -438,7 +453,7 @@ __device__ void cta_jacobi_svd(float2* X, int m, int n, int ld, float2* V, int l
           g.y += __shfl_xor_sync(0xffffffffu, g.y, o);
         }
         const float ag = hypotf(g.x, g.y);  // the phase g/|g| must have modulus 1
-        if (valid && ag > thr * sqrtf(a * b) && ag > 0.f) {
+        if (valid && ag > thr * sqrtf(a * b) && ag > floor_g && ag > 0.f) {
           const float zeta = (b - a) / (2.f * ag);
           const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
           const float c = rsqrtf(1.f + t * t);
@@ -465,6 +480,7 @@ __device__ void cta_jacobi_svd(float2* X, int m, int n, int ld, float2* V, int l
     __syncthreads();
   }
   svd_finish<NT>(X, m, n, ld, sig2, sigf, perm);
+  return sweep;
 }
 
 // Column norms of the rotated X (FP32 sums, also handed out in FP64) and their ordering.
@@ -493,7 +509,8 @@ __device__ void svd_finish(const float2* X, int m, int n, int ld, double* sig2, 
 // One pair rotation of the one-sided Jacobi method on two staged columns ci, cj of length
 // cs, whose first m entries are X and the rest V, by one warp (same rotation and threshold
 // as cta_jacobi_svd).  Returns whether it rotated.
-__device__ __forceinline__ bool warp_jacobi_pair(float2* ci, float2* cj, int m, int cs, float thr) {
+__device__ __forceinline__ bool warp_jacobi_pair(float2* ci, float2* cj, int m, int cs, float thr,
+                                                 float floor_g) {
   const int lane = threadIdx.x & 31;
   float a = 0.f, b = 0.f;
   float2 g = cz();
@@ -511,7 +528,7 @@ __device__ __forceinline__ bool warp_jacobi_pair(float2* ci, float2* cj, int m, 
     g.y += __shfl_xor_sync(FULL_MASK, g.y, o);
   }
   const float ag = hypotf(g.x, g.y);
-  if (!(ag > thr * sqrtf(a * b) && ag > 0.f)) return false;
+  if (!(ag > thr * sqrtf(a * b) && ag > floor_g && ag > 0.f)) return false;
   const float zeta = (b - a) / (2.f * ag);
   const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
   const float c = rsqrtf(1.f + t * t);
@@ -556,16 +573,13 @@ __device__ __forceinline__ void stage_cols(float2* S, float2* X, int m, int ld, 
 // its cross pairs in w rounds of disjoint pairs (a, (a + r) mod w).  Per sweep X and V
 // cross HBM about n / w times instead of about n times.
 template <int NT>
-__device__ void cta_jacobi_svd_staged(float2* X, int m, int n, int ld, float2* V, int ldv,
+__device__ int cta_jacobi_svd_staged(float2* X, int m, int n, int ld, float2* V, int ldv,
                                       double* sig2, float* sigf, int* perm, int* flag,
                                       double* red, float2* stage, size_t stage_elems) {
   const int cs = m + n;
   int w = (int)(stage_elems / (2 * (size_t)cs));
   if (w > n) w = n;
-  if (w < 2) {
-    cta_jacobi_svd<NT>(X, m, n, ld, V, ldv, sig2, sigf, perm, flag, red);
-    return;
-  }
+  if (w < 2) return cta_jacobi_svd<NT>(X, m, n, ld, V, ldv, sig2, sigf, perm, flag, red);
   constexpr int NW = NT / 32;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int idx = threadIdx.x; idx < n * n; idx += NT) {
@@ -574,11 +588,13 @@ __device__ void cta_jacobi_svd_staged(float2* X, int m, int n, int ld, float2* V
   }
   __syncthreads();
   const int nb = (n + w - 1) / w;
-  const float thr = 2.f * sqrtf((float)m) * 5.96e-8f;
+  const float thr = 2.f * sqrtf((float)m) * 5.96e-8f;  // as cta_jacobi_svd
+  const float floor_g = jacobi_floor<NT>(X, m, n, ld, red);
   float2* SI = stage;
   float2* SJ = stage + (size_t)w * cs;
   if (threadIdx.x == 0) *flag = 0;
-  for (int sweep = 0; sweep < 30; ++sweep) {
+  int sweep = 0;
+  for (; sweep < 30; ++sweep) {
     int rotated = 0;
     for (int I = 0; I < nb; ++I) {
       const int i0 = I * w, wi = (n - i0) < w ? (n - i0) : w;
@@ -598,7 +614,7 @@ __device__ void cta_jacobi_svd_staged(float2* X, int m, int n, int ld, float2* V
             cj = (rnd - p + (N - 1)) % (N - 1);
           }
           if (ci < wi && cj < wi && ci != cj)
-            rotated |= warp_jacobi_pair(SI + (size_t)ci * cs, SI + (size_t)cj * cs, m, cs, thr);
+            rotated |= warp_jacobi_pair(SI + (size_t)ci * cs, SI + (size_t)cj * cs, m, cs, thr, floor_g);
         }
         __syncthreads();
       }
@@ -610,7 +626,7 @@ __device__ void cta_jacobi_svd_staged(float2* X, int m, int n, int ld, float2* V
           for (int a = warp; a < wi; a += NW) {
             const int bcol = (a + r) % w;
             if (bcol < wj)
-              rotated |= warp_jacobi_pair(SI + (size_t)a * cs, SJ + (size_t)bcol * cs, m, cs, thr);
+              rotated |= warp_jacobi_pair(SI + (size_t)a * cs, SJ + (size_t)bcol * cs, m, cs, thr, floor_g);
           }
           __syncthreads();
         }
@@ -628,6 +644,7 @@ __device__ void cta_jacobi_svd_staged(float2* X, int m, int n, int ld, float2* V
   }
   __syncthreads();
   svd_finish<NT>(X, m, n, ld, sig2, sigf, perm);
+  return sweep + 1;
 }
 
 // ----------------------------------------------------------------------------- float-float

@@ -1238,8 +1238,16 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
     }
     __syncthreads();
     PHASE_MARK(2);
-    cta_jacobi_svd_staged<NT>(X, m, nn, m, V, nn, sm.sig2, sm.sigf, sm.perm, &sm.iv[5], sm.red,
-                              sm.stage, sm.stage_elems);
+    const int svd_sweeps = cta_jacobi_svd_staged<NT>(X, m, nn, m, V, nn, sm.sig2, sm.sigf,
+                                                     sm.perm, &sm.iv[5], sm.red, sm.stage,
+                                                     sm.stage_elems);
+    (void)svd_sweeps;
+#ifdef DCS_PHASE_TIMERS
+    if (threadIdx.x == 0 && nn >= 64) {
+      atomicAdd(&g_phase_cycles[20], (unsigned long long)svd_sweeps);
+      atomicAdd(&g_phase_cycles[21], 1ull);
+    }
+#endif
     PHASE_MARK(3);
     if (threadIdx.x == 0) {
       const int kk = trunc_rank(sm.sig2, sm.perm, nn, c.chi_max, c.tol);
