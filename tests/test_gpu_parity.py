@@ -49,7 +49,7 @@ def _state_fid(sim, pos, ref_mps):
 
 
 def _single_path_parity(circ, chi, shots, check_shots, seed=1, tol=1e-10, sweeps=2,
-                        state_check=True, path=0, prec=0):
+                        state_check=True, path=0, prec=0, bond_slack=0):
     sim = _sim(circ.n_qubits, chi, shots, circ.n_cbits, tol, sweeps, seed, path, prec)
     sim.init_state(shots)
     sim.run_circuit(circ)
@@ -65,7 +65,10 @@ def _single_path_parity(circ, chi, shots, check_shots, seed=1, tol=1e-10, sweeps
         assert res["bits"][s].tolist() == [int(x) for x in ref.c], f"shot {s}"
         if state_check:
             bonds, _, _ = sim.export_mps(s)
-            assert list(bonds) == ref.mps.bonds(), f"shot {s}: bond dimensions differ"
+            if bond_slack == 0:
+                assert list(bonds) == ref.mps.bonds(), f"shot {s}: bond dimensions differ"
+            else:  # ranks decided at the tolerance edge may differ by a few (FP32 vs FP64)
+                assert max(abs(int(x) - y) for x, y in zip(bonds, ref.mps.bonds())) <= bond_slack
             assert _state_fid(sim, s, ref.mps) >= 1 - STATE_TOL
         assert abs(res["p"][s] - ref.p) < P_TOL
         assert abs(res["F"][s] - ref.F) < f_tol(circ.n_qubits, len(ref.fids))
@@ -265,3 +268,40 @@ def test_global_tiles_multi_path():
         assert res["bits"][i].tolist() == [int(x) for x in b.c]
         assert _state_fid(sim, i, b.mps) >= 1 - STATE_TOL
         assert abs(res["p"][i] - b.p) < P_TOL
+
+
+# ---- the large-bond workload shapes at reduced depth (the oracle computes them exactly)
+
+def test_brickwork_n40_chi256_exact_layers():
+    # n = 40 random dynamic brickwork with chi_max = 256 (the large-bond slot capacity), the
+    # first 10 layers: bonds stay below chi_max, so every step is exact on both sides
+    circ = C.brickwork(40, 10, 0.1, 3)
+    _single_path_parity(circ, 256, 2, [0, 1])
+
+
+def test_brickwork_n64_chi1024_first_8_layers():
+    # n = 64, chi_max = 1024 (the largest capacity), measurement rate 0.02: the first 8
+    # layers, checked against the oracle shot by shot; middle bonds reach about 160.  At
+    # these sizes a singular value can sit at the 1e-10 truncation edge, where the FP32 and
+    # FP64 rank decisions differ by one; the state itself must still agree to 1e-6.
+    circ = C.brickwork(64, 8, 0.02, 5)
+    sim, _ = _single_path_parity(circ, 1024, 1, [0], bond_slack=2)
+    bonds, _, _ = sim.export_mps(0)
+    assert max(bonds) >= 128
+
+
+def test_multi_path_brickwork_large_bonds():
+    # multi-path ensemble on the large-bond kernels (chi_max = 48 > the shared-memory
+    # tiles): n = 12, top-M with M = 16
+    circ = C.brickwork(12, 10, 0.08, 7)
+    M = 16
+    sim = _sim(12, 48, 2 * M, circ.n_cbits)
+    sim.init_state(1, multipath=True)
+    sim.run_circuit(circ, max_branches=M)
+    res = sim.results()
+    ref = D.run_multi_path(circ, D.Params(chi_max=48), M=M)
+    assert res["n_active"] == len(ref) > 1
+    for i, b in enumerate(ref):
+        assert res["bits"][i].tolist() == [int(x) for x in b.c]
+        assert abs(res["p"][i] - b.p) < P_TOL
+        assert _state_fid(sim, i, b.mps) >= 1 - STATE_TOL
