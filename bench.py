@@ -181,7 +181,7 @@ def mps_bytes(bonds) -> int:
     return sum(8 * 2 * int(bonds[j]) * int(bonds[j + 1]) for j in range(len(bonds) - 1))
 
 
-def cpu_oracle_sample(seconds: float = 15.0, max_shots: int = 200):
+def cpu_oracle_sample(seconds: float = 15.0, max_shots: int = 5000):
     """The oracle (FP64 NumPy MPS, unchanged) on a bounded sample of the workload."""
     import circuits as C
     from oracle import drivers as D
@@ -231,16 +231,15 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def run_brick(args):
+def measure_brick(n, depth, p, chi, shots, sweeps, precision):
     """Random dynamic brickwork at a bounded depth and shot count: the time of each gate run
     (compression launches) and of the measurement runs, shots/s and one-site sweeps/s."""
     import torch
     import circuits as C
     from paper_2609_26516_b300 import Simulator
-    shots = args.shots if args.shots != SHOTS else 148
-    circ = C.brickwork(args.n, args.depth, args.p, 3)
-    sim = Simulator(args.n, args.chi, shots, circ.n_cbits, tol=TOL, sweeps=args.sweeps, seed=SEED,
-                    precision=args.precision)
+    circ = C.brickwork(n, depth, p, 3)
+    sim = Simulator(n, chi, shots, circ.n_cbits, tol=TOL, sweeps=sweeps, seed=SEED,
+                    precision=precision)
     runs, run = [], []
     for o in circ.ops:  # gate runs between measurement groups (each run is one chunk)
         if isinstance(o, C.Measure):
@@ -270,15 +269,25 @@ def run_brick(args):
     n_comp, n_sweeps = sim.counters()
     total_s = (sum(layer_ms) + sum(meas_ms)) / 1000.0
     bonds, _, _ = sim.export_mps(0)
-    print(json.dumps({
-        "workload": f"brickwork n={args.n} depth={args.depth} p={args.p} chi_max={args.chi} "
-                    f"s={args.sweeps} shots={shots} precision={'tf32x3' if args.precision else 'fp32'}",
+    out = {
+        "workload": f"brickwork n={n} depth={depth} p={p} chi_max={chi} s={sweeps} shots={shots} "
+                    f"precision={'tf32x3' if precision else 'fp32'}",
         "shots_per_s": shots / total_s, "sweeps_per_s": n_sweeps / total_s,
+        "compression_steps": n_comp, "sweeps": n_sweeps,
         "layer_ms": [round(x, 2) for x in layer_ms], "measure_ms_total": round(sum(meas_ms), 2),
-        "max_bond": int(max(bonds)), "F_shot0": float(sim.results()["F"][0])}), flush=True)
+        "max_bond": int(max(bonds)), "F_shot0": float(sim.results()["F"][0])}
+    del sim
+    torch.cuda.empty_cache()
+    return out
 
 
-def run_cgemm(args):
+def run_brick(args):
+    shots = args.shots if args.shots != SHOTS else 148
+    print(json.dumps(measure_brick(args.n, args.depth, args.p, args.chi, shots, args.sweeps,
+                                   args.precision)), flush=True)
+
+
+def measure_cgemm(chi, batch):
     """The contraction primitive alone at the site-contraction shape of chi_max: M = 2 chi,
     N = chi, K = 4 chi complex (the F = T2 R^T product with an MPO bond of 4), one problem
     per SM, SIMT vs tensor cores."""
@@ -286,9 +295,7 @@ def run_cgemm(args):
     import torch
     from paper_2609_26516_b300 import _native as N_
     lib = N_.load()
-    chi = args.chi
     M, Nn, K = 2 * chi, chi, 4 * chi
-    batch = args.shots if args.shots != SHOTS else 148
     g = torch.Generator(device="cuda").manual_seed(0)
     A = torch.randn((batch, M, K), dtype=torch.complex64, device="cuda", generator=g)
     B = torch.randn((batch, Nn, K), dtype=torch.complex64, device="cuda", generator=g)
@@ -316,7 +323,14 @@ def run_cgemm(args):
         out[name] = {"ms": ms, "tflops": out["flops_per_call"] / (ms / 1000.0) / 1e12}
     ref = (A[:2].to(torch.complex128) @ B[:2].to(torch.complex128).transpose(1, 2))
     out["rel_err_simt_last"] = float((Cm[:2].to(torch.complex128) - ref).norm() / ref.norm())
-    print(json.dumps(out), flush=True)
+    del A, B, Cm
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_cgemm(args):
+    batch = args.shots if args.shots != SHOTS else 148
+    print(json.dumps(measure_cgemm(args.chi, batch)), flush=True)
 
 
 def main():
@@ -327,6 +341,8 @@ def main():
     ap.add_argument("--impl", default="dcs", choices=["dcs", "reference"])
     ap.add_argument("--shots", type=int, default=SHOTS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the contraction and brickwork measurements after the GHZ line")
     ap.add_argument("--workload", default="ghz64", choices=["ghz64", "brick", "cgemm"],
                     help="ghz64: the benchmark line; brick / cgemm: extra measurements")
     ap.add_argument("--n", type=int, default=40)
@@ -492,6 +508,14 @@ def main():
         "gpu_launches_per_step": int(launches) // args.steps,
         "clocks": clk,
     }
+    if world == 1 and not args.no_extras:
+        # the other workload shapes, measured after the timed region: the contraction
+        # primitive at chi = 256 and random dynamic brickwork whose bonds reach chi_max = 128
+        # (truncation, sweeps), FP32 vs TF32x3
+        line["contraction"] = measure_cgemm(256, 148)
+        line["brickwork"] = {
+            "fp32": measure_brick(20, 12, 0.02, 128, 148, 2, 0),
+            "tf32x3": measure_brick(20, 12, 0.02, 128, 148, 2, 1)}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -307,7 +307,14 @@ __device__ __forceinline__ int warp_qr8x4(float2& x, int m, int n, float2& q) {
     bool skip = false;
     if (s32 > 1e-30f) {
       const float nrm = sqrtf(s32);
-      const float a0 = hypotf(x0.x, x0.y);
+      // |x_0|, exact for a real or imaginary x_0 (then x_0 / |x_0| is exactly +-1 or +-i and
+      // alpha has modulus nrm exactly); otherwise a plain square root unless the squares
+      // could underflow
+      const float ax = fabsf(x0.x), ay = fabsf(x0.y);
+      const float a0 = ay == 0.f ? ax
+                       : ax == 0.f ? ay
+                       : (fmaxf(ax, ay) > 1e-18f ? sqrtf(fmaf(x0.x, x0.x, x0.y * x0.y))
+                                                 : hypotf(x0.x, x0.y));
       const float inv = 1.f / sqrtf(2.f * nrm * (nrm + a0));
       alpha = a0 > 0.f ? make_float2(-x0.x / a0 * nrm, -x0.y / a0 * nrm) : make_float2(-nrm, 0.f);
       if (row >= k && row < m) {
@@ -411,7 +418,8 @@ __device__ int cta_jacobi_svd(float2* X, int m, int n, int ld, float2* V, int ld
   // rounding otherwise keeps rotating up to the sweep cap.  The floor sits two orders of
   // magnitude under the truncation tolerances used (1e-10 of the weight)
   const float thr = 2.f * sqrtf((float)m) * 5.96e-8f;
-  const float floor_g = jacobi_floor<NT>(X, m, n, ld, red);
+  // (small matrices converge in a few sweeps without the floor; it is not worth its pass)
+  const float floor_g = n > 16 ? jacobi_floor<NT>(X, m, n, ld, red) : 0.f;
   int sweep = 0;
   for (; sweep < 30 && N >= 2; ++sweep) {
     if (threadIdx.x == 0) *flag = 0;

@@ -843,17 +843,35 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_compress(DevCtx c,
     const int b0 = sm.bnd[q], b1 = sm.bnd[q + 1], b2 = sm.bnd[q + 2];
     gcopy<NT>(sm.S, site_ptr(c, bb, slot, q), b0 * 2 * b1);
     gcopy<NT>(sm.F, site_ptr(c, bb, slot, q + 1), b1 * 2 * b2);
-    if (threadIdx.x == 0) build_block(blk, G1, sm.creg, sm.G);
+    if (blk.composed) {
+      if (threadIdx.x < 16) sm.G[threadIdx.x] = blk.Gc[threadIdx.x];
+    } else if (threadIdx.x == 0) {
+      build_block(blk, G1, sm.creg, sm.G);
+    }
     __syncthreads();
     const int m = 2 * b0, nn = 2 * b2;
+    // X = Theta, column-major with leading dimension ldx (8 when every bond <= 4: the row
+    // and column of an entry then come from shifts)
+    const int ldx = C == 4 ? 8 : m;
     float2* X = sm.T;
     float2* V = sm.T + 4 * C * C;
     // P[(a t), (v b)] = sum_x B_q[a][t][x] B_{q+1}[x][v][b]
-    for (int idx = threadIdx.x; idx < m * nn; idx += NT) {
-      const int row = idx % m, col = idx / m;
-      float2 acc = cz();
-      for (int x = 0; x < b1; ++x) cfma(acc, sm.S[row * b1 + x], sm.F[x * nn + col]);
-      X[row + col * m] = acc;
+    if (C == 4) {
+      for (int idx = threadIdx.x; idx < 64; idx += NT) {
+        const int row = idx & 7, col = idx >> 3;
+        if (row < m && col < nn) {
+          float2 acc = cz();
+          for (int x = 0; x < b1; ++x) cfma(acc, sm.S[row * b1 + x], sm.F[x * nn + col]);
+          X[row + col * 8] = acc;
+        }
+      }
+    } else {
+      for (int idx = threadIdx.x; idx < m * nn; idx += NT) {
+        const int row = idx % m, col = idx / m;
+        float2 acc = cz();
+        for (int x = 0; x < b1; ++x) cfma(acc, sm.S[row * b1 + x], sm.F[x * nn + col]);
+        X[row + col * m] = acc;
+      }
     }
     __syncthreads();
     // Theta[(a s), (u b)] = sum_{t v} G[(s u), (t v)] P[(a t), (v b)]  (in place per (a, b))
@@ -863,7 +881,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_compress(DevCtx c,
 #pragma unroll
       for (int t = 0; t < 2; ++t)
 #pragma unroll
-        for (int v = 0; v < 2; ++v) in[t * 2 + v] = X[(a * 2 + t) + (v * b2 + bcol) * m];
+        for (int v = 0; v < 2; ++v) in[t * 2 + v] = X[(a * 2 + t) + (v * b2 + bcol) * ldx];
 #pragma unroll
       for (int o = 0; o < 4; ++o) {
         float2 acc = cz();
@@ -874,11 +892,19 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_compress(DevCtx c,
 #pragma unroll
       for (int s = 0; s < 2; ++s)
 #pragma unroll
-        for (int u = 0; u < 2; ++u) X[(a * 2 + s) + (u * b2 + bcol) * m] = out[s * 2 + u];
+        for (int u = 0; u < 2; ++u) X[(a * 2 + s) + (u * b2 + bcol) * ldx] = out[s * 2 + u];
     }
     __syncthreads();
     PHASE_MARK(12);
-    cta_jacobi_svd<NT>(X, m, nn, m, V, nn, sm.sig2, sm.sigf, sm.perm, &sm.iv[5], sm.red);
+    const int svd_sweeps =
+        cta_jacobi_svd<NT>(X, m, nn, ldx, V, nn, sm.sig2, sm.sigf, sm.perm, &sm.iv[5], sm.red);
+    (void)svd_sweeps;
+#ifdef DCS_PHASE_TIMERS
+    if (threadIdx.x == 0) {
+      atomicAdd(&g_phase_cycles[22], (unsigned long long)svd_sweeps);
+      atomicAdd(&g_phase_cycles[23], 1ull);
+    }
+#endif
     PHASE_MARK(13);
     int k;
     float inv;
@@ -915,7 +941,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_compress(DevCtx c,
       const int row = idx / k, kk = idx % k;
       const float sg = sm.sigf[sm.perm[kk]];
       const float sc = asc ? (sg > 0.f ? 1.f / sqrtf(sg) : 0.f) : inv;
-      pq[idx] = cscale(X[row + sm.perm[kk] * m], sc);
+      pq[idx] = cscale(X[row + sm.perm[kk] * ldx], sc);
     }
     float2* pq1 = site_ptr(c, bb, slot, q + 1);
     for (int idx = threadIdx.x; idx < k * nn; idx += NT) {
