@@ -387,7 +387,7 @@ __device__ float jacobi_floor(const float2* X, int m, int n, int ld, double* red
 
 // One-sided (Hestenes) Jacobi SVD of X (m x n, column-major, ld): rotates pairs of columns
 // until they are mutually orthogonal, X V = U Sigma, accumulating the unitary V (n x n,
-// column-major, ldv).  Pairs follow the circle-method tournament so each round rotates
+// column-major, ldv; not accumulated when V is null).  Pairs follow the circle-method tournament so each round rotates
 // disjoint pairs in parallel, one group of G lanes per pair.  A pair (i, j) with
 // Gram [[a, g], [conj g, b]] is rotated when |g| > 2 sqrt(m) eps sqrt(a b):
 // zeta = (b - a) / (2|g|), t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1+t^2),
@@ -401,7 +401,7 @@ __device__ void svd_finish(const float2* X, int m, int n, int ld, double* sig2, 
 template <int NT>
 __device__ int cta_jacobi_svd(float2* X, int m, int n, int ld, float2* V, int ldv,
                               double* sig2, float* sigf, int* perm, int* flag, double* red) {
-  for (int idx = threadIdx.x; idx < n * n; idx += NT) {
+  for (int idx = threadIdx.x; V != nullptr && idx < n * n; idx += NT) {
     const int i = idx % n, j = idx / n;
     V[i + j * ldv] = make_float2(i == j ? 1.f : 0.f, 0.f);
   }
@@ -473,7 +473,7 @@ __device__ int cta_jacobi_svd(float2* X, int m, int n, int ld, float2* V, int ld
             X[i + ci * ld] = make_float2(c * xi.x - s * xj.x, c * xi.y - s * xj.y);
             X[i + cj * ld] = make_float2(s * xi.x + c * xj.x, s * xi.y + c * xj.y);
           }
-          for (int i = gl; i < n; i += G) {
+          for (int i = gl; V != nullptr && i < n; i += G) {
             const float2 vi = V[i + ci * ldv];
             const float2 vj = cmul(ph, V[i + cj * ldv]);
             V[i + ci * ldv] = make_float2(c * vi.x - s * vj.x, c * vi.y - s * vj.y);
@@ -551,8 +551,8 @@ __device__ __forceinline__ bool warp_jacobi_pair(float2* ci, float2* cj, int m, 
   return true;
 }
 
-// Columns [c0, c0 + w) of X (m rows) and V (n rows) to or from the staging area, one staged
-// column of m + n entries each.
+// Columns [c0, c0 + w) of X (m rows) and V (n rows; n = 0 without V) to or from the staging
+// area, one staged column of m + n entries each.
 template <int NT>
 __device__ __forceinline__ void stage_cols(float2* S, float2* X, int m, int ld, float2* V,
                                            int n, int ldv, int c0, int w, bool in) {
@@ -561,7 +561,7 @@ __device__ __forceinline__ void stage_cols(float2* S, float2* X, int m, int ld, 
   for (int col = warp; col < w; col += NT / 32) {
     float2* sc = S + (size_t)col * cs;
     float2* xc = X + (size_t)(c0 + col) * ld;
-    float2* vc = V + (size_t)(c0 + col) * ldv;
+    float2* vc = n > 0 ? V + (size_t)(c0 + col) * ldv : nullptr;
     for (int i = lane; i < m; i += 32) {
       if (in) sc[i] = xc[i];
       else xc[i] = sc[i];
@@ -579,18 +579,20 @@ __device__ __forceinline__ void stage_cols(float2* S, float2* X, int m, int ld, 
 // together with the matching columns of V.  Block I stays staged while the blocks J > I pass
 // through.  The pairs inside I come first (circle method on its columns), then for each J
 // its cross pairs in w rounds of disjoint pairs (a, (a + r) mod w).  Per sweep X and V
-// cross HBM about n / w times instead of about n times.
+// cross HBM about n / w times instead of about n times.  Without V (null) only X is staged,
+// which doubles w.
 template <int NT>
 __device__ int cta_jacobi_svd_staged(float2* X, int m, int n, int ld, float2* V, int ldv,
                                       double* sig2, float* sigf, int* perm, int* flag,
                                       double* red, float2* stage, size_t stage_elems) {
-  const int cs = m + n;
+  const int nv = V != nullptr ? n : 0;  // V rows staged with each column (none without V)
+  const int cs = m + nv;
   int w = (int)(stage_elems / (2 * (size_t)cs));
   if (w > n) w = n;
   if (w < 2) return cta_jacobi_svd<NT>(X, m, n, ld, V, ldv, sig2, sigf, perm, flag, red);
   constexpr int NW = NT / 32;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int idx = threadIdx.x; idx < n * n; idx += NT) {
+  for (int idx = threadIdx.x; V != nullptr && idx < n * n; idx += NT) {
     const int i = idx % n, j = idx / n;
     V[i + (size_t)j * ldv] = make_float2(i == j ? 1.f : 0.f, 0.f);
   }
@@ -607,7 +609,7 @@ __device__ int cta_jacobi_svd_staged(float2* X, int m, int n, int ld, float2* V,
     for (int I = 0; I < nb; ++I) {
       const int i0 = I * w, wi = (n - i0) < w ? (n - i0) : w;
       __syncthreads();
-      stage_cols<NT>(SI, X, m, ld, V, n, ldv, i0, wi, true);
+      stage_cols<NT>(SI, X, m, ld, V, nv, ldv, i0, wi, true);
       __syncthreads();
       // pairs inside block I: circle method
       const int N = (wi + 1) & ~1;
@@ -628,7 +630,7 @@ __device__ int cta_jacobi_svd_staged(float2* X, int m, int n, int ld, float2* V,
       }
       for (int J = I + 1; J < nb; ++J) {
         const int j0 = J * w, wj = (n - j0) < w ? (n - j0) : w;
-        stage_cols<NT>(SJ, X, m, ld, V, n, ldv, j0, wj, true);
+        stage_cols<NT>(SJ, X, m, ld, V, nv, ldv, j0, wj, true);
         __syncthreads();
         for (int r = 0; r < w; ++r) {
           for (int a = warp; a < wi; a += NW) {
@@ -638,10 +640,10 @@ __device__ int cta_jacobi_svd_staged(float2* X, int m, int n, int ld, float2* V,
           }
           __syncthreads();
         }
-        stage_cols<NT>(SJ, X, m, ld, V, n, ldv, j0, wj, false);
+        stage_cols<NT>(SJ, X, m, ld, V, nv, ldv, j0, wj, false);
         __syncthreads();
       }
-      stage_cols<NT>(SI, X, m, ld, V, n, ldv, i0, wi, false);
+      stage_cols<NT>(SI, X, m, ld, V, nv, ldv, i0, wi, false);
     }
     if (lane == 0 && rotated) *flag = 1;
     __syncthreads();

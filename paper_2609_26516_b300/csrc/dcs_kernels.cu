@@ -1238,8 +1238,7 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
     const int b0 = bt[q], b1 = bt[q + 1], b2 = bt[q + 2];
     if (threadIdx.x == 0) build_block(blk, G1, sm.creg, sm.G);
     const int m = 2 * b0, nn = 2 * b2;
-    float2* X = sm.T;           // m x nn, column-major (fits in T + T2: 4 C^2)
-    float2* V = sm.T2;          // nn x nn
+    float2* X = sm.T;           // m x nn, column-major (fits in T: 4 C^2)
     // P[(a t), (v b)] = B_q[(a t), x] B_{q+1}[x, (v b)]
     wgemm<NT>(sm, m, nn, b1, site_ptr(c, bb, slot, q), b1, 1, false, site_ptr(c, bb, slot, q + 1),
                   nn, 1, false, X, 1, m);
@@ -1264,21 +1263,38 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
     }
     __syncthreads();
     PHASE_MARK(2);
-    const int svd_sweeps = cta_jacobi_svd_staged<NT>(X, m, nn, m, V, nn, sm.sig2, sm.sigf,
+    // Truncated SVD of Theta = U S V^H, one side only: the one-sided Jacobi method
+    // orthogonalises the columns of Theta (ascending: they become U S) or of Theta^H
+    // (descending: V S) without accumulating the rotations, and the factor on the other
+    // side comes from one GEMM with an untouched copy of Theta: S_k V_k^H = U_k^H Theta
+    // (ascending), U_k S_k = Theta V_k (descending).  Neither needs S^-1.
+    float2* Y = sm.T2;  // ascending: a copy of Theta; descending: Theta^H (nn x m)
+    for (int idx = threadIdx.x; idx < m * nn; idx += NT) {
+      if (asc) {
+        Y[idx] = X[idx];
+      } else {
+        const int row = idx % m, col = idx / m;
+        Y[col + (size_t)row * nn] = cconj(X[idx]);
+      }
+    }
+    __syncthreads();
+    float2* Z = asc ? X : Y;
+    const int zr = asc ? m : nn, zc = asc ? nn : m;
+    const int svd_sweeps = cta_jacobi_svd_staged<NT>(Z, zr, zc, zr, nullptr, 0, sm.sig2, sm.sigf,
                                                      sm.perm, &sm.iv[5], sm.red, sm.stage,
                                                      sm.stage_elems);
     (void)svd_sweeps;
 #ifdef DCS_PHASE_TIMERS
-    if (threadIdx.x == 0 && nn >= 64) {
+    if (threadIdx.x == 0 && zc >= 64) {
       atomicAdd(&g_phase_cycles[20], (unsigned long long)svd_sweeps);
       atomicAdd(&g_phase_cycles[21], 1ull);
     }
 #endif
     PHASE_MARK(3);
     if (threadIdx.x == 0) {
-      const int kk = trunc_rank(sm.sig2, sm.perm, nn, c.chi_max, c.tol);
+      const int kk = trunc_rank(sm.sig2, sm.perm, zc, c.chi_max, c.tol);
       double w = 0.0, tot = 0.0;
-      for (int i = 0; i < nn; ++i) tot += sm.sig2[i];
+      for (int i = 0; i < zc; ++i) tot += sm.sig2[i];
       for (int i = 0; i < kk; ++i) w += sm.sig2[sm.perm[i]];
       sm.iv[6] = kk;
       sm.dv[0] = w;
@@ -1289,17 +1305,30 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
     const int kk = sm.iv[6];
     const float inv = (float)(1.0 / sqrt(sm.dv[0]));
     float2* pq = site_ptr(c, bb, slot, q);  // singular values placed as in k_compress
-    for (int idx = threadIdx.x; idx < m * kk; idx += NT) {
-      const int row = idx / kk, k2 = idx % kk;
-      const float sg = sm.sigf[sm.perm[k2]];
-      const float sc = asc ? (sg > 0.f ? 1.f / sqrtf(sg) : 0.f) : inv;
-      pq[idx] = cscale(X[row + (size_t)sm.perm[k2] * m], sc);
-    }
     float2* pq1 = site_ptr(c, bb, slot, q + 1);
-    for (int idx = threadIdx.x; idx < kk * nn; idx += NT) {
-      const int k2 = idx / nn, col = idx % nn;
-      const float2 v = cconj(V[col + (size_t)sm.perm[k2] * nn]);
-      pq1[idx] = asc ? cscale(v, sqrtf(sm.sigf[sm.perm[k2]]) * inv) : v;
+    if (asc) {
+      // B_q = U_k (the kept columns, normalised), B_{q+1} = U_k^H Theta / ||S_k||
+      for (int idx = threadIdx.x; idx < m * kk; idx += NT) {
+        const int row = idx / kk, k2 = idx % kk;
+        const float sg = sm.sigf[sm.perm[k2]];
+        pq[idx] = cscale(X[row + (size_t)sm.perm[k2] * m], sg > 0.f ? 1.f / sqrtf(sg) : 0.f);
+      }
+      __syncthreads();
+      wgemm<NT>(sm, kk, nn, m, pq, 1, kk, true, Y, 1, m, false, pq1, nn, 1);
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < kk * nn; idx += NT) pq1[idx] = cscale(pq1[idx], inv);
+    } else {
+      // B_{q+1} = V_k^H (rows: the kept columns of Theta^H, normalised and conjugated),
+      // B_q = Theta V_k / ||S_k||
+      for (int idx = threadIdx.x; idx < kk * nn; idx += NT) {
+        const int k2 = idx / nn, col = idx % nn;
+        const float sg = sm.sigf[sm.perm[k2]];
+        pq1[idx] = cscale(cconj(Y[col + (size_t)sm.perm[k2] * nn]), sg > 0.f ? 1.f / sqrtf(sg) : 0.f);
+      }
+      __syncthreads();
+      wgemm<NT>(sm, m, kk, nn, X, 1, m, false, pq1, 1, nn, true, pq, kk, 1);
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < m * kk; idx += NT) pq[idx] = cscale(pq[idx], inv);
     }
     __syncthreads();
     if (threadIdx.x == 0) bt[q + 1] = kk;
