@@ -168,17 +168,106 @@ __device__ __forceinline__ void tc_teardown(TcState& t) {
   if (threadIdx.x < 32) tmem_dealloc(*t.tmem, TC_TMEM_COLS);
 }
 
+// The operand elements one thread stages per K-step.  Element e of a step is mapped so that
+// a warp covers 8 consecutive rows (bits 2-4 of e) by 4 consecutive complex k (bits 0-1):
+// its 8-byte (re, im) stores then fill whole core matrices (no bank conflicts) and its
+// global loads read 32-byte runs along K or 64-byte runs along M / N.  A is staged per
+// complex element (TC_M x TC_K), B per real row of B_r^T (2 TC_N x TC_K: row 2n holds
+// (Re b, -Im b), row 2n+1 holds (Im b, Re b)).
+template <int NT>
+struct TcFetch {
+  static constexpr int PER_A = TC_M * TC_K / NT;
+  static constexpr int PER_B = 2 * TC_N * TC_K / NT;
+  float2 a[PER_A];
+  float2 b[PER_B];
+};
+
+__device__ __forceinline__ void tc_elem(int e, int& row, int& kk) {
+  kk = (e & 3) | (((e >> 5) & 1) << 2);
+  row = ((e >> 2) & 7) | ((e >> 6) << 3);
+}
+
+// Global loads of K-step s into registers (zero outside the matrices).
+template <int NT>
+__device__ __forceinline__ void tc_fetch(TcFetch<NT>& f, int s, int m0, int n0, int M, int N,
+                                         int K, const float2* A, int sam, int sak, bool conjA,
+                                         const float2* B, int sbk, int sbn, bool conjB) {
+  const int k0 = s * TC_K;
+#pragma unroll
+  for (int i = 0; i < TcFetch<NT>::PER_A; ++i) {
+    int mm, kk;
+    tc_elem(threadIdx.x + i * NT, mm, kk);
+    const int gm = m0 + mm, gk = k0 + kk;
+    float2 v = cz();
+    if (gm < M && gk < K) {
+      v = A[(size_t)gm * sam + (size_t)gk * sak];
+      if (conjA) v.y = -v.y;
+    }
+    f.a[i] = v;
+  }
+#pragma unroll
+  for (int i = 0; i < TcFetch<NT>::PER_B; ++i) {
+    int nr, kk;
+    tc_elem(threadIdx.x + i * NT, nr, kk);
+    const int gk = k0 + kk, gn = n0 + (nr >> 1);
+    float2 v = cz();
+    if (gk < K && gn < N) {
+      v = B[(size_t)gk * sbk + (size_t)gn * sbn];
+      if (conjB) v.y = -v.y;
+    }
+    // the real row's (k = 2kk, 2kk+1) pair: (Re, -Im) for an even row, (Im, Re) for odd
+    f.b[i] = (nr & 1) ? make_float2(v.y, v.x) : make_float2(v.x, -v.y);
+  }
+}
+
+// Split the fetched pairs into hi / lo TF32 and store them in the canonical layouts.
+template <int NT>
+__device__ __forceinline__ void tc_stage_store(const TcFetch<NT>& f, float* st) {
+  float* Ahi = st;
+  float* Alo = Ahi + TC_A_FLOATS;
+  float* Bhi = Alo + TC_A_FLOATS;
+  float* Blo = Bhi + TC_B_FLOATS;
+#pragma unroll
+  for (int i = 0; i < TcFetch<NT>::PER_A; ++i) {
+    int mm, kk;
+    tc_elem(threadIdx.x + i * NT, mm, kk);
+    float2 h, l;
+    tf32_split(f.a[i].x, h.x, l.x);
+    tf32_split(f.a[i].y, h.y, l.y);
+    const int o = tc_off(mm, 2 * kk);
+    *reinterpret_cast<float2*>(Ahi + o) = h;
+    *reinterpret_cast<float2*>(Alo + o) = l;
+  }
+#pragma unroll
+  for (int i = 0; i < TcFetch<NT>::PER_B; ++i) {
+    int nr, kk;
+    tc_elem(threadIdx.x + i * NT, nr, kk);
+    float2 h, l;
+    tf32_split(f.b[i].x, h.x, l.x);
+    tf32_split(f.b[i].y, h.y, l.y);
+    const int o = tc_off(nr, 2 * kk);
+    *reinterpret_cast<float2*>(Bhi + o) = h;
+    *reinterpret_cast<float2*>(Blo + o) = l;
+  }
+}
+
 template <int NT>
 __device__ void cta_cgemm_tc(int M, int N, int K, const float2* A, int sam, int sak, bool conjA,
                              const float2* B, int sbk, int sbn, bool conjB, float2* Cm, int scm,
                              int scn, TcState& t) {
   static_assert(NT % 128 == 0, "the epilogue needs whole warp quadrants");
+  static_assert((TC_M * TC_K) % NT == 0 && (2 * TC_K * TC_N) % NT == 0, "staging per thread");
+  static_assert(TC_K == 8, "the element mapping covers 8 complex k per step");
   constexpr uint32_t IDESC = tc_idesc(128, 256);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t tbase = *t.tmem;
   const int ksteps = (K + TC_K - 1) / TC_K;
   for (int m0 = 0; m0 < M; m0 += TC_M)
     for (int n0 = 0; n0 < N; n0 += TC_N) {
+      // software pipeline: the global loads of K-step s+1 are in flight while step s is
+      // split, staged and multiplied
+      TcFetch<NT> f;
+      tc_fetch<NT>(f, 0, m0, n0, M, N, K, A, sam, sak, conjA, B, sbk, sbn, conjB);
       for (int s = 0; s < ksteps; ++s) {
         const int b = s & 1;
         float* st = t.stage + b * TC_STAGE_FLOATS;
@@ -191,58 +280,9 @@ __device__ void cta_cgemm_tc(int M, int N, int K, const float2* A, int sam, int 
           if (!mbar_wait(&t.mbar[b], (uint32_t)((t.uses[b] - 1) & 1))) *t.err = 1;
         }
         __syncthreads();
-        const int k0 = s * TC_K;
-        for (int idx = tid; idx < TC_M * TC_K; idx += NT) {
-          int mm, kk;
-          if (sak == 1) {
-            mm = idx / TC_K;
-            kk = idx % TC_K;
-          } else {
-            kk = idx / TC_M;
-            mm = idx % TC_M;
-          }
-          const int gm = m0 + mm, gk = k0 + kk;
-          float2 v = cz();
-          if (gm < M && gk < K) {
-            v = A[(size_t)gm * sam + (size_t)gk * sak];
-            if (conjA) v.y = -v.y;
-          }
-          float h, l;
-          tf32_split(v.x, h, l);
-          Ahi[tc_off(mm, 2 * kk)] = h;
-          Alo[tc_off(mm, 2 * kk)] = l;
-          tf32_split(v.y, h, l);
-          Ahi[tc_off(mm, 2 * kk + 1)] = h;
-          Alo[tc_off(mm, 2 * kk + 1)] = l;
-        }
-        for (int idx = tid; idx < TC_K * TC_N; idx += NT) {
-          int kk, nn;
-          if (sbn == 1) {
-            kk = idx / TC_N;
-            nn = idx % TC_N;
-          } else {
-            nn = idx / TC_K;
-            kk = idx % TC_K;
-          }
-          const int gk = k0 + kk, gn = n0 + nn;
-          float2 v = cz();
-          if (gk < K && gn < N) {
-            v = B[(size_t)gk * sbk + (size_t)gn * sbn];
-            if (conjB) v.y = -v.y;
-          }
-          float rh, rl, ih, il;
-          tf32_split(v.x, rh, rl);
-          tf32_split(v.y, ih, il);
-          // rows of the K-major B_r^T: real column nr = 2n (Re c), 2n+1 (Im c)
-          Bhi[tc_off(2 * nn, 2 * kk)] = rh;
-          Blo[tc_off(2 * nn, 2 * kk)] = rl;
-          Bhi[tc_off(2 * nn, 2 * kk + 1)] = -ih;
-          Blo[tc_off(2 * nn, 2 * kk + 1)] = -il;
-          Bhi[tc_off(2 * nn + 1, 2 * kk)] = ih;
-          Blo[tc_off(2 * nn + 1, 2 * kk)] = il;
-          Bhi[tc_off(2 * nn + 1, 2 * kk + 1)] = rh;
-          Blo[tc_off(2 * nn + 1, 2 * kk + 1)] = rl;
-        }
+        tc_stage_store<NT>(f, st);
+        if (s + 1 < ksteps)
+          tc_fetch<NT>(f, s + 1, m0, n0, M, N, K, A, sam, sak, conjA, B, sbk, sbn, conjB);
         fence_async_smem();
         tc_fence_before();
         __syncthreads();
