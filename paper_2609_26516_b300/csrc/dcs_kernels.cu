@@ -313,13 +313,14 @@ struct Work {
 
 
 __host__ __device__ inline size_t work_arrays_bytes(int C, bool big) {
-  return sizeof(float2) * (64 + 64 + 16 + 2 * C + (big ? (GBM + GBN) * GBK : 0)) +
+  (void)big;
+  return sizeof(float2) * (64 + 64 + 16 + 2 * C) +
          sizeof(double) * (32 + 2 * C + 8) + sizeof(float) * 4 * C +
          sizeof(int) * (2 * C + 2 * (DCS_MAX_QUBITS + 1) + 16) + sizeof(uint64_t) * DCS_CWORDS + 64;
 }
 // Large path: a 128-byte head (tensor-core barriers and counters) and a staging region that
-// serves the tensor-core GEMM tiles and the blocked SVD in turn, filling the CTA's shared
-// memory up to 224 KB.
+// serves the tensor-core GEMM tiles, the SIMT GEMM tiles and the blocked SVD in turn, filling
+// the CTA's shared memory up to 224 KB.
 constexpr size_t BIG_SMEM_BYTES = 224 * 1024;
 constexpr size_t BIG_HEAD_BYTES = 128;
 __host__ __device__ inline size_t big_stage_bytes(int C) {
@@ -363,10 +364,9 @@ __device__ void carve(Work& w, unsigned char* raw, int C, float2* big_area, bool
   w.G = w.W2 + 64;
   w.alph = w.G + 16;
   float2* tiles = w.alph + 2 * C;
-  if (big_area) {
-    w.gA = tiles;
+  if (big_area) {  // the SIMT GEMM tiles share the staging region
+    w.gA = w.stage;
     w.gB = w.gA + GBM * GBK;
-    tiles = w.gB + GBK * GBN;
   } else {
     w.gA = w.gB = nullptr;
   }

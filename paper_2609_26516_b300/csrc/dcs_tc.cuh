@@ -9,11 +9,13 @@
 //    lo = x - hi; A B ~ hi_A hi_B + hi_A lo_B + lo_A hi_B (the dropped lo lo term is
 //    ~2^-22 relative).
 // Tile: 128 complex rows x 128 complex columns (MMA M = 128, N = 256 real), K in steps of 8
-// complex (16 real = two MMAs of K = 8).  Operands are staged by all threads in the
-// canonical K-major layout without swizzle: 8-row x 16-byte core matrices, core matrices
-// along K 128 bytes apart (leading-dimension offset), 8-row groups 512 bytes apart (stride
-// offset).  Two staging buffers alternate; the MMAs of one stage run while the other is
-// filled.
+// complex (16 real = two MMAs of K = 8).  The raw complex operand tiles of the next K-steps
+// stream into a 4-deep shared-memory ring with cp.async (zero fill outside the matrices), so
+// global latency stays off the critical path.  From there all threads split them into hi/lo
+// TF32 in the canonical K-major layout without swizzle: 8-row x 16-byte core matrices, core
+// matrices along K 128 bytes apart (leading-dimension offset), 8-row groups 512 bytes apart
+// (stride offset).  Two canonical buffers alternate; the MMAs of one stage run while the
+// other is filled.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -28,7 +30,10 @@ constexpr int TC_K = 8;     // complex K per stage (16 real)
 constexpr int TC_A_FLOATS = TC_M * 2 * TC_K;        // one A copy (hi or lo): 128 x 16
 constexpr int TC_B_FLOATS = 2 * TC_N * 2 * TC_K;    // one B copy: 256 x 16
 constexpr int TC_STAGE_FLOATS = 2 * (TC_A_FLOATS + TC_B_FLOATS);
-constexpr int TC_SMEM_FLOATS = 2 * TC_STAGE_FLOATS;  // two stages: 96 KB
+constexpr int TC_RAW = 4;                            // raw operand ring depth (K-steps)
+constexpr int TC_RAW_ELEMS = TC_M * TC_K + TC_K * TC_N;  // complex elements per raw step
+// two canonical stages (96 KB) and the raw ring (64 KB)
+constexpr int TC_SMEM_FLOATS = 2 * TC_STAGE_FLOATS + TC_RAW * 2 * TC_RAW_ELEMS;
 constexpr int TC_TMEM_COLS = 256;
 constexpr long long TC_WAIT_LIMIT = 1ll << 26;      // bounded mbarrier spins
 
@@ -168,83 +173,89 @@ __device__ __forceinline__ void tc_teardown(TcState& t) {
   if (threadIdx.x < 32) tmem_dealloc(*t.tmem, TC_TMEM_COLS);
 }
 
-// The operand elements one thread stages per K-step.  Element e of a step is mapped so that
-// a warp covers 8 consecutive rows (bits 2-4 of e) by 4 consecutive complex k (bits 0-1):
-// its 8-byte (re, im) stores then fill whole core matrices (no bank conflicts) and its
-// global loads read 32-byte runs along K or 64-byte runs along M / N.  A is staged per
-// complex element (TC_M x TC_K), B per real row of B_r^T (2 TC_N x TC_K: row 2n holds
-// (Re b, -Im b), row 2n+1 holds (Im b, Re b)).
-template <int NT>
-struct TcFetch {
-  static constexpr int PER_A = TC_M * TC_K / NT;
-  static constexpr int PER_B = 2 * TC_N * TC_K / NT;
-  float2 a[PER_A];
-  float2 b[PER_B];
-};
+__device__ __forceinline__ void cp_async8(uint32_t saddr, const void* g, int bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" : : "r"(saddr), "l"(g), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N_PENDING>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" : : "n"(N_PENDING) : "memory");
+}
 
+// Raw tiles of K-step s into ring slot `raw` (A as [mm][kk], B as [kk][nn], complex), one
+// 8-byte cp.async per element; consecutive threads follow the contiguous global index.
+template <int NT>
+__device__ __forceinline__ void tc_raw_issue(float2* raw, int s, int m0, int n0, int M, int N,
+                                             int K, const float2* A, int sam, int sak,
+                                             const float2* B, int sbk, int sbn) {
+  const int k0 = s * TC_K;
+  float2* rA = raw;
+  float2* rB = raw + TC_M * TC_K;
+#pragma unroll
+  for (int e = threadIdx.x; e < TC_M * TC_K; e += NT) {
+    const int mm = sak == 1 ? e / TC_K : e % TC_M;
+    const int kk = sak == 1 ? e % TC_K : e / TC_M;
+    const int gm = m0 + mm, gk = k0 + kk;
+    const bool in = gm < M && gk < K;
+    cp_async8(smem_addr(rA + mm * TC_K + kk), in ? A + ((size_t)gm * sam + (size_t)gk * sak) : A,
+              in ? 8 : 0);
+  }
+#pragma unroll
+  for (int e = threadIdx.x; e < TC_K * TC_N; e += NT) {
+    const int kk = sbn == 1 ? e / TC_N : e % TC_K;
+    const int nn = sbn == 1 ? e % TC_N : e / TC_K;
+    const int gk = k0 + kk, gn = n0 + nn;
+    const bool in = gk < K && gn < N;
+    cp_async8(smem_addr(rB + kk * TC_N + nn), in ? B + ((size_t)gk * sbk + (size_t)gn * sbn) : B,
+              in ? 8 : 0);
+  }
+}
+
+// Element e of a K-step in the staging order: a warp covers 8 consecutive rows (bits 2-4 of
+// e) by 4 consecutive complex k (bits 0-1), so its 8-byte (re, im) stores fill whole core
+// matrices without bank conflicts.
 __device__ __forceinline__ void tc_elem(int e, int& row, int& kk) {
   kk = (e & 3) | (((e >> 5) & 1) << 2);
   row = ((e >> 2) & 7) | ((e >> 6) << 3);
 }
 
-// Global loads of K-step s into registers (zero outside the matrices).
+// Raw slot -> canonical hi / lo stage.  A per complex element (TC_M x TC_K); B per real row
+// of B_r^T (2 TC_N x TC_K: row 2n holds (Re b, -Im b), row 2n+1 holds (Im b, Re b)).
 template <int NT>
-__device__ __forceinline__ void tc_fetch(TcFetch<NT>& f, int s, int m0, int n0, int M, int N,
-                                         int K, const float2* A, int sam, int sak, bool conjA,
-                                         const float2* B, int sbk, int sbn, bool conjB) {
-  const int k0 = s * TC_K;
-#pragma unroll
-  for (int i = 0; i < TcFetch<NT>::PER_A; ++i) {
-    int mm, kk;
-    tc_elem(threadIdx.x + i * NT, mm, kk);
-    const int gm = m0 + mm, gk = k0 + kk;
-    float2 v = cz();
-    if (gm < M && gk < K) {
-      v = A[(size_t)gm * sam + (size_t)gk * sak];
-      if (conjA) v.y = -v.y;
-    }
-    f.a[i] = v;
-  }
-#pragma unroll
-  for (int i = 0; i < TcFetch<NT>::PER_B; ++i) {
-    int nr, kk;
-    tc_elem(threadIdx.x + i * NT, nr, kk);
-    const int gk = k0 + kk, gn = n0 + (nr >> 1);
-    float2 v = cz();
-    if (gk < K && gn < N) {
-      v = B[(size_t)gk * sbk + (size_t)gn * sbn];
-      if (conjB) v.y = -v.y;
-    }
-    // the real row's (k = 2kk, 2kk+1) pair: (Re, -Im) for an even row, (Im, Re) for odd
-    f.b[i] = (nr & 1) ? make_float2(v.y, v.x) : make_float2(v.x, -v.y);
-  }
-}
-
-// Split the fetched pairs into hi / lo TF32 and store them in the canonical layouts.
-template <int NT>
-__device__ __forceinline__ void tc_stage_store(const TcFetch<NT>& f, float* st) {
+__device__ __forceinline__ void tc_stage_from_raw(const float2* raw, float* st, bool conjA,
+                                                  bool conjB) {
+  const float2* rA = raw;
+  const float2* rB = raw + TC_M * TC_K;
   float* Ahi = st;
   float* Alo = Ahi + TC_A_FLOATS;
   float* Bhi = Alo + TC_A_FLOATS;
   float* Blo = Bhi + TC_B_FLOATS;
 #pragma unroll
-  for (int i = 0; i < TcFetch<NT>::PER_A; ++i) {
+  for (int e = threadIdx.x; e < TC_M * TC_K; e += NT) {
     int mm, kk;
-    tc_elem(threadIdx.x + i * NT, mm, kk);
+    tc_elem(e, mm, kk);
+    float2 v = rA[mm * TC_K + kk];
+    if (conjA) v.y = -v.y;
     float2 h, l;
-    tf32_split(f.a[i].x, h.x, l.x);
-    tf32_split(f.a[i].y, h.y, l.y);
+    tf32_split(v.x, h.x, l.x);
+    tf32_split(v.y, h.y, l.y);
     const int o = tc_off(mm, 2 * kk);
     *reinterpret_cast<float2*>(Ahi + o) = h;
     *reinterpret_cast<float2*>(Alo + o) = l;
   }
 #pragma unroll
-  for (int i = 0; i < TcFetch<NT>::PER_B; ++i) {
+  for (int e = threadIdx.x; e < 2 * TC_N * TC_K; e += NT) {
     int nr, kk;
-    tc_elem(threadIdx.x + i * NT, nr, kk);
+    tc_elem(e, nr, kk);
+    float2 v = rB[kk * TC_N + (nr >> 1)];
+    if (conjB) v.y = -v.y;
+    v = (nr & 1) ? make_float2(v.y, v.x) : make_float2(v.x, -v.y);
     float2 h, l;
-    tf32_split(f.b[i].x, h.x, l.x);
-    tf32_split(f.b[i].y, h.y, l.y);
+    tf32_split(v.x, h.x, l.x);
+    tf32_split(v.y, h.y, l.y);
     const int o = tc_off(nr, 2 * kk);
     *reinterpret_cast<float2*>(Bhi + o) = h;
     *reinterpret_cast<float2*>(Blo + o) = l;
@@ -256,18 +267,21 @@ __device__ void cta_cgemm_tc(int M, int N, int K, const float2* A, int sam, int 
                              const float2* B, int sbk, int sbn, bool conjB, float2* Cm, int scm,
                              int scn, TcState& t) {
   static_assert(NT % 128 == 0, "the epilogue needs whole warp quadrants");
-  static_assert((TC_M * TC_K) % NT == 0 && (2 * TC_K * TC_N) % NT == 0, "staging per thread");
   static_assert(TC_K == 8, "the element mapping covers 8 complex k per step");
   constexpr uint32_t IDESC = tc_idesc(128, 256);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t tbase = *t.tmem;
   const int ksteps = (K + TC_K - 1) / TC_K;
+  float2* ring = reinterpret_cast<float2*>(t.stage + 2 * TC_STAGE_FLOATS);
   for (int m0 = 0; m0 < M; m0 += TC_M)
     for (int n0 = 0; n0 < N; n0 += TC_N) {
-      // software pipeline: the global loads of K-step s+1 are in flight while step s is
-      // split, staged and multiplied
-      TcFetch<NT> f;
-      tc_fetch<NT>(f, 0, m0, n0, M, N, K, A, sam, sak, conjA, B, sbk, sbn, conjB);
+      __syncthreads();  // the ring's last reads (previous tile) are done
+#pragma unroll
+      for (int r = 0; r < TC_RAW - 1; ++r) {
+        if (r < ksteps)
+          tc_raw_issue<NT>(ring + r * TC_RAW_ELEMS, r, m0, n0, M, N, K, A, sam, sak, B, sbk, sbn);
+        cp_async_commit();
+      }
       for (int s = 0; s < ksteps; ++s) {
         const int b = s & 1;
         float* st = t.stage + b * TC_STAGE_FLOATS;
@@ -275,14 +289,19 @@ __device__ void cta_cgemm_tc(int M, int N, int K, const float2* A, int sam, int 
         float* Alo = Ahi + TC_A_FLOATS;
         float* Bhi = Alo + TC_A_FLOATS;
         float* Blo = Bhi + TC_B_FLOATS;
-        // the MMAs that last read this buffer must be done before it is overwritten
+        // refill the slot read in the previous step with step s + TC_RAW - 1
+        const int ahead = s + TC_RAW - 1;
+        if (ahead < ksteps)
+          tc_raw_issue<NT>(ring + (ahead % TC_RAW) * TC_RAW_ELEMS, ahead, m0, n0, M, N, K, A,
+                           sam, sak, B, sbk, sbn);
+        cp_async_commit();
+        cp_async_wait<TC_RAW - 1>();  // this thread's copies of step s have landed
+        // the MMAs that last read this canonical buffer must be done before it is overwritten
         if (tid == 0 && t.uses[b] > 0) {
           if (!mbar_wait(&t.mbar[b], (uint32_t)((t.uses[b] - 1) & 1))) *t.err = 1;
         }
         __syncthreads();
-        tc_stage_store<NT>(f, st);
-        if (s + 1 < ksteps)
-          tc_fetch<NT>(f, s + 1, m0, n0, M, N, K, A, sam, sak, conjA, B, sbk, sbn, conjB);
+        tc_stage_from_raw<NT>(ring + (s % TC_RAW) * TC_RAW_ELEMS, st, conjA, conjB);
         fence_async_smem();
         tc_fence_before();
         __syncthreads();
@@ -303,6 +322,7 @@ __device__ void cta_cgemm_tc(int M, int N, int K, const float2* A, int sam, int 
           t.uses[b] += 1;
         }
       }
+      cp_async_wait<0>();
       // epilogue: wait for the last stage (and the one before), read TMEM, write C
       if (tid == 0) {
         for (int b = 0; b < 2; ++b)
