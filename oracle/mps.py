@@ -30,12 +30,12 @@ The paper states only the one-site update.  Readings used for what it leaves ope
    for every block), the guess is W|A> up to that tolerance and is itself the optimum the
    sweeps converge to (f = 1 up to rounding): the sweeps are skipped, f is the product of
    the kept weight fractions and the centre stays where the guess left it.
-3. Otherwise s one-site sweeps against the exact target W|A> (W the chunk's MPO): left to
-   right first, alternating; each site takes F / ||F|| re-orthonormalised by QR (LQ when
+3. Otherwise s one-site sweeps against the exact target W|A> (W the chunk's MPO), starting
+   at the end of the chain nearest the centre the guess left (left to right when
+   c <= n-1-c), then alternating; each site takes F / ||F|| re-orthonormalised by QR (LQ when
    moving right to left), the triangular factor being dropped because the next site's
-   update is recomputed from the environments.  One direction is one sweep; with s even
-   the centre ends at site 0, with s odd at site n-1.  Bond dimensions do not change in
-   the sweeps.
+   update is recomputed from the environments.  One direction is one sweep; the centre ends
+   at the end the last sweep runs to.  Bond dimensions do not change in the sweeps.
 4. f is ||F||^2 at the last update of the last sweep: B is normalised with every other
    site orthonormal, W unitary and A normalised, so ||F|| = |<B|W A>|.
 """
@@ -222,27 +222,32 @@ def compress(A: MPS, blocks, W, chi_max: int, tol: float, sweeps: int, skip_exac
     """CompressionStep (Sec. "Simulating unitary quantum circuits with DMRG") with the
     readings in the module header.  ``blocks`` is the chunk as [(q, 4x4 or 2x2 matrix)],
     W its MPO.  A is not modified.  Returns (B, info), B normalised; after the sweeps its
-    centre is 0 (sweeps even) or n-1 (odd); an exact guess (reading 2) is returned as it is
-    unless ``skip_exact`` is False, which runs the sweeps on it all the same."""
+    centre is at the end the last sweep ran to; an exact guess (reading 2) is returned as it
+    is unless ``skip_exact`` is False, which runs the sweeps on it all the same."""
     assert sweeps >= 1
     n = A.n
     B0, kept, exact = initial_guess(A, blocks, chi_max, tol)
     if exact and skip_exact:
         f = float(np.prod(kept)) if kept else 1.0
         return B0, CompressInfo(f, [], kept)
-    move_centre(B0, 0)
+    first = 0 if B0.centre <= n - 1 - B0.centre else 1  # 0: left to right first
+    move_centre(B0, 0 if first == 0 else n - 1)
     B = B0.T
     one = np.ones((1, 1, 1), dtype=np.complex128)
     L: List = [None] * (n + 1)
     R: List = [None] * (n + 1)
     L[0] = one
     R[n] = one
-    for j in range(n - 1, 0, -1):
-        R[j] = env_right(R[j + 1], B[j], W[j], A.T[j])
+    if first == 0:
+        for j in range(n - 1, 0, -1):
+            R[j] = env_right(R[j + 1], B[j], W[j], A.T[j])
+    else:
+        for j in range(0, n - 1):
+            L[j + 1] = env_left(L[j], B[j], W[j], A.T[j])
     fids = []
-    centre = 0
+    centre = B0.centre
     for sw in range(sweeps):
-        if sw % 2 == 0:  # left to right
+        if (sw + first) % 2 == 0:  # left to right
             for j in range(0, n - 1):
                 F = site_env(L[j], W[j], A.T[j], R[j + 1])
                 bl, br = F.shape[0], F.shape[2]

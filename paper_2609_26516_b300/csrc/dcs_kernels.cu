@@ -975,11 +975,33 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_compress(DevCtx c,
   for (int j = 0; j < n; ++j)
     if (j < lo || j > hi) gcopy<NT>(site_ptr(c, bb, slot, j), site_ptr(c, kb, slot, j), at[j] * 2 * at[j + 1]);
   __syncthreads();
-  move_centre<NT>(c, sm, bb, slot, centre, 0);
-  // ---- right environments of the guess: R_j for j = n-1 .. 1 (mirrored env updates)
+  // the sweeps start at the end of the chain nearest the centre the guess left
+  const int first = centre <= n - 1 - centre ? 0 : 1;  // 0: left to right first
+  move_centre<NT>(c, sm, bb, slot, centre, first == 0 ? 0 : n - 1);
   if (threadIdx.x == 0) sm.E[0] = make_float2(1.f, 0.f);
   __syncthreads();
-  for (int j = n - 1; j >= 1; --j) {
+  // ---- left environments of the guess: L_j for j = 1 .. n-1 (first sweep right to left)
+  for (int j = 0; first == 1 && j < n - 1; ++j) {
+    if (threadIdx.x == 0) build_W(j, L, BK, G1, sm.creg, sm.W, &sm.iv[0], &sm.iv[1]);
+    __syncthreads();
+    const int dl = sm.iv[0], dr = sm.iv[1], Dm = dl > dr ? dl : dr;
+    const int nb = bt[j], nc = bt[j + 1], na = at[j], nx = at[j + 1];
+    const int m = 2 * nb;
+    gcopy<NT>(sm.S, site_ptr(c, kb, slot, j), na * 2 * nx);
+    const float2* Bj = site_ptr(c, bb, slot, j);
+    for (int idx = threadIdx.x; idx < m * nc; idx += NT) {  // Q[(b s), c] = B[b][s][c]
+      const int row = idx / nc, cc = idx % nc;
+      sm.R[row + cc * m] = Bj[idx];
+    }
+    __syncthreads();
+    c1_env_site<NT>(sm.E, sm.S, sm.T, nb, dl, na, nx, Dm);
+    c2_mix<NT>(sm.T, sm.W, nb, dl, dr, nx, Dm);
+    c4_env_update<NT>(sm.R, m, sm.T, sm.E, nb, dr, nx, nc, Dm);
+    gcopy<NT>(env_ptr(c.Lc, c, slot, j + 1), sm.E, nc * dr * nx);
+    __syncthreads();
+  }
+  // ---- right environments of the guess: R_j for j = n-1 .. 1 (mirrored env updates)
+  for (int j = n - 1; first == 0 && j >= 1; --j) {
     if (threadIdx.x == 0) build_W(j, L, BK, G1, sm.creg, sm.W, &sm.iv[0], &sm.iv[1]);
     __syncthreads();
     const int dl = sm.iv[0], dr = sm.iv[1], Dm = dl > dr ? dl : dr;
@@ -1011,7 +1033,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_compress(DevCtx c,
   for (int sw = 0; sw < c.sweeps; ++sw) {
     if (threadIdx.x == 0) sm.E[0] = make_float2(1.f, 0.f);
     __syncthreads();
-    if ((sw & 1) == 0) {  // left to right
+    if (((sw + first) & 1) == 0) {  // left to right
       for (int j = 0; j < n; ++j) {
         if (threadIdx.x == 0) build_W(j, L, BK, G1, sm.creg, sm.W, &sm.iv[0], &sm.iv[1]);
         __syncthreads();
@@ -1346,12 +1368,29 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
   for (int j = 0; j < n; ++j)
     if (j < lo || j > hi) gcopy<NT>(site_ptr(c, bb, slot, j), site_ptr(c, kb, slot, j), at[j] * 2 * at[j + 1]);
   __syncthreads();
-  move_centre<NT>(c, sm, bb, slot, centre, 0);
+  // the sweeps start at the end of the chain nearest the centre the guess left
+  const int first = centre <= n - 1 - centre ? 0 : 1;  // 0: left to right first
+  move_centre<NT>(c, sm, bb, slot, centre, first == 0 ? 0 : n - 1);
   PHASE_MARK(5);
-  // ---- right environments of the guess (mirrored env updates with B given)
   if (threadIdx.x == 0) sm.E[0] = make_float2(1.f, 0.f);
   __syncthreads();
-  for (int j = n - 1; j >= 1; --j) {
+  // ---- left environments of the guess (env updates with B given; first sweep right to left)
+  for (int j = 0; first == 1 && j < n - 1; ++j) {
+    if (threadIdx.x == 0) build_W(j, L, BK, G1, sm.creg, sm.W, &sm.iv[0], &sm.iv[1]);
+    __syncthreads();
+    const int dl = sm.iv[0], dr = sm.iv[1];
+    const int nb = bt[j], nc = bt[j + 1], na = at[j], nx = at[j + 1];
+    const float2* A = site_ptr(c, kb, slot, j);
+    const float2* Bj = site_ptr(c, bb, slot, j);
+    wgemm<NT>(sm, nb * dl, 2 * nx, na, sm.E, na, 1, false, A, 2 * nx, 1, false, sm.T, 2 * nx, 1);
+    mix_big<NT>(sm.T, dl * 2 * nx, 2 * nx, nx, 1, sm.T2, sm.W, nb, dl, dr, nx, false);
+    // L_{j+1}[c, (e x)] = sum_{(b s)} conj(B_j[(b s), c]) T2[(b s), (e x)]
+    wgemm<NT>(sm, nc, dr * nx, 2 * nb, Bj, 1, nc, true, sm.T2, dr * nx, 1, false, sm.E, dr * nx, 1);
+    gcopy<NT>(env_ptr(c.Lc, c, slot, j + 1), sm.E, nc * dr * nx);
+    __syncthreads();
+  }
+  // ---- right environments of the guess (mirrored env updates with B given)
+  for (int j = n - 1; first == 0 && j >= 1; --j) {
     if (threadIdx.x == 0) build_W(j, L, BK, G1, sm.creg, sm.W, &sm.iv[0], &sm.iv[1]);
     __syncthreads();
     const int dl = sm.iv[0], dr = sm.iv[1];
@@ -1382,7 +1421,7 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
     sm.use_tc = TC && (sw < c.sweeps - 1);
     if (threadIdx.x == 0) sm.E[0] = make_float2(1.f, 0.f);
     __syncthreads();
-    if ((sw & 1) == 0) {  // left to right
+    if (((sw + first) & 1) == 0) {  // left to right
       for (int j = 0; j < n; ++j) {
         if (threadIdx.x == 0) build_W(j, L, BK, G1, sm.creg, sm.W, &sm.iv[0], &sm.iv[1]);
         __syncthreads();

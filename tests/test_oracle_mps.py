@@ -128,12 +128,14 @@ def test_compress_exact_regime_equals_statevector(n):
     assert info.fidelities_per_sweep == []
     assert abs(info.f - 1.0) < 1e-12
     assert abs(abs(np.vdot(dense(B), want)) - 1.0) < 1e-12
-    # ... and sweeping it all the same returns the same state: the shortcut loses nothing
+    # ... and sweeping it all the same returns the same state: the shortcut loses nothing.
+    # The sweeps start at the end nearest the guess's centre and alternate.
+    first = 0 if B.centre <= n - 1 - B.centre else 1
     for s in (1, 2, 3):
         B2, info = M.compress(A.copy(), blocks, W, 64, 0.0, s, skip_exact=False)
         assert abs(info.f - 1.0) < 1e-12
         assert abs(abs(np.vdot(dense(B2), dense(B))) - 1.0) < 1e-12
-        assert B2.centre == (0 if s % 2 == 0 else n - 1)
+        assert B2.centre == (n - 1 if (s - 1 + first) % 2 == 0 else 0)
 
 
 @pytest.mark.parametrize("centre", [0, 3, 8])
@@ -162,11 +164,14 @@ def test_guess_block_order_starts_nearest_the_centre(centre):
             np.testing.assert_allclose(m @ m.conj().T, np.eye(al), atol=1e-12)
 
 
-@pytest.mark.parametrize("seed", [1, 2, 3])
-def test_compress_truncated_fidelity_definition_and_monotone(seed):
+@pytest.mark.parametrize("seed,centre", [(1, 0), (2, 0), (3, 0), (4, 7), (5, 7)])
+def test_compress_truncated_fidelity_definition_and_monotone(seed, centre):
+    # centre 0: the guess runs left to right and the sweeps start right to left; centre 7:
+    # the other way round
     rng = np.random.default_rng(seed)
     n = 8
     A = random_mps(rng, n, 3)  # bonds <= chi_max, as every compression leaves them
+    M.move_centre(A, centre)
     blocks = _layer_blocks(rng, n, seed % 2)
     W = LY.blocks_mpo(n, blocks)
     target = LY.chunk_unitary_dense(n, W) @ dense(A)
