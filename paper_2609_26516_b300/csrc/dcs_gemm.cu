@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(GEMM_NT, 1) k_cgemm(GemmArgs g, int mode, int*
     tc_teardown(t);
   } else {
     float2* sA = reinterpret_cast<float2*>(raw);
-    float2* sB = sA + GBM * GBK;
+    float2* sB = sA + GBM * GSA_LD;
     cta_cgemm<GEMM_NT>(g.M, g.N, g.K, A, (int)g.sam, (int)g.sak, g.conjA, B, (int)g.sbk,
                        (int)g.sbn, g.conjB, C, (int)g.scm, (int)g.scn, sA, sB);
   }
@@ -70,7 +70,7 @@ extern "C" dcs_status_t dcs_cgemm(int32_t mode, int32_t batch, int32_t M, int32_
              scm, scn, scb};
   const size_t smem = mode == DCS_GEMM_TENSOR
                           ? sizeof(float) * TC_SMEM_FLOATS + 64
-                          : sizeof(float2) * (GBM * GBK + GBK * GBN);
+                          : sizeof(float2) * GEMM_SIMT_SMEM_ELEMS;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (cudaFuncSetAttribute(k_cgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)

@@ -7,11 +7,17 @@
 namespace dcs {
 
 constexpr int GBM = 64, GBN = 64, GBK = 16;  // SIMT CTA GEMM tile
+// padded leading dimensions of the staged tiles (fewer bank conflicts on the transposing
+// stores; the B rows stay 16-byte aligned)
+constexpr int GSA_LD = GBK + 1, GSB_LD = GBN + 2;
+constexpr int GEMM_SIMT_SMEM_ELEMS = GBM * GSA_LD + GBK * GSB_LD;
 
 // ----------------------------------------------------------------------------- CTA GEMM
 // C[m, n] = sum_k opA(m, k) opB(k, n) with opA(m, k) = A[m sam + k sak] (conjugated if
 // conjA), opB(k, n) = B[k sbk + n sbn] (conjugated if conjB), C[m scm + n scn].  FP32 SIMT
-// with 64 x 64 x 16 shared-memory tiles; each thread owns an 8-element micro tile.
+// with 64 x 64 x 16 shared-memory tiles (sA, sB: GEMM_SIMT_SMEM_ELEMS complex); each thread
+// owns an 8-element micro tile, 2 rows x 4 columns at 512 threads, so a k step costs two
+// broadcast loads of A and two 16-byte loads of B for eight complex FMAs.
 template <int NT>
 __device__ void cta_cgemm(int M, int N, int K, const float2* A, int sam, int sak, bool conjA,
                           const float2* B, int sbk, int sbn, bool conjB, float2* Cm, int scm,
@@ -41,7 +47,7 @@ __device__ void cta_cgemm(int M, int N, int K, const float2* A, int sam, int sak
             v = A[(size_t)gm * sam + (size_t)gk * sak];
             if (conjA) v.y = -v.y;
           }
-          sA[mm * GBK + kk] = v;
+          sA[mm * GSA_LD + kk] = v;
         }
         for (int idx = tid; idx < GBK * GBN; idx += NT) {
           int kk, nn;
@@ -58,31 +64,52 @@ __device__ void cta_cgemm(int M, int N, int K, const float2* A, int sam, int sak
             v = B[(size_t)gk * sbk + (size_t)gn * sbn];
             if (conjB) v.y = -v.y;
           }
-          sB[kk * GBN + nn] = v;
+          sB[kk * GSB_LD + nn] = v;
         }
         __syncthreads();
-        // thread tid owns rows (tid / (GBN / 2)) * ... : PER outputs in one row, PER columns
-        const int row = tid / (GBN / PER);
-        const int col0 = (tid % (GBN / PER)) * PER;
+        if constexpr (NT == 512) {
+          // rows 2 ty, 2 ty + 1 and columns 4 tx .. 4 tx + 3, tx = tid mod 16
+          const int tx = tid & 15, ty = tid >> 4;
 #pragma unroll 4
-        for (int kk = 0; kk < GBK; ++kk) {
-          const float2 a = sA[row * GBK + kk];
+          for (int kk = 0; kk < GBK; ++kk) {
+            const float2 a0 = sA[(2 * ty) * GSA_LD + kk], a1 = sA[(2 * ty + 1) * GSA_LD + kk];
+            const float4 b01 = *reinterpret_cast<const float4*>(sB + kk * GSB_LD + 4 * tx);
+            const float4 b23 = *reinterpret_cast<const float4*>(sB + kk * GSB_LD + 4 * tx + 2);
+            const float2 bv[4] = {make_float2(b01.x, b01.y), make_float2(b01.z, b01.w),
+                                  make_float2(b23.x, b23.y), make_float2(b23.z, b23.w)};
 #pragma unroll
-          for (int i = 0; i < PER; ++i) cfma(acc[i], a, sB[kk * GBN + col0 + i]);
+            for (int i = 0; i < 4; ++i) {
+              cfma(acc[i], a0, bv[i]);
+              cfma(acc[4 + i], a1, bv[i]);
+            }
+          }
+        } else {
+          // PER outputs in one row
+          const int row = tid / (GBN / PER);
+          const int col0 = (tid % (GBN / PER)) * PER;
+#pragma unroll 4
+          for (int kk = 0; kk < GBK; ++kk) {
+            const float2 a = sA[row * GSA_LD + kk];
+#pragma unroll
+            for (int i = 0; i < PER; ++i) cfma(acc[i], a, sB[kk * GSB_LD + col0 + i]);
+          }
         }
         __syncthreads();
       }
-      const int row = tid / (GBN / PER);
-      const int col0 = (tid % (GBN / PER)) * PER;
-      const int gm = m0 + row;
-      if (gm < M) {
 #pragma unroll
-        for (int i = 0; i < PER; ++i) {
-          const int gn = n0 + col0 + i;
-          if (gn < N) {
-            float2* dst = Cm + (size_t)gm * scm + (size_t)gn * scn;
-            *dst = accumulate ? cadd(*dst, acc[i]) : acc[i];
-          }
+      for (int i = 0; i < PER; ++i) {
+        int row, col;
+        if constexpr (NT == 512) {
+          row = 2 * (tid >> 4) + (i >> 2);
+          col = 4 * (tid & 15) + (i & 3);
+        } else {
+          row = tid / (GBN / PER);
+          col = (tid % (GBN / PER)) * PER + i;
+        }
+        const int gm = m0 + row, gn = n0 + col;
+        if (gm < M && gn < N) {
+          float2* dst = Cm + (size_t)gm * scm + (size_t)gn * scn;
+          *dst = accumulate ? cadd(*dst, acc[i]) : acc[i];
         }
       }
     }

@@ -366,7 +366,7 @@ __device__ void carve(Work& w, unsigned char* raw, int C, float2* big_area, bool
   float2* tiles = w.alph + 2 * C;
   if (big_area) {  // the SIMT GEMM tiles share the staging region
     w.gA = w.stage;
-    w.gB = w.gA + GBM * GBK;
+    w.gB = w.gA + GBM * GSA_LD;
   } else {
     w.gA = w.gB = nullptr;
   }
