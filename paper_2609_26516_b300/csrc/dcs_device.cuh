@@ -121,13 +121,16 @@ __device__ __forceinline__ float block_sumf(float v, float* red) {
 // the column's magnitude; a column whose FP32 squared norm is below 1e-30 (a column of
 // rounding noise, where FP32 squares can underflow) is normalised from FP64 squares.
 // Scratch: tau[r] (2 or 0), alpha[r], red[NT/32] (double).
+// Householder reflectors of columns k0 .. k1-1 of X (m rows, ld), each applied to the
+// columns up to napply-1: the column loop of cta_qr (and of its blocked form, one panel at a
+// time).  Reflector k is left in X[k:, k] (unit vector), tau[k] = 2 (0: H_k = I), alpha[k]
+// the new diagonal entry.
 template <int NT>
-__device__ int cta_qr(float2* X, int m, int n, int ld, float2* Q, int ldq, float2* R, int ldr,
-                      float* tau, float2* alpha, double* red) {
-  const int r = m < n ? m : n;
+__device__ void house_columns(float2* X, int m, int ld, int k0, int k1, int napply, float* tau,
+                              float2* alpha, double* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int NW = NT / 32;
-  for (int k = 0; k < r; ++k) {
+  for (int k = k0; k < k1; ++k) {
     // FP32 norm; a column whose squared norm is below 1e-30 (where FP32 squares of its
     // entries may underflow) is redone from FP64 squares
     float s32 = 0.f;
@@ -202,7 +205,7 @@ __device__ int cta_qr(float2* X, int m, int n, int ld, float2* Q, int ldq, float
     }
     __syncthreads();
     if (!skip) {
-      for (int j = k + 1 + warp; j < n; j += NW) {
+      for (int j = k + 1 + warp; j < napply; j += NW) {
         float2 d = cz();
         for (int i = k + lane; i < m; i += 32) cfmac(d, X[i + k * ld], X[i + j * ld]);
 #pragma unroll
@@ -222,6 +225,15 @@ __device__ int cta_qr(float2* X, int m, int n, int ld, float2* Q, int ldq, float
     }
     __syncthreads();
   }
+}
+
+template <int NT>
+__device__ int cta_qr(float2* X, int m, int n, int ld, float2* Q, int ldq, float2* R, int ldr,
+                      float* tau, float2* alpha, double* red) {
+  const int r = m < n ? m : n;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int NW = NT / 32;
+  house_columns<NT>(X, m, ld, 0, r, n, tau, alpha, red);
   if (R != nullptr) {
     for (int idx = threadIdx.x; idx < r * n; idx += NT) {
       const int i = idx / n, j = idx % n;

@@ -401,6 +401,113 @@ __device__ __forceinline__ void wgemm(Work& sm, int M, int N, int K, const float
   }
 }
 
+// ----------------------------------------------------------------------------- blocked QR
+constexpr int QR_PB = 64;  // panel width of the blocked QR
+
+// Scratch (complex elements) of cta_qr_blocked for an m x n matrix.
+__host__ __device__ inline size_t qr_blocked_scratch(int m, int n) {
+  const int r = m < n ? m : n;
+  const size_t panels = (size_t)(r + QR_PB - 1) / QR_PB;
+  return panels * QR_PB * QR_PB + (size_t)m * QR_PB + 2 * (size_t)QR_PB * n + (size_t)m * n;
+}
+
+// Householder QR of F (m x n, column-major, ld m) with the explicit Q (m x r, r = min(m, n),
+// column-major, ldq) and no R; the reflectors are those of cta_qr.  Blocked: panels of
+// QR_PB columns are factored with house_columns; the panel's reflectors are gathered into
+// U (zeros above each reflector) with the compact WY form H_0 ... H_{b-1} = I - U T U^H,
+// T upper triangular (T_jj = tau_j, T[0:j, j] = -tau_j T[0:j, 0:j] U[:, 0:j]^H u_j); the
+// columns right of the panel take F -= U T^H (U^H F) in three GEMMs, and Q is accumulated
+// from the right, Q -= U T (U^H Q) per panel.  The GEMMs go through wgemm (tensor cores on
+// the TF32X3 path).  ws: qr_blocked_scratch(m, n) complex in global memory.
+template <int NT>
+__device__ int cta_qr_blocked(Work& sm, float2* F, int m, int n, float2* Q, int ldq, float2* ws) {
+  const int r = m < n ? m : n;
+  const int npan = (r + QR_PB - 1) / QR_PB;
+  float2* Tall = ws;                                   // npan x QR_PB x QR_PB, row-major
+  float2* U = Tall + (size_t)npan * QR_PB * QR_PB;     // mu x pb, column-major (ld mu)
+  float2* W = U + (size_t)m * QR_PB;                   // pb x cols, row-major
+  float2* W2 = W + (size_t)QR_PB * n;                  // pb x cols, row-major
+  float2* Y = W2 + (size_t)QR_PB * n;                  // mu x cols, column-major (ld mu)
+  // U of panel p0 from the reflectors stored in F
+  auto gather_u = [&](int p0, int pb) {
+    const int mu = m - p0;
+    for (int idx = threadIdx.x; idx < mu * pb; idx += NT) {
+      const int i = idx % mu, j = idx / mu;
+      U[idx] = (i >= j && sm.tau[p0 + j] != 0.f) ? F[(size_t)(p0 + i) + (size_t)(p0 + j) * m] : cz();
+    }
+    __syncthreads();
+  };
+  for (int p = 0; p < npan; ++p) {
+    const int p0 = p * QR_PB, pb = (r - p0) < QR_PB ? (r - p0) : QR_PB, mu = m - p0;
+    house_columns<NT>(F, m, m, p0, p0 + pb, p0 + pb, sm.tau, sm.alph, sm.red);
+    __syncthreads();
+    gather_u(p0, pb);
+    // S = U^H U into W, then T column by column (one thread per row of T)
+    float2* T = Tall + (size_t)p * QR_PB * QR_PB;
+    wgemm<NT>(sm, pb, pb, mu, U, mu, 1, true, U, 1, mu, false, W, pb, 1);
+    for (int j = 0; j < pb; ++j) {
+      const float tj = sm.tau[p0 + j];
+      if ((int)threadIdx.x < pb) {
+        const int i = threadIdx.x;
+        float2 v = cz();
+        if (i < j) {
+          for (int l = i; l < j; ++l) cfma(v, T[i * QR_PB + l], W[l * pb + j]);
+          v = cscale(v, -tj);
+        } else if (i == j) {
+          v = make_float2(tj, 0.f);
+        }
+        T[i * QR_PB + j] = v;
+      }
+      __syncthreads();
+    }
+    const int nt = n - p0 - pb;
+    if (nt > 0) {
+      float2* Ft = F + (size_t)p0 + (size_t)(p0 + pb) * m;
+      wgemm<NT>(sm, pb, nt, mu, U, mu, 1, true, Ft, 1, m, false, W, nt, 1);
+      wgemm<NT>(sm, pb, nt, pb, T, 1, QR_PB, true, W, nt, 1, false, W2, nt, 1);
+      wgemm<NT>(sm, mu, nt, pb, U, 1, mu, false, W2, nt, 1, false, Y, 1, mu);
+      for (int idx = threadIdx.x; idx < mu * nt; idx += NT) {
+        const int i = idx % mu, j = idx / mu;
+        float2& f = Ft[(size_t)i + (size_t)j * m];
+        f = csub(f, Y[idx]);
+      }
+      __syncthreads();
+    }
+  }
+  // Q = H_0 ... H_{r-1} [I_r; 0], panels applied from the last one
+  for (int idx = threadIdx.x; idx < m * r; idx += NT) {
+    const int i = idx % m, j = idx / m;
+    Q[(size_t)i + (size_t)j * ldq] = make_float2(i == j ? 1.f : 0.f, 0.f);
+  }
+  __syncthreads();
+  for (int p = npan - 1; p >= 0; --p) {
+    const int p0 = p * QR_PB, pb = (r - p0) < QR_PB ? (r - p0) : QR_PB, mu = m - p0;
+    const int qc = r - p0;
+    gather_u(p0, pb);
+    const float2* T = Tall + (size_t)p * QR_PB * QR_PB;
+    float2* Qs = Q + (size_t)p0 + (size_t)p0 * ldq;
+    wgemm<NT>(sm, pb, qc, mu, U, mu, 1, true, Qs, 1, ldq, false, W, qc, 1);
+    wgemm<NT>(sm, pb, qc, pb, T, QR_PB, 1, false, W, qc, 1, false, W2, qc, 1);
+    wgemm<NT>(sm, mu, qc, pb, U, 1, mu, false, W2, qc, 1, false, Y, 1, mu);
+    for (int idx = threadIdx.x; idx < mu * qc; idx += NT) {
+      const int i = idx % mu, j = idx / mu;
+      float2& q = Qs[(size_t)i + (size_t)j * ldq];
+      q = csub(q, Y[idx]);
+    }
+    __syncthreads();
+  }
+  return r;
+}
+
+// QR of a sweep's F (m x n in the work area) into Q = sm.R: the blocked form when the panel
+// pays off and its scratch fits the T tile (free at this point of a site update), else cta_qr.
+template <int NT>
+__device__ __forceinline__ int sweep_qr(Work& sm, int m, int n) {
+  if (n >= 2 * QR_PB && m >= QR_PB && qr_blocked_scratch(m, n) <= (size_t)8 * sm.C * sm.C)
+    return cta_qr_blocked<NT>(sm, sm.F, m, n, sm.R, m, sm.T);
+  return cta_qr<NT>(sm.F, m, n, m, sm.R, m, nullptr, 0, sm.tau, sm.alph, sm.red);
+}
+
 // ----------------------------------------------------------------------------- gauge moves
 // Move the orthogonality centre of MPS buffer `buf` of `slot` from j to j+1:
 // T_j = Q R (as (2 b_j) x b_{j+1}), T_j := Q, T_{j+1} := R T_{j+1}.
@@ -1439,7 +1546,7 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
         PHASE_MARK(7);
         float2* dst = site_ptr(c, bb, slot, j);
         if (j < n - 1) {
-          const int r = cta_qr<NT>(sm.F, m, nc, m, sm.R, m, nullptr, 0, sm.tau, sm.alph, sm.red);
+          const int r = sweep_qr<NT>(sm, m, nc);
           PHASE_MARK(8);
           for (int idx = threadIdx.x; idx < m * r; idx += NT) {
             const int row = idx / r, k2 = idx % r;
@@ -1482,7 +1589,7 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
         PHASE_MARK(7);
         float2* dst = site_ptr(c, bb, slot, j);
         if (j > 0) {
-          const int r = cta_qr<NT>(sm.F, m, nc, m, sm.R, m, nullptr, 0, sm.tau, sm.alph, sm.red);
+          const int r = sweep_qr<NT>(sm, m, nc);
           PHASE_MARK(8);
           for (int idx = threadIdx.x; idx < r * 2 * nb; idx += NT) {
             const int cc = idx % nb, s = (idx / nb) & 1, k2 = idx / (2 * nb);

@@ -86,6 +86,10 @@ def test_arena_bytes_and_argument_checks(lib):
     assert lib.dcs_arena_bytes(ctypes.byref(_cfg(N, chi_max=2048))) == 0
     assert lib.dcs_arena_bytes(ctypes.byref(_cfg(N, chi_max=64, kernel_path=1))) == 0
     assert lib.dcs_arena_bytes(ctypes.byref(_cfg(N, n_cbits=513))) == 0
+    # the largest chain the library takes, and one qubit more
+    assert lib.dcs_arena_bytes(ctypes.byref(_cfg(N, n_qubits=N.MAX_QUBITS))) > 0
+    assert lib.dcs_arena_bytes(ctypes.byref(_cfg(N, n_qubits=N.MAX_QUBITS + 1))) == 0
+    assert lib.dcs_arena_bytes(ctypes.byref(_cfg(N, n_qubits=1))) > 0
     ctx = ctypes.c_void_p()
     assert lib.dcs_create(ctypes.byref(ctx), ctypes.byref(_cfg(N, sweeps=0)), None, 0, None) == N.ERR_INVALID
     assert lib.dcs_create(ctypes.byref(ctx), ctypes.byref(_cfg(N, chi_max=2048)), None, 0, None) == N.ERR_UNSUPPORTED

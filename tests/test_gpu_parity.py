@@ -255,6 +255,14 @@ def test_global_tiles_tensor_cores_at_chi_96():
     _single_path_parity(circ, 96, 2, [0, 1], prec=1)
 
 
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp32", "tf32x3"])
+def test_global_tiles_blocked_qr_at_chi_128(prec):
+    # middle bonds saturate at 128 and are truncated: the sweeps' QRs of 256 x 128 and
+    # 128 x 128 matrices take the blocked (panel + GEMM) form
+    circ = C.brickwork(16, 14, 0.0, 21)
+    _single_path_parity(circ, 128, 2, [0, 1], prec=prec)
+
+
 def test_global_tiles_multi_path():
     circ = C.brickwork(8, 6, 0.2, 5)
     M = 8
@@ -305,3 +313,38 @@ def test_multi_path_brickwork_large_bonds():
         assert res["bits"][i].tolist() == [int(x) for x in b.c]
         assert abs(res["p"][i] - b.p) < P_TOL
         assert _state_fid(sim, i, b.mps) >= 1 - STATE_TOL
+
+
+# ---- edge cases: the largest chain, a single qubit, the smallest bond cap
+
+def test_ghz_max_qubits_128():
+    # n = 128 (the library's maximum), 64 data qubits and 63 random outcomes per shot
+    circ = C.ghz_dynamic(128)
+    shots = 256
+    sim = _sim(128, 8, shots, circ.n_cbits)
+    sim.init_state(shots)
+    sim.run_circuit(circ)
+    res = sim.results()
+    r = circ.meta["r"]
+    assert np.all(np.abs(res["p"] - 2.0 ** -r) < P_TOL * 2.0 ** -r)
+    prm = D.Params(chi_max=8)
+    for s in (0, 255):
+        ref = D.run_single_path(circ, prm, 1, s)
+        assert res["bits"][s].tolist() == [int(x) for x in ref.c]
+        assert _state_fid(sim, s, ref.mps) >= 1 - STATE_TOL
+
+
+def test_single_qubit_dynamic_circuit():
+    # n = 1: H, measure, X conditioned on the outcome, measure again (always 0)
+    circ = C.Circuit(1, 2, [C.Gate((0,), C.H), C.Measure(0, 0),
+                            C.Gate((0,), C.X, cond=C.Cond((0,), "xor", 1)), C.Measure(0, 1)])
+    _, res = _single_path_parity(circ, 1, 64, list(range(64)))
+    assert np.all(res["bits"][:, 1] == 0)
+    assert 10 < int(res["bits"][:, 0].sum()) < 54
+
+
+def test_bond_cap_one():
+    # chi_max = 1: every entangling layer is truncated to a product state
+    circ = C.brickwork(6, 4, 0.3, 2)
+    _, res = _single_path_parity(circ, 1, 8, list(range(8)))
+    assert np.all(res["F"] < 1.0)
