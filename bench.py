@@ -40,9 +40,9 @@ METRIC = "shots/s (single-path dynamic GHZ n=64, chi_max=8)"
 
 
 # DRAM bytes (read + write) per shot of the H + CNOT compression launch, from the ncu
-# capture summarised in profiles/k_compress_ghz64_hcnot.md (2,000 shots: 31.85 MB read,
-# 1.90 MB written).  Valid for the kernel build that capture measured.
-HCNOT_TRAFFIC_PER_SHOT = (31.849472e6 + 1.900544e6) / 2000
+# capture summarised in profiles/k_compress_ghz64_hcnot.md (2,000 shots: 31.86 MB read,
+# 1.89 MB written).  Valid for the kernel build that capture measured.
+HCNOT_TRAFFIC_PER_SHOT = (31.862784e6 + 1.885952e6) / 2000
 
 
 def measured_peaks():
