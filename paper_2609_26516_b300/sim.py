@@ -18,52 +18,62 @@ class DCSError(RuntimeError):
         self.status = status
 
 
-def _cond(cond) -> N.dcs_cond:
-    c = N.dcs_cond()
-    if cond is None:
-        c.op = N.COND_NONE
-        return c
-    c.op = {"xor": N.COND_XOR, "and": N.COND_AND}[cond.op]
-    c.value = int(cond.value)
-    for b in cond.bits:
-        c.mask[b >> 6] |= 1 << (b & 63)
-    return c
+def _op_dtype() -> np.dtype:
+    """NumPy view of one dcs_op record, field offsets taken from the ctypes declaration."""
+    co = N.dcs_op.cond.offset
+    return np.dtype({
+        "names": ["kind", "q0", "q1", "cbit", "m", "mask", "cop", "cval"],
+        "formats": [np.int32, np.int32, np.int32, np.int32, (np.float64, 32),
+                    (np.uint64, N.CWORDS), np.int32, np.int32],
+        "offsets": [N.dcs_op.kind.offset, N.dcs_op.q0.offset, N.dcs_op.q1.offset,
+                    N.dcs_op.cbit.offset, N.dcs_op.m.offset, co + N.dcs_cond.mask.offset,
+                    co + N.dcs_cond.op.offset, co + N.dcs_cond.value.offset],
+        "itemsize": ctypes.sizeof(N.dcs_op)})
+
+
+_OP_DTYPE = _op_dtype()
+_COND_OPS = {"xor": N.COND_XOR, "and": N.COND_AND}
 
 
 def encode_ops(ops: Sequence) -> ctypes.Array:
-    """circuits.Gate / Measure / Reset records -> dcs_op array."""
+    """circuits.Gate / Measure / Reset records -> dcs_op array (filled through a NumPy view
+    of the same bytes; the ctypes array keeps that buffer alive)."""
     from circuits import Gate, Measure, Reset  # input records only
 
-    arr = (N.dcs_op * max(1, len(ops)))()
+    rec = np.zeros(max(1, len(ops)), dtype=_OP_DTYPE)
+    kind, q0, q1, cbit = rec["kind"], rec["q0"], rec["q1"], rec["cbit"]
+    m, mask, cop, cval = rec["m"], rec["mask"], rec["cop"], rec["cval"]
     for i, o in enumerate(ops):
-        d = arr[i]
         if isinstance(o, Gate):
-            m = np.asarray(o.matrix, dtype=np.complex128).reshape(-1)
-            d.kind = N.OP_GATE1 if len(o.qubits) == 1 else N.OP_GATE2
-            d.q0 = o.qubits[0]
-            d.q1 = o.qubits[1] if len(o.qubits) == 2 else -1
-            for k, z in enumerate(m):
-                d.m[2 * k] = float(z.real)
-                d.m[2 * k + 1] = float(z.imag)
-            d.cond = _cond(o.cond)
+            u = np.asarray(o.matrix, dtype=np.complex128).reshape(-1).view(np.float64)
+            nq = len(o.qubits)
+            kind[i] = N.OP_GATE1 if nq == 1 else N.OP_GATE2
+            q0[i] = o.qubits[0]
+            q1[i] = o.qubits[1] if nq == 2 else -1
+            m[i, : u.shape[0]] = u
+            cd = o.cond
+            if cd is not None:
+                cop[i] = _COND_OPS[cd.op]
+                cval[i] = int(cd.value)
+                for b in cd.bits:
+                    mask[i, b >> 6] |= np.uint64(1 << (b & 63))
         elif isinstance(o, (Measure, Reset)):
-            d.kind = N.OP_MEASURE if isinstance(o, Measure) else N.OP_RESET
-            d.q0 = o.qubit
-            d.q1 = -1
-            d.cbit = o.cbit
-            d.cond = _cond(None)
+            kind[i] = N.OP_MEASURE if isinstance(o, Measure) else N.OP_RESET
+            q0[i] = o.qubit
+            q1[i] = -1
+            cbit[i] = o.cbit
         else:
             raise TypeError(o)
-    return arr
+    return (N.dcs_op * rec.shape[0]).from_buffer(rec)
 
 
 def bits_of(cwords: np.ndarray, n_bits: int) -> np.ndarray:
-    """Unpack [n, CWORDS] uint64 registers into [n, n_bits] uint8."""
-    cw = np.asarray(cwords, dtype=np.uint64)
-    out = np.zeros((cw.shape[0], n_bits), dtype=np.uint8)
-    for b in range(n_bits):
-        out[:, b] = ((cw[:, b >> 6] >> np.uint64(b & 63)) & np.uint64(1)).astype(np.uint8)
-    return out
+    """Unpack [n, CWORDS] uint64 registers into [n, n_bits] uint8 (bit b of the register is
+    bit b & 63 of word b >> 6)."""
+    cw = np.ascontiguousarray(np.asarray(cwords, dtype=np.uint64).astype("<u8", copy=False))
+    raw = cw.view(np.uint8).reshape(cw.shape[0], -1)[:, : (n_bits + 7) // 8]
+    bits = np.unpackbits(raw, axis=1, bitorder="little")
+    return np.ascontiguousarray(bits[:, :n_bits])
 
 
 class Simulator:

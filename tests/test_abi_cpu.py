@@ -112,3 +112,60 @@ def test_encode_ops_round_trip():
     cx = arr[7]
     assert cx.cond.op == N.COND_XOR and cx.cond.mask[0] == 0b10 and cx.cond.value == 1
     assert arr[5].kind == N.OP_MEASURE and arr[5].cbit == 0
+
+
+def _encode_fieldwise(ops):
+    """dcs_op records set one ctypes field at a time (the plain form of the binding's encoder)."""
+    import numpy as np
+    import circuits as C
+    from paper_2609_26516_b300 import _native as N
+    arr = (N.dcs_op * max(1, len(ops)))()
+    for i, o in enumerate(ops):
+        d = arr[i]
+        if isinstance(o, C.Gate):
+            m = np.asarray(o.matrix, dtype=np.complex128).reshape(-1)
+            d.kind = N.OP_GATE1 if len(o.qubits) == 1 else N.OP_GATE2
+            d.q0 = o.qubits[0]
+            d.q1 = o.qubits[1] if len(o.qubits) == 2 else -1
+            for k, z in enumerate(m):
+                d.m[2 * k] = float(z.real)
+                d.m[2 * k + 1] = float(z.imag)
+            if o.cond is not None:
+                d.cond.op = {"xor": N.COND_XOR, "and": N.COND_AND}[o.cond.op]
+                d.cond.value = int(o.cond.value)
+                for b in o.cond.bits:
+                    d.cond.mask[b >> 6] |= 1 << (b & 63)
+        else:
+            d.kind = N.OP_MEASURE if isinstance(o, C.Measure) else N.OP_RESET
+            d.q0, d.q1, d.cbit = o.qubit, -1, o.cbit
+    return arr
+
+
+def test_encode_ops_matches_fieldwise_encoding():
+    import numpy as np
+    import circuits as C
+    from paper_2609_26516_b300.sim import encode_ops
+    rng = np.random.default_rng(7)
+    u2 = C.haar_unitary(rng, 2)
+    extra = [C.Gate((3,), u2, cond=C.Cond((0, 65, 127, 300), "and", 0)),
+             C.Gate((0, 1), C.haar_su4(rng), cond=C.Cond((64,), "xor", 1)),
+             C.Reset(5, 511), C.Measure(2, 63)]
+    for ops in (C.teleport(3).ops, C.ghz_dynamic(64).ops, C.brickwork(12, 6, 0.3, 5).ops,
+                extra, []):
+        fast, ref = encode_ops(ops), _encode_fieldwise(ops)
+        assert len(fast) == len(ref)
+        assert bytes(fast) == bytes(ref)
+
+
+def test_bits_of_matches_plain_unpacking():
+    import numpy as np
+    from paper_2609_26516_b300.sim import bits_of
+    rng = np.random.default_rng(3)
+    cw = rng.integers(0, 2**63, size=(37, 8), dtype=np.int64).astype(np.uint64)
+    cw[:, 1] |= np.uint64(1) << np.uint64(63)
+    for n_bits in (1, 63, 64, 65, 200, 512):
+        got = bits_of(cw, n_bits)
+        want = np.array([[(int(cw[i, b >> 6]) >> (b & 63)) & 1 for b in range(n_bits)]
+                         for i in range(cw.shape[0])], dtype=np.uint8)
+        assert got.dtype == np.uint8 and got.shape == (37, n_bits)
+        np.testing.assert_array_equal(got, want)

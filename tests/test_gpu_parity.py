@@ -109,6 +109,12 @@ def test_ghz64_full_config_sampled_shots():
         assert _state_fid(sim, s, ref.mps) >= 1 - STATE_TOL
 
 
+def test_odd_slot_counts_every_shot():
+    # odd slot counts on the one-warp (4-wide tile) path: every shot against the oracle
+    _single_path_parity(C.ghz_dynamic(12), 8, 37, list(range(37)))
+    _single_path_parity(C.teleport(5), 4, 33, list(range(33)))
+
+
 # tol = 0 is not a parity case: FP32 rounding leaves singular values ~1e-7 where FP64 has
 # exact zeros, so the two sides would keep different (noise) bond directions.
 @pytest.mark.parametrize("chi,tol", [(8, 1e-10), (5, 1e-10), (32, 1e-12)])
