@@ -362,6 +362,67 @@ def measure_brick(n, depth, p, chi, shots, sweeps, precision):
     return out
 
 
+def _events_ms(fn, stream, reps):
+    import torch
+    a = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for i in range(reps):
+        fn(i)
+    e.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(e)
+
+
+def measure_ghz_plain(n_shots=200):
+    """The benchmark circuit run one shot at a time (a one-slot context, each shot its own
+    init and circuit call: table upload and one launch per chunk and measurement run), to set
+    beside the batched line."""
+    import circuits as C
+    from paper_2609_26516_b300 import Simulator
+    from paper_2609_26516_b300.sim import encode_ops
+    circ = C.ghz_dynamic(N_QUBITS)
+    ops, n_ops = encode_ops(circ.ops), len(circ.ops)
+    sim = Simulator(N_QUBITS, CHI_MAX, 1, circ.n_cbits, tol=TOL, sweeps=SWEEPS, seed=SEED)
+
+    def one(i):
+        sim.init_state(1, shot0=i)
+        sim.run_encoded(ops, n_ops)
+
+    _events_ms(one, sim.stream, 3)
+    l0 = sim.launches
+    ms = _events_ms(one, sim.stream, n_shots)
+    out = {"workload": f"dynamic GHZ n={N_QUBITS}, chi_max={CHI_MAX}, one shot per call, "
+                       f"{n_shots} shots in a row", "shots_per_s": n_shots / (ms / 1000.0),
+           "ms_per_shot": ms / n_shots, "launches_per_shot": (sim.launches - l0) / n_shots}
+    del sim
+    return out
+
+
+def measure_teleport(shots=1000, steps=20):
+    """Teleportation (3 qubits, chi_max = 4, 1000 shots in one batch): shots/s."""
+    import circuits as C
+    from paper_2609_26516_b300 import Simulator
+    from paper_2609_26516_b300.sim import encode_ops
+    circ = C.teleport(1)
+    ops, n_ops = encode_ops(circ.ops), len(circ.ops)
+    sim = Simulator(circ.n_qubits, 4, shots, circ.n_cbits, tol=TOL, sweeps=SWEEPS, seed=SEED)
+
+    def one(i):
+        sim.init_state(shots)
+        sim.run_encoded(ops, n_ops)
+
+    _events_ms(one, sim.stream, 3)
+    ms = _events_ms(one, sim.stream, steps)
+    res = sim.results()
+    out = {"workload": f"teleportation n=3, chi_max=4, {shots} shots per batch, {steps} "
+                       "batches in a row", "shots_per_s": steps * shots / (ms / 1000.0),
+           "ms_per_batch": ms / steps,
+           "max_abs_p_minus_quarter": float(np.max(np.abs(res["p"] - 0.25)))}
+    del sim
+    return out
+
+
 def run_brick(args):
     shots = args.shots if args.shots != SHOTS else 148
     print(json.dumps(measure_brick(args.n, args.depth, args.p, args.chi, shots, args.sweeps,
@@ -603,9 +664,12 @@ def main():
         "clocks": clk,
     }
     if world == 1 and not args.no_extras:
-        # the other workload shapes, measured after the timed region: the contraction
-        # primitive at chi = 256 and random dynamic brickwork whose bonds reach chi_max = 128
-        # (truncation, sweeps), FP32 vs TF32x3
+        # the other workload shapes, measured after the timed region: the same circuit one
+        # shot per call, teleportation, the contraction primitive at chi = 256 and random
+        # dynamic brickwork whose bonds reach chi_max = 128 (truncation, sweeps), FP32 vs
+        # TF32x3
+        line["ghz_one_shot_per_call"] = measure_ghz_plain(200)
+        line["teleport"] = measure_teleport(1000, 20)
         line["contraction"] = measure_cgemm(256, 148)
         line["brickwork"] = {
             "fp32": measure_brick(20, 12, 0.02, 128, 148, 2, 0),
