@@ -183,9 +183,12 @@ dcs_status_t dcs_branch_split(dcs_ctx_t ctx, int qubit, int cbit, double eps);
  * The retained branches keep their relative order; p is not renormalised. */
 dcs_status_t dcs_branch_topk(dcs_ctx_t ctx, int M);
 
-/* Synchronises and copies results to HOST buffers (each may be NULL): for the active slots
- * in list order, p (n doubles), F (n doubles), the register (n * DCS_CWORDS words), flags
- * (n bytes), and the number n of active slots. */
+/* Synchronises and copies results to HOST buffers (each may be NULL, each sized for
+ * n_slots entries): for the active slots in list order, p (n doubles), F (n doubles), the
+ * register (n * DCS_CWORDS words), flags (n bytes), and the number n of active slots.  The
+ * data comes down through the context's pinned host staging buffer, which grows (one
+ * cudaMallocHost) the first time it is too small.  DCS_ERR_OOM if the branch pool ran out
+ * during the circuit, DCS_ERR_CUDA on a copy or earlier asynchronous error. */
 dcs_status_t dcs_get_results(dcs_ctx_t ctx, double* p, double* fid, uint64_t* cbits,
                              int* n_active, uint8_t* flags);
 

@@ -169,6 +169,24 @@ struct DevProg {
   const uint8_t* bytes;
 };
 
+// The pinned host staging buffer, at least `total` bytes, with no copy still reading it.
+dcs_status_t ensure_stage(dcs_ctx_t c, size_t total) {
+  if (c->stage_pending) {
+    cudaError_t e = cudaEventSynchronize(c->stage_done);
+    if (e != cudaSuccess) return cuda_check(c, e, "cudaEventSynchronize");
+    c->stage_pending = false;
+  }
+  if (total > c->stage_bytes) {
+    if (c->stage) cudaFreeHost(c->stage);
+    c->stage = nullptr;
+    c->stage_bytes = 0;
+    cudaError_t e = cudaMallocHost(&c->stage, total);
+    if (e != cudaSuccess) return cuda_check(c, e, "cudaMallocHost");
+    c->stage_bytes = total;
+  }
+  return DCS_OK;
+}
+
 dcs_status_t upload(dcs_ctx_t c, const Program& P, const std::vector<uint8_t>& extra, DevProg& out) {
   size_t off = 0;
   auto sz = [&](size_t b) {
@@ -184,18 +202,7 @@ dcs_status_t upload(dcs_ctx_t c, const Program& P, const std::vector<uint8_t>& e
   const size_t oX = sz(extra.size());
   const size_t total = off;
   if (total > kProgBytes) return fail(c, DCS_ERR_OOM, "circuit tables exceed the program region");
-  if (c->stage_pending) {
-    cudaError_t e = cudaEventSynchronize(c->stage_done);
-    if (e != cudaSuccess) return cuda_check(c, e, "cudaEventSynchronize");
-    c->stage_pending = false;
-  }
-  if (total > c->stage_bytes) {
-    if (c->stage) cudaFreeHost(c->stage);
-    c->stage = nullptr;
-    cudaError_t e = cudaMallocHost(&c->stage, total);
-    if (e != cudaSuccess) return cuda_check(c, e, "cudaMallocHost");
-    c->stage_bytes = total;
-  }
+  if (dcs_status_t st = ensure_stage(c, total); st != DCS_OK) return st;
   auto put = [&](size_t o, const void* src, size_t b) {
     if (b) std::memcpy(c->stage + o, src, b);
   };
@@ -470,28 +477,49 @@ dcs_status_t dcs_get_results(dcs_ctx_t c, double* p, double* fid, uint64_t* cbit
   if (!c) return DCS_ERR_INVALID;
   dcs_status_t st = cuda_check(c, cudaStreamSynchronize(c->stream), "synchronize");
   if (st != DCS_OK) return st;
-  const int S = c->cfg.n_slots;
-  int cnt = 0, status = 0;
-  cudaMemcpy(&cnt, c->dev.count, sizeof(int), cudaMemcpyDeviceToHost);
-  cudaMemcpy(&status, c->dev.status, sizeof(int), cudaMemcpyDeviceToHost);
-  std::vector<int> order(S);
-  cudaMemcpy(order.data(), c->dev.order, S * sizeof(int), cudaMemcpyDeviceToHost);
-  if (n_active) *n_active = cnt;
-  auto gather = [&](void* dst, const void* src, size_t esz, size_t per) {
-    if (!dst) return;
-    std::vector<uint8_t> tmp((size_t)S * esz * per);
-    cudaMemcpy(tmp.data(), src, tmp.size(), cudaMemcpyDeviceToHost);
-    for (int i = 0; i < cnt; ++i)
-      std::memcpy(static_cast<uint8_t*>(dst) + (size_t)i * esz * per,
-                  tmp.data() + (size_t)order[i] * esz * per, esz * per);
+  // every per-slot array comes down into the pinned stage in one batch of async copies on
+  // the context's stream, then is gathered into the caller's buffers in list order
+  const size_t S = (size_t)c->cfg.n_slots;
+  size_t off = 0;
+  auto region = [&](size_t b) {
+    const size_t o = off;
+    off = align_up(off + b);
+    return o;
   };
-  gather(p, c->dev.p, sizeof(double), 1);
-  gather(fid, c->dev.F, sizeof(double), 1);
-  gather(cbits, c->dev.creg, sizeof(uint64_t), DCS_CWORDS);
-  if (flags) {
-    std::vector<uint32_t> fl(S);
-    cudaMemcpy(fl.data(), c->dev.flags, S * sizeof(uint32_t), cudaMemcpyDeviceToHost);
-    for (int i = 0; i < cnt; ++i) flags[i] = (uint8_t)fl[order[i]];
+  const size_t oH = region(2 * sizeof(int));
+  const size_t oO = region(S * sizeof(int));
+  const size_t oP = region(p ? S * sizeof(double) : 0);
+  const size_t oF = region(fid ? S * sizeof(double) : 0);
+  const size_t oC = region(cbits ? S * DCS_CWORDS * sizeof(uint64_t) : 0);
+  const size_t oL = region(flags ? S * sizeof(uint32_t) : 0);
+  if ((st = ensure_stage(c, off)) != DCS_OK) return st;
+  char* h = c->stage;
+  cudaError_t e = cudaSuccess;
+  auto get = [&](size_t o, const void* src, size_t b) {
+    if (b && e == cudaSuccess) e = cudaMemcpyAsync(h + o, src, b, cudaMemcpyDeviceToHost, c->stream);
+  };
+  get(oH, c->dev.count, sizeof(int));
+  get(oH + sizeof(int), c->dev.status, sizeof(int));
+  get(oO, c->dev.order, S * sizeof(int));
+  if (p) get(oP, c->dev.p, S * sizeof(double));
+  if (fid) get(oF, c->dev.F, S * sizeof(double));
+  if (cbits) get(oC, c->dev.creg, S * DCS_CWORDS * sizeof(uint64_t));
+  if (flags) get(oL, c->dev.flags, S * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if ((st = cuda_check(c, e, "result copy")) != DCS_OK) return st;
+  const int cnt = reinterpret_cast<const int*>(h + oH)[0];
+  const int status = reinterpret_cast<const int*>(h + oH)[1];
+  const int* order = reinterpret_cast<const int*>(h + oO);
+  if (n_active) *n_active = cnt;
+  for (int i = 0; i < cnt; ++i) {
+    const size_t slot = (size_t)order[i];
+    if (p) p[i] = reinterpret_cast<const double*>(h + oP)[slot];
+    if (fid) fid[i] = reinterpret_cast<const double*>(h + oF)[slot];
+    if (cbits) {
+      const uint64_t* src = reinterpret_cast<const uint64_t*>(h + oC) + slot * DCS_CWORDS;
+      for (int w = 0; w < DCS_CWORDS; ++w) cbits[(size_t)i * DCS_CWORDS + w] = src[w];
+    }
+    if (flags) flags[i] = (uint8_t)reinterpret_cast<const uint32_t*>(h + oL)[slot];
   }
   st = cuda_check(c, cudaGetLastError(), "result copy");
   if (st != DCS_OK) return st;

@@ -36,34 +36,55 @@ _COND_OPS = {"xor": N.COND_XOR, "and": N.COND_AND}
 
 
 def encode_ops(ops: Sequence) -> ctypes.Array:
-    """circuits.Gate / Measure / Reset records -> dcs_op array (filled through a NumPy view
-    of the same bytes; the ctypes array keeps that buffer alive)."""
+    """circuits.Gate / Measure / Reset records -> dcs_op array (filled column by column
+    through a NumPy view of the same bytes; the ctypes array keeps that buffer alive)."""
     from circuits import Gate, Measure, Reset  # input records only
 
-    rec = np.zeros(max(1, len(ops)), dtype=_OP_DTYPE)
-    kind, q0, q1, cbit = rec["kind"], rec["q0"], rec["q1"], rec["cbit"]
-    m, mask, cop, cval = rec["m"], rec["mask"], rec["cop"], rec["cval"]
+    n = len(ops)
+    rec = np.zeros(max(1, n), dtype=_OP_DTYPE)
+    kind = np.zeros(n, dtype=np.int32)
+    q0 = np.zeros(n, dtype=np.int32)
+    q1 = np.full(n, -1, dtype=np.int32)
+    cbit = np.zeros(n, dtype=np.int32)
+    g1, m1, g2, m2, conds = [], [], [], [], []
     for i, o in enumerate(ops):
         if isinstance(o, Gate):
-            u = np.asarray(o.matrix, dtype=np.complex128).reshape(-1).view(np.float64)
-            nq = len(o.qubits)
-            kind[i] = N.OP_GATE1 if nq == 1 else N.OP_GATE2
-            q0[i] = o.qubits[0]
-            q1[i] = o.qubits[1] if nq == 2 else -1
-            m[i, : u.shape[0]] = u
-            cd = o.cond
-            if cd is not None:
-                cop[i] = _COND_OPS[cd.op]
-                cval[i] = int(cd.value)
-                for b in cd.bits:
-                    mask[i, b >> 6] |= np.uint64(1 << (b & 63))
+            if len(o.qubits) == 1:
+                kind[i] = N.OP_GATE1
+                q0[i] = o.qubits[0]
+                g1.append(i)
+                m1.append(o.matrix)
+            else:
+                kind[i] = N.OP_GATE2
+                q0[i], q1[i] = o.qubits
+                g2.append(i)
+                m2.append(o.matrix)
+            if o.cond is not None:
+                conds.append((i, o.cond))
         elif isinstance(o, (Measure, Reset)):
             kind[i] = N.OP_MEASURE if isinstance(o, Measure) else N.OP_RESET
             q0[i] = o.qubit
-            q1[i] = -1
             cbit[i] = o.cbit
         else:
             raise TypeError(o)
+    if n:
+        rec["kind"][:n], rec["q0"][:n], rec["q1"][:n], rec["cbit"][:n] = kind, q0, q1, cbit
+    m = rec["m"]
+    if g1:
+        m[g1, :8] = np.asarray(m1, dtype=np.complex128).reshape(len(g1), 4).view(np.float64)
+    if g2:
+        m[g2, :32] = np.asarray(m2, dtype=np.complex128).reshape(len(g2), 16).view(np.float64)
+    if conds:
+        words = np.zeros((len(conds), N.CWORDS), dtype=np.uint64)
+        for r, (_, cd) in enumerate(conds):
+            w = [0] * N.CWORDS
+            for b in cd.bits:
+                w[b >> 6] |= 1 << (b & 63)
+            words[r] = w
+        rows = [i for i, _ in conds]
+        rec["mask"][rows] = words
+        rec["cop"][rows] = [_COND_OPS[cd.op] for _, cd in conds]
+        rec["cval"][rows] = [int(cd.value) for _, cd in conds]
     return (N.dcs_op * rec.shape[0]).from_buffer(rec)
 
 
