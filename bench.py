@@ -45,6 +45,23 @@ METRIC = "shots/s (single-path dynamic GHZ n=64, chi_max=8)"
 HCNOT_TRAFFIC_PER_SHOT = (31.862784e6 + 1.885952e6) / 2000
 
 
+def shard_shot0(rank: int, shots_per_rank: int) -> int:
+    """First global shot index of a rank.  Ranks take consecutive disjoint ranges, and the
+    outcome sampler is keyed by the global shot index, so the results of a shot do not depend
+    on which rank runs it."""
+    return rank * shots_per_rank
+
+
+def job_rate(t_step: float, world: int, shots_per_rank: int, dist=None, device="cpu"):
+    """Step time as the maximum over ranks, and the whole job's shots/s at that time."""
+    if dist is not None:
+        import torch
+        t = torch.tensor([t_step], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_step = float(t.item())
+    return t_step, world * shots_per_rank / t_step
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -529,7 +546,7 @@ def main():
     sim = Simulator(N_QUBITS, CHI_MAX, args.shots, circ.n_cbits, tol=TOL, sweeps=SWEEPS,
                     seed=SEED, device=f"cuda:{local}")
     stream = sim.stream
-    shot0 = rank * args.shots
+    shot0 = shard_shot0(rank, args.shots)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{local}")  # > L2 (126 MB)
 
     def step():
@@ -561,14 +578,10 @@ def main():
     launches = sim.launches - l0
     ms = [a.elapsed_time(b) for a, b in durs]
     clk = clocks.stop()
-    t_step = sum(ms) / len(ms) / 1000.0
-    if dist is not None:
-        t = torch.tensor([t_step], device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_step = float(t.item())
+    t_step, value = job_rate(sum(ms) / len(ms) / 1000.0, world, args.shots, dist,
+                             f"cuda:{local}")
     res = sim.results()
     n_comp, n_sweeps = sim.counters()  # of the last step (counters restart at init_state)
-    value = world * args.shots / t_step
     sweeps_s = world * n_sweeps / t_step
     comp_s = world * n_comp / t_step
 

@@ -22,3 +22,40 @@ def test_reference_arm_prints_one_json_line():
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "shots/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
+
+
+def _bench_rank(rank, world, port, out):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        t, v = bench.job_rate(0.010 * (rank + 1), world, 100, dist, "cpu")
+        out.put((rank, t, v, bench.shard_shot0(rank, 100)))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_ranks_time_is_max_and_shots_are_disjoint():
+    import multiprocessing as mp
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    out = ctx.Queue()
+    procs = [ctx.Process(target=_bench_rank, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = sorted(out.get(timeout=300) for _ in procs)
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    for rank, t, v, lo in got:
+        assert t == 0.020  # the slower rank's step time on every rank
+        assert abs(v - 2 * 100 / 0.020) < 1e-9
+        assert lo == 100 * rank
+    ranges = [set(range(lo, lo + 100)) for _, _, _, lo in got]
+    assert not (ranges[0] & ranges[1]) and (ranges[0] | ranges[1]) == set(range(200))

@@ -115,6 +115,29 @@ def test_odd_slot_counts_every_shot():
     _single_path_parity(C.teleport(5), 4, 33, list(range(33)))
 
 
+def test_shot_offset_reproduces_the_same_shots():
+    # the sampler is keyed by the global shot index shot0 + slot, so a batch started at
+    # shot0 = 20 gives shots 20.. of a batch started at 0 (how shots are split over ranks)
+    circ = C.ghz_dynamic(12)
+    a = _sim(12, 8, 64, circ.n_cbits)
+    a.init_state(64)
+    a.run_circuit(circ)
+    ra = a.results()
+    b = _sim(12, 8, 24, circ.n_cbits)
+    b.init_state(24, shot0=20)
+    b.run_circuit(circ)
+    rb = b.results()
+    assert rb["n_active"] == 24
+    np.testing.assert_array_equal(rb["bits"], ra["bits"][20:44])
+    np.testing.assert_allclose(rb["p"], ra["p"][20:44], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(rb["F"], ra["F"][20:44], rtol=0, atol=1e-12)
+    prm = D.Params(chi_max=8)
+    for i in (0, 7, 23):
+        ref = D.run_single_path(circ, prm, 1, 20 + i)
+        if not ref.flagged:
+            assert rb["bits"][i].tolist() == [int(x) for x in ref.c]
+
+
 # tol = 0 is not a parity case: FP32 rounding leaves singular values ~1e-7 where FP64 has
 # exact zeros, so the two sides would keep different (noise) bond directions.
 @pytest.mark.parametrize("chi,tol", [(8, 1e-10), (5, 1e-10), (32, 1e-12)])
