@@ -1,7 +1,7 @@
 """CPU FP64 oracle for the dynamic-circuit MPS simulator -- TEST INFRASTRUCTURE ONLY.
 
-Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may
-import this package.  The product (``paper_2609_26516_b300``) never imports it, and it
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline and reference legs of
+``bench.py`` may import this package.  The product (``paper_2609_26516_b300``) never imports it, and it
 never imports the product: the two share no code besides the seeded circuit generators in
 ``circuits``.
 
