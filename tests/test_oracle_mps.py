@@ -67,6 +67,25 @@ def test_measure_and_collapse_match_statevector():
     np.testing.assert_allclose(M.to_dense(m), want, atol=1e-12)
 
 
+def test_collapse_normalises_an_unnormalised_state():
+    # the rescale uses the raw slice weight r_m, so the post-measurement state has norm 1
+    # whatever the norm before (a state whose norm rounding moved); the conditional
+    # probability r_m / (r_0 + r_1) is unchanged by the scale
+    rng = np.random.default_rng(11)
+    m = random_mps(rng, 6, 4)
+    psi = M.to_dense(m).reshape(-1)
+    m.T[m.centre] = m.T[m.centre] * 1.7
+    r0, r1 = M.measure_probs(m, 3)
+    assert abs((r0 + r1) - 1.7 ** 2) < 1e-12
+    p0 = SV.probabilities(psi.reshape([2] * 6), 3)[0]
+    assert abs(r0 / (r0 + r1) - p0) < 1e-12
+    M.collapse(m, 3, 0, r0)
+    out = M.to_dense(m).reshape(-1)
+    assert abs(np.vdot(out, out).real - 1.0) < 1e-12
+    want = SV.project(psi.reshape([2] * 6), 3, 0, p0).reshape(-1)
+    assert abs(abs(np.vdot(want, out)) - 1.0) < 1e-12
+
+
 def test_blocks_mpo_matches_dense_layer():
     rng = np.random.default_rng(3)
     n = 5
