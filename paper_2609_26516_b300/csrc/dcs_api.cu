@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "dcs_kernels.cuh"
+#include "dcs_plan.h"
 #include "dcs_tables.h"
 
 
@@ -93,12 +94,6 @@ Layout make_layout(const dcs_config* c) {
 }
 
 // ----------------------------------------------------------------------------- program
-struct Step {
-  int kind;  // 0 layer, 1 measurement run
-  int idx;   // layer index, or first DMeas
-  int n;     // number of measurements
-};
-
 struct Program {
   std::vector<DLayer> layers;
   std::vector<DBlock> blocks;
@@ -615,69 +610,15 @@ dcs_status_t dcs_import_mps(dcs_ctx_t c, int pos, const void* host_buf, size_t b
 dcs_status_t dcs_run_circuit(dcs_ctx_t c, const dcs_op* ops, int n_ops, uint64_t meas_idx0,
                              int max_branches) {
   if (!c || (n_ops > 0 && !ops)) return fail(c, DCS_ERR_INVALID, "null argument");
-  const int n = c->cfg.n_qubits;
-  // lower resets, validate
-  std::vector<dcs_op> lo;
-  lo.reserve(n_ops + 8);
   for (int i = 0; i < n_ops; ++i) {
     dcs_status_t st = check_gate(c, ops[i]);
     if (st != DCS_OK) return st;
-    if (ops[i].kind == DCS_OP_RESET) {
-      dcs_op m = ops[i];
-      m.kind = DCS_OP_MEASURE;
-      lo.push_back(m);
-      dcs_op x;
-      std::memset(&x, 0, sizeof(x));
-      x.kind = DCS_OP_GATE1;
-      x.q0 = ops[i].q0;
-      x.q1 = -1;
-      x.m[2] = 1.0;  // X = [[0, 1], [1, 0]]
-      x.m[4] = 1.0;
-      x.cond.op = DCS_COND_XOR;
-      x.cond.value = 1;
-      x.cond.mask[ops[i].cbit >> 6] = 1ull << (ops[i].cbit & 63);
-      lo.push_back(x);
-    } else {
-      lo.push_back(ops[i]);
-    }
   }
-  // chunks (Sec. "Handling unitary chunks in dynamic circuits", one-layer reading)
+  // resets lowered, chunks and measurement runs (Sec. "Handling unitary chunks in dynamic
+  // circuits", one-layer reading)
   Program P;
-  std::vector<dcs_op> cur;
-  std::vector<char> busy(n, 0);
-  auto close = [&]() -> std::string {
-    std::string e;
-    if (!cur.empty()) e = add_layer(P, n, cur);
-    cur.clear();
-    std::fill(busy.begin(), busy.end(), 0);
-    return e;
-  };
-  uint64_t ord = meas_idx0;
-  for (const dcs_op& o : lo) {
-    if (o.kind == DCS_OP_MEASURE) {
-      std::string e = close();
-      if (!e.empty()) return fail(c, DCS_ERR_INVALID, e);
-      if (!P.steps.empty() && P.steps.back().kind == 1) {
-        P.steps.back().n++;
-      } else {
-        P.steps.push_back({1, (int)P.meas.size(), 1});
-      }
-      P.meas.push_back({o.q0, o.cbit, ord++});
-      continue;
-    }
-    if (o.kind == DCS_OP_GATE2 && (busy[o.q0] || busy[o.q1])) {
-      std::string e = close();
-      if (!e.empty()) return fail(c, DCS_ERR_INVALID, e);
-    }
-    if (c->cfg.chunk_k > 0 && (int)cur.size() >= c->cfg.chunk_k) {
-      std::string e = close();
-      if (!e.empty()) return fail(c, DCS_ERR_INVALID, e);
-    }
-    cur.push_back(o);
-    if (o.kind == DCS_OP_GATE2) busy[o.q0] = busy[o.q1] = 1;
-  }
-  std::string e = close();
-  if (!e.empty()) return fail(c, DCS_ERR_INVALID, e);
+  if (const char* e = plan_circuit(P, c->cfg.n_qubits, c->cfg.chunk_k, ops, n_ops, meas_idx0))
+    return fail(c, DCS_ERR_INVALID, e);
   if (P.layers.size() * sizeof(DLayer) > kProgBytes / 2)
     return fail(c, DCS_ERR_OOM, "too many chunks for one call");
   return run_steps(c, P, max_branches, nullptr);

@@ -1,24 +1,64 @@
-// Host-only driver of libdcs's chunk-table builder (build_layer in dcs_tables.h) for the CPU
-// tests: reads n and a file of dcs_op records (one chunk, circuit order), builds the chunk's
-// tables exactly as the library does before uploading them, and prints them as text.
+// Host-only driver of libdcs's table builder and circuit planner for the CPU tests.
+//   harness n ops.bin                      one chunk (dcs_op records, circuit order) through
+//                                          build_layer (dcs_tables.h): its tables as text
+//   harness plan n chunk_k idx0 ops.bin    a whole circuit through plan_circuit
+//                                          (dcs_plan.h): steps, chunks and measurements
 // No CUDA call is made; it runs without a GPU.
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
 #include <vector>
 
-#include "dcs_tables.h"
+#include "dcs_plan.h"
 
 using namespace dcs;
 
 namespace {
 
-struct Prog {  // the containers build_layer appends to
+struct Prog {  // the containers build_layer and plan_circuit append to
   std::vector<DLayer> layers;
   std::vector<DBlock> blocks;
   std::vector<DGate1> g1;
   std::vector<DCond> conds;
+  std::vector<DMeas> meas;
+  std::vector<Step> steps;
   bool overflow() const { return false; }
 };
+
+std::vector<dcs_op> read_ops(const char* path) {
+  std::vector<dcs_op> ops;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return ops;
+  dcs_op o;
+  while (std::fread(&o, sizeof(o), 1, f) == 1) ops.push_back(o);
+  std::fclose(f);
+  return ops;
+}
+
+int plan_main(int n, int chunk_k, unsigned long long idx0, const char* path) {
+  std::vector<dcs_op> ops = read_ops(path);
+  Prog P;
+  const char* e = plan_circuit(P, n, chunk_k, ops.data(), (int)ops.size(), idx0);
+  if (e) {
+    std::printf("ERR %s\n", e);
+    return 0;
+  }
+  for (const Step& st : P.steps) {
+    std::printf("STEP %d %d %d\n", st.kind, st.idx, st.n);
+    if (st.kind == 0) {
+      const DLayer& L = P.layers[st.idx];
+      std::printf("CHUNK %d %d %d", L.n_blocks, L.uncond, L.n_conds);
+      for (int j = 0; j < n; ++j) std::printf(" %d", L.site[j].kind);
+      std::printf("\n");
+    } else {
+      for (int i = 0; i < st.n; ++i) {
+        const DMeas& m = P.meas[st.idx + i];
+        std::printf("MEAS %d %d %llu\n", m.q, m.cbit, (unsigned long long)m.ordinal);
+      }
+    }
+  }
+  return 0;
+}
 
 void put_c16(const char* tag, const float2* a) {
   std::printf("%s", tag);
@@ -34,17 +74,16 @@ void put_cond(const DCond& c) {
 }  // namespace
 
 int main(int argc, char** argv) {
+  if (argc == 6 && std::strcmp(argv[1], "plan") == 0)
+    return plan_main(std::atoi(argv[2]), std::atoi(argv[3]), std::strtoull(argv[4], nullptr, 10),
+                     argv[5]);
   if (argc != 3) {
-    std::fprintf(stderr, "usage: %s n ops.bin\n", argv[0]);
+    std::fprintf(stderr, "usage: %s n ops.bin | %s plan n chunk_k idx0 ops.bin\n", argv[0],
+                 argv[0]);
     return 2;
   }
   const int n = std::atoi(argv[1]);
-  FILE* f = std::fopen(argv[2], "rb");
-  if (!f) return 2;
-  std::vector<dcs_op> ops;
-  dcs_op o;
-  while (std::fread(&o, sizeof(o), 1, f) == 1) ops.push_back(o);
-  std::fclose(f);
+  std::vector<dcs_op> ops = read_ops(argv[2]);
   Prog P;
   const char* e = build_layer(P, n, ops.data(), (int)ops.size());
   if (e) {

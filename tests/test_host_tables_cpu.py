@@ -77,6 +77,28 @@ def tables(tmp_path_factory):
         assert out.returncode == 0, out.stderr
         return _parse(out.stdout)
 
+    def plan(n, ops, chunk_k=0, idx0=0):
+        p = d / "circ.bin"
+        p.write_bytes(bytes(encode_ops(ops)) if ops else b"")
+        out = subprocess.run([exe, "plan", str(n), str(chunk_k), str(idx0), str(p)],
+                             capture_output=True, text=True, timeout=60)
+        assert out.returncode == 0, out.stderr
+        steps = []
+        for ln in out.stdout.splitlines():
+            t = ln.split()
+            if t[0] == "ERR":
+                return {"err": ln[4:]}
+            if t[0] == "STEP":
+                steps.append({"kind": int(t[1]), "n": int(t[3]), "items": []})
+            elif t[0] == "CHUNK":
+                v = [int(x) for x in t[1:]]
+                steps[-1]["items"].append({"n_blocks": v[0], "uncond": v[1], "n_conds": v[2],
+                                           "kinds": v[3:]})
+            elif t[0] == "MEAS":
+                steps[-1]["items"].append(tuple(int(x) for x in t[1:]))
+        return steps
+
+    run.plan = plan
     return run
 
 
@@ -243,3 +265,40 @@ def test_every_brickwork_chunk_matches_the_oracle(tables):
                                         if _holds(e[1], c)])
                     np.testing.assert_allclose(U, G, atol=4 * F32)
     assert seen >= 6
+
+
+def _oracle_chunk_summary(n, chunk):
+    kinds = [0] * n
+    for g in chunk:
+        if len(g.qubits) == 2:
+            q = min(g.qubits)
+            kinds[q], kinds[q + 1] = 2, 3
+    for g in chunk:
+        if len(g.qubits) == 1 and kinds[g.qubits[0]] == 0:
+            kinds[g.qubits[0]] = 1
+    return {"n_blocks": sum(len(g.qubits) == 2 for g in chunk),
+            "uncond": int(any(g.cond is None for g in chunk)),
+            "n_conds": sum(g.cond is not None for g in chunk), "kinds": kinds}
+
+
+@pytest.mark.parametrize("chunk_k", [0, 3])
+@pytest.mark.parametrize("name", ["teleport", "ghz", "brickwork"])
+def test_circuit_plan_matches_the_oracle_chunking(tables, name, chunk_k):
+    circ = {"teleport": C.teleport(2), "ghz": C.ghz_dynamic(20),
+            "brickwork": C.brickwork(9, 6, 0.3, 7)}[name]
+    idx0 = 5
+    steps = tables.plan(circ.n_qubits, circ.ops, chunk_k, idx0)
+    n, ref = LY.chunk_circuit(circ, chunk_k)
+    want, runs, ord_ = [], 0, idx0
+    for i, st in enumerate(ref):
+        if isinstance(st, list):
+            want.append(_oracle_chunk_summary(n, st))
+        else:
+            want.append((st.qubit, st.cbit, ord_))
+            ord_ += 1
+            runs += int(i == 0 or isinstance(ref[i - 1], list))
+    got = [item for s in steps for item in s["items"]]
+    assert got == want
+    # one launch per chunk and one per maximal run of consecutive measurements
+    assert sum(s["kind"] == 1 for s in steps) == runs
+    assert all(s["n"] == len(s["items"]) for s in steps if s["kind"] == 1)
