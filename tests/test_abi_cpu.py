@@ -169,3 +169,12 @@ def test_bits_of_matches_plain_unpacking():
                          for i in range(cw.shape[0])], dtype=np.uint8)
         assert got.dtype == np.uint8 and got.shape == (37, n_bits)
         np.testing.assert_array_equal(got, want)
+
+
+def test_phase_report_command_line():
+    import subprocess
+    import sys
+    out = subprocess.run([sys.executable, "-m", "paper_2609_26516_b300.phases", "--help"],
+                         capture_output=True, text=True, timeout=120,
+                         cwd=os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    assert out.returncode == 0 and "ghz64" in out.stdout and "brick" in out.stdout
