@@ -188,7 +188,9 @@ dcs_status_t dcs_branch_topk(dcs_ctx_t ctx, int M);
  * register (n * DCS_CWORDS words), flags (n bytes), and the number n of active slots.  The
  * data comes down through the context's pinned host staging buffer, which grows (one
  * cudaMallocHost) the first time it is too small.  DCS_ERR_OOM if the branch pool ran out
- * during the circuit, DCS_ERR_CUDA on a copy or earlier asynchronous error. */
+ * during the circuit, DCS_ERR_CUDA on a copy or earlier asynchronous error, or when the
+ * device's active count or slot list lies outside the pool (corrupted device state; nothing
+ * is written to the buffers then). */
 dcs_status_t dcs_get_results(dcs_ctx_t ctx, double* p, double* fid, uint64_t* cbits,
                              int* n_active, uint8_t* flags);
 

@@ -505,6 +505,12 @@ dcs_status_t dcs_get_results(dcs_ctx_t c, double* p, double* fid, uint64_t* cbit
   const int cnt = reinterpret_cast<const int*>(h + oH)[0];
   const int status = reinterpret_cast<const int*>(h + oH)[1];
   const int* order = reinterpret_cast<const int*>(h + oO);
+  // the caller's buffers hold n_slots entries: a count or slot index outside the pool can
+  // only come from corrupted device state, and is reported instead of written out
+  if (cnt < 0 || (size_t)cnt > S) return fail(c, DCS_ERR_CUDA, "active count out of range");
+  for (int i = 0; i < cnt; ++i)
+    if (order[i] < 0 || (size_t)order[i] >= S)
+      return fail(c, DCS_ERR_CUDA, "slot list out of range");
   if (n_active) *n_active = cnt;
   for (int i = 0; i < cnt; ++i) {
     const size_t slot = (size_t)order[i];
