@@ -537,13 +537,21 @@ static dcs_status_t slot_of(dcs_ctx_t c, int pos, int& slot, int& kb, std::vecto
   cudaMemcpy(&cnt, c->dev.count, sizeof(int), cudaMemcpyDeviceToHost);
   if (pos < 0 || pos >= cnt) return fail(c, DCS_ERR_INVALID, "slot is not active");
   cudaMemcpy(&slot, c->dev.order + pos, sizeof(int), cudaMemcpyDeviceToHost);
+  // values read back from the device index host arrays and size host copies below: a value
+  // outside its range can only come from corrupted device state and is reported
+  if (slot < 0 || slot >= c->cfg.n_slots) return fail(c, DCS_ERR_CUDA, "slot list out of range");
   cudaMemcpy(&kb, c->dev.ketbuf + slot, sizeof(int), cudaMemcpyDeviceToHost);
   cudaMemcpy(&centre, c->dev.centre + slot, sizeof(int), cudaMemcpyDeviceToHost);
   const int n = c->cfg.n_qubits;
+  if (kb != 0 && kb != 1) return fail(c, DCS_ERR_CUDA, "buffer flag out of range");
   bonds.assign(n + 1, 0);
   cudaMemcpy(bonds.data(), c->dev.bonds + ((size_t)slot * 2 + kb) * (n + 1), (n + 1) * sizeof(int),
              cudaMemcpyDeviceToHost);
-  return cuda_check(c, cudaGetLastError(), "slot query");
+  if (st = cuda_check(c, cudaGetLastError(), "slot query"); st != DCS_OK) return st;
+  if (centre < 0 || centre >= n) return fail(c, DCS_ERR_CUDA, "centre out of range");
+  for (int v : bonds)
+    if (v < 1 || v > c->dev.chi_cap) return fail(c, DCS_ERR_CUDA, "bond out of range");
+  return DCS_OK;
 }
 
 dcs_status_t dcs_export_mps(dcs_ctx_t c, int pos, void* host_buf, size_t* bytes) {
