@@ -178,3 +178,21 @@ def test_phase_report_command_line():
                          capture_output=True, text=True, timeout=120,
                          cwd=os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     assert out.returncode == 0 and "ghz64" in out.stdout and "brick" in out.stdout
+
+
+def test_noalloc_argument_checks_need_no_device(lib):
+    # sizes beyond the fixed scratch and invalid arguments are refused before any CUDA call
+    from paper_2609_26516_b300 import _native as N
+    arr = (N.dcs_op * 1)()
+    d = ctypes.c_void_p(1)  # never dereferenced: every call below returns first
+
+    def call(n=8, chi=8, sweeps=2, n_gates=0, centre=0, gates=arr):
+        return lib.dcs_compress_noalloc(n, chi, 1e-10, sweeps, gates, n_gates, None, d, d,
+                                        centre, d, d, None, d, None)
+
+    assert call(n=65) == N.ERR_OOM
+    assert call(chi=16) == N.ERR_OOM
+    assert call(n_gates=257) == N.ERR_OOM
+    assert call(sweeps=0) == N.ERR_INVALID
+    assert call(centre=8) == N.ERR_INVALID
+    assert call(n_gates=1) == N.ERR_INVALID  # record of kind 0: not a gate
