@@ -1,16 +1,24 @@
-"""Build libdcs.so in-tree for sm_103a with nvcc (no GPU needed to compile)."""
+"""Build libdcs.so in-tree for sm_103a with nvcc (no GPU needed to compile).
+
+Every translation unit is compiled to an object file in parallel, then the objects are
+linked into the shared library.  Objects are rebuilt only when a source or header is newer
+than the library."""
 from __future__ import annotations
 
 import os
 import shutil
 import subprocess
 import sys
+from concurrent.futures import ThreadPoolExecutor
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.environ.get("DCS_LIB_PATH", os.path.join(HERE, "libdcs.so"))
-SOURCES = ["dcs_api.cu", "dcs_kernels.cu", "dcs_noalloc.cu", "dcs_gemm.cu"]
+OBJ = os.path.join(HERE, "_build")
+SOURCES = ["dcs_api.cu", "dcs_k_small.cu", "dcs_k_big.cu", "dcs_k_big_tc.cu", "dcs_k_ops.cu",
+           "dcs_noalloc.cu", "dcs_gemm.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
 
 
 def nvcc() -> str:
@@ -18,6 +26,15 @@ def nvcc() -> str:
         if cand and os.path.exists(cand):
             return cand
     raise RuntimeError("nvcc not found")
+
+
+def _compile(src: str, extra, verbose: bool):
+    obj = os.path.join(OBJ, os.path.basename(src) + ".o")
+    cmd = [nvcc(), *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
+    if verbose:
+        cmd.insert(1, "-Xptxas=-v")
+    res = subprocess.run(cmd, capture_output=True, text=True)
+    return obj, res
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
@@ -28,17 +45,22 @@ def build(force: bool = False, verbose: bool = False) -> str:
         t = os.path.getmtime(LIB)
         if all(os.path.getmtime(d) <= t for d in deps):
             return LIB
+    os.makedirs(OBJ, exist_ok=True)
     extra = os.environ.get("DCS_NVCC_FLAGS", "").split()
-    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
-           *extra, "-o", LIB + ".tmp", *srcs, "-lcudart"]
-    if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-    res = subprocess.run(cmd, capture_output=True, text=True)
+    with ThreadPoolExecutor(max_workers=len(srcs)) as ex:
+        results = list(ex.map(lambda s: _compile(s, extra, verbose), srcs))
+    failed = False
+    for obj, res in results:
+        if res.returncode != 0 or verbose:
+            sys.stderr.write(res.stdout + res.stderr)
+        failed |= res.returncode != 0
+    if failed:
+        raise RuntimeError("nvcc failed building libdcs.so")
+    link = [nvcc(), *ARCH, "-shared", "-o", LIB + ".tmp", *[o for o, _ in results], "-lcudart"]
+    res = subprocess.run(link, capture_output=True, text=True)
     if res.returncode != 0:
         sys.stderr.write(res.stdout + res.stderr)
-        raise RuntimeError("nvcc failed building libdcs.so")
-    if verbose:
-        sys.stderr.write(res.stderr)
+        raise RuntimeError("nvcc failed linking libdcs.so")
     os.replace(LIB + ".tmp", LIB)
     return LIB
 
