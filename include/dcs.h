@@ -130,7 +130,11 @@ size_t dcs_arena_bytes(const dcs_config* cfg);
 
 /* InitializeTN: bind a context to the caller's device arena and stream.  Carves the arena;
  * does not touch device memory.  cfg is copied.  Fails with DCS_ERR_OOM if arena_bytes <
- * dcs_arena_bytes(cfg), DCS_ERR_UNSUPPORTED if chi_max > DCS_MAX_CHI_FUSED. */
+ * dcs_arena_bytes(cfg), DCS_ERR_UNSUPPORTED if chi_max > DCS_MAX_CHI (or chi_max >
+ * DCS_MAX_CHI_FUSED with DCS_PATH_SHARED).
+ * Arena layout: per slot two MPS buffers and one environment cache, sized by the bond
+ * capacities cap_b = min(C, 2^min(b, n-b)) (C >= chi_max the bond cap of the kernel path):
+ * site j holds cap_j x 2 x cap_{j+1} complex64, bond b's environment cap_b x 4 x cap_b. */
 dcs_status_t dcs_create(dcs_ctx_t* ctx, const dcs_config* cfg, void* dev_arena,
                         size_t arena_bytes, dcs_stream_t stream);
 
@@ -200,7 +204,8 @@ dcs_status_t dcs_get_results(dcs_ctx_t ctx, double* p, double* fid, uint64_t* cb
  * on output; host_buf == NULL only queries the size. */
 dcs_status_t dcs_export_mps(dcs_ctx_t ctx, int slot, void* host_buf, size_t* bytes);
 
-/* Restore a slot's MPS from the dcs_export_mps format (bonds must not exceed the caps). */
+/* Restore a slot's MPS from the dcs_export_mps format.  Bond b must lie in 1 .. cap_b
+ * (see dcs_create), bonds 0 and n must be 1; otherwise DCS_ERR_INVALID. */
 dcs_status_t dcs_import_mps(dcs_ctx_t ctx, int slot, const void* host_buf, size_t bytes);
 
 /* Runs a whole dynamic circuit (ops in order) from the current state: resets are lowered
@@ -263,9 +268,14 @@ dcs_status_t dcs_cgemm(int32_t mode, int32_t batch, int32_t M, int32_t N, int32_
  *   conditions read, or NULL for all zeros.
  *   ket: DEVICE buffer of the input MPS, site j at complex64 offset j * 2 * Cc^2, Cc = 4 if
  *   chi_max <= 4 else 8, each site packed row-major as [chi_l][2][chi_r]; ket_bonds: DEVICE
- *   int32[n_qubits + 1]; ket_centre: its orthogonality centre (host int).  Read only.
+ *   int32[n_qubits + 1] with ket_bonds[0] = ket_bonds[n] = 1 and every bond in 1 .. Cc;
+ *   ket_centre: its orthogonality centre (host int).  Read only.
  *   bra, bra_bonds, bra_centre (may be NULL), f: DEVICE outputs in the same layout; f is one
  *   double.  If every gate is skipped by its condition, the ket is copied through, f = 1.
+ *   Failures found on the device are reported in the outputs (the call itself has returned
+ *   DCS_OK by then): ket bonds outside the rule above give bra_bonds[0] = 0, bra_centre = -1
+ *   and f = NaN, with no tensor read or written; a NaN/Inf met in the step or a bounded
+ *   device wait that gave up gives f = NaN.
  *
  * The first call on a device looks up the scratch array's device address for that device
  * (with the device current); make that first call before any stream capture.  Calls share

@@ -26,11 +26,11 @@ constexpr size_t kProgBytes = 32ull << 20;  // device copy of one call's tables
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-  size_t mps0, mps1, lc, rc, bonds, centre, ketbuf, p, F, rr, creg, flags, shot, order, count,
+  size_t mps0, mps1, env, offs, bonds, centre, ketbuf, p, F, rr, creg, flags, shot, order, count,
       status, plan, counters, prog, work, total;
   bool big;
   size_t work_stride;
-  int chi_cap, site_stride, env_stride;
+  int chi_cap;
   size_t mps_slot_stride, env_slot_stride;
 };
 
@@ -59,10 +59,7 @@ Layout make_layout(const dcs_config* c) {
   pick_path(c, L.big);
   L.chi_cap = L.big ? big_chi(c->chi_max) : fused_chi(c->chi_max);
   L.work_stride = L.big ? big_work_elems(L.chi_cap) : 0;
-  L.site_stride = 2 * L.chi_cap * L.chi_cap;
-  L.env_stride = 4 * L.chi_cap * L.chi_cap;
-  L.mps_slot_stride = n * (size_t)L.site_stride;
-  L.env_slot_stride = (n + 1) * (size_t)L.env_stride;
+  layout_offsets((int)n, L.chi_cap, nullptr, nullptr, &L.mps_slot_stride, &L.env_slot_stride);
   size_t off = 0;
   auto take = [&](size_t bytes) {
     const size_t o = off;
@@ -71,8 +68,8 @@ Layout make_layout(const dcs_config* c) {
   };
   L.mps0 = take(S * L.mps_slot_stride * sizeof(float2));
   L.mps1 = take(S * L.mps_slot_stride * sizeof(float2));
-  L.lc = take(S * L.env_slot_stride * sizeof(float2));
-  L.rc = take(S * L.env_slot_stride * sizeof(float2));
+  L.env = take(S * L.env_slot_stride * sizeof(float2));
+  L.offs = take(2 * (n + 1) * sizeof(size_t));
   L.bonds = take(S * 2 * (n + 1) * sizeof(int32_t));
   L.centre = take(S * sizeof(int32_t));
   L.ketbuf = take(S * sizeof(int32_t));
@@ -135,6 +132,7 @@ struct dcs_ctx_s {
   // (2 chi_q) x (2 chi_{q+2}) matrix); QR steps, measurements and single-qubit gates never
   // raise a bond.  The shared-memory tile of a launch is the smallest one above this bound.
   std::vector<int> ub;
+  std::vector<size_t> site_off, env_off;  // host copy of the bond-sized layout offsets
   int tile() const {
     int m = 1;
     for (int v : ub) m = std::max(m, v);
@@ -323,15 +321,14 @@ dcs_status_t dcs_create(dcs_ctx_t* out, const dcs_config* cfg, void* dev_arena, 
   d.n = cfg->n_qubits;
   d.chi_cap = lay.chi_cap;
   d.n_slots = cfg->n_slots;
-  d.site_stride = lay.site_stride;
-  d.env_stride = lay.env_stride;
   d.mps_slot_stride = lay.mps_slot_stride;
   d.env_slot_stride = lay.env_slot_stride;
   char* a = c->arena;
   d.mps[0] = reinterpret_cast<float2*>(a + lay.mps0);
   d.mps[1] = reinterpret_cast<float2*>(a + lay.mps1);
-  d.Lc = reinterpret_cast<float2*>(a + lay.lc);
-  d.Rc = reinterpret_cast<float2*>(a + lay.rc);
+  d.env = reinterpret_cast<float2*>(a + lay.env);
+  d.site_off = reinterpret_cast<const size_t*>(a + lay.offs);
+  d.env_off = d.site_off + (cfg->n_qubits + 1);
   d.bonds = reinterpret_cast<int32_t*>(a + lay.bonds);
   d.centre = reinterpret_cast<int32_t*>(a + lay.centre);
   d.ketbuf = reinterpret_cast<int32_t*>(a + lay.ketbuf);
@@ -354,6 +351,10 @@ dcs_status_t dcs_create(dcs_ctx_t* out, const dcs_config* cfg, void* dev_arena, 
   d.tol = cfg->tol;
   d.sweeps = cfg->sweeps;
   c->ub.assign(cfg->n_qubits + 1, 1);
+  c->site_off.assign(cfg->n_qubits + 1, 0);
+  c->env_off.assign(cfg->n_qubits + 1, 0);
+  size_t me = 0, ee = 0;
+  layout_offsets(cfg->n_qubits, lay.chi_cap, c->site_off.data(), c->env_off.data(), &me, &ee);
   if (cudaEventCreateWithFlags(&c->stage_done, cudaEventDisableTiming) != cudaSuccess) {
     delete c;
     return DCS_ERR_CUDA;
@@ -395,7 +396,7 @@ dcs_status_t dcs_init_state(dcs_ctx_t c, int n_active, int multipath, uint64_t s
   c->multipath = multipath ? 1 : 0;
   c->ub.assign(c->cfg.n_qubits + 1, 1);
   launch_init(c->dev, n_active, c->multipath, shot0, c->stream);
-  c->launches++;
+  c->launches += 2;
   return post_launch(c, "init");
 }
 
@@ -551,6 +552,8 @@ static dcs_status_t slot_of(dcs_ctx_t c, int pos, int& slot, int& kb, std::vecto
   if (centre < 0 || centre >= n) return fail(c, DCS_ERR_CUDA, "centre out of range");
   for (int v : bonds)
     if (v < 1 || v > c->dev.chi_cap) return fail(c, DCS_ERR_CUDA, "bond out of range");
+  for (int j = 0; j <= n; ++j)
+    if (bonds[j] > bond_cap(j, n, c->dev.chi_cap)) return fail(c, DCS_ERR_CUDA, "bond out of range");
   return DCS_OK;
 }
 
@@ -576,7 +579,7 @@ dcs_status_t dcs_export_mps(dcs_ctx_t c, int pos, void* host_buf, size_t* bytes)
   size_t off = 4 * (size_t)(n + 3);
   for (int j = 0; j < n; ++j) {
     const size_t len = (size_t)b[j] * 2 * b[j + 1];
-    cudaMemcpy(o + off, c->dev.mps[kb] + (size_t)slot * c->dev.mps_slot_stride + (size_t)j * c->dev.site_stride,
+    cudaMemcpy(o + off, c->dev.mps[kb] + (size_t)slot * c->dev.mps_slot_stride + c->site_off[j],
                len * sizeof(float2), cudaMemcpyDeviceToHost);
     off += len * sizeof(float2);
   }
@@ -604,13 +607,14 @@ dcs_status_t dcs_import_mps(dcs_ctx_t c, int pos, const void* host_buf, size_t b
     return fail(c, DCS_ERR_INVALID, "malformed MPS header");
   size_t need = sizeof(int32_t) * (n + 3);
   for (int j = 0; j <= n; ++j)
-    if (b[j] < 1 || b[j] > c->dev.chi_cap) return fail(c, DCS_ERR_INVALID, "bond above capacity");
+    if (b[j] < 1 || b[j] > bond_cap(j, n, c->dev.chi_cap))
+      return fail(c, DCS_ERR_INVALID, "bond above capacity");
   for (int j = 0; j < n; ++j) need += sizeof(float2) * (size_t)b[j] * 2 * b[j + 1];
   if (bytes < need) return fail(c, DCS_ERR_INVALID, "import buffer too small");
   size_t off = 4 * (size_t)(n + 3);
   for (int j = 0; j < n; ++j) {
     const size_t len = (size_t)b[j] * 2 * b[j + 1];
-    cudaMemcpy(c->dev.mps[kb] + (size_t)slot * c->dev.mps_slot_stride + (size_t)j * c->dev.site_stride,
+    cudaMemcpy(c->dev.mps[kb] + (size_t)slot * c->dev.mps_slot_stride + c->site_off[j],
                in + off, len * sizeof(float2), cudaMemcpyHostToDevice);
     off += len * sizeof(float2);
   }

@@ -177,10 +177,10 @@ static __device__ __noinline__ void build_block(const DBlock& b, const DGate1* G
 }
 
 __device__ __forceinline__ float2* site_ptr(const DevCtx& c, int buf, int slot, int j) {
-  return c.mps[buf] + (size_t)slot * c.mps_slot_stride + (size_t)j * c.site_stride;
+  return c.mps[buf] + (size_t)slot * c.mps_slot_stride + __ldg(c.site_off + j);
 }
-__device__ __forceinline__ float2* env_ptr(float2* base, const DevCtx& c, int slot, int j) {
-  return base + (size_t)slot * c.env_slot_stride + (size_t)j * c.env_stride;
+__device__ __forceinline__ float2* env_ptr(const DevCtx& c, int slot, int b) {
+  return c.env + (size_t)slot * c.env_slot_stride + __ldg(c.env_off + b);
 }
 __device__ __forceinline__ int* bonds_ptr(const DevCtx& c, int slot, int buf) {
   return c.bonds + ((size_t)slot * 2 + buf) * (c.n + 1);

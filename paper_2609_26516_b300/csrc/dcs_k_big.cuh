@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
     mix_big<NT>(sm.T, dl * 2 * nx, 2 * nx, nx, 1, sm.T2, sm.W, nb, dl, dr, nx, false);
     // L_{j+1}[c, (e x)] = sum_{(b s)} conj(B_j[(b s), c]) T2[(b s), (e x)]
     wgemm<NT>(sm, nc, dr * nx, 2 * nb, Bj, 1, nc, true, sm.T2, dr * nx, 1, false, sm.E, dr * nx, 1);
-    gcopy<NT>(env_ptr(c.Lc, c, slot, j + 1), sm.E, nc * dr * nx);
+    gcopy<NT>(env_ptr(c, slot, j + 1), sm.E, nc * dr * nx);
     __syncthreads();
   }
   // ---- right environments of the guess (mirrored env updates with B given)
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
     // R_j[b, (d a)] = sum_{(c s)} conj(Q'[(c s), b]) T2[(c s), (d a)]
     wgemm<NT>(sm, bl, dl * al, 2 * br, sm.R, ldq, 1, true, sm.T2, dl * al, 1, false, sm.E, dl * al,
                   1);
-    gcopy<NT>(env_ptr(c.Rc, c, slot, j), sm.E, bl * dl * al);
+    gcopy<NT>(env_ptr(c, slot, j), sm.E, bl * dl * al);
     __syncthreads();
   }
   PHASE_MARK(6);
@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
         const int nb = bt[j], nc = bt[j + 1], na = at[j], nx = at[j + 1];
         const float2* A = site_ptr(c, kb, slot, j);
         const float2* Rn = sm.R;
-        if (j < n - 1) Rn = env_ptr(c.Rc, c, slot, j + 1);
+        if (j < n - 1) Rn = env_ptr(c, slot, j + 1);
         else if (threadIdx.x == 0) sm.R[0] = make_float2(1.f, 0.f);
         __syncthreads();
         wgemm<NT>(sm, nb * dl, 2 * nx, na, sm.E, na, 1, false, A, 2 * nx, 1, false, sm.T, 2 * nx, 1);
@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
             dst[idx] = sm.R[row + (size_t)k2 * m];
           }
           wgemm<NT>(sm, r, dr * nx, m, sm.R, m, 1, true, sm.T2, dr * nx, 1, false, sm.E, dr * nx, 1);
-          gcopy<NT>(env_ptr(c.Lc, c, slot, j + 1), sm.E, r * dr * nx);
+          gcopy<NT>(env_ptr(c, slot, j + 1), sm.E, r * dr * nx);
           __syncthreads();
           if (threadIdx.x == 0) bt[j + 1] = r;
           __syncthreads();
@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
         const int nb = bt[j + 1], nc = bt[j], na = at[j + 1], nx = at[j];
         const float2* A = site_ptr(c, kb, slot, j);
         const float2* Ln = sm.R;
-        if (j > 0) Ln = env_ptr(c.Lc, c, slot, j);
+        if (j > 0) Ln = env_ptr(c, slot, j);
         else if (threadIdx.x == 0) sm.R[0] = make_float2(1.f, 0.f);
         __syncthreads();
         // T1[(c e), (a t)] = sum_x E[(c e), x] A[(a t), x]
@@ -354,7 +354,7 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
             dst[idx] = sm.R[(cc * 2 + s) + (size_t)k2 * m];
           }
           wgemm<NT>(sm, r, dl * nx, m, sm.R, m, 1, true, sm.T2, dl * nx, 1, false, sm.E, dl * nx, 1);
-          gcopy<NT>(env_ptr(c.Rc, c, slot, j), sm.E, r * dl * nx);
+          gcopy<NT>(env_ptr(c, slot, j), sm.E, r * dl * nx);
           __syncthreads();
           if (threadIdx.x == 0) bt[j] = r;
           __syncthreads();

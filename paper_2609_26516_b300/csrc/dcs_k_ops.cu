@@ -104,6 +104,15 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_measure(DevCtx c, 
 }
 
 // ----------------------------------------------------------------------------- init
+// The bond-sized layout offsets (layout_offsets) written to the arena's offset tables.
+__global__ void k_layout(DevCtx c) {
+  if (threadIdx.x == 0) {
+    size_t me = 0, ee = 0;
+    layout_offsets(c.n, c.chi_cap, const_cast<size_t*>(c.site_off), const_cast<size_t*>(c.env_off),
+                   &me, &ee);
+  }
+}
+
 __global__ void k_init(DevCtx c, int n_active, int multipath, uint64_t shot0) {
   const int slot = blockIdx.x;
   const int n = c.n;
@@ -383,6 +392,7 @@ static void measure_c(const DevCtx& c, int C, const DMeas* meas, int n_meas, int
 }
 
 void launch_init(const DevCtx& c, int n_active, int multipath, uint64_t shot0, cudaStream_t s) {
+  k_layout<<<1, 32, 0, s>>>(c);
   k_init<<<c.n_slots, 64, 0, s>>>(c, n_active, multipath, shot0);
 }
 

@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_compress(DevCtx c,
     c1_env_site<NT>(sm.E, sm.S, sm.T, nb, dl, na, nx, Dm);
     c2_mix<NT>(sm.T, sm.W, nb, dl, dr, nx, Dm);
     c4_env_update<NT>(sm.R, m, sm.T, sm.E, nb, dr, nx, nc, Dm);
-    gcopy<NT>(env_ptr(c.Lc, c, slot, j + 1), sm.E, nc * dr * nx);
+    gcopy<NT>(env_ptr(c, slot, j + 1), sm.E, nc * dr * nx);
     __syncthreads();
   }
   // ---- right environments of the guess: R_j for j = n-1 .. 1 (mirrored env updates)
@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_compress(DevCtx c,
     c1_env_site<NT>(sm.E, sm.S, sm.T, br, dr, ar, al, Dm);
     c2_mix<NT>(sm.T, sm.W2, br, dr, dl, al, Dm);
     c4_env_update<NT>(sm.R, ldq, sm.T, sm.E, br, dl, al, bl, Dm);
-    gcopy<NT>(env_ptr(c.Rc, c, slot, j), sm.E, bl * dl * al);
+    gcopy<NT>(env_ptr(c, slot, j), sm.E, bl * dl * al);
     __syncthreads();
   }
   // ---- one-site sweeps
@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_compress(DevCtx c,
         const int dl = sm.iv[0], dr = sm.iv[1], Dm = dl > dr ? dl : dr;
         const int nb = bt[j], nc = bt[j + 1], na = at[j], nx = at[j + 1];
         gcopy<NT>(sm.S, site_ptr(c, kb, slot, j), na * 2 * nx);
-        if (j < n - 1) gcopy<NT>(sm.R, env_ptr(c.Rc, c, slot, j + 1), nc * dr * nx);
+        if (j < n - 1) gcopy<NT>(sm.R, env_ptr(c, slot, j + 1), nc * dr * nx);
         else if (threadIdx.x == 0) sm.R[0] = make_float2(1.f, 0.f);
         __syncthreads();
         c1_env_site<NT>(sm.E, sm.S, sm.T, nb, dl, na, nx, Dm);
@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_compress(DevCtx c,
             dst[idx] = sm.R[row + k * m];
           }
           c4_env_update<NT>(sm.R, m, sm.T, sm.E, nb, dr, nx, r, Dm);
-          gcopy<NT>(env_ptr(c.Lc, c, slot, j + 1), sm.E, r * dr * nx);
+          gcopy<NT>(env_ptr(c, slot, j + 1), sm.E, r * dr * nx);
           __syncthreads();
           if (threadIdx.x == 0) bt[j + 1] = r;
           __syncthreads();
@@ -328,7 +328,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_compress(DevCtx c,
           const int x = idx % na, t = (idx / na) & 1, a = idx / (2 * na);
           sm.S[(x * 2 + t) * nx + a] = A[idx];
         }
-        if (j > 0) gcopy<NT>(sm.R, env_ptr(c.Lc, c, slot, j), nc * dl * nx);
+        if (j > 0) gcopy<NT>(sm.R, env_ptr(c, slot, j), nc * dl * nx);
         else if (threadIdx.x == 0) sm.R[0] = make_float2(1.f, 0.f);
         __syncthreads();
         c1_env_site<NT>(sm.E, sm.S, sm.T, nb, dr, na, nx, Dm);
@@ -344,7 +344,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_compress(DevCtx c,
             dst[idx] = sm.R[(cc * 2 + s) + k * m];
           }
           c4_env_update<NT>(sm.R, m, sm.T, sm.E, nb, dl, nx, r, Dm);
-          gcopy<NT>(env_ptr(c.Rc, c, slot, j), sm.E, r * dl * nx);
+          gcopy<NT>(env_ptr(c, slot, j), sm.E, r * dl * nx);
           __syncthreads();
           if (threadIdx.x == 0) bt[j] = r;
           __syncthreads();

@@ -62,15 +62,16 @@ struct DMeas {
 // Device view of a context (passed by value to every kernel).
 struct DevCtx {
   int32_t n;         // sites
-  int32_t chi_cap;   // slot capacity per bond (>= chi_max)
+  int32_t chi_cap;   // bond capacity (>= chi_max); bond b holds at most bond_cap(b, n, chi_cap)
   int32_t n_slots;
-  int32_t site_stride;       // complex elements per site (2 chi_cap^2)
-  int32_t env_stride;        // complex elements per environment (4 chi_cap^2)
+  const size_t* site_off;    // [n+1] complex-element offset of site j in a slot's MPS buffer
+  const size_t* env_off;     // [n+1] offset of the environment of bond b in a slot's cache
   size_t mps_slot_stride;    // complex elements per slot per MPS buffer
-  size_t env_slot_stride;    // complex elements per slot per environment cache
+  size_t env_slot_stride;    // complex elements per slot of the environment cache
   float2* mps[2];            // MPS buffer pair
-  float2* Lc;                // left environment cache
-  float2* Rc;                // right environment cache
+  float2* env;               // environment cache: bond b holds L_b or R_b, whichever the
+                             // sweep reads next (a left-to-right step reads R_{j+1} before it
+                             // writes L_{j+1} over it; right to left mirrored)
   int32_t* bonds;            // [slot][2][n+1]
   int32_t* centre;           // [slot]
   int32_t* ketbuf;           // [slot] which MPS buffer holds the ket
@@ -94,10 +95,37 @@ struct DevCtx {
   int32_t sweeps;
 };
 
+// Capacity of bond b (0..n) of an n-site MPS whose bonds are capped at C: min(C,
+// 2^min(b, n-b)), the largest Schmidt rank of a cut into b and n-b qubits (paragraph
+// "Matrix Product States": the bond dimensions chi_b vary along the chain).
+__host__ __device__ inline int bond_cap(int b, int n, int C) {
+  const int e = b < n - b ? b : n - b;
+  if (e >= 30) return C;
+  return C < (1 << e) ? C : (1 << e);
+}
+
+// Bond-sized layout of one slot: site j ([chi_j][2][chi_{j+1}], complex) at site_off[j],
+// the environment of bond b ([beta_b][D <= 4][alpha_b]) at env_off[b]; every region starts
+// on a 256-byte boundary.  Returns the per-slot sizes through mps_elems / env_elems.
+__host__ __device__ inline void layout_offsets(int n, int C, size_t* site_off, size_t* env_off,
+                                               size_t* mps_elems, size_t* env_elems) {
+  size_t s = 0, e = 0;
+  for (int b = 0; b <= n; ++b) {
+    const size_t cb = (size_t)bond_cap(b, n, C);
+    if (site_off) site_off[b] = s;
+    if (env_off) env_off[b] = e;
+    if (b < n) s += ((cb * 2 * (size_t)bond_cap(b + 1, n, C)) + 31) / 32 * 32;
+    e += (4 * cb * cb + 31) / 32 * 32;
+  }
+  *mps_elems = s;
+  *env_elems = e;
+}
+
 // plan layout (int32 words): [0] n_copy, [1] n_coll, [2] new count,
 // then copy pairs (src, dst) x n_slots, then collapse records (slot, m) x n_slots.
 constexpr int PLAN_HDR = 4;
 
+// two launches: the layout offset tables, then the initial state of every slot
 void launch_init(const DevCtx& c, int n_active, int multipath, uint64_t shot0, cudaStream_t s);
 // tile_chi: shared-memory tile (4, 8, 16 or 32), at least every bond the launch can meet
 void launch_compress(const DevCtx& c, int tile_chi, const DLayer* L, const DBlock* B,

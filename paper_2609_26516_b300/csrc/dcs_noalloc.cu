@@ -56,7 +56,7 @@ FixedProg g_prog;
 size_t up(size_t x) { return (x + 255) / 256 * 256; }
 
 struct Carve {
-  size_t mps, lc, rc, bonds, ints, dbl, creg, flags, shot, plan, layer, blocks, g1, conds, total;
+  size_t mps, env, offs, bonds, ints, dbl, creg, flags, shot, plan, layer, blocks, g1, conds, total;
 };
 
 Carve carve(int n, int C) {
@@ -69,8 +69,8 @@ Carve carve(int n, int C) {
   };
   const size_t env = (size_t)(n + 1) * 4 * C * C * sizeof(float2);
   k.mps = take((size_t)n * 2 * C * C * sizeof(float2));  // the second MPS buffer
-  k.lc = take(env);
-  k.rc = take(env);
+  k.env = take(env);
+  k.offs = take(2 * (size_t)(n + 1) * sizeof(size_t));
   k.bonds = take(2 * (size_t)(n + 1) * sizeof(int32_t));
   k.ints = take(8 * sizeof(int32_t));   // centre, ketbuf, order, count, status
   k.dbl = take(4 * sizeof(double));     // p, F, rr[2]
@@ -94,23 +94,39 @@ struct Creg {
 // caller's ket is read only: it is copied into the caller's bra buffer, which serves as the
 // slot's first MPS buffer (an exact step updates it in place; otherwise the result lands in
 // the scratch MPS buffer and k_noalloc_finish copies it over).
+//
+// The caller's bonds are checked here, on the device, before any kernel indexes with them:
+// bond 0 and bond n must be 1 and every bond must lie in 1 .. C (the site stride holds
+// C x 2 x C).  A malformed list leaves the active count at 0, so the compression kernel
+// returns at once, and k_noalloc_finish reports the failure.
 __global__ void k_noalloc_prepare(DevCtx c, const int32_t* ket_bonds, int centre, Creg creg,
                                   const float2* ket) {
-  const int n = c.n;
+  const int n = c.n, C = c.chi_cap;
+  const size_t stride = 2 * (size_t)C * C;
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = (ket_bonds[0] != 1 || ket_bonds[n] != 1) ? 1 : 0;
+  __syncthreads();
   for (int i = threadIdx.x; i <= n; i += blockDim.x) {
-    c.bonds[i] = ket_bonds[i];
-    c.bonds[n + 1 + i] = ket_bonds[i];
+    const int b = ket_bonds[i];
+    if (b < 1 || b > C) atomicOr(&bad, 1);
   }
-  for (int j = 0; j < n; ++j) {
-    long long len = (long long)ket_bonds[j] * 2 * ket_bonds[j + 1];
-    len = len < 0 ? 0 : (len > (long long)c.site_stride ? (long long)c.site_stride : len);
-    for (int e = threadIdx.x; e < (int)len; e += blockDim.x)
-      c.mps[0][(size_t)j * c.site_stride + e] = ket[(size_t)j * c.site_stride + e];
+  __syncthreads();
+  for (int i = threadIdx.x; i <= n; i += blockDim.x) {
+    const int b = bad ? 1 : ket_bonds[i];
+    c.bonds[i] = b;
+    c.bonds[n + 1 + i] = b;
+    const_cast<size_t*>(c.site_off)[i] = (size_t)i * stride;
+    const_cast<size_t*>(c.env_off)[i] = (size_t)i * 2 * stride;
+  }
+  for (int j = 0; j < n && !bad; ++j) {
+    const int len = ket_bonds[j] * 2 * ket_bonds[j + 1];
+    for (int e = threadIdx.x; e < len; e += blockDim.x)
+      c.mps[0][(size_t)j * stride + e] = ket[(size_t)j * stride + e];
   }
   if (threadIdx.x < DCS_CWORDS) c.creg[threadIdx.x] = creg.w[threadIdx.x];
   if (threadIdx.x == 0) {
     c.order[0] = 0;
-    *c.count = 1;
+    *c.count = bad ? 0 : 1;
     *c.status = 0;
     c.centre[0] = centre;
     c.ketbuf[0] = 0;
@@ -125,10 +141,22 @@ __global__ void k_noalloc_prepare(DevCtx c, const int32_t* ket_bonds, int centre
 
 // Bond dimensions and centre of the result.  The bra buffer already holds it unless the
 // step swapped buffers (the sweeps ran): then it is copied over from the scratch buffer.  A
-// slot left unchanged (every gate skipped by its condition) hands back the input.
+// slot left unchanged (every gate skipped by its condition) hands back the input; an empty
+// chunk sets f = 1 here.  Failures become visible in the outputs: malformed ket bonds give
+// bra_bonds[0] = 0, bra_centre = -1 and f = NaN; a NaN/Inf met in the step, or a bounded
+// device wait that gave up, gives f = NaN.
 __global__ void k_noalloc_finish(DevCtx c, int32_t* bra_bonds, int32_t* bra_centre,
-                                 float2* bra) {
+                                 float2* bra, double* f, int empty) {
   const int n = c.n;
+  const size_t stride = 2 * (size_t)c.chi_cap * c.chi_cap;
+  if (*c.count == 0) {
+    if (threadIdx.x == 0) {
+      bra_bonds[0] = 0;
+      if (bra_centre) *bra_centre = -1;
+      *f = __longlong_as_double(0x7ff8000000000000ll);
+    }
+    return;
+  }
   const int buf = c.ketbuf[0];
   const int* bd = c.bonds + buf * (n + 1);
   for (int i = threadIdx.x; i <= n; i += blockDim.x) bra_bonds[i] = bd[i];
@@ -136,10 +164,15 @@ __global__ void k_noalloc_finish(DevCtx c, int32_t* bra_bonds, int32_t* bra_cent
     for (int j = 0; j < n; ++j) {
       const int len = bd[j] * 2 * bd[j + 1];
       for (int e = threadIdx.x; e < len; e += blockDim.x)
-        bra[(size_t)j * c.site_stride + e] = c.mps[1][(size_t)j * c.site_stride + e];
+        bra[(size_t)j * stride + e] = c.mps[1][(size_t)j * stride + e];
     }
   }
-  if (threadIdx.x == 0 && bra_centre) *bra_centre = c.centre[0];
+  if (threadIdx.x == 0) {
+    if (bra_centre) *bra_centre = c.centre[0];
+    if (empty) *f = 1.0;
+    if ((c.flags[0] & DCS_FLAG_NUMERICAL) || *c.status != 0)
+      *f = __longlong_as_double(0x7ff8000000000000ll);
+  }
 }
 
 }  // namespace
@@ -158,8 +191,15 @@ extern "C" dcs_status_t dcs_compress_noalloc(int32_t n_qubits, int32_t chi_max, 
   if (n_qubits > DCS_NOALLOC_MAX_QUBITS || chi_max > DCS_NOALLOC_MAX_CHI ||
       n_gates > DCS_NOALLOC_MAX_GATES)
     return DCS_ERR_OOM;  // beyond what the fixed scratch holds
-  for (int i = 0; i < n_gates; ++i)
-    if (gates[i].kind != DCS_OP_GATE1 && gates[i].kind != DCS_OP_GATE2) return DCS_ERR_INVALID;
+  for (int i = 0; i < n_gates; ++i) {
+    const dcs_op& o = gates[i];
+    if (o.kind != DCS_OP_GATE1 && o.kind != DCS_OP_GATE2) return DCS_ERR_INVALID;
+    const bool two = o.kind == DCS_OP_GATE2;
+    if (o.q0 < 0 || o.q0 >= n_qubits || (two && (o.q1 < 0 || o.q1 >= n_qubits)))
+      return DCS_ERR_INVALID;
+    if (o.cond.op != DCS_COND_NONE && o.cond.op != DCS_COND_XOR && o.cond.op != DCS_COND_AND)
+      return DCS_ERR_INVALID;
+  }
   const int C = fused_chi(chi_max);
   const Carve k = carve(n_qubits, C);
   if (k.total > DCS_NOALLOC_SCRATCH_BYTES) return DCS_ERR_OOM;
@@ -178,26 +218,19 @@ extern "C" dcs_status_t dcs_compress_noalloc(int32_t n_qubits, int32_t chi_max, 
   char* base = static_cast<char*>(g_scratch_addr[dev]);
 
   g_prog.clear();
-  for (int i = 0; i < n_gates; ++i) {
-    const dcs_op& o = gates[i];
-    const bool two = o.kind == DCS_OP_GATE2;
-    if (o.q0 < 0 || o.q0 >= n_qubits || (two && (o.q1 < 0 || o.q1 >= n_qubits)))
-      return DCS_ERR_INVALID;
-  }
   if (n_gates > 0 && build_layer(g_prog, n_qubits, gates, n_gates) != nullptr) return DCS_ERR_INVALID;
 
   DevCtx d{};
   d.n = n_qubits;
   d.chi_cap = C;
   d.n_slots = 1;
-  d.site_stride = 2 * C * C;
-  d.env_stride = 4 * C * C;
-  d.mps_slot_stride = (size_t)n_qubits * d.site_stride;
-  d.env_slot_stride = (size_t)(n_qubits + 1) * d.env_stride;
+  d.mps_slot_stride = (size_t)n_qubits * 2 * C * C;
+  d.env_slot_stride = (size_t)(n_qubits + 1) * 4 * C * C;
   d.mps[0] = static_cast<float2*>(bra);
   d.mps[1] = reinterpret_cast<float2*>(base + k.mps);
-  d.Lc = reinterpret_cast<float2*>(base + k.lc);
-  d.Rc = reinterpret_cast<float2*>(base + k.rc);
+  d.env = reinterpret_cast<float2*>(base + k.env);
+  d.site_off = reinterpret_cast<const size_t*>(base + k.offs);
+  d.env_off = d.site_off + (n_qubits + 1);
   d.bonds = reinterpret_cast<int32_t*>(base + k.bonds);
   int32_t* ints = reinterpret_cast<int32_t*>(base + k.ints);
   d.centre = ints + 0;
@@ -242,13 +275,10 @@ extern "C" dcs_status_t dcs_compress_noalloc(int32_t n_qubits, int32_t chi_max, 
       return DCS_ERR_CUDA;
     launch_compress(d, C, dl, db, dg, dc, f, s);
     if (cudaGetLastError() != cudaSuccess) return DCS_ERR_CUDA;
-  } else {
-    // an empty chunk: nothing to compress, f = 1
-    const double one = 1.0;
-    if (cudaMemcpyAsync(f, &one, sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess)
-      return DCS_ERR_CUDA;
   }
-  k_noalloc_finish<<<1, 128, 0, s>>>(d, bra_bonds, bra_centre, static_cast<float2*>(bra));
+  // an empty chunk has nothing to compress: k_noalloc_finish writes f = 1
+  k_noalloc_finish<<<1, 128, 0, s>>>(d, bra_bonds, bra_centre, static_cast<float2*>(bra), f,
+                                     n_gates == 0 ? 1 : 0);
   if (cudaGetLastError() != cudaSuccess) return DCS_ERR_CUDA;
   return DCS_OK;
 }

@@ -75,13 +75,30 @@ def _cfg(N, **kw):
     return N.dcs_config(**base)
 
 
+def _slot_elems(n, C):
+    cap = [min(C, 2 ** min(b, n - b)) for b in range(n + 1)]
+    return sum(2 * 2 * cap[j] * cap[j + 1] for j in range(n)) + sum(4 * c * c for c in cap)
+
+
+@pytest.mark.parametrize("n,chi,slots,limit_gb", [(40, 256, 512, 80), (64, 1024, 64, 230),
+                                                    (32, 512, 128, 140)])
+def test_arena_fits_the_large_bond_workloads(lib, n, chi, slots, limit_gb):
+    # bond-sized sites and a single environment cache: the large-bond workloads fit the
+    # B300's HBM (n = 64, chi_max = 1024, 64 slots needed 432 GB with fixed-stride sites)
+    from paper_2609_26516_b300 import _native as N
+    nb = lib.dcs_arena_bytes(ctypes.byref(_cfg(N, n_qubits=n, chi_max=chi, n_slots=slots)))
+    assert slots * _slot_elems(n, chi) * 8 < nb < limit_gb * 1e9
+
+
 def test_arena_bytes_and_argument_checks(lib):
     from paper_2609_26516_b300 import _native as N
     cfg = _cfg(N)
     nb = lib.dcs_arena_bytes(ctypes.byref(cfg))
-    # two MPS buffers + two environment caches dominate: 10^4 slots x (2*64*128 + 2*65*256) x 8 B
-    assert nb > 10000 * (2 * 64 * 128 + 2 * 65 * 256) * 8
-    assert nb < 2 * 10000 * (2 * 64 * 128 + 2 * 65 * 256) * 8
+    # two MPS buffers + one environment cache dominate, sized by the bond capacities
+    # cap_b = min(C, 2^min(b, n - b)) (C = 8 here): site j holds cap_j 2 cap_{j+1} complex64,
+    # bond b's environment cap_b 4 cap_b
+    assert nb > 10000 * _slot_elems(64, 8) * 8
+    assert nb < 1.25 * 10000 * _slot_elems(64, 8) * 8
     assert lib.dcs_arena_bytes(ctypes.byref(_cfg(N, n_qubits=0))) == 0
     assert lib.dcs_arena_bytes(ctypes.byref(_cfg(N, chi_max=2048))) == 0
     assert lib.dcs_arena_bytes(ctypes.byref(_cfg(N, chi_max=64, kernel_path=1))) == 0
@@ -171,15 +188,6 @@ def test_bits_of_matches_plain_unpacking():
         np.testing.assert_array_equal(got, want)
 
 
-def test_phase_report_command_line():
-    import subprocess
-    import sys
-    out = subprocess.run([sys.executable, "-m", "paper_2609_26516_b300.phases", "--help"],
-                         capture_output=True, text=True, timeout=120,
-                         cwd=os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
-    assert out.returncode == 0 and "ghz64" in out.stdout and "brick" in out.stdout
-
-
 def test_noalloc_argument_checks_need_no_device(lib):
     # sizes beyond the fixed scratch and invalid arguments are refused before any CUDA call
     from paper_2609_26516_b300 import _native as N
@@ -196,3 +204,8 @@ def test_noalloc_argument_checks_need_no_device(lib):
     assert call(sweeps=0) == N.ERR_INVALID
     assert call(centre=8) == N.ERR_INVALID
     assert call(n_gates=1) == N.ERR_INVALID  # record of kind 0: not a gate
+    g = (N.dcs_op * 1)()
+    g[0].kind, g[0].q0, g[0].q1 = N.OP_GATE1, 0, -1
+    g[0].m[0] = g[0].m[6] = 1.0
+    g[0].cond.op = 7  # neither NONE, XOR nor AND
+    assert call(n_gates=1, gates=g) == N.ERR_INVALID

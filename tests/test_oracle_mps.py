@@ -306,3 +306,89 @@ def test_teleport_chi2_paper_setting():
         psi = M.to_dense(b.mps)
         bob = psi[b.path[0], b.path[1], :]
         assert abs(abs(np.vdot(bob, inp)) ** 2 - 1.0) < 1e-12
+
+
+# ----------------------------------------------------------------------------- truncated guess
+# Pins of the initial guess in the truncated regime (reading 1 of the oracle's compression
+# step: blocks applied in canonical form, each followed by a truncated SVD).  In canonical
+# form with the centre on the block, the SVD of the two-site tensor is the Schmidt
+# decomposition of the whole state at the block's middle bond, so each truncation must equal
+# the Eckart-Young best rank-k approximation of the dense state at that cut, renormalised,
+# and its kept weight fraction is sum_{i<k} s_i^2 / sum_i s_i^2 of the dense singular values.
+
+
+def _dense_gate2(psi, q, G):
+    """(G on qubits q, q+1) psi for psi of shape (2,)*n, G over |s_q s_{q+1}>."""
+    out = np.tensordot(G.reshape(2, 2, 2, 2), psi, axes=([2, 3], [q, q + 1]))
+    return np.moveaxis(out, [0, 1], [q, q + 1])
+
+
+def _eckart_young(psi, cut, k):
+    """Best rank-k approximation of psi across (first `cut` qubits | rest), normalised, and
+    the kept weight fraction."""
+    Mx = psi.reshape(2 ** cut, -1)
+    U, s, Vh = np.linalg.svd(Mx, full_matrices=False)
+    assert s[k - 1] > s[k] * (1 + 1e-6), "degenerate cut: the truncation is not unique"
+    Mk = (U[:, :k] * s[:k]) @ Vh[:k]
+    w, tot = float(np.sum(s[:k] ** 2)), float(np.sum(s ** 2))
+    return (Mk / np.sqrt(w)).reshape(psi.shape), w / tot
+
+
+def _assert_canonical(m):
+    for j in range(m.centre):
+        t = m.T[j]
+        g = np.einsum("asb,asc->bc", t.conj(), t)
+        np.testing.assert_allclose(g, np.eye(g.shape[0]), atol=1e-12)
+    for j in range(m.centre + 1, m.n):
+        t = m.T[j]
+        g = np.einsum("asb,csb->ac", t, t.conj())
+        np.testing.assert_allclose(g, np.eye(g.shape[0]), atol=1e-12)
+
+
+@pytest.mark.parametrize("n,q,chi", [(3, 0, 1), (3, 1, 1), (4, 1, 2), (4, 0, 1), (4, 2, 1)])
+@pytest.mark.parametrize("start", ["left", "right"])
+def test_guess_single_truncated_block_is_eckart_young(n, q, chi, start):
+    rng = np.random.default_rng(100 * n + 10 * q + chi)
+    A = random_mps(rng, n, 4)
+    M.move_centre(A, 0 if start == "left" else n - 1)
+    G = C.haar_su4(rng)
+    B, kept, exact = M.initial_guess(A, [(q, G)], chi, 1e-10)
+    want, frac = _eckart_young(_dense_gate2(M.to_dense(A), q, G), q + 1, chi)
+    assert not exact
+    np.testing.assert_allclose(M.to_dense(B), want, atol=1e-12)
+    assert abs(kept[0] - frac) < 1e-12 and frac < 1 - 1e-6
+    assert B.bonds()[q + 1] == chi
+    # ascending (centre left of the block) leaves the centre on q+1, descending on q
+    assert B.centre == (q + 1 if start == "left" else q)
+    _assert_canonical(B)
+    assert abs(np.linalg.norm(M.to_dense(B)) - 1) < 1e-12
+
+
+@pytest.mark.parametrize("start", ["left", "right"])
+def test_guess_two_truncated_blocks_sequential_eckart_young(start):
+    # blocks on (1, 2) and (3, 4) of 6 qubits, both cut to chi = 2: the guess truncates the
+    # block nearest the centre first; each truncation is the dense Eckart-Young projection
+    # of the state the previous one left, and the kept weights are those fractions
+    n, chi = 6, 2
+    rng = np.random.default_rng(61)
+    A = random_mps(rng, n, 8)
+    M.move_centre(A, 0 if start == "left" else n - 1)
+    G1, G3 = C.haar_su4(rng), C.haar_su4(rng)
+    B, kept, exact = M.initial_guess(A, [(1, G1), (3, G3)], chi, 1e-10)
+    psi = _dense_gate2(_dense_gate2(M.to_dense(A), 1, G1), 3, G3)
+    order = [1, 3] if start == "left" else [3, 1]
+    fracs = []
+    for q in order:
+        psi, fr = _eckart_young(psi, q + 1, chi)
+        fracs.append(fr)
+    assert not exact
+    np.testing.assert_allclose(M.to_dense(B), psi, atol=1e-11)
+    np.testing.assert_allclose(kept, fracs, atol=1e-12)
+    assert abs(np.prod(kept) - np.prod(fracs)) < 1e-12 and np.prod(fracs) < 1 - 1e-4
+    assert B.centre == (4 if start == "left" else 1)
+    _assert_canonical(B)
+    # the two orders give different states here, so the test fixes the order
+    other = _dense_gate2(_dense_gate2(M.to_dense(A), 1, G1), 3, G3)
+    for q in order[::-1]:
+        other, _ = _eckart_young(other, q + 1, chi)
+    assert np.linalg.norm(other - psi) > 1e-6

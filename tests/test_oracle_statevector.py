@@ -226,3 +226,20 @@ def test_single_path_sampling_converges():
     chi2 = sum((counts.get(k, 0) - N * 0.25) ** 2 / (N * 0.25) for k in ideal)
     assert chi2 < 16.27
     assert SV.tvd(ideal, emp) < 0.05
+
+
+def test_topk_non_degenerate_values_near_the_tie_scale():
+    # keys round(p / (1e-5 p_max)): values more than a key unit apart are ordered by size
+    # whatever their list order; values inside one unit share a key and keep list order.
+    # 1e-5 is the probability tolerance of the accuracy contract, so two p values the
+    # contract cannot tell apart are never ordered by their rounding.
+    pmax = 0.2
+    ps = [pmax * (1 - 6e-5), pmax, pmax * (1 - 3e-5), 0.1]
+    assert SV.topk_select(ps, 1) == [1]
+    assert SV.topk_select(ps, 2) == [1, 2]
+    assert SV.topk_select(ps, 3) == [0, 1, 2]
+    assert SV.topk_select([pmax * (1 - 3e-5), pmax * (1 - 6e-5), pmax], 2) == [0, 2]
+    base = pmax * (1 - 10e-5)  # key 99990, a whole unit below its neighbours
+    assert SV.topk_select([base, base * (1 + 2e-7), pmax], 2) == [0, 2]
+    assert SV.topk_select([base * (1 + 2e-7), base, pmax], 2) == [0, 2]
+    assert SV.topk_select([base, base * (1 + 2.5e-5), pmax], 2) == [1, 2]

@@ -128,3 +128,32 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
                                     dummy, None, dummy, None) == N.ERR_OOM
     assert lib.dcs_compress_noalloc(8, 8, 1e-10, 0, arr, 0, None, dummy, dummy, 0, dummy,
                                     dummy, None, dummy, None) == N.ERR_INVALID
+
+
+def test_noalloc_reports_malformed_ket_bonds():
+    # a ket bond above the site capacity (Cc = 8 for chi_max = 8) is caught on the device
+    # before any tensor is indexed: bra_bonds[0] = 0, bra_centre = -1, f = NaN
+    from paper_2609_26516_b300 import _native as N
+    from paper_2609_26516_b300.sim import encode_ops
+
+    n, chi, Cc = 6, 8, 8
+    stride = 2 * Cc * Cc
+    lib = N.load()
+    gates = [C.Gate((1, 2), C.haar_su4(np.random.default_rng(2)))]
+    arr = encode_ops(gates)
+    ket = torch.zeros(n * stride, dtype=torch.complex64, device="cuda")
+    bra = torch.zeros_like(ket)
+    for bad in ([1, 2, 4, Cc + 1, 4, 2, 1], [2, 2, 4, 4, 4, 2, 1], [1, 2, 0, 4, 4, 2, 1]):
+        ket_bonds = torch.tensor(bad, dtype=torch.int32, device="cuda")
+        bra_bonds = torch.full((n + 1,), 5, dtype=torch.int32, device="cuda")
+        bra_centre = torch.zeros(1, dtype=torch.int32, device="cuda")
+        f = torch.zeros(1, dtype=torch.float64, device="cuda")
+        st = lib.dcs_compress_noalloc(
+            n, chi, 1e-10, 2, arr, len(gates), None, ctypes.c_void_p(ket.data_ptr()),
+            ctypes.c_void_p(ket_bonds.data_ptr()), 0, ctypes.c_void_p(bra.data_ptr()),
+            ctypes.c_void_p(bra_bonds.data_ptr()), ctypes.c_void_p(bra_centre.data_ptr()),
+            ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        assert st == N.OK
+        torch.cuda.synchronize()
+        assert int(bra_bonds[0].item()) == 0 and int(bra_centre.item()) == -1
+        assert np.isnan(f.item())
