@@ -1,16 +1,27 @@
 """Benchmark of the dynamic-circuit MPS simulator on one B300 (or N, weak scaling).
 
-Workload (default): dynamic GHZ preparation on n = 64 qubits (32 data on even sites, 32
-ancillas on odd sites), chi_max = 8, 2 one-site sweeps per compression step, truncation
-tolerance 1e-10, single-path, 10,000 shots per GPU in one batch.  One step is one pass of
-the whole hot path over the batch: InitializeState, then the circuit (4 compression steps,
-64 mid-circuit measurements with sampling, collapse and register writes, conditional X
-layers).  Metric: shots/s (whole job); sweeps/s reported beside it.
+Workload: random dynamic brickwork (the stand-in for the paper's random dynamic circuits,
+Sec. "Random dynamic circuits"), n = 40 qubits, depth 40, measurement rate p = 0.1 with an
+outcome-conditioned Haar U(2) on the right neighbour, chi_max = 256, truncation tolerance
+1e-10, s = 2 one-site sweeps per compression step, single-path, 512 shots per GPU in one
+batch, seeded synthetic circuit (generator seed 3, sampler seed 1).
+
+One step is one segment of the circuit over the whole batch: the compression of one chunk
+(the previous layer's conditional gates and one layer of Haar SU(4) gates: initial guess,
+environment cache, two sweeps, on every shot) and that layer's mid-circuit measurements
+(MeasureProb, sampling, collapse, register writes).  Segments 0-13, in which the bonds grow
+to chi_max, prepare the state untimed; the warm-up and timed steps are the segments that
+follow, in circuit order (when the circuit runs out it is restarted, untimed).
+
+Metric: one-site compression sweeps per second over all shots (the line's value, mixed
+precision: TF32x3 tensor-core contractions with an FP32 last sweep), the plain FP32 path
+timed on the same segments beside it, shots/s, and the error of each against the FP64 oracle
+on one sampled compression step.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl dcs|reference]
 
-The reference arm (--impl reference) is the CPU FP64 oracle run on a bounded sample of the
-same workload on the host cores.  Under torchrun only rank 0 runs it.
+The reference arm (--impl reference) is the CPU FP64 oracle on the same workload, one
+segment of one shot per step, on the host cores.  Under torchrun only rank 0 runs it.
 """
 from __future__ import annotations
 
@@ -29,20 +40,24 @@ if ROOT not in sys.path:
 
 import numpy as np  # noqa: E402
 
-N_QUBITS = 64
-CHI_MAX = 8
-SWEEPS = 2
+N_QUBITS = 40
+DEPTH = 40
+P_MEAS = 0.1
+CHI_MAX = 256
 TOL = 1e-10
-SHOTS = 10000
+SWEEPS = 2
+SHOTS = 512
+CIRCUIT_SEED = 3
 SEED = 1
-WORKLOAD = "dynamic GHZ n=64 (32 data + 32 ancilla), chi_max=8, s=2, tol=1e-10, single-path, 10000 shots/GPU"
-METRIC = "shots/s (single-path dynamic GHZ n=64, chi_max=8)"
-
-
-# DRAM bytes (read + write) per shot of the H + CNOT compression launch, from the ncu
-# capture summarised in profiles/k_compress_ghz64_hcnot.md (2,000 shots: 31.86 MB read,
-# 1.89 MB written).  Valid for the kernel build that capture measured.
-HCNOT_TRAFFIC_PER_SHOT = (31.862784e6 + 1.885952e6) / 2000
+PREFIX = 14          # segments that grow the bonds to chi_max (untimed preparation)
+SAMPLE_SEGMENT = 16  # the compression step compared with the oracle
+PREC_FP32, PREC_TF32X3 = 0, 1
+WORKLOAD = (f"random dynamic brickwork n={N_QUBITS}, depth {DEPTH}, p={P_MEAS}, "
+            f"chi_max={CHI_MAX}, tol={TOL:g}, s={SWEEPS}, single-path, {SHOTS} shots/GPU "
+            "batched; step = one circuit segment (one compression + its measurements)")
+METRIC = ("compression sweeps/s & shots/s, batched mixed vs plain FP32, at fidelity>=1-1e-6 "
+          "(random dynamic brickwork n=40, chi_max=256)")
+TF32_PER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor rate
 
 
 def shard_shot0(rank: int, shots_per_rank: int) -> int:
@@ -52,14 +67,14 @@ def shard_shot0(rank: int, shots_per_rank: int) -> int:
     return rank * shots_per_rank
 
 
-def job_rate(t_step: float, world: int, shots_per_rank: int, dist=None, device="cpu"):
-    """Step time as the maximum over ranks, and the whole job's shots/s at that time."""
+def job_rate(t_step: float, world: int, units_per_rank: float, dist=None, device="cpu"):
+    """Step time as the maximum over ranks, and the whole job's units/s at that time."""
     if dist is not None:
         import torch
         t = torch.tensor([t_step], dtype=torch.float64, device=device)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         t_step = float(t.item())
-    return t_step, world * shots_per_rank / t_step
+    return t_step, world * units_per_rank / t_step
 
 
 def measured_peaks():
@@ -67,7 +82,8 @@ def measured_peaks():
     if os.path.exists(p):
         with open(p) as fh:
             return json.load(fh), "measured"
-    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0,
+            "sm_max_mhz": 2032.0}, "fallback"
 
 
 class ClockSampler:
@@ -193,55 +209,230 @@ class ClockSampler:
                 "source": "nvml 5 ms" if self.proc is None else "nvidia-smi 50 ms"}
 
 
-def mps_bytes(bonds) -> int:
-    """complex64 bytes of an MPS with the given bond dimensions."""
-    return sum(8 * 2 * int(bonds[j]) * int(bonds[j + 1]) for j in range(len(bonds) - 1))
+# ----------------------------------------------------------------------------- workload
 
 
-def _limit_blas_threads():
+def workload():
+    """The circuit and its segments (one chunk and the measurements after it, each)."""
+    import circuits as C
+    circ = C.brickwork(N_QUBITS, DEPTH, P_MEAS, CIRCUIT_SEED)
+    return circ, C.split_layers(circ)
+
+
+def split_segment(ops):
+    """(gates, measurements) of a segment: the chunk comes first, the measurements after."""
+    from circuits import Measure, Reset
+    k = next((i for i, o in enumerate(ops) if isinstance(o, (Measure, Reset))), len(ops))
+    return ops[:k], ops[k:]
+
+
+def mpo_bonds(gates, n):
+    """MPO bond dimension per bond of a chunk: 4 across each two-qubit gate (Haar SU(4) has
+    full operator-Schmidt rank), 1 elsewhere."""
+    D = np.ones(n + 1, dtype=np.float64)
+    for g in gates:
+        if len(g.qubits) == 2:
+            D[min(g.qubits) + 1] = 4.0
+    return D
+
+
+def contraction_flops(alpha, beta, D, sweeps):
+    """Algorithmic real flops of one compression step per slot (rows of alpha / beta: ket and
+    bra bond dimensions): each one-site update costs 8 (2 b_l D_l a_l a_r + 4 b_l b_r D_r a_r +
+    4 b_l a_r D_l D_r) (T1 = L A, the MPO mix, F = T2 R and the environment update; a complex
+    multiply-add is 8 flops), each environment of the cache 8 (2 b_l D_l a_l a_r + 2 b_l b_r
+    D_r a_r + 4 b_l a_r D_l D_r); the guess and the QR factorisations are not counted."""
+    a = np.asarray(alpha, dtype=np.float64)
+    b = np.asarray(beta, dtype=np.float64)
+    al, ar, bl, br = a[:, :-1], a[:, 1:], b[:, :-1], b[:, 1:]
+    Dl, Dr = D[:-1][None, :], D[1:][None, :]
+    t1 = 2 * bl * Dl * al * ar
+    mix = 4 * bl * ar * Dl * Dr
+    site = 8 * (t1 + 4 * bl * br * Dr * ar + mix)
+    env = 8 * (t1 + 2 * bl * br * Dr * ar + mix)
+    return sweeps * site.sum(axis=1) + env[:, :-1].sum(axis=1)
+
+
+class SegmentRunner:
+    """A batch of shots driven through the circuit one segment at a time."""
+
+    def __init__(self, sim, segs, shots, shot0):
+        from paper_2609_26516_b300.sim import encode_ops
+        self.sim, self.segs, self.shots, self.shot0 = sim, segs, shots, shot0
+        self.enc = []
+        self.meas0 = []
+        count = 0
+        from circuits import Measure, Reset
+        for ops in segs:
+            g, m = split_segment(ops)
+            self.enc.append((encode_ops(g) if g else None, len(g), encode_ops(m) if m else None,
+                             len(m)))
+            self.meas0.append(count)
+            count += sum(isinstance(o, (Measure, Reset)) for o in ops)
+        self.pos = None
+
+    def restart(self):
+        self.sim.init_state(self.shots, shot0=self.shot0)
+        for k in range(PREFIX):
+            self.run(k)
+        self.pos = PREFIX
+
+    def next_segment(self):
+        """Index of the next segment to run, restarting the circuit (untimed) at its end."""
+        if self.pos is None or self.pos >= len(self.segs):
+            self.restart()
+        k = self.pos
+        self.pos += 1
+        return k
+
+    def run(self, k, mid=None):
+        """Segment k: the chunk's compression, then the measurement run (mid: an event
+        recorded between the two)."""
+        ge, gn, me, mn = self.enc[k]
+        if ge is not None:
+            self.sim.run_encoded(ge, gn, self.meas0[k])
+        if mid is not None:
+            mid.record(self.sim.stream)
+        if me is not None:
+            self.sim.run_encoded(me, mn, self.meas0[k])
+
+
+def time_arm(precision, segs, shots, shot0, warmup, steps, local, flush, clocks=None,
+             barrier=lambda: None):
+    """Device-timed steps of one precision arm: per step the compression launch and the whole
+    segment (CUDA events on the library's stream, L2 flushed between steps), the one-site
+    sweeps run, the algorithmic contraction flops and the library's launches."""
+    import torch
+    from paper_2609_26516_b300 import Simulator
+    circ_cbits = max(1, sum(1 for ops in segs for o in ops if hasattr(o, "cbit")))
+    sim = Simulator(N_QUBITS, CHI_MAX, shots, circ_cbits, tol=TOL, sweeps=SWEEPS, seed=SEED,
+                    precision=precision, device=f"cuda:{local}")
+    run = SegmentRunner(sim, segs, shots, shot0)
+    for _ in range(warmup):
+        run.run(run.next_segment())
+    torch.cuda.synchronize()
+    stream = sim.stream
+    recs = []
+    if clocks is not None:
+        clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    for _ in range(steps):
+        k = run.next_segment()
+        alpha = sim.bonds()
+        c0 = sim.counters()[1]
+        l0 = sim.launches
+        flush.fill_(1)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            run.run(k, mid=e1)
+            e2.record(stream)
+        torch.cuda.synchronize()
+        launches = sim.launches - l0
+        beta = sim.bonds()
+        sw = sim.counters()[1] - c0
+        g, _ = split_segment(segs[k])
+        fl = contraction_flops(alpha, beta, mpo_bonds(g, N_QUBITS), SWEEPS)
+        frac = sw / (SWEEPS * len(fl))  # share of the shots whose step ran its sweeps
+        recs.append({"segment": k, "ms": e0.elapsed_time(e2), "compress_ms": e0.elapsed_time(e1),
+                     "sweeps": int(sw), "flops": float(fl.sum() * frac),
+                     "launches": int(launches)})
+    barrier()
+    clk = clocks.stop() if clocks is not None else None
+    return sim, run, recs, clk
+
+
+def oracle_sample():
+    """The oracle's own shot-0 state before SAMPLE_SEGMENT (the common input of the sampled
+    step) and its compression of that segment's chunk, probabilities of the segment's first
+    measured qubit after it."""
+    import circuits as C
+    from oracle import drivers as D, layers as LY, mps as OM
+    circ, segs = workload()
+    prm = D.Params(chi_max=CHI_MAX, tol=TOL, sweeps=SWEEPS)
+    r = D.SinglePathRun(circ.n_qubits, circ.n_cbits, prm, SEED, 0)
+    for k in range(SAMPLE_SEGMENT):
+        r.run(segs[k])
+    A = r.mps.copy()
+    gates, meas = split_segment(segs[SAMPLE_SEGMENT])
+    blocks, _ = LY.chunk_blocks(N_QUBITS, gates, r.c)
+    B, info = OM.compress(A, blocks, LY.blocks_mpo(N_QUBITS, blocks), CHI_MAX, TOL, SWEEPS)
+    q = meas[0].qubit if meas else 0
+    r0, r1 = OM.measure_probs(B.copy(), q)
+    return {"A": A, "c": r.c.copy(), "gates": gates, "B": B, "f": info.f, "q": q,
+            "p0": r0 / (r0 + r1), "run": r}
+
+
+def _overlap(A, B):
+    E = np.ones((1, 1), dtype=np.complex128)
+    for a, b in zip(A, B):
+        # E'[u, v] = sum_{x, s, y} conj(a[x, s, u]) E[x, y] b[y, s, v], as two products
+        t = np.tensordot(E, np.asarray(b, dtype=np.complex128), axes=(1, 0))
+        E = np.tensordot(np.conj(np.asarray(a, dtype=np.complex128)), t, axes=([0, 1], [0, 1]))
+    return E[0, 0]
+
+
+def sample_error(precision, ref, local):
+    """Error of one precision arm against the FP64 oracle on the sampled step: the oracle's
+    state is imported into a one-shot context (rounded to complex64), both compress the same
+    chunk, and the results are compared: state infidelity 1 - |<psi_gpu|psi_oracle>|^2,
+    |f_gpu - f_oracle| and |p0_gpu - p0_oracle| of the next measured qubit."""
+    import torch
+    from paper_2609_26516_b300 import Simulator
+    ncb = max(1, len(ref["c"]))
+    sim = Simulator(N_QUBITS, CHI_MAX, 1, ncb, tol=TOL, sweeps=SWEEPS, seed=SEED,
+                    precision=precision, device=f"cuda:{local}")
+    sim.init_state(1)
+    sim.import_mps(0, ref["A"].T, ref["A"].centre)
+    # the chunk's conditions read the oracle's register, which the imported context does
+    # not hold: they are evaluated on the host and the chunk handed over holds the gates
+    # that apply, unconditioned
+    from oracle.statevector import cond_holds
+    gates = [type(g)(g.qubits, g.matrix) for g in ref["gates"] if cond_holds(g.cond, ref["c"])]
+    fid = torch.zeros(1, dtype=torch.float64, device=f"cuda:{local}")
+    sim.apply_layer(gates, fid)
+    p0 = sim.measure_prob(ref["q"])
+    torch.cuda.synchronize()
+    _, _, T = sim.export_mps(0)
+    B = ref["B"].T
+    ab = _overlap(T, B)
+    inf = 1.0 - abs(ab) ** 2 / (_overlap(T, T).real * _overlap(B, B).real)
+    out = {"state_infidelity": float(max(inf, 0.0)), "f_abs_err": abs(fid.item() - ref["f"]),
+           "p0_abs_err": abs(float(p0[0].item()) - ref["p0"]), "f_oracle": ref["f"],
+           "step": f"segment {SAMPLE_SEGMENT}, shot 0, oracle's own input state"}
+    out["meets_contract"] = bool(out["state_infidelity"] <= 1e-6 and out["p0_abs_err"] <= 1e-5)
+    del sim
+    torch.cuda.empty_cache()
+    return out
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+
+
+def _blas_threads():
+    """Threads of the BLAS the oracle's NumPy calls (threadpoolctl), else the host cores
+    (OpenBLAS and MKL start one thread per core by default)."""
     try:
-        from threadpoolctl import threadpool_limits
-        return threadpool_limits(1)
+        from threadpoolctl import threadpool_info
+        return max((int(x.get("num_threads", 1)) for x in threadpool_info()), default=1)
     except Exception:  # pragma: no cover
-        return None
+        return host_cores()
 
 
-_ORACLE = {}
-
-
-def _oracle_run(first: int, max_shots: int, seconds: float) -> int:
-    """Shots first, first+1, ... of the workload through the oracle (FP64 NumPy MPS,
-    unchanged) until max_shots or the time bound; returns how many ran."""
-    if "run" not in _ORACLE:
-        import circuits as C
-        from oracle import drivers as D
-        _ORACLE["circ"] = C.ghz_dynamic(N_QUBITS)
-        _ORACLE["prm"] = D.Params(chi_max=CHI_MAX, tol=TOL, sweeps=SWEEPS)
-        _ORACLE["run"] = D.run_single_path
-    t0 = time.perf_counter()
-    done = 0
-    while done < max_shots and (time.perf_counter() - t0) < seconds:
-        _ORACLE["run"](_ORACLE["circ"], _ORACLE["prm"], SEED, first + done)
-        done += 1
-    return done
-
-
-def _oracle_worker_init(ready):
-    try:
-        _ORACLE["blas"] = _limit_blas_threads()
-        _oracle_run(0, 1, 60.0)  # imports and circuit set-up happen before any timed call
-    except Exception as e:  # reported by the first task, so the pool does not respawn
-        _ORACLE["error"] = repr(e)
-    try:
-        ready.wait(timeout=300)
-    except Exception:
-        pass
-
-
-def _oracle_worker(args) -> int:
-    if "error" in _ORACLE:
-        raise RuntimeError("oracle worker set-up failed: " + _ORACLE["error"])
-    return _oracle_run(*args)
+def oracle_steps(run, segs, first, n_steps, seconds=None):
+    """The oracle (FP64 NumPy MPS, unchanged) continuing one shot's run segment by segment:
+    per segment its wall time and the one-site sweeps it ran."""
+    out = []
+    t_all = time.perf_counter()
+    for k in range(first, first + n_steps):
+        if seconds is not None and out and time.perf_counter() - t_all > seconds:
+            break
+        s0 = run.sweeps_run
+        t0 = time.perf_counter()
+        run.run(segs[k % len(segs)])
+        out.append((time.perf_counter() - t0, run.sweeps_run - s0))
+    return out
 
 
 def host_cores() -> int:
@@ -251,205 +442,84 @@ def host_cores() -> int:
         return os.cpu_count() or 1
 
 
-class OraclePool:
-    """The oracle on every host core: one spawned process per core (spawned, not forked,
-    since the parent has a CUDA context), each on its own range of shot indices, BLAS held
-    to one thread per process.  Shots are independent, so this is the oracle as it stands,
-    run side by side."""
-
-    def __init__(self, workers: int):
-        import multiprocessing as mp
-        ctx = mp.get_context("spawn")
-        self.workers = workers
-        ready = ctx.Barrier(workers + 1)
-        self.pool = ctx.Pool(workers, initializer=_oracle_worker_init, initargs=(ready,))
-        try:
-            ready.wait(timeout=300)  # every process has imported and run one untimed shot
-        except Exception:
-            self.pool.terminate()
-            raise RuntimeError("oracle pool did not start")
-        self.next_shot = 0
-
-    def run(self, seconds: float, max_shots_per_worker: int):
-        jobs = []
-        for w in range(self.workers):
-            jobs.append((self.next_shot + w * max_shots_per_worker, max_shots_per_worker, seconds))
-        self.next_shot += self.workers * max_shots_per_worker
-        t0 = time.perf_counter()
-        done = self.pool.map(_oracle_worker, jobs, chunksize=1)
-        return sum(done), time.perf_counter() - t0
-
-    def close(self):
-        self.pool.close()
-        self.pool.join()
-
-
-def cpu_oracle_sample(seconds: float = 15.0, max_shots: int = 5000):
-    """The oracle (FP64 NumPy MPS, unchanged) on one core, on a bounded sample of the
-    workload: shots 0, 1, ... until max_shots or the time bound."""
-    lim = _limit_blas_threads()
-    _oracle_run(0, 1, 60.0)  # set-up outside the timed sample
-    t0 = time.perf_counter()
-    shots = _oracle_run(0, max_shots, seconds)
-    dt = time.perf_counter() - t0
-    del lim
-    return shots, dt
-
-
 def run_reference(args):
+    """The oracle on the same workload: shot 0 prepared through the first segments (untimed),
+    then one segment per step, BLAS on the host cores."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    cores = host_cores()
-    pool = OraclePool(cores)
-    shots_per_step = []
-    times = []
-    try:
-        for i in range(args.warmup + args.steps):
-            n, dt = pool.run(seconds=2.0, max_shots_per_worker=40)
-            if i >= args.warmup:
-                shots_per_step.append(n)
-                times.append(dt)
-    finally:
-        pool.close()
-    total_shots, total_t = sum(shots_per_step), sum(times)
-    value = total_shots / total_t
+    from oracle import drivers as D
+    circ, segs = workload()
+    prm = D.Params(chi_max=CHI_MAX, tol=TOL, sweeps=SWEEPS)
+    run = D.SinglePathRun(circ.n_qubits, circ.n_cbits, prm, SEED, 0)
+    for k in range(PREFIX):
+        run.run(segs[k])
+    warm = oracle_steps(run, segs, PREFIX, args.warmup)
+    del warm
+    rec = oracle_steps(run, segs, PREFIX + args.warmup, args.steps)
+    t = sum(x[0] for x in rec)
+    sw = sum(x[1] for x in rec)
+    value = sw / t
+    cores = _blas_threads()
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": "shots/s",
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "sweeps/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1000 * total_t / args.steps, "higher_is_better": True,
+        "ms_per_step": 1000 * t / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": "oracle on distinct shots of the same "
-                   f"circuit, {cores} processes, at most 2 s or 40 shots each per step"},
-        "cpu_baseline": {"value": value, "unit": "shots/s", "cores": cores, "kind": "oracle",
-                         "sample": f"{total_shots} shots over {args.steps} steps"},
-        "e2e": {"value": value, "unit": "shots/s", "h2d_bytes_per_step": 0,
+        "config": {"workload": WORKLOAD, "sample": "the oracle on shot 0, one segment per step "
+                   f"(segments {PREFIX + args.warmup}..{PREFIX + args.warmup + args.steps - 1}, "
+                   f"after {PREFIX} untimed segments and {args.warmup} warm-up segments)"},
+        "shots_per_s": value / (SWEEPS * DEPTH),
+        "cpu_baseline": {"value": value, "unit": "sweeps/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{sw} one-site sweeps over {args.steps} segments of shot 0, "
+                                   f"FP64 NumPy, BLAS on {cores} threads"},
+        "e2e": {"value": value, "unit": "sweeps/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-def measure_brick(n, depth, p, chi, shots, sweeps, precision):
-    """Random dynamic brickwork at a bounded depth and shot count: the time of each gate run
-    (compression launches) and of the measurement runs, shots/s and one-site sweeps/s."""
+# ----------------------------------------------------------------------------- extras
+
+
+def measure_ghz(shots=10000, steps=10):
+    """Dynamic GHZ preparation, n = 64 (32 data + 32 ancilla qubits), chi_max = 8, 10^4 shots
+    per batch: shots/s (the small-bond kernels)."""
     import torch
     import circuits as C
     from paper_2609_26516_b300 import Simulator
-    circ = C.brickwork(n, depth, p, 3)
-    sim = Simulator(n, chi, shots, circ.n_cbits, tol=TOL, sweeps=sweeps, seed=SEED,
-                    precision=precision)
-    runs, run = [], []
-    for o in circ.ops:  # gate runs between measurement groups (each run is one chunk)
-        if isinstance(o, C.Measure):
-            if run:
-                runs.append(run)
-                run = []
-            if runs and isinstance(runs[-1][0], C.Measure):
-                runs[-1].append(o)
-            else:
-                runs.append([o])
-        else:
-            run.append(o)
-    if run:
-        runs.append(run)
-    sim.init_state(shots)
-    layer_ms, meas_ms = [], []
-    n_meas = 0
-    for grp in runs:
-        a = torch.cuda.Event(enable_timing=True)
-        e = torch.cuda.Event(enable_timing=True)
-        a.record(sim.stream)
-        sim.run_circuit(grp, meas_idx0=n_meas)
-        e.record(sim.stream)
-        n_meas += sum(isinstance(o, C.Measure) for o in grp)
-        torch.cuda.synchronize()
-        (meas_ms if isinstance(grp[0], C.Measure) else layer_ms).append(a.elapsed_time(e))
-    n_comp, n_sweeps = sim.counters()
-    total_s = (sum(layer_ms) + sum(meas_ms)) / 1000.0
-    bonds, _, _ = sim.export_mps(0)
-    out = {
-        "workload": f"brickwork n={n} depth={depth} p={p} chi_max={chi} s={sweeps} shots={shots} "
-                    f"precision={'tf32x3' if precision else 'fp32'}",
-        "shots_per_s": shots / total_s, "sweeps_per_s": n_sweeps / total_s,
-        "compression_steps": n_comp, "sweeps": n_sweeps,
-        "layer_ms": [round(x, 2) for x in layer_ms], "measure_ms_total": round(sum(meas_ms), 2),
-        "max_bond": int(max(bonds)), "F_shot0": float(sim.results()["F"][0])}
+    from paper_2609_26516_b300.sim import encode_ops
+    circ = C.ghz_dynamic(64)
+    ops, n_ops = encode_ops(circ.ops), len(circ.ops)
+    sim = Simulator(64, 8, shots, circ.n_cbits, tol=TOL, sweeps=SWEEPS, seed=SEED)
+
+    def one():
+        sim.init_state(shots)
+        sim.run_encoded(ops, n_ops)
+
+    for _ in range(3):
+        one()
+    a = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    a.record(sim.stream)
+    for _ in range(steps):
+        one()
+    e.record(sim.stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(e) / steps
+    res = sim.results()
+    out = {"workload": f"dynamic GHZ n=64, chi_max=8, {shots} shots per batch",
+           "shots_per_s": shots / (ms / 1000.0), "ms_per_batch": ms,
+           "max_rel_p_err": float(np.max(np.abs(res["p"] / 2.0 ** -circ.meta["r"] - 1)))}
     del sim
     torch.cuda.empty_cache()
     return out
 
 
-def _events_ms(fn, stream, reps):
-    import torch
-    a = torch.cuda.Event(enable_timing=True)
-    e = torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    for i in range(reps):
-        fn(i)
-    e.record(stream)
-    torch.cuda.synchronize()
-    return a.elapsed_time(e)
-
-
-def measure_ghz_plain(n_shots=200):
-    """The benchmark circuit run one shot at a time (a one-slot context, each shot its own
-    init and circuit call: table upload and one launch per chunk and measurement run), to set
-    beside the batched line."""
-    import circuits as C
-    from paper_2609_26516_b300 import Simulator
-    from paper_2609_26516_b300.sim import encode_ops
-    circ = C.ghz_dynamic(N_QUBITS)
-    ops, n_ops = encode_ops(circ.ops), len(circ.ops)
-    sim = Simulator(N_QUBITS, CHI_MAX, 1, circ.n_cbits, tol=TOL, sweeps=SWEEPS, seed=SEED)
-
-    def one(i):
-        sim.init_state(1, shot0=i)
-        sim.run_encoded(ops, n_ops)
-
-    _events_ms(one, sim.stream, 3)
-    l0 = sim.launches
-    ms = _events_ms(one, sim.stream, n_shots)
-    out = {"workload": f"dynamic GHZ n={N_QUBITS}, chi_max={CHI_MAX}, one shot per call, "
-                       f"{n_shots} shots in a row", "shots_per_s": n_shots / (ms / 1000.0),
-           "ms_per_shot": ms / n_shots, "launches_per_shot": (sim.launches - l0) / n_shots}
-    del sim
-    return out
-
-
-def measure_teleport(shots=1000, steps=20):
-    """Teleportation (3 qubits, chi_max = 4, 1000 shots in one batch): shots/s."""
-    import circuits as C
-    from paper_2609_26516_b300 import Simulator
-    from paper_2609_26516_b300.sim import encode_ops
-    circ = C.teleport(1)
-    ops, n_ops = encode_ops(circ.ops), len(circ.ops)
-    sim = Simulator(circ.n_qubits, 4, shots, circ.n_cbits, tol=TOL, sweeps=SWEEPS, seed=SEED)
-
-    def one(i):
-        sim.init_state(shots)
-        sim.run_encoded(ops, n_ops)
-
-    _events_ms(one, sim.stream, 3)
-    ms = _events_ms(one, sim.stream, steps)
-    res = sim.results()
-    out = {"workload": f"teleportation n=3, chi_max=4, {shots} shots per batch, {steps} "
-                       "batches in a row", "shots_per_s": steps * shots / (ms / 1000.0),
-           "ms_per_batch": ms / steps,
-           "max_abs_p_minus_quarter": float(np.max(np.abs(res["p"] - 0.25)))}
-    del sim
-    return out
-
-
-def run_brick(args):
-    shots = args.shots if args.shots != SHOTS else 148
-    print(json.dumps(measure_brick(args.n, args.depth, args.p, args.chi, shots, args.sweeps,
-                                   args.precision)), flush=True)
-
-
 def measure_cgemm(chi, batch):
     """The contraction primitive alone at the site-contraction shape of chi_max: M = 2 chi,
-    N = chi, K = 4 chi complex (the F = T2 R^T product with an MPO bond of 4), one problem
-    per SM, SIMT vs tensor cores."""
+    N = chi, K = 4 chi complex (F = T2 R^T with an MPO bond of 4), one problem per CTA,
+    CUDA cores vs tensor cores."""
     import ctypes
     import torch
     from paper_2609_26516_b300 import _native as N_
@@ -480,51 +550,33 @@ def measure_cgemm(chi, batch):
                 times.append(a.elapsed_time(e))
         ms = statistics.median(times)
         out[name] = {"ms": ms, "tflops": out["flops_per_call"] / (ms / 1000.0) / 1e12}
-    ref = (A[:2].to(torch.complex128) @ B[:2].to(torch.complex128).transpose(1, 2))
-    out["rel_err_simt_last"] = float((Cm[:2].to(torch.complex128) - ref).norm() / ref.norm())
     del A, B, Cm
     torch.cuda.empty_cache()
     return out
 
 
-def run_cgemm(args):
-    batch = args.shots if args.shots != SHOTS else 148
-    print(json.dumps(measure_cgemm(args.chi, batch)), flush=True)
+# ----------------------------------------------------------------------------- main
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="dcs", choices=["dcs", "reference"])
     ap.add_argument("--shots", type=int, default=SHOTS)
+    ap.add_argument("--fp32-steps", type=int, default=3,
+                    help="timed steps of the plain FP32 arm (the same segments as the first "
+                         "steps of the mixed arm)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extras", action="store_true",
-                    help="skip the contraction and brickwork measurements after the GHZ line")
-    ap.add_argument("--workload", default="ghz64", choices=["ghz64", "brick", "cgemm"],
-                    help="ghz64: the benchmark line; brick / cgemm: extra measurements")
-    ap.add_argument("--n", type=int, default=40)
-    ap.add_argument("--depth", type=int, default=40)
-    ap.add_argument("--p", type=float, default=0.1)
-    ap.add_argument("--chi", type=int, default=256)
-    ap.add_argument("--sweeps", type=int, default=2)
-    ap.add_argument("--precision", type=int, default=0, help="0 FP32, 1 TF32x3 (large chi)")
+    ap.add_argument("--no-extras", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
         return
-    if args.workload == "brick":
-        run_brick(args)
-        return
-    if args.workload == "cgemm":
-        run_cgemm(args)
-        return
     args.warmup = max(args.warmup, 3)
 
     import torch
-    import circuits as C
-    from paper_2609_26516_b300 import Simulator
     from paper_2609_26516_b300.sim import encode_ops
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -540,153 +592,124 @@ def main():
         if dist is not None:
             dist.barrier()
 
-    circ = C.ghz_dynamic(N_QUBITS)
-    ops = encode_ops(circ.ops)
-    n_ops = len(circ.ops)
-    sim = Simulator(N_QUBITS, CHI_MAX, args.shots, circ.n_cbits, tol=TOL, sweeps=SWEEPS,
-                    seed=SEED, device=f"cuda:{local}")
-    stream = sim.stream
+    circ, segs = workload()
     shot0 = shard_shot0(rank, args.shots)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{local}")  # > L2 (126 MB)
 
-    def step():
-        sim.init_state(args.shots, shot0=shot0)
-        sim.run_encoded(ops, n_ops)
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-
-    # ---- device-timed region: K steps, L2 flushed between steps (outside the events)
+    # ---- mixed-precision arm: the line's value
+    t_prep = time.perf_counter()
     clocks = ClockSampler(local)
-    clocks.start()
-    barrier()
-    torch.cuda.synchronize()
-    l0 = sim.launches
-    durs = []
-    with torch.cuda.stream(stream):
-        for _ in range(args.steps):
-            flush.fill_(1)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            step()
-            e1.record(stream)
-            durs.append((e0, e1))
-    torch.cuda.synchronize()
-    barrier()
-    launches = sim.launches - l0
-    ms = [a.elapsed_time(b) for a, b in durs]
-    clk = clocks.stop()
-    t_step, value = job_rate(sum(ms) / len(ms) / 1000.0, world, args.shots, dist,
-                             f"cuda:{local}")
-    res = sim.results()
-    n_comp, n_sweeps = sim.counters()  # of the last step (counters restart at init_state)
-    sweeps_s = world * n_sweeps / t_step
-    comp_s = world * n_comp / t_step
-
-    # ---- dominant kernel: the compression launch of the first chunk (H + CNOT layer),
-    # timed alone on the library's stream, L2 flushed before it
-    layer_ops = circ.ops[: N_QUBITS // 2 + (N_QUBITS // 2 - 1)]
-    gl = encode_ops(layer_ops)
-    k_ms = []
-    for i in range(6):
-        sim.init_state(args.shots, shot0=shot0)
-        flush.fill_(1)
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        sim.lib.dcs_apply_layer(sim.ctx, gl, len(layer_ops), None)
-        b.record(stream)
-        torch.cuda.synchronize()
-        if i >= 2:
-            k_ms.append(a.elapsed_time(b))
-    comp_ms = statistics.median(k_ms)
-    # algorithmic bytes of that launch per shot: read the ket (|0...0>, bonds 1) and write the
-    # bra (bonds 2 across each H+CNOT pair); the guess is exact, so no environment traffic
-    n = N_QUBITS
-    ket = [1] * (n + 1)
-    bra = [1] + [2 if (b_ % 2 == 1) else 1 for b_ in range(1, n)] + [1]
-    bytes_launch = args.shots * (mps_bytes(ket) + mps_bytes(bra))
-    achieved = bytes_launch / (comp_ms / 1000.0) / 1e9
+    sim, run, recs, clk = time_arm(PREC_TF32X3, segs, args.shots, shot0, args.warmup,
+                                   args.steps, local, flush, clocks, barrier)
+    ms = [r["ms"] for r in recs]
+    t_step, value = job_rate(sum(ms) / len(ms) / 1000.0, world,
+                             sum(r["sweeps"] for r in recs) / len(recs), dist, f"cuda:{local}")
+    launches = sum(r["launches"] for r in recs)
+    comp_ms = sum(r["compress_ms"] for r in recs) / len(recs)
+    flops = sum(r["flops"] for r in recs) / len(recs)
+    achieved = flops / (comp_ms / 1000.0) / 1e12
     peaks, peak_kind = measured_peaks()
+    peak_tf32 = float(peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])) * TF32_PER_BF16
 
-    # ---- end to end through the C ABI with host buffers (tables up, results down)
-    e2e_t = []
+    # ---- end to end through the C ABI: each step encodes the segment on the host, uploads
+    # its tables from the pinned stage and reads the results back
+    e2e_t, e2e_sw = [], []
     up0 = sim.bytes_uploaded
-    for _ in range(3):
+    n_e2e = min(args.steps, 3)
+    for _ in range(n_e2e):
+        k = run.next_segment()
+        c0 = sim.counters()[1]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        sim.init_state(args.shots, shot0=shot0)
-        arr = encode_ops(circ.ops)
-        sim.run_encoded(arr, n_ops)
-        sim.results()
+        g, m = split_segment(segs[k])
+        if g:
+            sim.run_encoded(encode_ops(g), len(g), run.meas0[k])
+        if m:
+            sim.run_encoded(encode_ops(m), len(m), run.meas0[k])
+        res = sim.results()
         e2e_t.append(time.perf_counter() - t0)
-    h2d = (sim.bytes_uploaded - up0) // 3
+        e2e_sw.append(sim.counters()[1] - c0)
+    h2d = (sim.bytes_uploaded - up0) // n_e2e
     d2h = 8 + args.shots * (4 + 8 + 8 + 8 * 8 + 4)
-    e2e_value = world * args.shots / statistics.median(e2e_t)
+    _, e2e_value = job_rate(sum(e2e_t) / n_e2e, world, sum(e2e_sw) / n_e2e, dist, f"cuda:{local}")
+    F_mean = float(np.mean(res["F"]))
+    del sim, run
+    torch.cuda.empty_cache()
+
+    # ---- plain FP32 arm on the same segments
+    n32 = min(args.fp32_steps, args.steps)
+    sim32, run32, recs32, _ = time_arm(PREC_FP32, segs, args.shots, shot0, args.warmup, n32,
+                                       local, flush, None, barrier)
+    del sim32, run32
+    torch.cuda.empty_cache()
+    ms32 = [r["ms"] for r in recs32]
+    _, value32 = job_rate(sum(ms32) / len(ms32) / 1000.0, world,
+                          sum(r["sweeps"] for r in recs32) / len(recs32), dist, f"cuda:{local}")
+    same = [r["ms"] for r in recs[: len(recs32)]]
+    speedup = (sum(ms32) / len(ms32)) / (sum(same) / len(same))
+    wall = time.perf_counter() - t_prep
 
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return
-    cpu = cpu1 = None
+
+    # ---- error against the FP64 oracle on one sampled step, each arm; the oracle's timing
+    # on the same workload continues that run (rank 0, one GPU only)
+    err = {}
+    cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        ns, dt = cpu_oracle_sample(seconds=10.0)
-        cpu1 = {"value": ns / dt, "unit": "shots/s", "cores": 1, "kind": "oracle",
-                "sample": f"{ns} shots of the same circuit (shots 0..{ns - 1}), FP64 NumPy, "
-                          f"{dt:.1f} s"}
-        cores = host_cores()
-        pool = OraclePool(cores)
-        try:
-            ns, dt = pool.run(seconds=10.0, max_shots_per_worker=5000)
-        finally:
-            pool.close()
-        cpu = {"value": ns / dt, "unit": "shots/s", "cores": cores, "kind": "oracle",
-               "sample": f"{ns} shots of the same circuit over {cores} processes (one per "
-                         f"host core, distinct shots), FP64 NumPy, {dt:.1f} s wall"}
+        ref = oracle_sample()
+        err = {"tf32x3": sample_error(PREC_TF32X3, ref, local),
+               "fp32": sample_error(PREC_FP32, ref, local)}
+        cores = _blas_threads()
+        rec = oracle_steps(ref["run"], segs, SAMPLE_SEGMENT, 4, seconds=20.0)
+        t_o = sum(x[0] for x in rec)
+        sw_o = sum(x[1] for x in rec)
+        cpu = {"value": sw_o / t_o, "unit": "sweeps/s", "cores": cores, "kind": "oracle",
+               "sample": f"shot 0, segments {SAMPLE_SEGMENT}..{SAMPLE_SEGMENT + len(rec) - 1} "
+                         f"({sw_o} one-site sweeps, {t_o:.1f} s), FP64 NumPy, BLAS on {cores} "
+                         "threads"}
+    mean_sweeps = sum(r["sweeps"] for r in recs) / len(recs)
     line = {
-        "metric": METRIC, "value": value, "unit": "shots/s", "n_gpus": world,
+        "metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1000.0,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "tf32x3",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "shots_per_gpu": args.shots,
+                   "segments_timed": [r["segment"] for r in recs],
+                   "precision": "TF32x3 tensor-core contractions, FP32 last sweep",
                    "l2": "flushed between timed steps (256 MB write outside the events)",
                    "parallelism": f"shots sharded over {world} GPU(s), no collective"},
-        "sweeps_per_s": sweeps_s,
-        "sweeps_note": ("every compression step of this circuit is exact at chi_max = 8 (no "
-                        "block truncates beyond tol), so its sweeps are skipped (f = 1); the "
-                        "brickwork extra below runs them") if n_sweeps == 0 else None,
-        "compression_steps_per_s": comp_s,
-        "roofline": {"bound": "hbm", "kernel": "k_compress<32> (H+CNOT chunk, all shots)",
-                     "achieved": achieved, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
-                     "frac": achieved / float(peaks["hbm_gbs"]),
-                     "traffic": HCNOT_TRAFFIC_PER_SHOT * args.shots,
-                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, "
-                                       "2,000-shot capture scaled by shots",
-                     "peak_source": f"hbm_gbs of MEASURED_PEAKS.json ({peak_kind})",
-                     "note": "issue/latency-bound: a dependent chain of bond-2 operations "
-                             "per shot (neither roof binds; see profiles/)",
-                     "launch_ms": comp_ms},
+        "shots_per_s": value / (SWEEPS * DEPTH),
+        "shots_per_s_note": "sweeps/s over the 2 sweeps x 40 layers of a shot: the rate of a "
+                            "whole circuit if every layer cost a saturated one",
+        "sweeps_per_step": mean_sweeps,
+        "fp32": {"value": value32, "unit": "sweeps/s", "steps": len(recs32),
+                 "ms_per_step": sum(ms32) / len(ms32),
+                 "segments_timed": [r["segment"] for r in recs32]},
+        "mixed_over_fp32": speedup,
+        "error_vs_oracle": err,
+        "F_mean_after_e2e": F_mean,
+        "roofline": {"bound": "tensor", "kernel": "k_compress_big<512,TC> (one compression, "
+                     "all shots)", "achieved": achieved, "peak": peak_tf32, "unit": "TFLOP/s",
+                     "frac": achieved / peak_tf32, "traffic": None,
+                     "flops_per_launch": flops, "launch_ms": comp_ms,
+                     "peak_source": f"bf16_tflops_sustained of MEASURED_PEAKS.json ({peak_kind}) "
+                                    "x nominal TF32/BF16 ratio 1.1/2.25",
+                     "flops_source": "algorithmic contraction flops from the bond dimensions "
+                                     "before and after each step (guess SVD and QR excluded)"},
         "cpu_baseline": cpu,
-        "cpu_baseline_1core": cpu1,
-        "e2e": {"value": e2e_value, "unit": "shots/s", "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h)},
+        "e2e": {"value": e2e_value, "unit": "sweeps/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h), "steps": n_e2e},
         "gpu_launches": int(launches),
-        "gpu_launches_per_step": int(launches) // args.steps,
+        "gpu_launches_per_step": launches / len(recs),
         "clocks": clk,
+        "bench_wall_s": wall,
     }
     if world == 1 and not args.no_extras:
-        # the other workload shapes, measured after the timed region: the same circuit one
-        # shot per call, teleportation, the contraction primitive at chi = 256 and random
-        # dynamic brickwork whose bonds reach chi_max = 128 (truncation, sweeps), FP32 vs
-        # TF32x3
-        line["ghz_one_shot_per_call"] = measure_ghz_plain(200)
-        line["teleport"] = measure_teleport(1000, 20)
+        line["ghz64"] = measure_ghz()
         line["contraction"] = measure_cgemm(256, 148)
-        line["brickwork"] = {
-            "fp32": measure_brick(20, 12, 0.02, 128, 148, 2, 0),
-            "tf32x3": measure_brick(20, 12, 0.02, 128, 148, 2, 1)}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -52,6 +52,10 @@ class Cond:
 
     ``op == "xor"``: phi = (XOR of the listed bits) == value   (single bit, prefix parity)
     ``op == "and"``: phi = (AND of the listed bits) == value
+    ``op == "or"``: phi = (OR of the listed bits) == value
+    ``op == "table"``: any Boolean function of at most 5 bits, given by its truth table: the
+    listed bits, taken in ascending bit order, form the index i = sum_k c[b_k] 2^k (b_0 the
+    smallest), and phi = bit i of ``value`` (a non-negative integer below 2^32).
     """
 
     bits: Tuple[int, ...]
@@ -248,3 +252,28 @@ def brickwork(n: int, depth: int, p_meas: float, seed: int) -> Circuit:
                 ops.append(Gate((q + 1,), u, cond=Cond((bits[q],), "xor", 1), name="cU"))
     return Circuit(n, max(cbit, 1), ops, name=f"brick{n}x{depth}",
                    meta={"depth": depth, "p": p_meas, "seed": seed})
+
+
+def split_layers(circ: Circuit) -> List[List[Op]]:
+    """The circuit cut into segments of one chunk and the measurements that follow it: a cut
+    before the first non-measurement after a measurement, and before a two-qubit gate that
+    touches a qubit already carrying a two-qubit gate of the segment.  For ``brickwork``
+    segment l holds the conditional gates of layer l-1, the two-qubit gates of layer l and
+    the measurements of layer l.  Concatenated, the segments give the circuit back."""
+    out: List[List[Op]] = []
+    cur: List[Op] = []
+    busy: set = set()
+    prev_meas = False
+    for op in circ.ops:
+        meas = isinstance(op, (Measure, Reset))
+        two = isinstance(op, Gate) and len(op.qubits) == 2
+        if cur and ((prev_meas and not meas) or (two and busy & set(op.qubits))):
+            out.append(cur)
+            cur, busy = [], set()
+        cur.append(op)
+        if two:
+            busy |= set(op.qubits)
+        prev_meas = meas
+    if cur:
+        out.append(cur)
+    return out

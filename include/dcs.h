@@ -61,10 +61,21 @@ typedef enum {
 /* largest bond dimension */
 #define DCS_MAX_CHI 1024
 
-typedef enum { DCS_COND_NONE = 0, DCS_COND_XOR = 1, DCS_COND_AND = 2 } dcs_cond_op;
+typedef enum {
+  DCS_COND_NONE = 0,
+  DCS_COND_XOR = 1,
+  DCS_COND_AND = 2,
+  DCS_COND_OR = 3,
+  DCS_COND_TABLE = 4
+} dcs_cond_op;
 
-/* phi(c) of a classically controlled operation: XOR (parity) or AND of the bits set in
- * mask, compared with value (0 or 1).  op == DCS_COND_NONE: always true. */
+/* phi(c) of a classically controlled operation (Sec. "Classically controlled operations":
+ * a Boolean function of the classical register).  XOR (parity), AND or OR of the bits set in
+ * mask, compared with value (0 or 1); DCS_COND_TABLE: any Boolean function of at most 5
+ * bits, given by its truth table -- the bits set in mask, in ascending bit order, form the
+ * index i (the smallest bit is bit 0 of i) and phi = bit i of (uint32_t)value.
+ * op == DCS_COND_NONE: always true.  A TABLE condition with more than 5 bits in mask is
+ * refused with DCS_ERR_INVALID. */
 typedef struct {
   uint64_t mask[DCS_CWORDS];
   int32_t op;
@@ -197,6 +208,12 @@ dcs_status_t dcs_branch_topk(dcs_ctx_t ctx, int M);
  * is written to the buffers then). */
 dcs_status_t dcs_get_results(dcs_ctx_t ctx, double* p, double* fid, uint64_t* cbits,
                              int* n_active, uint8_t* flags);
+
+/* Synchronises and copies the bond dimensions of every active slot, in list order, to the
+ * HOST buffer bonds (n_slots x (n_qubits + 1) int32, row i = slot i of the list: chi_0 ..
+ * chi_n of its current MPS); *n_active receives the number of rows written.  DCS_ERR_CUDA
+ * if a copy fails or the device's slot list lies outside the pool. */
+dcs_status_t dcs_get_bonds(dcs_ctx_t ctx, int32_t* bonds, int* n_active);
 
 /* Checkpoint: synchronises and writes the MPS of active slot `slot` (list position) to a
  * HOST buffer: int32 n, int32 bonds[n+1], int32 centre, then the site tensors

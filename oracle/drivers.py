@@ -45,42 +45,61 @@ class ShotResult:
     fids: List[float]
 
 
+class SinglePathRun:
+    """One run of Alg. 1 carried across calls: ``run(ops)`` continues it with the next ops.
+    Calls that each end where a chunk closes (at a measurement, or at the end of the circuit)
+    make the same chunks, draws and compressions as one pass over the concatenated ops."""
+
+    def __init__(self, n: int, n_cbits: int, prm: Params, seed: int, shot: int):
+        self.n, self.n_cbits, self.prm, self.seed, self.shot = n, n_cbits, prm, seed, shot
+        self.mps = product_zero(n)
+        self.c = np.zeros(n_cbits, dtype=np.int64)
+        self.p, self.F = 1.0, 1.0
+        self.outcomes, self.p0s, self.flagged, self.fids = [], [], [], []
+        self.ordinal = 0
+        self.sweeps_run = 0
+
+    def run(self, ops, stop_after_flag: bool = False) -> None:
+        n, steps = chunk_circuit(Circuit(self.n, self.n_cbits, list(ops)), self.prm.k)
+        for st in steps:
+            if isinstance(st, Measure):
+                r0, r1 = measure_probs(self.mps, st.qubit)
+                p0 = r0 / (r0 + r1)
+                u = uniform(self.seed, self.shot, self.ordinal)
+                m = 0 if u < p0 else 1
+                if abs(u - p0) < FLAG_WINDOW:
+                    self.flagged.append(self.ordinal)
+                pm = p0 if m == 0 else 1.0 - p0
+                if pm <= P_EPS:
+                    raise FloatingPointError("collapse onto an outcome of zero probability")
+                collapse(self.mps, st.qubit, m, r0 if m == 0 else r1)
+                self.p *= pm
+                self.c[st.cbit] = m
+                self.outcomes.append(m)
+                self.p0s.append(p0)
+                self.ordinal += 1
+                if self.flagged and stop_after_flag:
+                    return
+            else:
+                blocks, empty = chunk_blocks(n, st, self.c)
+                if empty:
+                    continue
+                self.mps, info = compress(self.mps, blocks, blocks_mpo(n, blocks),
+                                          self.prm.chi_max, self.prm.tol, self.prm.sweeps)
+                self.F *= info.f
+                self.fids.append(info.f)
+                self.sweeps_run += len(info.fidelities_per_sweep)
+
+    def result(self) -> ShotResult:
+        return ShotResult(self.p, self.F, self.c, self.mps, self.outcomes, self.p0s,
+                          self.flagged, self.fids)
+
+
 def run_single_path(circ: Circuit, prm: Params, seed: int, shot: int,
                     stop_after_flag: bool = False) -> ShotResult:
-    n, steps = chunk_circuit(circ, prm.k)
-    mps = product_zero(n)
-    c = np.zeros(circ.n_cbits, dtype=np.int64)
-    p, F = 1.0, 1.0
-    outcomes, p0s, flagged, fids = [], [], [], []
-    ordinal = 0
-    for st in steps:
-        if isinstance(st, Measure):
-            r0, r1 = measure_probs(mps, st.qubit)
-            p0 = r0 / (r0 + r1)
-            u = uniform(seed, shot, ordinal)
-            m = 0 if u < p0 else 1
-            if abs(u - p0) < FLAG_WINDOW:
-                flagged.append(ordinal)
-            pm = p0 if m == 0 else 1.0 - p0
-            if pm <= P_EPS:
-                raise FloatingPointError("collapse onto an outcome of zero probability")
-            collapse(mps, st.qubit, m, r0 if m == 0 else r1)
-            p *= pm
-            c[st.cbit] = m
-            outcomes.append(m)
-            p0s.append(p0)
-            ordinal += 1
-            if flagged and stop_after_flag:
-                break
-        else:
-            blocks, empty = chunk_blocks(n, st, c)
-            if empty:
-                continue
-            mps, info = compress(mps, blocks, blocks_mpo(n, blocks), prm.chi_max, prm.tol,
-                                 prm.sweeps)
-            F *= info.f
-            fids.append(info.f)
-    return ShotResult(p, F, c, mps, outcomes, p0s, flagged, fids)
+    r = SinglePathRun(circ.n_qubits, circ.n_cbits, prm, seed, shot)
+    r.run(circ.ops, stop_after_flag)
+    return r.result()
 
 
 @dataclass

@@ -79,7 +79,9 @@ def project(psi: np.ndarray, q: int, m: int, p_m: float) -> np.ndarray:
 
 def cond_holds(cond: Optional[Cond], c: np.ndarray) -> bool:
     """phi(c) of a classically controlled operation (Sec. "Classically controlled
-    operations"): XOR or AND of the listed bits compared with ``value``."""
+    operations": phi is a Boolean function of the register): XOR, AND or OR of the listed
+    bits compared with ``value``, or a truth table (``op == "table"``: bit i of ``value``,
+    i the listed bits read in ascending order as a binary number, smallest bit first)."""
     if cond is None:
         return True
     vals = [int(c[b]) for b in cond.bits]
@@ -89,6 +91,13 @@ def cond_holds(cond: Optional[Cond], c: np.ndarray) -> bool:
             v ^= x
     elif cond.op == "and":
         v = int(all(vals))
+    elif cond.op == "or":
+        v = int(any(vals))
+    elif cond.op == "table":
+        idx = 0
+        for k, b in enumerate(sorted(cond.bits)):
+            idx += int(c[b]) << k
+        return (int(cond.value) >> idx) & 1 == 1
     else:
         raise ValueError(cond.op)
     return v == int(cond.value)

@@ -18,7 +18,7 @@ PREC_FP32, PREC_TF32X3 = 0, 1
 OK, ERR_INVALID, ERR_OOM, ERR_ZERO_PROB, ERR_NUMERICAL, ERR_TIMEOUT, ERR_CUDA, ERR_UNSUPPORTED = range(8)
 STATUS_NAMES = ["OK", "INVALID", "OOM", "ZERO_PROB", "NUMERICAL", "TIMEOUT", "CUDA", "UNSUPPORTED"]
 
-COND_NONE, COND_XOR, COND_AND = 0, 1, 2
+COND_NONE, COND_XOR, COND_AND, COND_OR, COND_TABLE = 0, 1, 2, 3, 4
 OP_GATE1, OP_GATE2, OP_MEASURE, OP_RESET = 1, 2, 3, 4
 
 FLAG_DRAW_NEAR_THRESHOLD = 1
@@ -60,6 +60,7 @@ SIGNATURES = {
     "dcs_branch_split": (_c.c_int, [_P, _c.c_int, _c.c_int, _c.c_double]),
     "dcs_branch_topk": (_c.c_int, [_P, _c.c_int]),
     "dcs_get_results": (_c.c_int, [_P, _P, _P, _P, _c.POINTER(_c.c_int), _P]),
+    "dcs_get_bonds": (_c.c_int, [_P, _P, _c.POINTER(_c.c_int)]),
     "dcs_export_mps": (_c.c_int, [_P, _c.c_int, _P, _c.POINTER(_c.c_size_t)]),
     "dcs_import_mps": (_c.c_int, [_P, _c.c_int, _P, _c.c_size_t]),
     "dcs_run_circuit": (_c.c_int, [_P, _c.POINTER(dcs_op), _c.c_int, _c.c_uint64, _c.c_int]),

@@ -240,7 +240,7 @@ dcs_status_t check_gate(dcs_ctx_t c, const dcs_op& o) {
   } else {
     return fail(c, DCS_ERR_INVALID, "unknown operation kind");
   }
-  if (o.cond.op != DCS_COND_NONE && o.cond.op != DCS_COND_XOR && o.cond.op != DCS_COND_AND)
+  if (!cond_valid(o.cond))
     return fail(c, DCS_ERR_INVALID, "unknown condition op");
   if ((o.kind == DCS_OP_MEASURE || o.kind == DCS_OP_RESET) && o.cond.op != DCS_COND_NONE)
     return fail(c, DCS_ERR_INVALID, "measurements cannot be classically controlled");
@@ -527,6 +527,30 @@ dcs_status_t dcs_get_results(dcs_ctx_t c, double* p, double* fid, uint64_t* cbit
   if (st != DCS_OK) return st;
   if (status & (1 << DCS_ERR_OOM)) return fail(c, DCS_ERR_OOM, "branch pool exhausted");
   if (status & (1 << DCS_ERR_UNSUPPORTED)) return fail(c, DCS_ERR_UNSUPPORTED, "branch pool above 1024 slots");
+  return DCS_OK;
+}
+
+dcs_status_t dcs_get_bonds(dcs_ctx_t c, int32_t* bonds, int* n_active) {
+  if (!c || !bonds) return fail(c, DCS_ERR_INVALID, "null argument");
+  dcs_status_t st = cuda_check(c, cudaStreamSynchronize(c->stream), "synchronize");
+  if (st != DCS_OK) return st;
+  const size_t S = (size_t)c->cfg.n_slots, n1 = (size_t)c->cfg.n_qubits + 1;
+  std::vector<int> cnt_v(1), order(S), kb(S), all(S * 2 * n1);
+  cudaMemcpy(cnt_v.data(), c->dev.count, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaMemcpy(order.data(), c->dev.order, S * sizeof(int), cudaMemcpyDeviceToHost);
+  cudaMemcpy(kb.data(), c->dev.ketbuf, S * sizeof(int), cudaMemcpyDeviceToHost);
+  cudaMemcpy(all.data(), c->dev.bonds, all.size() * sizeof(int), cudaMemcpyDeviceToHost);
+  if ((st = cuda_check(c, cudaGetLastError(), "bond copy")) != DCS_OK) return st;
+  const int cnt = cnt_v[0];
+  if (cnt < 0 || (size_t)cnt > S) return fail(c, DCS_ERR_CUDA, "active count out of range");
+  for (int i = 0; i < cnt; ++i) {
+    const int slot = order[i];
+    if (slot < 0 || (size_t)slot >= S || (kb[slot] != 0 && kb[slot] != 1))
+      return fail(c, DCS_ERR_CUDA, "slot list out of range");
+    std::memcpy(bonds + (size_t)i * n1, all.data() + ((size_t)slot * 2 + kb[slot]) * n1,
+                n1 * sizeof(int32_t));
+  }
+  if (n_active) *n_active = cnt;
   return DCS_OK;
 }
 

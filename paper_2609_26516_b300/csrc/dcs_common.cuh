@@ -61,6 +61,27 @@ __device__ __forceinline__ bool cond_holds(const DCond& cd, const uint64_t* c) {
     for (int w = 0; w < DCS_CWORDS; ++w) par ^= __popcll(c[w] & cd.mask[w]) & 1;
     return par == cd.value;
   }
+  if (cd.op == DCS_COND_OR) {
+    bool any = false;
+#pragma unroll
+    for (int w = 0; w < DCS_CWORDS; ++w) any = any || ((c[w] & cd.mask[w]) != 0ull);
+    return (int)any == cd.value;
+  }
+  if (cd.op == DCS_COND_TABLE) {
+    // the masked bits in ascending order form the index into the truth table
+    uint32_t idx = 0;
+    int k = 0;
+    for (int w = 0; w < DCS_CWORDS; ++w) {
+      uint64_t m = cd.mask[w];
+      while (m != 0ull && k < 5) {
+        const int b = __ffsll((long long)m) - 1;
+        idx |= (uint32_t)((c[w] >> b) & 1ull) << k;
+        ++k;
+        m &= m - 1ull;
+      }
+    }
+    return (((uint32_t)cd.value >> idx) & 1u) != 0u;
+  }
   bool all = true;
 #pragma unroll
   for (int w = 0; w < DCS_CWORDS; ++w) all = all && ((c[w] & cd.mask[w]) == cd.mask[w]);

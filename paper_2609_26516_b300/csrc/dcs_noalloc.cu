@@ -197,7 +197,7 @@ extern "C" dcs_status_t dcs_compress_noalloc(int32_t n_qubits, int32_t chi_max, 
     const bool two = o.kind == DCS_OP_GATE2;
     if (o.q0 < 0 || o.q0 >= n_qubits || (two && (o.q1 < 0 || o.q1 >= n_qubits)))
       return DCS_ERR_INVALID;
-    if (o.cond.op != DCS_COND_NONE && o.cond.op != DCS_COND_XOR && o.cond.op != DCS_COND_AND)
+    if (!cond_valid(o.cond))
       return DCS_ERR_INVALID;
   }
   const int C = fused_chi(chi_max);

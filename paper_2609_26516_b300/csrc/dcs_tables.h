@@ -69,6 +69,17 @@ inline void svd4(const cd M[16], double sig[4], cd MV[16], cd Vm[16]) {
   }
 }
 
+// A condition the device can evaluate: a known op, and at most 5 bits for a truth table.
+inline bool cond_valid(const dcs_cond& c) {
+  if (c.op == DCS_COND_NONE || c.op == DCS_COND_XOR || c.op == DCS_COND_AND ||
+      c.op == DCS_COND_OR)
+    return true;
+  if (c.op != DCS_COND_TABLE) return false;
+  int bits = 0;
+  for (int w = 0; w < DCS_CWORDS; ++w) bits += __builtin_popcountll(c.mask[w]);
+  return bits <= 5;
+}
+
 inline DCond to_dcond(const dcs_cond& c) {
   DCond d;
   std::memset(&d, 0, sizeof(d));

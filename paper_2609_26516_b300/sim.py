@@ -32,7 +32,7 @@ def _op_dtype() -> np.dtype:
 
 
 _OP_DTYPE = _op_dtype()
-_COND_OPS = {"xor": N.COND_XOR, "and": N.COND_AND}
+_COND_OPS = {"xor": N.COND_XOR, "and": N.COND_AND, "or": N.COND_OR, "table": N.COND_TABLE}
 
 
 def encode_ops(ops: Sequence) -> ctypes.Array:
@@ -84,7 +84,8 @@ def encode_ops(ops: Sequence) -> ctypes.Array:
         rows = [i for i, _ in conds]
         rec["mask"][rows] = words
         rec["cop"][rows] = [_COND_OPS[cd.op] for _, cd in conds]
-        rec["cval"][rows] = [int(cd.value) for _, cd in conds]
+        # a truth table is a 32-bit word stored in the int32 field
+        rec["cval"][rows] = [int(np.uint32(int(cd.value)).view(np.int32)) for _, cd in conds]
     return (N.dcs_op * rec.shape[0]).from_buffer(rec)
 
 
@@ -211,6 +212,14 @@ class Simulator:
         n = cnt.value
         return {"n_active": n, "p": p[:n], "F": F[:n], "cwords": cw[:n], "flags": fl[:n],
                 "bits": bits_of(cw[:n], self.n_cbits)}
+
+    def bonds(self) -> np.ndarray:
+        """[n_active, n_qubits + 1] bond dimensions of the active slots, in list order."""
+        out = np.zeros((self.n_slots, self.n_qubits + 1), dtype=np.int32)
+        cnt = ctypes.c_int(0)
+        self._check(self.lib.dcs_get_bonds(self.ctx, out.ctypes.data_as(ctypes.c_void_p),
+                                           ctypes.byref(cnt)))
+        return out[: cnt.value]
 
     def export_mps(self, pos: int):
         """(bonds, centre, [tensors [chi_l, 2, chi_r] complex64]) of active slot ``pos``."""

@@ -16,11 +16,11 @@ def test_reference_arm_prints_one_json_line():
     lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
     assert len(lines) == 1
     d = json.loads(lines[0])
-    assert d["impl"] == "reference" and d["unit"] == "shots/s" and d["value"] > 0
+    assert d["impl"] == "reference" and d["unit"] == "sweeps/s" and d["value"] > 0
     assert d["higher_is_better"] is True and d["steps"] == 1 and d["warmup"] == 1
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"]
-    assert d["e2e"] == {"value": d["value"], "unit": "shots/s", "h2d_bytes_per_step": 0,
+    assert d["e2e"] == {"value": d["value"], "unit": "sweeps/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
 
 
@@ -59,3 +59,35 @@ def test_two_ranks_time_is_max_and_shots_are_disjoint():
         assert lo == 100 * rank
     ranges = [set(range(lo, lo + 100)) for _, _, _, lo in got]
     assert not (ranges[0] & ranges[1]) and (ranges[0] | ranges[1]) == set(range(200))
+
+
+def test_contraction_flops_count():
+    # every bond chi, MPO bonds 4 on odd bonds: per site 8 (2 chi^3 D_l + 4 chi^3 D_r +
+    # 4 chi^2 D_l D_r) per sweep, the environment cache 8 (2 chi^3 D_l + 2 chi^3 D_r + 4 chi^2
+    # D_l D_r) per site but the last
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import bench
+    n, chi = 6, 16
+    a = np.full((2, n + 1), chi)
+    a[:, 0] = a[:, n] = 1
+    D = np.array([1.0 if b % 2 == 0 else 4.0 for b in range(n + 1)])
+    got = bench.contraction_flops(a, a, D, 2)
+    want = 0.0
+    for j in range(n):
+        bl, br, Dl, Dr = a[0, j], a[0, j + 1], D[j], D[j + 1]
+        site = 8 * (2 * bl * Dl * bl * br + 4 * bl * br * Dr * br + 4 * bl * br * Dl * Dr)
+        env = 8 * (2 * bl * Dl * bl * br + 2 * bl * br * Dr * br + 4 * bl * br * Dl * Dr)
+        want += 2 * site + (env if j < n - 1 else 0)
+    assert np.allclose(got, want)
+
+
+def test_workload_segments_are_chunk_then_measurements():
+    sys.path.insert(0, ROOT)
+    import circuits as C
+    import bench
+    circ, segs = bench.workload()
+    assert sum(segs, []) == circ.ops and len(segs) == bench.DEPTH + 1
+    for ops in segs:
+        g, m = bench.split_segment(ops)
+        assert all(isinstance(o, C.Gate) for o in g) and all(isinstance(o, C.Measure) for o in m)

@@ -35,8 +35,9 @@ def _overlap(A, B):
     """<A|B> of two MPS by transfer matrices (host FP64, any n)."""
     E = np.ones((1, 1), dtype=np.complex128)
     for a, b in zip(A, B):
-        E = np.einsum("xy,xsu,ysv->uv", E, np.conj(np.asarray(a, dtype=np.complex128)),
-                      np.asarray(b, dtype=np.complex128))
+        # E'[u, v] = sum_{x, s, y} conj(a[x, s, u]) E[x, y] b[y, s, v], as two products
+        t = np.tensordot(E, np.asarray(b, dtype=np.complex128), axes=(1, 0))
+        E = np.tensordot(np.conj(np.asarray(a, dtype=np.complex128)), t, axes=([0, 1], [0, 1]))
     return E[0, 0]
 
 
@@ -377,3 +378,45 @@ def test_bond_cap_one():
     circ = C.brickwork(6, 4, 0.3, 2)
     _, res = _single_path_parity(circ, 1, 8, list(range(8)))
     assert np.all(res["F"] < 1.0)
+
+
+# ---- general Boolean conditions and the final measurement of Bob's qubit
+
+def test_general_boolean_conditions():
+    # X on q3 iff majority(c0, c1, c2) (a truth-table condition), X on q4 iff c0 OR c2;
+    # then q3 and q4 are measured: their bits must equal those functions on every shot
+    ops = [C.Gate((q,), C.H) for q in range(3)]
+    ops += [C.Measure(q, q) for q in range(3)]
+    ops += [C.Gate((3,), C.X, cond=C.Cond((0, 1, 2), "table", 0b11101000)),
+            C.Gate((4,), C.X, cond=C.Cond((0, 2), "or", 1)),
+            C.Gate((2, 3), C.CNOT), C.Gate((2, 3), C.CNOT)]  # identity pair: a two-qubit block
+    ops += [C.Measure(3, 3), C.Measure(4, 4)]
+    circ = C.Circuit(5, 5, ops)
+    _, res = _single_path_parity(circ, 4, 256, list(range(0, 256, 17)))
+    b = res["bits"].astype(int)
+    maj = (b[:, 0] + b[:, 1] + b[:, 2] >= 2).astype(int)
+    assert np.array_equal(b[:, 3], maj)
+    assert np.array_equal(b[:, 4], b[:, 0] | b[:, 2])
+    assert 0 < maj.sum() < 256
+
+
+def test_teleport_bob_measurement_eight_paths():
+    # multi-path teleportation with Bob's final measurement (Sec. "Quantum teleportation
+    # protocol"): eight paths, p = 0.25 Pr(m_Bob), Pr(0) ~ 0.37 for the printed input state
+    from conftest import read_golden_kv
+    g = read_golden_kv("teleport_paper.txt")
+    amps = (complex(g["input_re0"], g["input_im0"]), complex(g["input_re1"], g["input_im1"]))
+    circ = C.teleport(amplitudes=amps, bob_measure=True)
+    sim = _sim(3, 4, 16, circ.n_cbits)
+    sim.init_state(1, multipath=True)
+    sim.run_circuit(circ)
+    res = sim.results()
+    ref = SV.run_multi_path(circ)
+    assert res["n_active"] == len(ref) == 8
+    for i, b in enumerate(ref):
+        assert res["bits"][i].tolist() == [int(x) for x in b.path]
+        assert abs(res["p"][i] - b.p) < P_TOL
+        want = g["path_p_bob0"] if b.path[2] == 0 else g["path_p_bob1"]
+        assert abs(res["p"][i] - want) < g["printed_abs_tol"]
+    p0 = sum(res["p"][i] for i in range(8) if res["bits"][i][2] == 0)
+    assert abs(p0 - g["bob_p0"]) < g["printed_abs_tol"]

@@ -392,3 +392,17 @@ def test_guess_two_truncated_blocks_sequential_eckart_young(start):
     for q in order[::-1]:
         other, _ = _eckart_young(other, q + 1, chi)
     assert np.linalg.norm(other - psi) > 1e-6
+
+
+def test_single_path_run_in_segments_equals_one_pass():
+    # the oracle's step-wise Alg. 1 (used for bounded CPU timings) makes the same draws and
+    # compressions as one pass when each call ends at a measurement run
+    circ = C.brickwork(10, 8, 0.2, 4)
+    prm = D.Params(chi_max=8, tol=1e-10, sweeps=2)
+    one = D.run_single_path(circ, prm, 2, 5)
+    r = D.SinglePathRun(circ.n_qubits, circ.n_cbits, prm, 2, 5)
+    for seg in C.split_layers(circ):
+        r.run(seg)
+    two = r.result()
+    assert two.outcomes == one.outcomes and two.fids == one.fids and two.p == one.p
+    np.testing.assert_allclose(M.to_dense(two.mps), M.to_dense(one.mps), atol=1e-12)

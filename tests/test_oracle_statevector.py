@@ -243,3 +243,24 @@ def test_topk_non_degenerate_values_near_the_tie_scale():
     assert SV.topk_select([base, base * (1 + 2e-7), pmax], 2) == [0, 2]
     assert SV.topk_select([base * (1 + 2e-7), base, pmax], 2) == [0, 2]
     assert SV.topk_select([base, base * (1 + 2.5e-5), pmax], 2) == [1, 2]
+
+
+def test_general_boolean_conditions_by_enumeration():
+    # Sec. "Classically controlled operations": phi is a Boolean function of the register.
+    # Truth tables of three bits (index = c_b0 + 2 c_b1 + 4 c_b2 over the bits in ascending
+    # order) against the functions written out, on every register value
+    import itertools
+    cases = {0b11101000: lambda a, b, c: int(a + b + c >= 2),   # majority
+             0b11111110: lambda a, b, c: int(a or b or c),
+             0b10010110: lambda a, b, c: a ^ b ^ c,
+             0b10000000: lambda a, b, c: int(a and b and c),
+             0b00100100: lambda a, b, c: int((a == 0 and b == 1 and c == 0) or
+                                             (a == 1 and b == 0 and c == 1))}
+    for table, fn in cases.items():
+        for bits in itertools.product([0, 1], repeat=3):
+            creg = np.array([0, bits[0], 0, bits[1], bits[2]], dtype=np.int64)
+            # listed in any order; the index reads them in ascending bit order (1, 3, 4)
+            cond = C.Cond((4, 1, 3), "table", table)
+            assert SV.cond_holds(cond, creg) == bool(fn(*bits))
+            assert SV.cond_holds(C.Cond((1, 3, 4), "or", 1), creg) == any(bits)
+            assert SV.cond_holds(C.Cond((1, 3, 4), "or", 0), creg) == (not any(bits))

@@ -25,8 +25,9 @@ F_TOL = 1e-6
 def _overlap(A, B):
     E = np.ones((1, 1), dtype=np.complex128)
     for a, b in zip(A, B):
-        E = np.einsum("xy,xsu,ysv->uv", E, np.conj(np.asarray(a, dtype=np.complex128)),
-                      np.asarray(b, dtype=np.complex128))
+        # E'[u, v] = sum_{x, s, y} conj(a[x, s, u]) E[x, y] b[y, s, v], as two products
+        t = np.tensordot(E, np.asarray(b, dtype=np.complex128), axes=(1, 0))
+        E = np.tensordot(np.conj(np.asarray(a, dtype=np.complex128)), t, axes=([0, 1], [0, 1]))
     return E[0, 0]
 
 
