@@ -669,6 +669,182 @@ __device__ int cta_jacobi_svd_staged(float2* X, int m, int n, int ld, float2* V,
   return sweep + 1;
 }
 
+// The rotation of one pair (x_i held by this warp in registers, x_j given in registers too),
+// as warp_jacobi_pair, with the squared norms a = ||x_i||^2, b = ||x_j||^2 kept from the
+// columns' last change instead of re-read: the same threshold, angle and phase; the new
+// norms are summed while the rotated columns are formed.  Returns whether it rotated.
+template <int MR>
+__device__ __forceinline__ bool reg_jacobi_pair(float2 (&xi)[MR], float2 (&xj)[MR], float& a,
+                                                float& b, float thr, float floor_g) {
+  float2 g = cz();
+#pragma unroll
+  for (int k = 0; k < MR; ++k) cfmac(g, xi[k], xj[k]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    g.x += __shfl_xor_sync(FULL_MASK, g.x, o);
+    g.y += __shfl_xor_sync(FULL_MASK, g.y, o);
+  }
+  const float ag = hypotf(g.x, g.y);
+  if (!(ag > thr * sqrtf(a * b) && ag > floor_g && ag > 0.f)) return false;
+  const float zeta = (b - a) / (2.f * ag);
+  const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+  const float c = rsqrtf(1.f + t * t);
+  const float s = c * t;
+  const float2 ph = make_float2(g.x / ag, -g.y / ag);  // e^{-i phi}
+  float na = 0.f, nb = 0.f;
+#pragma unroll
+  for (int k = 0; k < MR; ++k) {
+    const float2 u = xi[k];
+    const float2 v = cmul(ph, xj[k]);
+    xi[k] = make_float2(c * u.x - s * v.x, c * u.y - s * v.y);
+    xj[k] = make_float2(s * u.x + c * v.x, s * u.y + c * v.y);
+    na += cabs2(xi[k]);
+    nb += cabs2(xj[k]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    na += __shfl_xor_sync(FULL_MASK, na, o);
+    nb += __shfl_xor_sync(FULL_MASK, nb, o);
+  }
+  a = na;
+  b = nb;
+  return true;
+}
+
+// cta_jacobi_svd_staged without V for m <= 32 MR rows, with less shared-memory traffic: the
+// columns are taken in blocks I of CPW NW (CPW per warp).  The pairs inside I are rotated in
+// shared memory (circle method, warp_jacobi_pair); then each warp holds its CPW columns of
+// I in registers while the columns after I stream through the staging area in blocks J,
+// round r pairing column a of I with column (a + r) mod R of J (R = max(|I|, |J|): disjoint
+// pairs within a round), so a pair moves one column through shared memory instead of three
+// reads and two writes.  Every pair of columns is still rotated once per sweep, with the
+// rotation, threshold and stopping rule of cta_jacobi_svd_staged.
+template <int NT, int MR, int CPW>
+__device__ __noinline__ int cta_jacobi_svd_regs(float2* X, int m, int n, int ld, double* sig2,
+                                                float* sigf, int* perm, int* flag, double* red,
+                                                float2* stage, size_t stage_elems) {
+  constexpr int NW = NT / 32;
+  constexpr int W = CPW * NW;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // staged J columns (m complex each) and their squared norms behind them
+  int wjcap = (int)((stage_elems * sizeof(float2)) / ((size_t)m * sizeof(float2) + sizeof(float)));
+  if (wjcap > n) wjcap = n;
+  float* bnorm = reinterpret_cast<float*>(stage + (size_t)wjcap * m);
+  const float thr = 2.f * sqrtf((float)m) * 5.96e-8f;  // as cta_jacobi_svd
+  const float floor_g = jacobi_floor<NT>(X, m, n, ld, red);
+  if (threadIdx.x == 0) *flag = 0;
+  int sweep = 0;
+  for (; sweep < 30; ++sweep) {
+    int rotated = 0;
+    for (int i0 = 0; i0 < n; i0 += W) {
+      const int wi = (n - i0) < W ? (n - i0) : W;
+      __syncthreads();
+      stage_cols<NT>(stage, X, m, ld, nullptr, 0, 0, i0, wi, true);
+      __syncthreads();
+      // pairs inside I: circle method in shared memory
+      const int N = (wi + 1) & ~1;
+      for (int rnd = 0; rnd < N - 1; ++rnd) {
+        for (int p = warp; p < N / 2; p += NW) {
+          int ci, cj;
+          if (p == 0) {
+            ci = rnd;
+            cj = N - 1;
+          } else {
+            ci = (rnd + p) % (N - 1);
+            cj = (rnd - p + (N - 1)) % (N - 1);
+          }
+          if (ci < wi && cj < wi && ci != cj)
+            rotated |= warp_jacobi_pair(stage + (size_t)ci * m, stage + (size_t)cj * m, m, m, thr, floor_g);
+        }
+        __syncthreads();
+      }
+      // this warp's columns of I into registers, with their squared norms
+      float2 xr[CPW][MR];
+      float an[CPW];
+#pragma unroll
+      for (int c = 0; c < CPW; ++c) {
+        const int col = warp + c * NW;
+        float sacc = 0.f;
+#pragma unroll
+        for (int k = 0; k < MR; ++k) {
+          const int row = lane + 32 * k;
+          xr[c][k] = (col < wi && row < m) ? stage[(size_t)col * m + row] : cz();
+          sacc += cabs2(xr[c][k]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(FULL_MASK, sacc, o);
+        an[c] = sacc;
+      }
+      __syncthreads();  // the staging area now serves the J blocks
+      for (int j0 = i0 + wi; j0 < n; j0 += wjcap) {
+        const int wj = (n - j0) < wjcap ? (n - j0) : wjcap;
+        stage_cols<NT>(stage, X, m, ld, nullptr, 0, 0, j0, wj, true);
+        __syncthreads();
+        for (int col = warp; col < wj; col += NW) {
+          float sacc = 0.f;
+          for (int row = lane; row < m; row += 32) sacc += cabs2(stage[(size_t)col * m + row]);
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(FULL_MASK, sacc, o);
+          if (lane == 0) bnorm[col] = sacc;
+        }
+        __syncthreads();
+        const int R = wi > wj ? wi : wj;
+        for (int r = 0; r < R; ++r) {
+#pragma unroll
+          for (int c = 0; c < CPW; ++c) {
+            const int a = warp + c * NW;
+            const int bcol = (a + r) % R;
+            if (a < wi && bcol < wj) {
+              float2* sc = stage + (size_t)bcol * m;
+              float2 xj[MR];
+#pragma unroll
+              for (int k = 0; k < MR; ++k) {
+                const int row = lane + 32 * k;
+                xj[k] = row < m ? sc[row] : cz();
+              }
+              float bb = bnorm[bcol];
+              if (reg_jacobi_pair<MR>(xr[c], xj, an[c], bb, thr, floor_g)) {
+                rotated = 1;
+#pragma unroll
+                for (int k = 0; k < MR; ++k) {
+                  const int row = lane + 32 * k;
+                  if (row < m) sc[row] = xj[k];
+                }
+                __syncwarp();
+                if (lane == 0) bnorm[bcol] = bb;
+              }
+            }
+          }
+          __syncthreads();
+        }
+        stage_cols<NT>(stage, X, m, ld, nullptr, 0, 0, j0, wj, false);
+        __syncthreads();
+      }
+      // this warp's columns of I back to X
+#pragma unroll
+      for (int c = 0; c < CPW; ++c) {
+        const int col = warp + c * NW;
+        if (col < wi) {
+#pragma unroll
+          for (int k = 0; k < MR; ++k) {
+            const int row = lane + 32 * k;
+            if (row < m) X[(size_t)(i0 + col) * ld + row] = xr[c][k];
+          }
+        }
+      }
+    }
+    if (lane == 0 && rotated) *flag = 1;
+    __syncthreads();
+    const int any = *flag;
+    __syncthreads();
+    if (threadIdx.x == 0) *flag = 0;
+    if (!any) break;
+  }
+  __syncthreads();
+  svd_finish<NT>(X, m, n, ld, sig2, sigf, perm);
+  return sweep + 1;
+}
+
 // ----------------------------------------------------------------------------- float-float
 // Sums of squares to about FP64 accuracy on the FP32 pipe (an FP64 instruction costs a
 // whole warp dozens of cycles on this part): a value is an unevaluated sum hi + lo, squares

@@ -7,6 +7,14 @@
 namespace dcs {
 
 // ----------------------------------------------------------------------------- large tiles
+// The guess SVD of a two-site tensor with at most 512 rows runs cta_jacobi_svd_regs with
+// DCS_SVD_CPW columns per warp in registers (DCS_SVD_REGS 0: cta_jacobi_svd_staged).
+#ifndef DCS_SVD_REGS
+#define DCS_SVD_REGS 1
+#endif
+#ifndef DCS_SVD_CPW
+#define DCS_SVD_CPW 2
+#endif
 
 
 // T2[b][s][e][x] = sum_{d,t} T1(b, d, t, x) W(d, s, t, e) with T1 at
@@ -167,9 +175,13 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
     __syncthreads();
     float2* Z = asc ? X : Y;
     const int zr = asc ? m : nn, zc = asc ? nn : m;
-    const int svd_sweeps = cta_jacobi_svd_staged<NT>(Z, zr, zc, zr, nullptr, 0, sm.sig2, sm.sigf,
-                                                     sm.perm, &sm.iv[5], sm.red, sm.stage,
-                                                     sm.stage_elems);
+    // columns of up to 512 rows: the register-resident variant
+    const int svd_sweeps =
+        (DCS_SVD_REGS && zr <= 512 && zc >= 2 * (NT / 32))
+            ? cta_jacobi_svd_regs<NT, 16, DCS_SVD_CPW>(Z, zr, zc, zr, sm.sig2, sm.sigf, sm.perm, &sm.iv[5],
+                                          sm.red, sm.stage, sm.stage_elems)
+            : cta_jacobi_svd_staged<NT>(Z, zr, zc, zr, nullptr, 0, sm.sig2, sm.sigf, sm.perm,
+                                        &sm.iv[5], sm.red, sm.stage, sm.stage_elems);
     (void)svd_sweeps;
 #ifdef DCS_PHASE_TIMERS
     if (threadIdx.x == 0 && zc >= 64) {
