@@ -104,9 +104,11 @@ typedef struct {
  * DCS_PREC_FP32: FP32 CUDA-core GEMMs; DCS_PREC_TF32X3: tcgen05 tensor-core GEMMs with TF32
  * inputs split in three products (x = hi + lo) and FP32 accumulation for the initial guess,
  * the environment cache and every sweep but the last, which runs in FP32 as refinement (its
- * f is the reported partial fidelity).  The shared-memory kernels (chi_max <= 32) always use
+ * f is the reported partial fidelity); DCS_PREC_BF16X3: the same with BF16 hi / lo parts
+ * (kind::f16 MMAs, about 2^-16 relative per product instead of 2^-22, half the tensor-pipe
+ * time), the last sweep again FP32.  The shared-memory kernels (chi_max <= 32) always use
  * FP32 CUDA cores. */
-typedef enum { DCS_PREC_FP32 = 0, DCS_PREC_TF32X3 = 1 } dcs_precision;
+typedef enum { DCS_PREC_FP32 = 0, DCS_PREC_TF32X3 = 1, DCS_PREC_BF16X3 = 2 } dcs_precision;
 
 typedef enum {
   DCS_PATH_AUTO = 0,    /* shared-memory tiles up to chi_max = 32, global tiles above */
@@ -257,10 +259,12 @@ dcs_status_t dcs_get_counters(dcs_ctx_t ctx, uint64_t* compressions, uint64_t* s
  * mode DCS_GEMM_SIMT: FP32 CUDA-core GEMM with shared-memory tiles.
  * mode DCS_GEMM_TENSOR: tcgen05 tensor-core GEMM (TF32 inputs, FP32 accumulators in tensor
  * memory) with each operand split as x = hi + lo (3 products), FP32-level accuracy;
+ * mode DCS_GEMM_TENSOR_BF16X3: the same with BF16 parts (kind::f16), about 2^-16 relative;
  * err_dev: DEVICE int set to 1 if a bounded completion wait gave up (result invalid).
  * One CTA per problem; asynchronous on `stream`. */
 #define DCS_GEMM_SIMT 0
 #define DCS_GEMM_TENSOR 1
+#define DCS_GEMM_TENSOR_BF16X3 2
 dcs_status_t dcs_cgemm(int32_t mode, int32_t batch, int32_t M, int32_t N, int32_t K,
                        const void* A, int64_t sam, int64_t sak, int64_t sab, int32_t conjA,
                        const void* B, int64_t sbk, int64_t sbn, int64_t sbb, int32_t conjB,

@@ -12,8 +12,8 @@ MAX_QUBITS = 128
 MAX_CHI_FUSED = 32
 MAX_CHI = 1024
 PATH_AUTO, PATH_SHARED, PATH_GLOBAL = 0, 1, 2
-GEMM_SIMT, GEMM_TENSOR = 0, 1
-PREC_FP32, PREC_TF32X3 = 0, 1
+GEMM_SIMT, GEMM_TENSOR, GEMM_TENSOR_BF16X3 = 0, 1, 2
+PREC_FP32, PREC_TF32X3, PREC_BF16X3 = 0, 1, 2
 
 OK, ERR_INVALID, ERR_OOM, ERR_ZERO_PROB, ERR_NUMERICAL, ERR_TIMEOUT, ERR_CUDA, ERR_UNSUPPORTED = range(8)
 STATUS_NAMES = ["OK", "INVALID", "OOM", "ZERO_PROB", "NUMERICAL", "TIMEOUT", "CUDA", "UNSUPPORTED"]

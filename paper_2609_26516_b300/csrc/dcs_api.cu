@@ -38,7 +38,8 @@ bool valid_cfg(const dcs_config* c) {
   return c && c->n_qubits >= 1 && c->n_qubits <= DCS_MAX_QUBITS && c->chi_max >= 1 &&
          c->sweeps >= 1 && c->n_slots >= 1 && c->n_cbits >= 0 && c->n_cbits <= 64 * DCS_CWORDS &&
          c->tol >= 0.0 && c->chunk_k >= 0 &&
-         (c->precision == DCS_PREC_FP32 || c->precision == DCS_PREC_TF32X3) &&
+         (c->precision == DCS_PREC_FP32 || c->precision == DCS_PREC_TF32X3 ||
+          c->precision == DCS_PREC_BF16X3) &&
          c->kernel_path >= DCS_PATH_AUTO && c->kernel_path <= DCS_PATH_GLOBAL;
 }
 
@@ -344,7 +345,9 @@ dcs_status_t dcs_create(dcs_ctx_t* out, const dcs_config* cfg, void* dev_arena, 
   d.plan = reinterpret_cast<int32_t*>(a + lay.plan);
   d.counters = reinterpret_cast<unsigned long long*>(a + lay.counters);
   d.work = lay.big ? reinterpret_cast<float2*>(a + lay.work) : nullptr;
-  d.use_tc = (lay.big && cfg->precision == DCS_PREC_TF32X3) ? 1 : 0;
+  d.use_tc = !lay.big ? 0
+             : cfg->precision == DCS_PREC_TF32X3 ? 1
+             : cfg->precision == DCS_PREC_BF16X3 ? 2 : 0;
   d.work_stride = lay.work_stride;
   d.seed = cfg->seed;
   d.chi_max = cfg->chi_max;

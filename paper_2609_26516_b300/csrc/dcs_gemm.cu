@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(GEMM_NT, 1) k_cgemm(GemmArgs g, int mode, int*
   const float2* A = g.A + (size_t)b * g.sab;
   const float2* B = g.B + (size_t)b * g.sbb;
   float2* C = g.C + (size_t)b * g.scb;
-  if (mode == DCS_GEMM_TENSOR) {
+  if (mode == DCS_GEMM_TENSOR || mode == DCS_GEMM_TENSOR_BF16X3) {
     TcState t;
     t.stage = reinterpret_cast<float*>(raw);
     uint64_t* tail = reinterpret_cast<uint64_t*>(t.stage + TC_SMEM_FLOATS);
@@ -39,6 +39,7 @@ __global__ void __launch_bounds__(GEMM_NT, 1) k_cgemm(GemmArgs g, int mode, int*
     t.tmem = reinterpret_cast<uint32_t*>(t.uses + 2);
     t.err = reinterpret_cast<int*>(t.tmem + 1);
     tc_setup(t);
+    t.bf16 = mode == DCS_GEMM_TENSOR_BF16X3;
     cta_cgemm_tc<GEMM_NT>(g.M, g.N, g.K, A, (int)g.sam, (int)g.sak, g.conjA, B, (int)g.sbk,
                           (int)g.sbn, g.conjB, C, (int)g.scm, (int)g.scn, t);
     if (threadIdx.x == 0 && *t.err) atomicOr(err, 1);
@@ -58,17 +59,18 @@ extern "C" dcs_status_t dcs_cgemm(int32_t mode, int32_t batch, int32_t M, int32_
                                  int32_t conjA, const void* B, int64_t sbk, int64_t sbn,
                                  int64_t sbb, int32_t conjB, void* C, int64_t scm, int64_t scn,
                                  int64_t scb, int32_t* err_dev, dcs_stream_t stream) {
-  if (batch < 0 || M < 0 || N < 0 || K < 0 || (mode != DCS_GEMM_SIMT && mode != DCS_GEMM_TENSOR))
+  const bool tensor = mode == DCS_GEMM_TENSOR || mode == DCS_GEMM_TENSOR_BF16X3;
+  if (batch < 0 || M < 0 || N < 0 || K < 0 || (mode != DCS_GEMM_SIMT && !tensor))
     return DCS_ERR_INVALID;
   if (batch == 0 || M == 0 || N == 0) return DCS_OK;
-  if (!A || !B || !C || (mode == DCS_GEMM_TENSOR && !err_dev)) return DCS_ERR_INVALID;
+  if (!A || !B || !C || (tensor && !err_dev)) return DCS_ERR_INVALID;
   const long long lim = 1ll << 31;
   if (sam >= lim || sak >= lim || sbk >= lim || sbn >= lim || scm >= lim || scn >= lim)
     return DCS_ERR_UNSUPPORTED;
   GemmArgs g{M, N, K, static_cast<const float2*>(A), sam, sak, sab, conjA,
              static_cast<const float2*>(B), sbk, sbn, sbb, conjB, static_cast<float2*>(C),
              scm, scn, scb};
-  const size_t smem = mode == DCS_GEMM_TENSOR
+  const size_t smem = tensor
                           ? sizeof(float) * TC_SMEM_FLOATS + 64
                           : sizeof(float2) * GEMM_SIMT_SMEM_ELEMS;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

@@ -82,7 +82,10 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
       return;
     }
   }
-  if (TC) tc_setup(sm.tc);
+  if (TC) {
+    tc_setup(sm.tc);
+    sm.tc.bf16 = c.use_tc == 2;
+  }
   const int kb = c.ketbuf[slot], bb = 1 - kb;
   const int* kbonds = bonds_ptr(c, slot, kb);
   for (int i = threadIdx.x; i <= n; i += NT) {

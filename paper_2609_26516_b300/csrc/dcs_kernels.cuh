@@ -87,7 +87,8 @@ struct DevCtx {
   int32_t* plan;             // branch plan scratch
   unsigned long long* counters;  // [0] compression steps run, [1] sweeps run (since init)
   float2* work;              // per-slot work area of the large-tile kernels (nullptr: small)
-  int32_t use_tc;            // large-tile contractions on the tensor cores (3xTF32)
+  int32_t use_tc;            // large-tile contractions on the tensor cores: 0 no,
+                             // 1 3xTF32, 2 BF16x3
   size_t work_stride;        // complex elements per slot of `work`
   uint64_t seed;
   int32_t chi_max;

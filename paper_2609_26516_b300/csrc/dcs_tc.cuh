@@ -7,7 +7,10 @@
 //    so that (A_r B_r)[m][2n] = Re c and [m][2n+1] = Im c;
 //  * 3xTF32: every operand x = hi + lo with hi = x with the low 13 mantissa bits cleared and
 //    lo = x - hi; A B ~ hi_A hi_B + hi_A lo_B + lo_A hi_B (the dropped lo lo term is
-//    ~2^-22 relative).
+//    ~2^-22 relative);
+//  * or BF16x3 (kind::f16 with BF16 operands): hi = x rounded to BF16, lo = x - hi rounded
+//    to BF16, the same three products; each MMA covers K = 16 where TF32 takes two of K = 8,
+//    at about 2^-16 relative accuracy (the dropped lo lo term and the rounding of lo).
 // Tile: 128 complex rows x 128 complex columns (MMA M = 128, N = 256 real), K in steps of 8
 // complex (16 real = two MMAs of K = 8).  The raw complex operand tiles of the next K-steps
 // stream into a 4-deep shared-memory ring with cp.async (zero fill outside the matrices), so
@@ -18,6 +21,7 @@
 // other is filled.
 #pragma once
 #include <cstdint>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "dcs_device.cuh"
@@ -53,6 +57,10 @@ __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32
 __host__ __device__ constexpr uint32_t tc_idesc(int M, int N) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
+// The same for kind::f16 with A = B = BF16 (bits 7-9, 10-12 = 1), D = F32.
+__host__ __device__ constexpr uint32_t tc_idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
 
 __device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
                                        uint32_t idesc, uint32_t accumulate) {
@@ -60,6 +68,17 @@ __device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+      :
+      : "r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                            uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
       :
       : "r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
@@ -143,6 +162,22 @@ __device__ __forceinline__ int tc_off(int row, int kr) {
   return (((row >> 3) * 4 + (kr >> 2)) * 32) + (row & 7) * 4 + (kr & 3);
 }
 
+// The BF16 operands: 16-bit index of element (row, kr), core matrices of 8 rows x 8 values
+// (16 bytes a row), the two along K 128 bytes apart, 8-row groups 256 bytes apart.
+__device__ __forceinline__ int tc_off16(int row, int kr) {
+  return (((row >> 3) * 2 + (kr >> 3)) * 64) + (row & 7) * 8 + (kr & 7);
+}
+
+// x = hi + lo in BF16 (round to nearest), packed with the next real column: (a, b) -> two
+// 32-bit words (hi_a | hi_b << 16) and (lo_a | lo_b << 16).
+__device__ __forceinline__ void bf16_split2(float a, float b, uint32_t& hi, uint32_t& lo) {
+  const __nv_bfloat16 ha = __float2bfloat16_rn(a), hb = __float2bfloat16_rn(b);
+  const __nv_bfloat16 la = __float2bfloat16_rn(a - __bfloat162float(ha));
+  const __nv_bfloat16 lb = __float2bfloat16_rn(b - __bfloat162float(hb));
+  hi = (uint32_t)__bfloat16_as_ushort(ha) | ((uint32_t)__bfloat16_as_ushort(hb) << 16);
+  lo = (uint32_t)__bfloat16_as_ushort(la) | ((uint32_t)__bfloat16_as_ushort(lb) << 16);
+}
+
 // Per-CTA state of the tensor-core GEMM (in shared memory).
 struct TcState {
   float* stage;        // TC_SMEM_FLOATS, 16-byte aligned
@@ -150,6 +185,7 @@ struct TcState {
   int* uses;           // 2 commit counters
   uint32_t* tmem;      // TMEM base address (written by tmem_alloc)
   int* err;            // set to 1 if a bounded wait gave up
+  bool bf16;           // BF16x3 products instead of 3xTF32
 };
 
 // One thread initialises the barriers; warp 0 allocates TMEM.  All threads call.
@@ -160,6 +196,7 @@ __device__ __forceinline__ void tc_setup(TcState& t) {
     t.uses[0] = t.uses[1] = 0;
     *t.err = 0;
   }
+  t.bf16 = false;
   if (threadIdx.x < 32) tmem_alloc(t.tmem, TC_TMEM_COLS);
   tc_fence_before();
   __syncthreads();
@@ -225,6 +262,43 @@ __device__ __forceinline__ void tc_elem(int e, int& row, int& kk) {
 // Raw slot -> canonical hi / lo stage.  A per complex element (TC_M x TC_K); B per real row
 // of B_r^T (2 TC_N x TC_K: row 2n holds (Re b, -Im b), row 2n+1 holds (Im b, Re b)).
 template <int NT>
+__device__ __forceinline__ void tc_stage_from_raw_bf16(const float2* raw, float* st, bool conjA,
+                                                       bool conjB) {
+  const float2* rA = raw;
+  const float2* rB = raw + TC_M * TC_K;
+  // per copy: A 128 x 16 and B 256 x 16 BF16 values
+  uint16_t* Ahi = reinterpret_cast<uint16_t*>(st);
+  uint16_t* Alo = Ahi + TC_M * 16;
+  uint16_t* Bhi = Alo + TC_M * 16;
+  uint16_t* Blo = Bhi + 2 * TC_N * 16;
+#pragma unroll
+  for (int e = threadIdx.x; e < TC_M * TC_K; e += NT) {
+    int mm, kk;
+    tc_elem(e, mm, kk);
+    float2 v = rA[mm * TC_K + kk];
+    if (conjA) v.y = -v.y;
+    uint32_t h, l;
+    bf16_split2(v.x, v.y, h, l);
+    const int o = tc_off16(mm, 2 * kk);
+    *reinterpret_cast<uint32_t*>(Ahi + o) = h;
+    *reinterpret_cast<uint32_t*>(Alo + o) = l;
+  }
+#pragma unroll
+  for (int e = threadIdx.x; e < 2 * TC_N * TC_K; e += NT) {
+    int nr, kk;
+    tc_elem(e, nr, kk);
+    float2 v = rB[kk * TC_N + (nr >> 1)];
+    if (conjB) v.y = -v.y;
+    v = (nr & 1) ? make_float2(v.y, v.x) : make_float2(v.x, -v.y);
+    uint32_t h, l;
+    bf16_split2(v.x, v.y, h, l);
+    const int o = tc_off16(nr, 2 * kk);
+    *reinterpret_cast<uint32_t*>(Bhi + o) = h;
+    *reinterpret_cast<uint32_t*>(Blo + o) = l;
+  }
+}
+
+template <int NT>
 __device__ __forceinline__ void tc_stage_from_raw(const float2* raw, float* st, bool conjA,
                                                   bool conjB) {
   const float2* rA = raw;
@@ -269,6 +343,8 @@ __device__ void cta_cgemm_tc(int M, int N, int K, const float2* A, int sam, int 
   static_assert(NT % 128 == 0, "the epilogue needs whole warp quadrants");
   static_assert(TC_K == 8, "the element mapping covers 8 complex k per step");
   constexpr uint32_t IDESC = tc_idesc(128, 256);
+  constexpr uint32_t IDESC16 = tc_idesc_bf16(128, 256);
+  const bool bf = t.bf16;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t tbase = *t.tmem;
   const int ksteps = (K + TC_K - 1) / TC_K;
@@ -301,23 +377,36 @@ __device__ void cta_cgemm_tc(int M, int N, int K, const float2* A, int sam, int 
           if (!mbar_wait(&t.mbar[b], (uint32_t)((t.uses[b] - 1) & 1))) *t.err = 1;
         }
         __syncthreads();
-        tc_stage_from_raw<NT>(ring + (s % TC_RAW) * TC_RAW_ELEMS, st, conjA, conjB);
+        if (bf) tc_stage_from_raw_bf16<NT>(ring + (s % TC_RAW) * TC_RAW_ELEMS, st, conjA, conjB);
+        else tc_stage_from_raw<NT>(ring + (s % TC_RAW) * TC_RAW_ELEMS, st, conjA, conjB);
         fence_async_smem();
         tc_fence_before();
         __syncthreads();
         if (tid == 0) {
           tc_fence_after();
-          const float* As[3] = {Ahi, Ahi, Alo};
-          const float* Bs[3] = {Bhi, Blo, Bhi};
+          if (bf) {
+            // BF16 copies: A hi / lo 4 KB each, B hi / lo 8 KB each; one MMA of K = 16 per
+            // product (both K core matrices of the stage)
+            const uint32_t a0 = smem_addr(st), b0 = a0 + 2 * 4096;
+            const uint32_t as[3] = {a0, a0, a0 + 4096};
+            const uint32_t bs[3] = {b0, b0 + 8192, b0};
 #pragma unroll
-          for (int p = 0; p < 3; ++p)
+            for (int p = 0; p < 3; ++p)
+              tc_mma_bf16(tbase, tc_desc(as[p], 128, 256), tc_desc(bs[p], 128, 256), IDESC16,
+                          (s > 0 || p > 0) ? 1u : 0u);
+          } else {
+            const float* As[3] = {Ahi, Ahi, Alo};
+            const float* Bs[3] = {Bhi, Blo, Bhi};
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              // K-chunks 2h, 2h+1 of this stage: start two core matrices (256 B) further
-              const uint64_t ad = tc_desc(smem_addr(As[p]) + h * 256, 128, 512);
-              const uint64_t bd = tc_desc(smem_addr(Bs[p]) + h * 256, 128, 512);
-              tc_mma(tbase, ad, bd, IDESC, (s > 0 || p > 0 || h > 0) ? 1u : 0u);
-            }
+            for (int p = 0; p < 3; ++p)
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                // K-chunks 2h, 2h+1 of this stage: start two core matrices (256 B) further
+                const uint64_t ad = tc_desc(smem_addr(As[p]) + h * 256, 128, 512);
+                const uint64_t bd = tc_desc(smem_addr(Bs[p]) + h * 256, 128, 512);
+                tc_mma(tbase, ad, bd, IDESC, (s > 0 || p > 0 || h > 0) ? 1u : 0u);
+              }
+          }
           tc_commit(&t.mbar[b]);
           t.uses[b] += 1;
         }

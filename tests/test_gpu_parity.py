@@ -271,7 +271,7 @@ def test_global_tiles_ghz_and_teleport():
     _single_path_parity(C.teleport(4), 4, 64, list(range(0, 64, 13)), path=2)
 
 
-@pytest.mark.parametrize("prec", [0, 1], ids=["fp32", "tf32x3"])
+@pytest.mark.parametrize("prec", [0, 1, 2], ids=["fp32", "tf32x3", "bf16x3"])
 def test_global_tiles_ragged_chi_above_shared_limit(prec):
     # chi_max = 40 is above the shared-memory tiles and not a multiple of the GEMM tile
     circ = C.brickwork(14, 16, 0.02, 9)  # the middle bonds reach 40 and are truncated
@@ -285,7 +285,7 @@ def test_global_tiles_tensor_cores_at_chi_96():
     _single_path_parity(circ, 96, 2, [0, 1], prec=1)
 
 
-@pytest.mark.parametrize("prec", [0, 1], ids=["fp32", "tf32x3"])
+@pytest.mark.parametrize("prec", [0, 1, 2], ids=["fp32", "tf32x3", "bf16x3"])
 def test_global_tiles_blocked_qr_at_chi_128(prec):
     # middle bonds saturate at 128 and are truncated: the sweeps' QRs of 256 x 128 and
     # 128 x 128 matrices take the blocked (panel + GEMM) form

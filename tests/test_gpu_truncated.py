@@ -19,8 +19,8 @@ from test_gpu_parity import P_TOL, STATE_TOL, _overlap, _sim, _single_path_parit
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-PRECS = [0, 1]
-PREC_IDS = ["fp32", "tf32x3"]
+PRECS = [0, 1, 2]
+PREC_IDS = ["fp32", "tf32x3", "bf16x3"]
 
 
 def _fid_T(A, B):
