@@ -536,6 +536,14 @@ __device__ __forceinline__ int sweep_qr(Work& sm, int m, int n) {
 }
 
 // ----------------------------------------------------------------------------- gauge moves
+// A gauge move of an m x n site matrix takes the blocked QR (panels + GEMMs) when the tiles
+// are in the global work area, the panel pays off and its scratch fits the T tile.
+template <int NT>
+__device__ __forceinline__ bool hop_blocked(const Work& sm, int m, int n) {
+  return NT >= 128 && sm.gA != nullptr && n >= 2 * QR_PB && m >= QR_PB &&
+         qr_blocked_scratch(m, n) <= (size_t)8 * sm.C * sm.C;
+}
+
 // Move the orthogonality centre of MPS buffer `buf` of `slot` from j to j+1:
 // T_j = Q R (as (2 b_j) x b_{j+1}), T_j := Q, T_{j+1} := R T_{j+1}.
 template <int NT>
@@ -549,8 +557,20 @@ static __device__ void hop_right(const DevCtx& c, Work& sm, int buf, int slot, i
     sm.F[row + x * m] = src[idx];
   }
   __syncthreads();
-  const int r = cta_qr<NT>(sm.F, m, br, m, sm.R, m, sm.E, br, sm.tau, sm.alph, sm.red);
   float2* dst = site_ptr(c, buf, slot, j);
+  int r;
+  if (hop_blocked<NT>(sm, m, br)) {
+    // large tiles: blocked Householder QR for Q, then R = Q^H T_j (one GEMM on the
+    // untouched site), FP32-accurate products
+    r = cta_qr_blocked<NT>(sm, sm.F, m, br, sm.R, m, sm.T);
+    const bool tc = sm.use_tc;
+    sm.use_tc = tc && !sm.tc.bf16;
+    wgemm<NT>(sm, r, br, m, sm.R, m, 1, true, src, br, 1, false, sm.E, br, 1);
+    sm.use_tc = tc;
+    __syncthreads();
+  } else {
+    r = cta_qr<NT>(sm.F, m, br, m, sm.R, m, sm.E, br, sm.tau, sm.alph, sm.red);
+  }
   for (int idx = threadIdx.x; idx < m * r; idx += NT) {
     const int row = idx / r, k = idx % r;
     dst[idx] = sm.R[row + k * m];
@@ -588,8 +608,22 @@ static __device__ void hop_left(const DevCtx& c, Work& sm, int buf, int slot, in
     sm.F[(x * 2 + t) + a * m] = src[idx];
   }
   __syncthreads();
-  const int r = cta_qr<NT>(sm.F, m, bl, m, sm.R, m, sm.E, bl, sm.tau, sm.alph, sm.red);
   float2* dst = site_ptr(c, buf, slot, j);
+  int r;
+  if (hop_blocked<NT>(sm, m, bl)) {
+    // large tiles: blocked QR for Q', then R' = Q'^H T_j' from a copy of T_j' ((x t) x a,
+    // in the S tile, which the large path does not use otherwise)
+    gcopy<NT>(sm.S, sm.F, m * bl);
+    __syncthreads();
+    r = cta_qr_blocked<NT>(sm, sm.F, m, bl, sm.R, m, sm.T);
+    const bool tc = sm.use_tc;
+    sm.use_tc = tc && !sm.tc.bf16;
+    wgemm<NT>(sm, r, bl, m, sm.R, m, 1, true, sm.S, 1, m, false, sm.E, bl, 1);
+    sm.use_tc = tc;
+    __syncthreads();
+  } else {
+    r = cta_qr<NT>(sm.F, m, bl, m, sm.R, m, sm.E, bl, sm.tau, sm.alph, sm.red);
+  }
   for (int idx = threadIdx.x; idx < r * 2 * br; idx += NT) {
     const int x = idx % br, t = (idx / br) & 1, k = idx / (2 * br);
     dst[idx] = sm.R[(x * 2 + t) + k * m];
