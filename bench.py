@@ -533,7 +533,7 @@ def measure_cgemm(chi, batch):
     st = torch.cuda.current_stream()
     out = {"workload": f"complex GEMM M={M} N={Nn} K={K} batch={batch} (B transposed)",
            "flops_per_call": 8.0 * M * Nn * K * batch}
-    for mode, name in ((1, "tensor_tf32x3"), (0, "simt_fp32")):
+    for mode, name in ((1, "tensor_tf32x3"), (2, "tensor_bf16x3"), (0, "simt_fp32")):
         times = []
         for i in range(5):
             a = torch.cuda.Event(enable_timing=True)

@@ -24,6 +24,12 @@
 #pragma once
 #include <cstdio>
 
+// Whether this translation unit's kernels run the tensor-core GEMM (only the TF32X3 / BF16X3
+// compression kernel does; keeping its code out of the others keeps their registers free).
+#ifndef DCS_TU_TENSOR_CORES
+#define DCS_TU_TENSOR_CORES 0
+#endif
+
 #include "dcs_device.cuh"
 #include "dcs_gemm.cuh"
 #include "dcs_kernels.cuh"
@@ -350,6 +356,7 @@ __host__ __device__ inline size_t work_arrays_bytes(int C, bool big) {
 // the CTA's shared memory up to 224 KB.
 constexpr size_t BIG_SMEM_BYTES = 224 * 1024;
 constexpr size_t BIG_HEAD_BYTES = 128;
+static_assert(TC_HEAD_BYTES <= (int)BIG_HEAD_BYTES, "tensor-core barriers exceed the head");
 __host__ __device__ inline size_t big_stage_bytes(int C) {
   const size_t rest = work_arrays_bytes(C, true) + BIG_HEAD_BYTES;
   return rest < BIG_SMEM_BYTES ? ((BIG_SMEM_BYTES - rest) & ~(size_t)127) : 0;
@@ -370,13 +377,14 @@ static __device__ void carve(Work& w, unsigned char* raw, int C, float2* big_are
   if (big_area) {  // head (barriers, counters), then the 128-byte aligned staging region
     uint64_t* head = reinterpret_cast<uint64_t*>(raw);
     w.tc.mbar = head;
-    w.tc.uses = reinterpret_cast<int*>(head + 2);
+    w.tc.uses = reinterpret_cast<int*>(head + TC_NBAR);
     w.tc.tmem = reinterpret_cast<uint32_t*>(w.tc.uses + 2);
     w.tc.err = reinterpret_cast<int*>(w.tc.tmem + 1);
     raw += BIG_HEAD_BYTES;
     w.stage = reinterpret_cast<float2*>(raw);
     w.stage_elems = big_stage_bytes(C) / sizeof(float2);
     w.tc.stage = reinterpret_cast<float*>(raw);
+    w.tc.stage_bytes = big_stage_bytes(C);
     raw += big_stage_bytes(C);
   }
   uint64_t* c64 = reinterpret_cast<uint64_t*>(raw);
@@ -413,17 +421,21 @@ static __device__ void carve(Work& w, unsigned char* raw, int C, float2* big_are
   w.iv = w.abnd + DCS_MAX_QUBITS + 1;
 }
 
-// Complex GEMM of the large tiles: tensor cores when enabled and the shape fills at least
-// half an MMA tile in M and N, the SIMT tiles otherwise.
+// Complex GEMM of the large tiles: tensor cores when enabled, the shape fills at least half
+// an MMA tile in M and N and K spans 16 stages or more (shorter products, such as the panel
+// updates of the blocked QR, cost more in pipeline set-up than they save), the SIMT tiles
+// otherwise.
 template <int NT>
 __device__ __forceinline__ void wgemm(Work& sm, int M, int N, int K, const float2* A, int sam,
                                       int sak, bool conjA, const float2* B, int sbk, int sbn,
                                       bool conjB, float2* Cm, int scm, int scn) {
   if constexpr (NT >= 128) {
-    if (sm.use_tc && M >= 64 && N >= 64 && K >= 16) {
+#if DCS_TU_TENSOR_CORES
+    if (sm.use_tc && M >= 64 && N >= 64 && K >= 128) {
       cta_cgemm_tc<NT>(M, N, K, A, sam, sak, conjA, B, sbk, sbn, conjB, Cm, scm, scn, sm.tc);
       return;
     }
+#endif
     cta_cgemm<NT>(M, N, K, A, sam, sak, conjA, B, sbk, sbn, conjB, Cm, scm, scn, sm.gA, sm.gB);
   }
 }

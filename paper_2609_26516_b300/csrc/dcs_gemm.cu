@@ -11,6 +11,9 @@ namespace {
 using namespace dcs;
 
 constexpr int GEMM_NT = 512;
+// staging of the tensor-core mode: three raw stages and two TF32 stage buffers (four BF16)
+constexpr size_t GEMM_TC_STAGE_BYTES =
+    (size_t)(TC_RAW * TC_RAW_STAGE_FLOATS + TC_MIN_PIPE * TC_STAGE_FLOATS) * sizeof(float);
 
 struct GemmArgs {
   int M, N, K;
@@ -33,9 +36,10 @@ __global__ void __launch_bounds__(GEMM_NT, 1) k_cgemm(GemmArgs g, int mode, int*
   if (mode == DCS_GEMM_TENSOR || mode == DCS_GEMM_TENSOR_BF16X3) {
     TcState t;
     t.stage = reinterpret_cast<float*>(raw);
-    uint64_t* tail = reinterpret_cast<uint64_t*>(t.stage + TC_SMEM_FLOATS);
+    t.stage_bytes = GEMM_TC_STAGE_BYTES;
+    uint64_t* tail = reinterpret_cast<uint64_t*>(raw + GEMM_TC_STAGE_BYTES);
     t.mbar = tail;
-    t.uses = reinterpret_cast<int*>(tail + 2);
+    t.uses = reinterpret_cast<int*>(tail + TC_NBAR);
     t.tmem = reinterpret_cast<uint32_t*>(t.uses + 2);
     t.err = reinterpret_cast<int*>(t.tmem + 1);
     tc_setup(t);
@@ -71,7 +75,7 @@ extern "C" dcs_status_t dcs_cgemm(int32_t mode, int32_t batch, int32_t M, int32_
              static_cast<const float2*>(B), sbk, sbn, sbb, conjB, static_cast<float2*>(C),
              scm, scn, scb};
   const size_t smem = tensor
-                          ? sizeof(float) * TC_SMEM_FLOATS + 64
+                          ? GEMM_TC_STAGE_BYTES + 256
                           : sizeof(float2) * GEMM_SIMT_SMEM_ELEMS;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (cudaFuncSetAttribute(k_cgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=

@@ -1,4 +1,5 @@
 // The large-tile compression kernel with tcgen05 tensor-core contractions (TF32X3).
+#define DCS_TU_TENSOR_CORES 1
 #include "dcs_k_big.cuh"
 
 namespace dcs {

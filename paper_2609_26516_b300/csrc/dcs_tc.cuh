@@ -11,14 +11,17 @@
 //  * or BF16x3 (kind::f16 with BF16 operands): hi = x rounded to BF16, lo = x - hi rounded
 //    to BF16, the same three products; each MMA covers K = 16 where TF32 takes two of K = 8,
 //    at about 2^-16 relative accuracy (the dropped lo lo term and the rounding of lo).
-// Tile: 128 complex rows x 128 complex columns (MMA M = 128, N = 256 real), K in steps of 8
-// complex (16 real = two MMAs of K = 8).  The raw complex operand tiles of the next K-steps
-// stream into a 4-deep shared-memory ring with cp.async (zero fill outside the matrices), so
-// global latency stays off the critical path.  From there all threads split them into hi/lo
-// TF32 in the canonical K-major layout without swizzle: 8-row x 16-byte core matrices, core
-// matrices along K 128 bytes apart (leading-dimension offset), 8-row groups 512 bytes apart
-// (stride offset).  Two canonical buffers alternate; the MMAs of one stage run while the
-// other is filled.
+// Tile: 128 complex rows x 128 complex columns (MMA M = 128, N = 256 real), K in stages of
+// 8 complex (16 real).  The CTA's warps are specialised: warp 0 issues the MMAs (one
+// thread), the other warps load the complex operands of the coming stages from global
+// memory, split them (hi / lo) and write them in the canonical K-major layout without
+// swizzle (8-row x 16-byte core matrices, core matrices along K 128 bytes apart: the
+// leading-dimension offset; 8-row groups 512 bytes apart for TF32, 256 for BF16: the stride
+// offset) into a ring of stage buffers.  Per stage a "full" mbarrier collects one arrival per
+// loader warp and an "empty" one the MMAs' completion (tcgen05.commit), so the loaders run up
+// to a ring's length ahead of the tensor core and no CTA barrier sits in the K loop.  After a
+// tile's last stage a "done" commit releases the epilogue (TMEM -> registers -> C, all
+// warps).  Every mbarrier wait is bounded and flags *err when it gives up.
 #pragma once
 #include <cstdint>
 #include <cuda_bf16.h>
@@ -33,11 +36,18 @@ constexpr int TC_N = 128;   // complex columns per tile (MMA N = 256 real)
 constexpr int TC_K = 8;     // complex K per stage (16 real)
 constexpr int TC_A_FLOATS = TC_M * 2 * TC_K;        // one A copy (hi or lo): 128 x 16
 constexpr int TC_B_FLOATS = 2 * TC_N * 2 * TC_K;    // one B copy: 256 x 16
-constexpr int TC_STAGE_FLOATS = 2 * (TC_A_FLOATS + TC_B_FLOATS);
-constexpr int TC_RAW = 4;                            // raw operand ring depth (K-steps)
-constexpr int TC_RAW_ELEMS = TC_M * TC_K + TC_K * TC_N;  // complex elements per raw step
-// two canonical stages (96 KB) and the raw ring (64 KB)
-constexpr int TC_SMEM_FLOATS = 2 * TC_STAGE_FLOATS + TC_RAW * 2 * TC_RAW_ELEMS;
+constexpr int TC_STAGE_FLOATS = 2 * (TC_A_FLOATS + TC_B_FLOATS);  // 48 KB (TF32)
+constexpr int TC_STAGE16_BYTES = TC_STAGE_FLOATS * 2;              // 24 KB (BF16)
+constexpr int TC_MAX_PIPE = 6;        // stage buffers at most
+constexpr int TC_MIN_PIPE = 2;
+constexpr int TC_RAW = 3;             // raw operand stages in flight per loader thread
+constexpr int TC_RAW_MIN = 2;         // (two where shared memory is short)
+// one raw stage of a 512-thread CTA: 480 loader threads x 8 elements (30 KB); the
+// 512-thread kernels are the ones that run the tensor-core GEMM
+constexpr int TC_RAW_STAGE_FLOATS = 8 * 480 * 2;
+// the smallest staging region the tensor-core GEMM runs in: two TF32 stages and two raw ones
+constexpr int TC_SMEM_FLOATS = TC_MIN_PIPE * TC_STAGE_FLOATS + TC_RAW_MIN * TC_RAW_STAGE_FLOATS;
+constexpr int TC_NBAR = 2 * TC_MAX_PIPE + 1;  // full[], empty[], done
 constexpr int TC_TMEM_COLS = 256;
 constexpr long long TC_WAIT_LIMIT = 1ll << 26;      // bounded mbarrier spins
 
@@ -180,21 +190,29 @@ __device__ __forceinline__ void bf16_split2(float a, float b, uint32_t& hi, uint
 
 // Per-CTA state of the tensor-core GEMM (in shared memory).
 struct TcState {
-  float* stage;        // TC_SMEM_FLOATS, 16-byte aligned
-  uint64_t* mbar;      // 2 mbarriers
-  int* uses;           // 2 commit counters
+  float* stage;        // stage ring, 16-byte aligned
+  size_t stage_bytes;  // its size
+  uint64_t* mbar;      // TC_NBAR mbarriers: full[TC_MAX_PIPE], empty[TC_MAX_PIPE], done
+  int* uses;           // [0] stages and [1] tiles run since tc_setup (the barriers' phases)
   uint32_t* tmem;      // TMEM base address (written by tmem_alloc)
   int* err;            // set to 1 if a bounded wait gave up
   bool bf16;           // BF16x3 products instead of 3xTF32
 };
 
+// Bytes of the smem head tc_setup needs: the mbarriers, the two counters, TMEM base, error.
+constexpr int TC_HEAD_BYTES = 8 * TC_NBAR + 4 * 4;
+
 // One thread initialises the barriers; warp 0 allocates TMEM.  All threads call.
 __device__ __forceinline__ void tc_setup(TcState& t) {
   if (threadIdx.x == 0) {
-    mbar_init(&t.mbar[0], 1);
-    mbar_init(&t.mbar[1], 1);
+    for (int i = 0; i < TC_MAX_PIPE; ++i) {
+      mbar_init(&t.mbar[i], (uint32_t)(blockDim.x / 32 - 1));  // full: one per loader warp
+      mbar_init(&t.mbar[TC_MAX_PIPE + i], 1);                 // empty: the MMAs' commit
+    }
+    mbar_init(&t.mbar[2 * TC_MAX_PIPE], 1);                    // done
     t.uses[0] = t.uses[1] = 0;
     *t.err = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   t.bf16 = false;
   if (threadIdx.x < 32) tmem_alloc(t.tmem, TC_TMEM_COLS);
@@ -222,35 +240,6 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" : : "n"(N_PENDING) : "memory");
 }
 
-// Raw tiles of K-step s into ring slot `raw` (A as [mm][kk], B as [kk][nn], complex), one
-// 8-byte cp.async per element; consecutive threads follow the contiguous global index.
-template <int NT>
-__device__ __forceinline__ void tc_raw_issue(float2* raw, int s, int m0, int n0, int M, int N,
-                                             int K, const float2* A, int sam, int sak,
-                                             const float2* B, int sbk, int sbn) {
-  const int k0 = s * TC_K;
-  float2* rA = raw;
-  float2* rB = raw + TC_M * TC_K;
-#pragma unroll
-  for (int e = threadIdx.x; e < TC_M * TC_K; e += NT) {
-    const int mm = sak == 1 ? e / TC_K : e % TC_M;
-    const int kk = sak == 1 ? e % TC_K : e / TC_M;
-    const int gm = m0 + mm, gk = k0 + kk;
-    const bool in = gm < M && gk < K;
-    cp_async8(smem_addr(rA + mm * TC_K + kk), in ? A + ((size_t)gm * sam + (size_t)gk * sak) : A,
-              in ? 8 : 0);
-  }
-#pragma unroll
-  for (int e = threadIdx.x; e < TC_K * TC_N; e += NT) {
-    const int kk = sbn == 1 ? e / TC_N : e % TC_K;
-    const int nn = sbn == 1 ? e % TC_N : e / TC_K;
-    const int gk = k0 + kk, gn = n0 + nn;
-    const bool in = gk < K && gn < N;
-    cp_async8(smem_addr(rB + kk * TC_N + nn), in ? B + ((size_t)gk * sbk + (size_t)gn * sbn) : B,
-              in ? 8 : 0);
-  }
-}
-
 // Element e of a K-step in the staging order: a warp covers 8 consecutive rows (bits 2-4 of
 // e) by 4 consecutive complex k (bits 0-1), so its 8-byte (re, im) stores fill whole core
 // matrices without bank conflicts.
@@ -259,81 +248,87 @@ __device__ __forceinline__ void tc_elem(int e, int& row, int& kk) {
   row = ((e >> 2) & 7) | ((e >> 6) << 3);
 }
 
-// Raw slot -> canonical hi / lo stage.  A per complex element (TC_M x TC_K); B per real row
-// of B_r^T (2 TC_N x TC_K: row 2n holds (Re b, -Im b), row 2n+1 holds (Im b, Re b)).
-template <int NT>
-__device__ __forceinline__ void tc_stage_from_raw_bf16(const float2* raw, float* st, bool conjA,
-                                                       bool conjB) {
-  const float2* rA = raw;
-  const float2* rB = raw + TC_M * TC_K;
-  // per copy: A 128 x 16 and B 256 x 16 BF16 values
-  uint16_t* Ahi = reinterpret_cast<uint16_t*>(st);
-  uint16_t* Alo = Ahi + TC_M * 16;
-  uint16_t* Bhi = Alo + TC_M * 16;
-  uint16_t* Blo = Bhi + 2 * TC_N * 16;
-#pragma unroll
-  for (int e = threadIdx.x; e < TC_M * TC_K; e += NT) {
-    int mm, kk;
-    tc_elem(e, mm, kk);
-    float2 v = rA[mm * TC_K + kk];
-    if (conjA) v.y = -v.y;
+// One operand element of a stage, loaded from global memory (zero outside the matrices):
+// A element e of the stage (TC_M x TC_K complex) and B element e (2 TC_N real rows x TC_K:
+// row 2n holds (Re b, -Im b), row 2n+1 (Im b, Re b) of B's column n).
+__device__ __forceinline__ float2 tc_load_a(int e, int m0, int k0, int M, int K, const float2* A,
+                                            int sam, int sak, bool conjA) {
+  int mm, kk;
+  tc_elem(e, mm, kk);
+  const int gm = m0 + mm, gk = k0 + kk;
+  // plain loads: the operands may have been written earlier in the same kernel
+  float2 v = (gm < M && gk < K) ? A[(size_t)gm * sam + (size_t)gk * sak] : cz();
+  if (conjA) v.y = -v.y;
+  return v;
+}
+__device__ __forceinline__ float2 tc_load_b(int e, int n0, int k0, int N, int K, const float2* B,
+                                            int sbk, int sbn, bool conjB) {
+  int nr, kk;
+  tc_elem(e, nr, kk);
+  const int gn = n0 + (nr >> 1), gk = k0 + kk;
+  float2 v = (gn < N && gk < K) ? B[(size_t)gk * sbk + (size_t)gn * sbn] : cz();
+  if (conjB) v.y = -v.y;
+  return (nr & 1) ? make_float2(v.y, v.x) : make_float2(v.x, -v.y);
+}
+
+// Element e's hi / lo parts into the canonical stage st (A: which = 0, B: which = 1).
+__device__ __forceinline__ void tc_store(float* st, bool bf, int which, int e, float2 v) {
+  int row, kk;
+  tc_elem(e, row, kk);
+  if (bf) {
+    uint16_t* base = reinterpret_cast<uint16_t*>(st);
+    uint16_t* hi = which == 0 ? base : base + 2 * TC_M * 16;
+    uint16_t* lo = which == 0 ? base + TC_M * 16 : base + 2 * TC_M * 16 + 2 * TC_N * 16;
     uint32_t h, l;
     bf16_split2(v.x, v.y, h, l);
-    const int o = tc_off16(mm, 2 * kk);
-    *reinterpret_cast<uint32_t*>(Ahi + o) = h;
-    *reinterpret_cast<uint32_t*>(Alo + o) = l;
-  }
-#pragma unroll
-  for (int e = threadIdx.x; e < 2 * TC_N * TC_K; e += NT) {
-    int nr, kk;
-    tc_elem(e, nr, kk);
-    float2 v = rB[kk * TC_N + (nr >> 1)];
-    if (conjB) v.y = -v.y;
-    v = (nr & 1) ? make_float2(v.y, v.x) : make_float2(v.x, -v.y);
-    uint32_t h, l;
-    bf16_split2(v.x, v.y, h, l);
-    const int o = tc_off16(nr, 2 * kk);
-    *reinterpret_cast<uint32_t*>(Bhi + o) = h;
-    *reinterpret_cast<uint32_t*>(Blo + o) = l;
+    const int o = tc_off16(row, 2 * kk);
+    *reinterpret_cast<uint32_t*>(hi + o) = h;
+    *reinterpret_cast<uint32_t*>(lo + o) = l;
+  } else {
+    float* hi = which == 0 ? st : st + 2 * TC_A_FLOATS;
+    float* lo = which == 0 ? st + TC_A_FLOATS : st + 2 * TC_A_FLOATS + TC_B_FLOATS;
+    float2 h, l;
+    tf32_split(v.x, h.x, l.x);
+    tf32_split(v.y, h.y, l.y);
+    const int o = tc_off(row, 2 * kk);
+    *reinterpret_cast<float2*>(hi + o) = h;
+    *reinterpret_cast<float2*>(lo + o) = l;
   }
 }
 
-template <int NT>
-__device__ __forceinline__ void tc_stage_from_raw(const float2* raw, float* st, bool conjA,
-                                                  bool conjB) {
-  const float2* rA = raw;
-  const float2* rB = raw + TC_M * TC_K;
-  float* Ahi = st;
-  float* Alo = Ahi + TC_A_FLOATS;
-  float* Bhi = Alo + TC_A_FLOATS;
-  float* Blo = Bhi + TC_B_FLOATS;
+// The three products of one stage (issued by one thread).
+__device__ __forceinline__ void tc_issue_stage(uint32_t tbase, const float* st, bool bf,
+                                               bool first) {
+  constexpr uint32_t IDESC = tc_idesc(128, 256);
+  constexpr uint32_t IDESC16 = tc_idesc_bf16(128, 256);
+  const uint32_t a0 = smem_addr(st);
+  if (bf) {
+    // A hi / lo 4 KB each, B hi / lo 8 KB each; one MMA of K = 16 per product
+    const uint32_t b0 = a0 + 2 * 4096;
+    const uint32_t as[3] = {a0, a0, a0 + 4096};
+    const uint32_t bs[3] = {b0, b0 + 8192, b0};
 #pragma unroll
-  for (int e = threadIdx.x; e < TC_M * TC_K; e += NT) {
-    int mm, kk;
-    tc_elem(e, mm, kk);
-    float2 v = rA[mm * TC_K + kk];
-    if (conjA) v.y = -v.y;
-    float2 h, l;
-    tf32_split(v.x, h.x, l.x);
-    tf32_split(v.y, h.y, l.y);
-    const int o = tc_off(mm, 2 * kk);
-    *reinterpret_cast<float2*>(Ahi + o) = h;
-    *reinterpret_cast<float2*>(Alo + o) = l;
-  }
+    for (int p = 0; p < 3; ++p)
+      tc_mma_bf16(tbase, tc_desc(as[p], 128, 256), tc_desc(bs[p], 128, 256), IDESC16,
+                  (!first || p > 0) ? 1u : 0u);
+  } else {
+    const uint32_t b0 = a0 + 2 * TC_A_FLOATS * 4;
+    const uint32_t as[3] = {a0, a0, a0 + TC_A_FLOATS * 4};
+    const uint32_t bs[3] = {b0, b0 + TC_B_FLOATS * 4, b0};
 #pragma unroll
-  for (int e = threadIdx.x; e < 2 * TC_N * TC_K; e += NT) {
-    int nr, kk;
-    tc_elem(e, nr, kk);
-    float2 v = rB[kk * TC_N + (nr >> 1)];
-    if (conjB) v.y = -v.y;
-    v = (nr & 1) ? make_float2(v.y, v.x) : make_float2(v.x, -v.y);
-    float2 h, l;
-    tf32_split(v.x, h.x, l.x);
-    tf32_split(v.y, h.y, l.y);
-    const int o = tc_off(nr, 2 * kk);
-    *reinterpret_cast<float2*>(Bhi + o) = h;
-    *reinterpret_cast<float2*>(Blo + o) = l;
+    for (int p = 0; p < 3; ++p)
+#pragma unroll
+      for (int h = 0; h < 2; ++h)  // K-chunks 2h, 2h+1: two core matrices (256 B) further
+        tc_mma(tbase, tc_desc(as[p] + h * 256, 128, 512), tc_desc(bs[p] + h * 256, 128, 512),
+               IDESC, (!first || p > 0 || h > 0) ? 1u : 0u);
   }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.release.cta.shared::cta.b64 st, [%0];\n\t}"
+               :
+               : "r"(smem_addr(mbar))
+               : "memory");
 }
 
 template <int NT>
@@ -342,81 +337,130 @@ __device__ void cta_cgemm_tc(int M, int N, int K, const float2* A, int sam, int 
                              int scn, TcState& t) {
   static_assert(NT % 128 == 0, "the epilogue needs whole warp quadrants");
   static_assert(TC_K == 8, "the element mapping covers 8 complex k per step");
-  constexpr uint32_t IDESC = tc_idesc(128, 256);
-  constexpr uint32_t IDESC16 = tc_idesc_bf16(128, 256);
+  constexpr int NL = NT - 32;  // loader threads (warps 1 ..)
+  constexpr int PA = (TC_M * TC_K + NL - 1) / NL;
+  constexpr int PB = (2 * TC_N * TC_K + NL - 1) / NL;
   const bool bf = t.bf16;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t tbase = *t.tmem;
+  const size_t sstride = bf ? (size_t)TC_STAGE16_BYTES : (size_t)TC_STAGE_FLOATS * 4;
+  // the raw ring (rawd stages of every loader thread's elements) sits at the end of the
+  // staging region, the stage buffers before it: three raw stages when two stage buffers
+  // still fit beside them, else two
+  constexpr size_t RAW_STAGE = (size_t)(PA + PB) * NL * sizeof(float2);
+  const int rawd = t.stage_bytes >= TC_RAW * RAW_STAGE + TC_MIN_PIPE * sstride ? TC_RAW : TC_RAW_MIN;
+  int pipe = (int)((t.stage_bytes - rawd * RAW_STAGE) / sstride);
+  pipe = pipe > TC_MAX_PIPE ? TC_MAX_PIPE : pipe;
+  float2* raw = reinterpret_cast<float2*>(reinterpret_cast<char*>(t.stage) + t.stage_bytes -
+                                          rawd * RAW_STAGE);
   const int ksteps = (K + TC_K - 1) / TC_K;
-  float2* ring = reinterpret_cast<float2*>(t.stage + 2 * TC_STAGE_FLOATS);
+  uint64_t* full = t.mbar;
+  uint64_t* empty = t.mbar + TC_MAX_PIPE;
+  uint64_t* done = t.mbar + 2 * TC_MAX_PIPE;
+  __syncthreads();  // earlier writes of the operands; the counters below are settled
+  const int g0 = t.uses[0], tile0 = t.uses[1];
+  int ntile = 0;
   for (int m0 = 0; m0 < M; m0 += TC_M)
     for (int n0 = 0; n0 < N; n0 += TC_N) {
-      __syncthreads();  // the ring's last reads (previous tile) are done
-#pragma unroll
-      for (int r = 0; r < TC_RAW - 1; ++r) {
-        if (r < ksteps)
-          tc_raw_issue<NT>(ring + r * TC_RAW_ELEMS, r, m0, n0, M, N, K, A, sam, sak, B, sbk, sbn);
-        cp_async_commit();
-      }
-      for (int s = 0; s < ksteps; ++s) {
-        const int b = s & 1;
-        float* st = t.stage + b * TC_STAGE_FLOATS;
-        float* Ahi = st;
-        float* Alo = Ahi + TC_A_FLOATS;
-        float* Bhi = Alo + TC_A_FLOATS;
-        float* Blo = Bhi + TC_B_FLOATS;
-        // refill the slot read in the previous step with step s + TC_RAW - 1
-        const int ahead = s + TC_RAW - 1;
-        if (ahead < ksteps)
-          tc_raw_issue<NT>(ring + (ahead % TC_RAW) * TC_RAW_ELEMS, ahead, m0, n0, M, N, K, A,
-                           sam, sak, B, sbk, sbn);
-        cp_async_commit();
-        cp_async_wait<TC_RAW - 1>();  // this thread's copies of step s have landed
-        // the MMAs that last read this canonical buffer must be done before it is overwritten
-        if (tid == 0 && t.uses[b] > 0) {
-          if (!mbar_wait(&t.mbar[b], (uint32_t)((t.uses[b] - 1) & 1))) *t.err = 1;
-        }
-        __syncthreads();
-        if (bf) tc_stage_from_raw_bf16<NT>(ring + (s % TC_RAW) * TC_RAW_ELEMS, st, conjA, conjB);
-        else tc_stage_from_raw<NT>(ring + (s % TC_RAW) * TC_RAW_ELEMS, st, conjA, conjB);
-        fence_async_smem();
-        tc_fence_before();
-        __syncthreads();
-        if (tid == 0) {
-          tc_fence_after();
-          if (bf) {
-            // BF16 copies: A hi / lo 4 KB each, B hi / lo 8 KB each; one MMA of K = 16 per
-            // product (both K core matrices of the stage)
-            const uint32_t a0 = smem_addr(st), b0 = a0 + 2 * 4096;
-            const uint32_t as[3] = {a0, a0, a0 + 4096};
-            const uint32_t bs[3] = {b0, b0 + 8192, b0};
-#pragma unroll
-            for (int p = 0; p < 3; ++p)
-              tc_mma_bf16(tbase, tc_desc(as[p], 128, 256), tc_desc(bs[p], 128, 256), IDESC16,
-                          (s > 0 || p > 0) ? 1u : 0u);
-          } else {
-            const float* As[3] = {Ahi, Ahi, Alo};
-            const float* Bs[3] = {Bhi, Blo, Bhi};
-#pragma unroll
-            for (int p = 0; p < 3; ++p)
-#pragma unroll
-              for (int h = 0; h < 2; ++h) {
-                // K-chunks 2h, 2h+1 of this stage: start two core matrices (256 B) further
-                const uint64_t ad = tc_desc(smem_addr(As[p]) + h * 256, 128, 512);
-                const uint64_t bd = tc_desc(smem_addr(Bs[p]) + h * 256, 128, 512);
-                tc_mma(tbase, ad, bd, IDESC, (s > 0 || p > 0 || h > 0) ? 1u : 0u);
-              }
+      const int gbase = g0 + ntile * ksteps;
+      if (warp == 0) {
+        if (lane == 0) {
+          for (int s = 0; s < ksteps; ++s) {
+            const int g = gbase + s, slot = g % pipe;
+            if (!mbar_wait(&full[slot], (uint32_t)((g / pipe) & 1))) *t.err = 1;
+            tc_fence_after();
+            tc_issue_stage(tbase, reinterpret_cast<const float*>(
+                                      reinterpret_cast<const char*>(t.stage) + slot * sstride),
+                           bf, s == 0);
+            tc_commit(&empty[slot]);
           }
-          tc_commit(&t.mbar[b]);
-          t.uses[b] += 1;
+          tc_commit(done);
+          if (!mbar_wait(done, (uint32_t)((tile0 + ntile) & 1))) *t.err = 1;
         }
+        __syncwarp();
+      } else {
+        // loader warps: each thread copies its own elements of stage s + TC_RAW - 1 into its
+        // own slots of the raw ring (cp.async, zero fill outside the matrices), then splits
+        // its elements of stage s from there into the canonical stage buffer
+        const int lt = tid - 32;
+        // per element: the global offset at k = 0 (-1 outside the matrix) and the packed
+        // stage index e (bits 0-15), k within the stage (16-18) and odd real row (19)
+        int ga[PA], gb[PB], ma[PA], mb[PB];
+#pragma unroll
+        for (int i = 0; i < PA; ++i) {
+          const int e = lt + i * NL;
+          int mm, kk;
+          tc_elem(e < TC_M * TC_K ? e : 0, mm, kk);
+          const bool ok = e < TC_M * TC_K && m0 + mm < M;
+          ga[i] = ok ? (m0 + mm) * sam + kk * sak : -1;
+          ma[i] = e < TC_M * TC_K ? (e | (kk << 16)) : -1;
+        }
+#pragma unroll
+        for (int i = 0; i < PB; ++i) {
+          const int e = lt + i * NL;
+          int nr, kk;
+          tc_elem(e < 2 * TC_N * TC_K ? e : 0, nr, kk);
+          const bool ok = e < 2 * TC_N * TC_K && n0 + (nr >> 1) < N;
+          gb[i] = ok ? kk * sbk + (n0 + (nr >> 1)) * sbn : -1;
+          mb[i] = e < 2 * TC_N * TC_K ? (e | (kk << 16) | ((nr & 1) << 19)) : -1;
+        }
+        const int adv_a = TC_K * sak, adv_b = TC_K * sbk;
+        auto raw_slot = [&](int s, int i) {  // this thread's slot i of raw stage s
+          return raw + ((size_t)((s % rawd) * (PA + PB) + i) * NL + lt);
+        };
+        auto issue = [&](int s) {
+          if (s < ksteps) {
+            const int k0 = s * TC_K;
+#pragma unroll
+            for (int i = 0; i < PA; ++i) {
+              const bool in = ga[i] >= 0 && k0 + ((ma[i] >> 16) & 7) < K;
+              cp_async8(smem_addr(raw_slot(s, i)), in ? A + ((size_t)ga[i] + (size_t)s * adv_a) : A,
+                        in ? 8 : 0);
+            }
+#pragma unroll
+            for (int i = 0; i < PB; ++i) {
+              const bool in = gb[i] >= 0 && k0 + ((mb[i] >> 16) & 7) < K;
+              cp_async8(smem_addr(raw_slot(s, PA + i)),
+                        in ? B + ((size_t)gb[i] + (size_t)s * adv_b) : B, in ? 8 : 0);
+            }
+          }
+          cp_async_commit();
+        };
+        for (int r = 0; r < rawd - 1; ++r) issue(r);
+        for (int s = 0; s < ksteps; ++s) {
+          issue(s + rawd - 1);
+          // this thread's copies of stage s have landed
+          if (rawd == TC_RAW) cp_async_wait<TC_RAW - 1>();
+          else cp_async_wait<TC_RAW_MIN - 1>();
+          const int g = gbase + s, slot = g % pipe;
+          // the MMAs that last read this buffer (stage g - pipe) must have completed
+          if (g >= pipe && lane == 0) {
+            if (!mbar_wait(&empty[slot], (uint32_t)(((g / pipe) - 1) & 1))) *t.err = 1;
+          }
+          __syncwarp();
+          float* st = reinterpret_cast<float*>(reinterpret_cast<char*>(t.stage) + slot * sstride);
+#pragma unroll
+          for (int i = 0; i < PA; ++i) {
+            if (ma[i] < 0) continue;
+            float2 v = *raw_slot(s, i);
+            if (conjA) v.y = -v.y;
+            tc_store(st, bf, 0, ma[i] & 0xFFFF, v);
+          }
+#pragma unroll
+          for (int i = 0; i < PB; ++i) {
+            if (mb[i] < 0) continue;
+            float2 v = *raw_slot(s, PA + i);
+            if (conjB) v.y = -v.y;
+            v = ((mb[i] >> 19) & 1) ? make_float2(v.y, v.x) : make_float2(v.x, -v.y);
+            tc_store(st, bf, 1, mb[i] & 0xFFFF, v);
+          }
+          fence_async_smem();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&full[slot]);
+        }
+        cp_async_wait<0>();
       }
-      cp_async_wait<0>();
-      // epilogue: wait for the last stage (and the one before), read TMEM, write C
-      if (tid == 0) {
-        for (int b = 0; b < 2; ++b)
-          if (t.uses[b] > 0 && !mbar_wait(&t.mbar[b], (uint32_t)((t.uses[b] - 1) & 1))) *t.err = 1;
-      }
+      // epilogue: the tile's accumulators are complete (done) once thread 0 passes
       tc_fence_before();
       __syncthreads();
       tc_fence_after();
@@ -437,7 +481,13 @@ __device__ void cta_cgemm_tc(int M, int N, int K, const float2* A, int sam, int 
       tc_fence_before();
       __syncthreads();
       tc_fence_after();
+      ++ntile;
     }
+  if (tid == 0) {
+    t.uses[0] = g0 + ntile * ksteps;
+    t.uses[1] = tile0 + ntile;
+  }
+  __syncthreads();
 }
 
 }  // namespace dcs
