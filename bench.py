@@ -516,6 +516,74 @@ def measure_ghz(shots=10000, steps=10):
     return out
 
 
+def _run_segments(sim, segs, count, multipath_m=0):
+    """Runs the first `count` segments of a circuit on a context, timing each with CUDA
+    events on the library's stream; returns per-segment ms and the sweeps run."""
+    import torch
+    from circuits import Measure, Reset
+    ms, m0 = [], 0
+    for ops in segs[:count]:
+        a = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        a.record(sim.stream)
+        sim.run_circuit(ops, meas_idx0=m0, max_branches=multipath_m)
+        e.record(sim.stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(e))
+        m0 += sum(isinstance(o, (Measure, Reset)) for o in ops)
+    return ms, sim.counters()[1]
+
+
+def measure_multipath(layers=16, M=64, chi=512, n=32):
+    """The multi-path ensemble workload (n = 32, depth 30, p = 0.05, top-M with M = 64 of a
+    128-slot pool, chi_max = 512): its first `layers` segments, BF16x3 and plain FP32."""
+    import torch
+    import circuits as C
+    from paper_2609_26516_b300 import Simulator
+    circ = C.brickwork(n, 30, 0.05, CIRCUIT_SEED)
+    segs = C.split_layers(circ)
+    out = {"workload": f"multi-path brickwork n={n}, depth 30 (first {layers} segments), p=0.05, "
+                       f"M={M}, chi_max={chi}, s=2"}
+    for prec, name in ((2, "bf16x3"), (0, "fp32")):
+        sim = Simulator(n, chi, 2 * M, circ.n_cbits, tol=TOL, sweeps=SWEEPS, seed=SEED,
+                        precision=prec)
+        sim.init_state(1, multipath=True)
+        ms, sw = _run_segments(sim, segs, layers, M)
+        res = sim.results()
+        bonds = sim.bonds()
+        out[name] = {"ms_total": sum(ms), "segment_ms": [round(x, 1) for x in ms],
+                     "sweeps": int(sw), "sweeps_per_s": sw / (sum(ms) / 1000.0),
+                     "branches": int(res["n_active"]), "retained_p": float(res["p"].sum()),
+                     "max_bond": int(bonds.max()), "min_branch_max_bond": int(bonds.max(axis=1).min()),
+                     "arena_gb": sim.arena_bytes / 1e9}
+        del sim
+        torch.cuda.empty_cache()
+    out["mixed_over_fp32"] = out["fp32"]["ms_total"] / out["bf16x3"]["ms_total"]
+    return out
+
+
+def measure_large_chi(layers=8, shots=64, chi=1024, n=64):
+    """The large-chi workload (n = 64, depth 64, p = 0.02, chi_max = 1024, s = 3, 64 shots):
+    its first `layers` segments (bonds up to 2^8), TF32x3, and the arena it takes."""
+    import torch
+    import circuits as C
+    from paper_2609_26516_b300 import Simulator
+    circ = C.brickwork(n, 64, 0.02, 5)
+    segs = C.split_layers(circ)
+    sim = Simulator(n, chi, shots, circ.n_cbits, tol=TOL, sweeps=3, seed=SEED, precision=1)
+    sim.init_state(shots)
+    ms, sw = _run_segments(sim, segs, layers)
+    bonds = sim.bonds()
+    out = {"workload": f"large-chi brickwork n={n}, depth 64 (first {layers} segments), p=0.02, "
+                       f"chi_max={chi}, s=3, {shots} shots, TF32x3",
+           "arena_gb": sim.arena_bytes / 1e9, "ms_total": sum(ms),
+           "segment_ms": [round(x, 1) for x in ms], "sweeps": int(sw),
+           "max_bond": int(bonds.max()), "F_mean": float(sim.results()["F"].mean())}
+    del sim
+    torch.cuda.empty_cache()
+    return out
+
+
 def measure_cgemm(chi, batch):
     """The contraction primitive alone at the site-contraction shape of chi_max: M = 2 chi,
     N = chi, K = 4 chi complex (F = T2 R^T with an MPO bond of 4), one problem per CTA,
@@ -555,6 +623,24 @@ def measure_cgemm(chi, batch):
     return out
 
 
+def run_profile_case(args):
+    """The first segments of the workload with a small shot count: the last compression
+    launch is a saturated one of the workload's shape, for a profiler to capture."""
+    import torch
+    from paper_2609_26516_b300 import Simulator
+    circ, segs = workload()
+    sim = Simulator(N_QUBITS, CHI_MAX, args.shots, circ.n_cbits, tol=TOL, sweeps=SWEEPS,
+                    seed=SEED, precision=args.precision)
+    sim.init_state(args.shots)
+    run = SegmentRunner(sim, segs, args.shots, 0)
+    for k in range(args.profile_segments):
+        run.run(k)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": f"{args.profile_segments} segments", "shots": args.shots,
+                      "precision": args.precision, "max_bond": int(sim.bonds().max()),
+                      "launches": sim.launches}), flush=True)
+
+
 # ----------------------------------------------------------------------------- main
 
 
@@ -570,9 +656,16 @@ def main():
                          "steps of the mixed arm)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--profile-segments", type=int, default=0,
+                    help="run only the first K segments of the workload with --shots shots at "
+                         "--precision (a small case for a profiler) and exit")
+    ap.add_argument("--precision", type=int, default=PREC_TF32X3)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.profile_segments > 0:
+        run_profile_case(args)
         return
     args.warmup = max(args.warmup, 3)
 
@@ -710,6 +803,9 @@ def main():
     if world == 1 and not args.no_extras:
         line["ghz64"] = measure_ghz()
         line["contraction"] = measure_cgemm(256, 148)
+        line["contraction_chi512"] = measure_cgemm(512, 148)
+        line["multipath"] = measure_multipath()
+        line["large_chi"] = measure_large_chi()
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
