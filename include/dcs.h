@@ -195,6 +195,15 @@ dcs_status_t dcs_collapse(dcs_ctx_t ctx, int qubit, int cbit, const uint8_t* out
  * Fails with DCS_ERR_OOM (state unchanged) if the children exceed the pool. */
 dcs_status_t dcs_branch_split(dcs_ctx_t ctx, int qubit, int cbit, double eps);
 
+/* Adaptive pruning of the branch ensemble (the paper's conclusion names pruning strategies
+ * beyond top-M as future work).  With p_min > 0, every later branch split (dcs_branch_split,
+ * and the measurements of dcs_run_circuit in multi-path mode) drops the children whose path
+ * probability p_gamma p_m is below p_min, after the top-M rule; the child that comes first in
+ * the key order of dcs_branch_topk always stays, so the ensemble never empties.  The dropped
+ * mass is missing from the sum of p, as with top-M.  p_min = 0 (the default) turns it off;
+ * p_min outside [0, 1) is refused with DCS_ERR_INVALID.  Host-only, takes effect at once. */
+dcs_status_t dcs_set_pruning(dcs_ctx_t ctx, double p_min);
+
 /* TopKByWeight (Alg. 2): if more than M branches are active keep the M with the largest
  * p_gamma, compared through the key round(p / (1e-5 * max p)); equal keys keep list order.
  * The retained branches keep their relative order; p is not renormalised. */

@@ -9,7 +9,8 @@ p *= p_m, c_j := m.
 Multi path (Alg. 2, Sec. "Multi-path simulation"): every branch compresses its chunk; at a
 measurement every branch spawns the children m in {0, 1} with p_m > P_EPS (m = 0 first,
 parents in list order) with p_{gamma m} = p_gamma p_m, F copied; then, if more than M
-branches are active, the M with the largest p are kept (ties: ``topk_select``).
+branches are active, the M with the largest p are kept (ties: ``topk_select``), and with
+adaptive pruning (p_min > 0) branches below p_min are dropped (``prune_select``).
 """
 from __future__ import annotations
 
@@ -22,7 +23,7 @@ from circuits import Circuit, Measure
 from .layers import blocks_mpo, chunk_blocks, chunk_circuit
 from .mps import MPS, collapse, compress, measure_probs, product_zero
 from .philox import uniform
-from .statevector import FLAG_WINDOW, P_EPS, topk_select
+from .statevector import FLAG_WINDOW, P_EPS, prune_select
 
 
 @dataclass
@@ -112,7 +113,7 @@ class MPBranch:
 
 
 def run_multi_path(circ: Circuit, prm: Params, M: Optional[int] = None,
-                   max_steps: Optional[int] = None) -> List[MPBranch]:
+                   max_steps: Optional[int] = None, p_min: float = 0.0) -> List[MPBranch]:
     n, steps = chunk_circuit(circ, prm.k)
     Lst = [MPBranch(1.0, 1.0, np.zeros(circ.n_cbits, dtype=np.int64), product_zero(n))]
     for si, st in enumerate(steps):
@@ -132,8 +133,8 @@ def run_multi_path(circ: Circuit, prm: Params, M: Optional[int] = None,
                         c[st.cbit] = m
                         nxt.append(MPBranch(b.p * pm, b.F, c, child, b.path + [m]))
             Lst = nxt
-            if M is not None and len(Lst) > M:
-                keep = topk_select([b.p for b in Lst], M)
+            if (M is not None and len(Lst) > M) or p_min > 0.0:
+                keep = prune_select([b.p for b in Lst], M, p_min)
                 Lst = [Lst[i] for i in keep]
         else:
             for b in Lst:

@@ -172,10 +172,26 @@ def topk_select(ps: List[float], M: int, tau: float = 1e-5) -> List[int]:
     return sorted(order[:M])
 
 
-def run_multi_path(circ: Circuit, M: Optional[int] = None) -> List[Branch]:
+def prune_select(ps: List[float], M: Optional[int], p_min: float = 0.0,
+                 tau: float = 1e-5) -> List[int]:
+    """Indices (in list order) of the branches kept after a measurement: the top-M rule of
+    Alg. 2 (``topk_select``; all when M is None), then adaptive pruning (the paper names
+    pruning beyond top-M as future work; reading: a branch whose path probability is below
+    the absolute threshold p_min is dropped, except the first branch of the key order, so
+    the list never empties)."""
+    keep = list(range(len(ps))) if (M is None or len(ps) <= M) else topk_select(ps, M, tau)
+    if p_min <= 0.0 or not keep:
+        return keep
+    pmax = max(ps)
+    keys = {i: int(np.floor(ps[i] / (tau * pmax) + 0.5)) for i in keep}
+    first = min(keep, key=lambda i: (-keys[i], i))
+    return [i for i in keep if ps[i] >= p_min or i == first]
+
+
+def run_multi_path(circ: Circuit, M: Optional[int] = None, p_min: float = 0.0) -> List[Branch]:
     """Alg. 2 on the exact state vector: every outcome with p_m > P_EPS spawns a child
-    (m = 0 child before m = 1, parents in list order); after each measurement, if more
-    than M branches are active keep the M with the largest p (``topk_select``)."""
+    (m = 0 child before m = 1, parents in list order); after each measurement the kept
+    branches are chosen by ``prune_select`` (top-M, then the probability threshold)."""
     circ = lower_resets(circ)
     L = [Branch(1.0, np.zeros(circ.n_cbits, dtype=np.int64), zero_state(circ.n_qubits))]
     for op in circ.ops:
@@ -196,8 +212,8 @@ def run_multi_path(circ: Circuit, M: Optional[int] = None) -> List[Branch]:
                         nxt.append(Branch(b.p * pm, c, project(b.psi, op.qubit, m, rm),
                                           b.path + [m]))
             L = nxt
-            if M is not None and len(L) > M:
-                keep = topk_select([b.p for b in L], M)
+            if (M is not None and len(L) > M) or p_min > 0.0:
+                keep = prune_select([b.p for b in L], M, p_min)
                 L = [L[i] for i in keep]
         else:
             raise TypeError(op)

@@ -59,6 +59,7 @@ SIGNATURES = {
     "dcs_collapse": (_c.c_int, [_P, _c.c_int, _c.c_int, _c.POINTER(_c.c_uint8)]),
     "dcs_branch_split": (_c.c_int, [_P, _c.c_int, _c.c_int, _c.c_double]),
     "dcs_branch_topk": (_c.c_int, [_P, _c.c_int]),
+    "dcs_set_pruning": (_c.c_int, [_P, _c.c_double]),
     "dcs_get_results": (_c.c_int, [_P, _P, _P, _P, _c.POINTER(_c.c_int), _P]),
     "dcs_get_bonds": (_c.c_int, [_P, _P, _c.POINTER(_c.c_int)]),
     "dcs_export_mps": (_c.c_int, [_P, _c.c_int, _P, _c.POINTER(_c.c_size_t)]),

@@ -127,6 +127,7 @@ struct dcs_ctx_s {
   uint64_t launches = 0;
   uint64_t uploaded = 0;
   int multipath = 0;
+  double prune_pmin = 0.0;  // adaptive pruning threshold of branch splits (0: off)
   // Upper bound on every bond dimension any slot can have, per bond, tracked from the
   // circuit alone: a two-qubit block on (q, q+1) makes bond q+1 at most
   // min(chi_max, 2 ub[q], 2 ub[q+2], 2^min(q+1, n-q-1)) (the truncated SVD of a
@@ -284,7 +285,8 @@ dcs_status_t run_steps(dcs_ctx_t c, const Program& P, int max_branches,
                        c->stream);
         c->launches++;
         int l = 0;
-        launch_branch_split(c->dev, m.q, m.cbit, 1e-12, max_branches, c->stream, &l);
+        launch_branch_split(c->dev, m.q, m.cbit, 1e-12, max_branches, c->prune_pmin, c->stream,
+                            &l);
         c->launches += l;
         if ((st = post_launch(c, "branch split")) != DCS_OK) return st;
       }
@@ -458,9 +460,15 @@ dcs_status_t dcs_branch_split(dcs_ctx_t c, int qubit, int cbit, double eps) {
   dcs_status_t st = measure_common(c, qubit, cbit, 0, MEAS_PROB, nullptr, nullptr);
   if (st != DCS_OK) return st;
   int l = 0;
-  launch_branch_split(c->dev, qubit, cbit, eps, 0, c->stream, &l);
+  launch_branch_split(c->dev, qubit, cbit, eps, 0, c->prune_pmin, c->stream, &l);
   c->launches += l;
   return post_launch(c, "branch split");
+}
+
+dcs_status_t dcs_set_pruning(dcs_ctx_t c, double p_min) {
+  if (!c || !(p_min >= 0.0) || p_min >= 1.0) return fail(c, DCS_ERR_INVALID, "p_min must lie in [0, 1)");
+  c->prune_pmin = p_min;
+  return DCS_OK;
 }
 
 dcs_status_t dcs_branch_topk(dcs_ctx_t c, int M) {

@@ -158,7 +158,7 @@ __device__ __forceinline__ long long topk_key(double p, double pmax) {
 // kept when p_m > eps), optionally pruned to M, assigned to slots: the first kept child of a
 // parent inherits the parent's slot, a second one takes a free slot (copied from the
 // parent before the collapses run).
-__global__ void k_branch_plan(DevCtx c, double eps, int M, int cbit) {
+__global__ void k_branch_plan(DevCtx c, double eps, int M, int cbit, double pmin) {
   __shared__ int s_nchild[1024];
   __shared__ int s_start[1025];
   __shared__ double s_cp[2048];
@@ -215,16 +215,20 @@ __global__ void k_branch_plan(DevCtx c, double eps, int M, int cbit) {
     s_pmax = pm;
   }
   __syncthreads();
+  // kept: the top M by key (all when M = 0 or no more than M), then, with adaptive pruning,
+  // only those with p >= pmin (the first of the key order always stays)
+  const bool topm = M > 0 && nch > M;
   for (int i = threadIdx.x; i < nch; i += blockDim.x) {
     int keep = 1;
-    if (M > 0 && nch > M) {
+    if (topm || pmin > 0.0) {
       const long long ki = topk_key(s_cp[i], s_pmax);
       int rank = 0;
       for (int j = 0; j < nch; ++j) {
         const long long kj = topk_key(s_cp[j], s_pmax);
         rank += (kj > ki) || (kj == ki && j < i);
       }
-      keep = rank < M;
+      keep = topm ? rank < M : 1;
+      if (pmin > 0.0 && rank > 0 && !(s_cp[i] >= pmin)) keep = 0;
     }
     s_keep[i] = keep;
   }
@@ -411,9 +415,9 @@ void launch_measure(const DevCtx& c, int tile_chi, const DMeas* meas, int n_meas
   }
 }
 
-void launch_branch_split(const DevCtx& c, int q, int cbit, double eps, int M, cudaStream_t s,
-                         int* launches) {
-  k_branch_plan<<<1, 256, 0, s>>>(c, eps, M, cbit);
+void launch_branch_split(const DevCtx& c, int q, int cbit, double eps, int M, double pmin,
+                         cudaStream_t s, int* launches) {
+  k_branch_plan<<<1, 256, 0, s>>>(c, eps, M, cbit, pmin);
   k_branch_copy<<<c.n_slots, 128, 0, s>>>(c);
   k_branch_collapse<<<c.n_slots, 128, 0, s>>>(c, q, cbit);
   *launches += 3;

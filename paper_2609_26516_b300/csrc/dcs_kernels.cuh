@@ -133,7 +133,9 @@ void launch_compress(const DevCtx& c, int tile_chi, const DLayer* L, const DBloc
                      const DGate1* G1, const DCond* C, double* fid_out, cudaStream_t s);
 void launch_measure(const DevCtx& c, int tile_chi, const DMeas* meas, int n_meas, int mode,
                     const uint8_t* forced, double* p0_out, cudaStream_t s);
-void launch_branch_split(const DevCtx& c, int q, int cbit, double eps, int M,
+// pmin > 0: adaptive pruning, children with p < pmin are dropped (the first of the key
+// order stays)
+void launch_branch_split(const DevCtx& c, int q, int cbit, double eps, int M, double pmin,
                          cudaStream_t s, int* launches);
 void launch_branch_topk(const DevCtx& c, int M, cudaStream_t s);
 int fused_chi(int chi_max);          // shared-memory tile for chi_max (0 if above 32)

@@ -195,6 +195,9 @@ class Simulator:
     def branch_split(self, qubit: int, cbit: int, eps: float = 1e-12):
         self._check(self.lib.dcs_branch_split(self.ctx, qubit, cbit, eps))
 
+    def set_pruning(self, p_min: float):
+        self._check(self.lib.dcs_set_pruning(self.ctx, p_min))
+
     def branch_topk(self, M: int):
         self._check(self.lib.dcs_branch_topk(self.ctx, M))
 

@@ -420,3 +420,38 @@ def test_teleport_bob_measurement_eight_paths():
         assert abs(res["p"][i] - want) < g["printed_abs_tol"]
     p0 = sum(res["p"][i] for i in range(8) if res["bits"][i][2] == 0)
     assert abs(p0 - g["bob_p0"]) < g["printed_abs_tol"]
+
+
+def test_multi_path_adaptive_pruning():
+    # branches whose path probability falls below p_min are dropped after each measurement
+    # (beyond top-M); branch by branch against the oracle's ensemble with the same rule
+    circ = C.brickwork(10, 8, 0.25, 8)
+    p_min = 2e-3
+    ref = D.run_multi_path(circ, D.Params(chi_max=16), M=32, p_min=p_min)
+    full = D.run_multi_path(circ, D.Params(chi_max=16), M=32)
+    sim = _sim(10, 16, 64, circ.n_cbits)
+    sim.set_pruning(p_min)
+    sim.init_state(1, multipath=True)
+    sim.run_circuit(circ, max_branches=32)
+    res = sim.results()
+    assert res["n_active"] == len(ref) < len(full)
+    for i, b in enumerate(ref):
+        assert res["bits"][i].tolist() == [int(x) for x in b.c]
+        assert abs(res["p"][i] - b.p) < P_TOL
+        assert _state_fid(sim, i, b.mps) >= 1 - STATE_TOL
+    assert np.all(res["p"] >= p_min) or res["n_active"] == 1
+
+
+def test_final_register_sampling_distribution():
+    # every qubit measured at the end of a random circuit: per-shot outcomes bit-exact with
+    # the oracle, and the empirical distribution of 8192 shots close to the exact one
+    n = 6
+    base = C.brickwork(n, 6, 0.0, 12)
+    circ = C.Circuit(n, n, base.ops + [C.Measure(q, q) for q in range(n)])
+    shots = 8192
+    _, res = _single_path_parity(circ, 8, shots, list(range(0, shots, 1024)))
+    psi = SV.run_single_path(base, 1, 0).psi.reshape(-1)
+    exact = np.abs(psi) ** 2
+    idx = (res["bits"].astype(np.int64) * (1 << np.arange(n - 1, -1, -1))).sum(axis=1)
+    emp = np.bincount(idx, minlength=2 ** n) / shots
+    assert 0.5 * np.abs(emp - exact).sum() < 0.06

@@ -264,3 +264,31 @@ def test_general_boolean_conditions_by_enumeration():
             assert SV.cond_holds(cond, creg) == bool(fn(*bits))
             assert SV.cond_holds(C.Cond((1, 3, 4), "or", 1), creg) == any(bits)
             assert SV.cond_holds(C.Cond((1, 3, 4), "or", 0), creg) == (not any(bits))
+
+
+def test_adaptive_pruning_selection_and_ensemble():
+    # prune_select: the top-M rule, then branches below p_min dropped except the first of
+    # the key order; by brute force on a list
+    ps = [0.30, 0.01, 0.20, 0.004, 0.20, 0.09]
+    assert SV.prune_select(ps, None, 0.05) == [0, 2, 4, 5]
+    assert SV.prune_select(ps, 3, 0.05) == [0, 2, 4]
+    assert SV.prune_select(ps, None, 0.5) == [0]          # never empty: the first stays
+    assert SV.prune_select(ps, None, 0.0) == list(range(6))
+    # the pruned ensemble is the full one with every branch below p_min removed at each
+    # measurement: each survivor has the same p and register as in the unpruned run, and
+    # each unpruned leaf whose prefixes all stayed above p_min survives
+    circ = C.brickwork(6, 5, 0.4, 8)
+    full = SV.run_multi_path(circ)
+    pruned = SV.run_multi_path(circ, p_min=0.02)
+    byp = {tuple(b.path): b.p for b in full}
+    assert 0 < len(pruned) < len(full)
+    for b in pruned:
+        assert abs(byp[tuple(b.path)] - b.p) < 1e-12
+        assert b.p >= 0.02 or len(pruned) == 1
+    # a leaf survives iff every prefix probability of its path is >= p_min; recompute the
+    # prefix probabilities from the full run's branch list at each measurement depth
+    def prefix_p(path):
+        return sum(bb.p for bb in full if tuple(bb.path[:len(path)]) == tuple(path))
+    for b in full:
+        ok = all(prefix_p(b.path[:d]) >= 0.02 for d in range(1, len(b.path) + 1))
+        assert ok == (tuple(b.path) in {tuple(x.path) for x in pruned})
