@@ -660,12 +660,18 @@ def main():
                     help="run only the first K segments of the workload with --shots shots at "
                          "--precision (a small case for a profiler) and exit")
     ap.add_argument("--precision", type=int, default=PREC_TF32X3)
+    ap.add_argument("--cgemm", type=int, nargs=2, metavar=("CHI", "BATCH"), default=None,
+                    help="only the contraction primitive at the site shape of CHI, BATCH "
+                         "problems (a small case for a profiler)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
         return
     if args.profile_segments > 0:
         run_profile_case(args)
+        return
+    if args.cgemm is not None:
+        print(json.dumps(measure_cgemm(*args.cgemm)), flush=True)
         return
     args.warmup = max(args.warmup, 3)
 
