@@ -15,8 +15,8 @@ follow, in circuit order (when the circuit runs out it is restarted, untimed).
 
 Metric: one-site compression sweeps per second over all shots (the line's value, mixed
 precision: TF32x3 tensor-core contractions with an FP32 last sweep), the plain FP32 path
-timed on the same segments beside it, shots/s, and the error of each against the FP64 oracle
-on one sampled compression step.
+timed on the same segments beside it (and the BF16x3 mode), shots/s, and the error of each
+against the FP64 oracle on one sampled compression step.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl dcs|reference]
 
@@ -51,7 +51,7 @@ CIRCUIT_SEED = 3
 SEED = 1
 PREFIX = 14          # segments that grow the bonds to chi_max (untimed preparation)
 SAMPLE_SEGMENT = 16  # the compression step compared with the oracle
-PREC_FP32, PREC_TF32X3 = 0, 1
+PREC_FP32, PREC_TF32X3, PREC_BF16X3 = 0, 1, 2
 WORKLOAD = (f"random dynamic brickwork n={N_QUBITS}, depth {DEPTH}, p={P_MEAS}, "
             f"chi_max={CHI_MAX}, tol={TOL:g}, s={SWEEPS}, single-path, {SHOTS} shots/GPU "
             "batched; step = one circuit segment (one compression + its measurements)")
@@ -746,6 +746,14 @@ def main():
                           sum(r["sweeps"] for r in recs32) / len(recs32), dist, f"cuda:{local}")
     same = [r["ms"] for r in recs[: len(recs32)]]
     speedup = (sum(ms32) / len(ms32)) / (sum(same) / len(same))
+    # ---- BF16x3 arm on the same segments
+    sim16, run16, recs16, _ = time_arm(PREC_BF16X3, segs, args.shots, shot0, args.warmup, n32,
+                                       local, flush, None, barrier)
+    del sim16, run16
+    torch.cuda.empty_cache()
+    ms16 = [r["ms"] for r in recs16]
+    _, value16 = job_rate(sum(ms16) / len(ms16) / 1000.0, world,
+                          sum(r["sweeps"] for r in recs16) / len(recs16), dist, f"cuda:{local}")
     wall = time.perf_counter() - t_prep
 
     if rank != 0:
@@ -760,6 +768,7 @@ def main():
     if world == 1 and not args.no_cpu_baseline:
         ref = oracle_sample()
         err = {"tf32x3": sample_error(PREC_TF32X3, ref, local),
+               "bf16x3": sample_error(PREC_BF16X3, ref, local),
                "fp32": sample_error(PREC_FP32, ref, local)}
         cores = _blas_threads()
         rec = oracle_steps(ref["run"], segs, SAMPLE_SEGMENT, 4, seconds=20.0)
@@ -787,6 +796,10 @@ def main():
         "fp32": {"value": value32, "unit": "sweeps/s", "steps": len(recs32),
                  "ms_per_step": sum(ms32) / len(ms32),
                  "segments_timed": [r["segment"] for r in recs32]},
+        "bf16x3": {"value": value16, "unit": "sweeps/s", "steps": len(recs16),
+                   "ms_per_step": sum(ms16) / len(ms16),
+                   "segments_timed": [r["segment"] for r in recs16],
+                   "over_fp32": (sum(ms32) / len(ms32)) / (sum(ms16) / len(ms16))},
         "mixed_over_fp32": speedup,
         "error_vs_oracle": err,
         "F_mean_after_e2e": F_mean,
