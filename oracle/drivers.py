@@ -20,7 +20,8 @@ from typing import List, Optional
 import numpy as np
 
 from circuits import Circuit, Measure
-from .layers import blocks_mpo, chunk_blocks, chunk_circuit
+from .layers import (blocks_mpo, chunk_blocks, chunk_circuit, chunk_sublayer_blocks,
+                     compose_mpo)
 from .mps import MPS, collapse, compress, measure_probs, product_zero
 from .philox import uniform
 from .statevector import FLAG_WINDOW, P_EPS, prune_select
@@ -31,7 +32,8 @@ class Params:
     chi_max: int = 8
     tol: float = 1e-10
     sweeps: int = 2
-    k: int = 0  # maximum ops per chunk (0: one-layer rule only)
+    k: int = 0  # maximum ops per chunk (0: no limit)
+    layers: int = 1  # sub-layers per chunk (1: the one-layer rule)
 
 
 @dataclass
@@ -44,6 +46,18 @@ class ShotResult:
     p0s: List[float]
     flagged: List[int]
     fids: List[float]
+
+
+def _chunk_operator(n, chunk, c, layers):
+    """The chunk's blocks and MPO for register c: one layer of disjoint blocks, or with
+    several sub-layers the list of their blocks and the composed MPO."""
+    if layers <= 1:
+        blocks, empty = chunk_blocks(n, chunk, c)
+        return blocks, blocks_mpo(n, blocks), empty
+    sub, empty = chunk_sublayer_blocks(n, chunk, c)
+    if len(sub) == 1:
+        return sub[0], blocks_mpo(n, sub[0]), empty
+    return sub, compose_mpo([blocks_mpo(n, b) for b in sub]), empty
 
 
 class SinglePathRun:
@@ -61,7 +75,8 @@ class SinglePathRun:
         self.sweeps_run = 0
 
     def run(self, ops, stop_after_flag: bool = False) -> None:
-        n, steps = chunk_circuit(Circuit(self.n, self.n_cbits, list(ops)), self.prm.k)
+        n, steps = chunk_circuit(Circuit(self.n, self.n_cbits, list(ops)), self.prm.k,
+                                 self.prm.layers)
         for st in steps:
             if isinstance(st, Measure):
                 r0, r1 = measure_probs(self.mps, st.qubit)
@@ -82,11 +97,11 @@ class SinglePathRun:
                 if self.flagged and stop_after_flag:
                     return
             else:
-                blocks, empty = chunk_blocks(n, st, self.c)
+                blocks, W, empty = _chunk_operator(n, st, self.c, self.prm.layers)
                 if empty:
                     continue
-                self.mps, info = compress(self.mps, blocks, blocks_mpo(n, blocks),
-                                          self.prm.chi_max, self.prm.tol, self.prm.sweeps)
+                self.mps, info = compress(self.mps, blocks, W, self.prm.chi_max, self.prm.tol,
+                                          self.prm.sweeps)
                 self.F *= info.f
                 self.fids.append(info.f)
                 self.sweeps_run += len(info.fidelities_per_sweep)
@@ -114,7 +129,7 @@ class MPBranch:
 
 def run_multi_path(circ: Circuit, prm: Params, M: Optional[int] = None,
                    max_steps: Optional[int] = None, p_min: float = 0.0) -> List[MPBranch]:
-    n, steps = chunk_circuit(circ, prm.k)
+    n, steps = chunk_circuit(circ, prm.k, prm.layers)
     Lst = [MPBranch(1.0, 1.0, np.zeros(circ.n_cbits, dtype=np.int64), product_zero(n))]
     for si, st in enumerate(steps):
         if max_steps is not None and si >= max_steps:
@@ -138,11 +153,10 @@ def run_multi_path(circ: Circuit, prm: Params, M: Optional[int] = None,
                 Lst = [Lst[i] for i in keep]
         else:
             for b in Lst:
-                blocks, empty = chunk_blocks(n, st, b.c)
+                blocks, W, empty = _chunk_operator(n, st, b.c, prm.layers)
                 if empty:
                     continue
-                b.mps, info = compress(b.mps, blocks, blocks_mpo(n, blocks), prm.chi_max,
-                                       prm.tol, prm.sweeps)
+                b.mps, info = compress(b.mps, blocks, W, prm.chi_max, prm.tol, prm.sweeps)
                 b.F *= info.f
     return Lst
 

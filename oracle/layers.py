@@ -26,20 +26,26 @@ from .statevector import cond_holds, lower_resets
 Step = Union[List[Gate], Measure]
 
 
-def chunk_circuit(circ: Circuit, k: int = 0) -> Tuple[int, List[Step]]:
+def chunk_circuit(circ: Circuit, k: int = 0, layers: int = 1) -> Tuple[int, List[Step]]:
     """Split the (reset-lowered) circuit into unitary chunks (lists of Gates) and
-    measurements, in order.  Returns (n_qubits, steps)."""
+    measurements, in order.  Returns (n_qubits, steps).
+
+    A chunk holds up to ``layers`` sub-layers: a two-qubit gate touching a qubit that already
+    carries a two-qubit gate of the current sub-layer opens a new sub-layer, or closes the
+    chunk when it has ``layers`` of them (``layers`` = 1: the one-layer rule).  Measurements
+    and the k-operation limit close it as well."""
     circ = lower_resets(circ)
     n = circ.n_qubits
     steps: List[Step] = []
     cur: List[Gate] = []
-    busy = set()  # qubits carrying a two-qubit gate of the current chunk
+    busy = set()  # qubits carrying a two-qubit gate of the current sub-layer
+    nsub = 1
 
     def close():
-        nonlocal cur, busy
+        nonlocal cur, busy, nsub
         if cur:
             steps.append(cur)
-        cur, busy = [], set()
+        cur, busy, nsub = [], set(), 1
 
     for op in circ.ops:
         if isinstance(op, Measure):
@@ -53,7 +59,11 @@ def chunk_circuit(circ: Circuit, k: int = 0) -> Tuple[int, List[Step]]:
             if abs(a - b) != 1:
                 raise ValueError("only nearest-neighbour two-qubit gates are supported")
             if a in busy or b in busy:
-                close()
+                if nsub < layers:
+                    nsub += 1
+                    busy = set()
+                else:
+                    close()
         elif len(op.qubits) != 1:
             raise ValueError("gates act on one or two qubits")
         if k > 0 and len(cur) >= k:
@@ -63,6 +73,22 @@ def chunk_circuit(circ: Circuit, k: int = 0) -> Tuple[int, List[Step]]:
             busy.update(op.qubits)
     close()
     return n, steps
+
+
+def sublayers(chunk: List[Gate]) -> List[List[Gate]]:
+    """A chunk's gates cut into sub-layers by the one-layer rule (a two-qubit gate touching a
+    qubit that carries a two-qubit gate of the current sub-layer starts the next one);
+    single-qubit gates stay with the sub-layer they follow."""
+    out: List[List[Gate]] = [[]]
+    busy = set()
+    for g in chunk:
+        if len(g.qubits) == 2 and (set(g.qubits) & busy):
+            out.append([])
+            busy = set()
+        out[-1].append(g)
+        if len(g.qubits) == 2:
+            busy.update(g.qubits)
+    return out
 
 
 def _pair_matrix(g: Gate, q: int) -> np.ndarray:
@@ -137,3 +163,29 @@ def chunk_unitary_dense(n: int, W) -> np.ndarray:
         T = np.einsum("aoiD,DpjE->aopijE", T.reshape(1, 2 ** j, 2 ** j, -1), W[j])
         T = T.reshape(1, 2 ** (j + 1), 2 ** (j + 1), -1)
     return T.reshape(2 ** n, 2 ** n)
+
+
+def chunk_sublayer_blocks(n: int, chunk: List[Gate], c: np.ndarray):
+    """The blocks of each sub-layer of a chunk for register c (``chunk_blocks`` per
+    sub-layer), and whether every gate of the chunk is skipped."""
+    subs = sublayers(chunk)
+    blocks = [chunk_blocks(n, sub, c)[0] for sub in subs]
+    applied = [g for g in chunk if cond_holds(g.cond, c)]
+    return blocks, len(applied) == 0
+
+
+def compose_mpo(Ws):
+    """MPO of sub-layers applied in order (Ws[0] first): per site
+    W[(d_1 .. d_L), s, t, (e_1 .. e_L)] = sum over the inner physical indices of
+    W_L[d_L, s, u, e_L] ... W_1[d_1, v, t, e_1]; bond dimensions multiply."""
+    out = Ws[0]
+    for W2 in Ws[1:]:
+        nxt = []
+        for a, b in zip(out, W2):
+            # a: [Da, s', t, Ea] applied first; b: [Db, s, s', Eb]
+            # bonds grouped (a's, b's) on both sides of the site
+            c = np.einsum("dsue,auvf->adsvfe", b, a)
+            Da, Db, Ea, Eb = a.shape[0], b.shape[0], a.shape[3], b.shape[3]
+            nxt.append(c.reshape(Da * Db, 2, 2, Ea * Eb))
+        out = nxt
+    return out

@@ -218,15 +218,32 @@ def initial_guess(A: MPS, blocks, chi_max: int, tol: float):
     return B, kept, exact
 
 
+def initial_guess_layers(A: MPS, sub_blocks, chi_max: int, tol: float):
+    """The initial guess of a chunk of several sub-layers (each a list of disjoint blocks):
+    ``initial_guess`` applied sub-layer after sub-layer, each starting from the state and
+    centre the previous one left; the kept weight fractions of all truncations, and whether
+    none discarded more than tol."""
+    B, kept, exact = A, [], True
+    for blocks in sub_blocks:
+        B, k, e = initial_guess(B, blocks, chi_max, tol)
+        kept += k
+        exact = exact and e
+    return B, kept, exact
+
+
 def compress(A: MPS, blocks, W, chi_max: int, tol: float, sweeps: int, skip_exact: bool = True):
     """CompressionStep (Sec. "Simulating unitary quantum circuits with DMRG") with the
-    readings in the module header.  ``blocks`` is the chunk as [(q, 4x4 or 2x2 matrix)],
+    readings in the module header.  ``blocks`` is the chunk as [(q, 4x4 or 2x2 matrix)], or
+    for a chunk of several sub-layers a list of such lists (the guess takes them in order),
     W its MPO.  A is not modified.  Returns (B, info), B normalised; after the sweeps its
     centre is at the end the last sweep ran to; an exact guess (reading 2) is returned as it
     is unless ``skip_exact`` is False, which runs the sweeps on it all the same."""
     assert sweeps >= 1
     n = A.n
-    B0, kept, exact = initial_guess(A, blocks, chi_max, tol)
+    if blocks and isinstance(blocks[0], list):  # a chunk of several sub-layers
+        B0, kept, exact = initial_guess_layers(A, blocks, chi_max, tol)
+    else:
+        B0, kept, exact = initial_guess(A, blocks, chi_max, tol)
     if exact and skip_exact:
         f = float(np.prod(kept)) if kept else 1.0
         return B0, CompressInfo(f, [], kept)

@@ -406,3 +406,92 @@ def test_single_path_run_in_segments_equals_one_pass():
     two = r.result()
     assert two.outcomes == one.outcomes and two.fids == one.fids and two.p == one.p
     np.testing.assert_allclose(M.to_dense(two.mps), M.to_dense(one.mps), atol=1e-12)
+
+
+# ----------------------------------------------------------------------------- multi-layer
+# Chunks of several layers (Sec. "Handling unitary chunks in dynamic circuits": a chunk
+# holds up to k operations), with the composed MPO (bond dimensions multiply) and the guess
+# taken sub-layer by sub-layer.
+
+
+def _dense_of_gates(n, gates, c):
+    want = np.zeros((2 ** n, 2 ** n), dtype=np.complex128)
+    for col in range(2 ** n):
+        e = np.zeros(2 ** n, dtype=np.complex128)
+        e[col] = 1
+        v = e.reshape((2,) * n)
+        for g in gates:
+            if SV.cond_holds(g.cond, c):
+                v = SV.apply_gate(v, g.qubits, g.matrix)
+        want[:, col] = v.reshape(-1)
+    return want
+
+
+@pytest.mark.parametrize("layers", [2, 3])
+def test_composed_mpo_matches_dense_chunk(layers):
+    rng = np.random.default_rng(40 + layers)
+    n = 5
+    circ = C.brickwork(n, layers, 0.0, 17)
+    chunk = [op for op in circ.ops]
+    chunk.insert(2, C.Gate((3,), C.haar_unitary(rng, 2)))
+    chunk.append(C.Gate((0,), C.X, cond=C.Cond((0,), "xor", 1)))
+    for c0 in (0, 1):
+        c = np.array([c0])
+        sub, empty = LY.chunk_sublayer_blocks(n, chunk, c)
+        assert not empty and len(sub) == layers
+        W = LY.compose_mpo([LY.blocks_mpo(n, b) for b in sub])
+        np.testing.assert_allclose(LY.chunk_unitary_dense(n, W), _dense_of_gates(n, chunk, c),
+                                   atol=1e-12)
+        # brickwork layers alternate bonds: two layers give D = 4, three give 16 on the
+        # bonds the first and third layer both cross
+        assert max(w.shape[3] for w in W) == (4 if layers == 2 else 16)
+
+
+def test_multi_layer_chunking_rules():
+    circ = C.brickwork(6, 6, 0.0, 2)
+    assert len(LY.chunk_circuit(circ)[1]) == 6
+    assert len(LY.chunk_circuit(circ, layers=2)[1]) == 3
+    assert len(LY.chunk_circuit(circ, layers=3)[1]) == 2
+    assert len(LY.chunk_circuit(circ, layers=4)[1]) == 2
+    n, steps = LY.chunk_circuit(circ, layers=3)
+    assert [len(LY.sublayers(s)) for s in steps] == [3, 3]
+    # a measurement still closes a chunk
+    circ2 = C.brickwork(6, 6, 0.5, 2)
+    n, steps = LY.chunk_circuit(circ2, layers=4)
+    for st in steps:
+        if isinstance(st, list):
+            assert len(LY.sublayers(st)) <= 4
+
+
+@pytest.mark.parametrize("layers", [2, 3])
+def test_multi_layer_exact_regime_equals_statevector(layers):
+    # chi large enough for every cut: the multi-layer compression is exact, the outcomes are
+    # those of the state-vector oracle and the final state equals its state
+    circ = C.brickwork(8, 7, 0.15, 21)
+    for shot in (0, 3):
+        ref = SV.run_single_path(circ, 1, shot)
+        got = D.run_single_path(circ, D.Params(chi_max=16, layers=layers), 1, shot)
+        assert got.outcomes == ref.outcomes
+        v = M.to_dense(got.mps).reshape(-1)
+        assert abs(abs(np.vdot(v, ref.psi.reshape(-1))) ** 2 - 1) < 1e-10
+        assert abs(got.F - 1) < 1e-10
+
+
+def test_multi_layer_truncated_fidelity_is_monotone():
+    rng = np.random.default_rng(9)
+    n = 8
+    A = random_mps(rng, n, 8)
+    circ = C.brickwork(n, 3, 0.0, 5)
+    chunk = list(circ.ops)
+    sub, _ = LY.chunk_sublayer_blocks(n, chunk, np.zeros(1, dtype=np.int64))
+    W = LY.compose_mpo([LY.blocks_mpo(n, b) for b in sub])
+    target = LY.chunk_unitary_dense(n, W) @ M.to_dense(A).reshape(-1)
+    prev = 0.0
+    for s in (1, 2, 3, 4):
+        B, info = M.compress(A.copy(), sub, W, 4, 1e-10, s, skip_exact=False)
+        v = M.to_dense(B).reshape(-1)
+        f_true = abs(np.vdot(v, target)) ** 2
+        assert abs(info.f - f_true) < 1e-10 and info.f <= 1 + 1e-12
+        assert info.f >= prev - 1e-12
+        prev = info.f
+    assert prev < 1 - 1e-3
