@@ -140,19 +140,31 @@ def collapse(mps: MPS, q: int, m: int, r_m: float) -> None:
 # ----------------------------------------------------------------------------- compression
 
 
+# The three sums below are evaluated one pair of tensors at a time, in the order written
+# (the usual order of MPS environment updates).  A single four-tensor einsum is the same sum,
+# but numpy caps its intermediates at the largest operand and, once the MPO bond reaches 16,
+# falls back to one loop nest over every index (hours instead of milliseconds).
+
+
 def env_left(L, B, W, A):
     """L_{j+1}[c,e,x] = sum L_j[b,d,a] conj(B_j[b,s,c]) W_j[d,s,t,e] A_j[a,t,x]."""
-    return np.einsum("bda,bsc,dste,atx->cex", L, B.conj(), W, A, **EINSUM)
+    t = np.einsum("bda,atx->bdtx", L, A, **EINSUM)
+    t = np.einsum("bdtx,dste->bsex", t, W, **EINSUM)
+    return np.einsum("bsex,bsc->cex", t, B.conj(), **EINSUM)
 
 
 def env_right(R, B, W, A):
     """R_j[b,d,a] = sum R_{j+1}[c,e,x] conj(B_j[b,s,c]) W_j[d,s,t,e] A_j[a,t,x]."""
-    return np.einsum("cex,bsc,dste,atx->bda", R, B.conj(), W, A, **EINSUM)
+    t = np.einsum("cex,atx->ceat", R, A, **EINSUM)
+    t = np.einsum("ceat,dste->csda", t, W, **EINSUM)
+    return np.einsum("csda,bsc->bda", t, B.conj(), **EINSUM)
 
 
 def site_env(L, W, A, R):
     """F_j[b,s,c] = sum L_j[b,d,a] W_j[d,s,t,e] A_j[a,t,x] R_{j+1}[c,e,x]."""
-    return np.einsum("bda,dste,atx,cex->bsc", L, W, A, R, **EINSUM)
+    t = np.einsum("bda,atx->bdtx", L, A, **EINSUM)
+    t = np.einsum("bdtx,dste->bsex", t, W, **EINSUM)
+    return np.einsum("bsex,cex->bsc", t, R, **EINSUM)
 
 
 def trunc_rank(s: np.ndarray, cap: int, tol: float) -> int:

@@ -427,7 +427,7 @@ def _dense_of_gates(n, gates, c):
     return want
 
 
-@pytest.mark.parametrize("layers", [2, 3])
+@pytest.mark.parametrize("layers", [2, 3, 4])
 def test_composed_mpo_matches_dense_chunk(layers):
     rng = np.random.default_rng(40 + layers)
     n = 5
@@ -442,9 +442,28 @@ def test_composed_mpo_matches_dense_chunk(layers):
         W = LY.compose_mpo([LY.blocks_mpo(n, b) for b in sub])
         np.testing.assert_allclose(LY.chunk_unitary_dense(n, W), _dense_of_gates(n, chunk, c),
                                    atol=1e-12)
-        # brickwork layers alternate bonds: two layers give D = 4, three give 16 on the
-        # bonds the first and third layer both cross
+        # brickwork layers alternate bonds: two layers give D = 4, three and four give 16 on
+        # the bonds the first and third layer both cross
         assert max(w.shape[3] for w in W) == (4 if layers == 2 else 16)
+
+
+@pytest.mark.parametrize("layers", [2, 3])
+def test_composed_mpo_of_stacked_layers_matches_dense(layers):
+    # every sub-layer on the same pairs: bond dimensions 4^layers, the product still the
+    # dense chunk (sub-layers applied in order)
+    n = 4
+    lay = C.split_layers(C.brickwork(n, 2 * layers, 0.0, 23))
+    chunk = [g for i in range(layers) for g in lay[2 * i]]
+    c = np.zeros(1, dtype=np.int64)
+    sub, empty = LY.chunk_sublayer_blocks(n, chunk, c)
+    assert len(sub) == layers
+    W = LY.compose_mpo([LY.blocks_mpo(n, b) for b in sub])
+    assert max(w.shape[3] for w in W) == 4 ** layers
+    np.testing.assert_allclose(LY.chunk_unitary_dense(n, W), _dense_of_gates(n, chunk, c),
+                               atol=1e-12)
+    # the reversed order is a different operator: the composition order is pinned
+    Wr = LY.compose_mpo([LY.blocks_mpo(n, b) for b in sub[::-1]])
+    assert np.abs(LY.chunk_unitary_dense(n, Wr) - _dense_of_gates(n, chunk, c)).max() > 1e-3
 
 
 def test_multi_layer_chunking_rules():
@@ -463,7 +482,7 @@ def test_multi_layer_chunking_rules():
             assert len(LY.sublayers(st)) <= 4
 
 
-@pytest.mark.parametrize("layers", [2, 3])
+@pytest.mark.parametrize("layers", [2, 3, 4])
 def test_multi_layer_exact_regime_equals_statevector(layers):
     # chi large enough for every cut: the multi-layer compression is exact, the outcomes are
     # those of the state-vector oracle and the final state equals its state
