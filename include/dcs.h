@@ -60,6 +60,7 @@ typedef enum {
 #define DCS_MAX_CHI_FUSED 32
 /* largest bond dimension */
 #define DCS_MAX_CHI 1024
+#define DCS_MAX_CHUNK_LAYERS 4 /* gate layers one chunk may hold (chunk_layers) */
 
 typedef enum {
   DCS_COND_NONE = 0,
@@ -121,7 +122,11 @@ typedef struct {
   int32_t chi_max;      /* bond-dimension cap (the paper's chi) */
   double tol;           /* relative discarded weight allowed per truncation */
   int32_t sweeps;       /* one-site sweeps per compression step (the paper's s), >= 1 */
-  int32_t chunk_k;      /* maximum operations per chunk (the paper's k); 0 = one layer */
+  int32_t chunk_k;      /* maximum operations per chunk (the paper's k); 0 = no limit */
+  int32_t chunk_layers; /* maximum gate layers per chunk, 0 .. DCS_MAX_CHUNK_LAYERS (0 and 1:
+                           one layer, MPO bond <= 4); a chunk of L layers is compressed in one
+                           step against their composed MPO (bond <= 4^L), its guess taken
+                           layer by layer; L > 1 runs on the global work area only */
   int32_t precision;    /* dcs_precision */
   int32_t kernel_path;  /* dcs_kernel_path */
   int32_t n_cbits;      /* classical register size m, <= 64 * DCS_CWORDS */
@@ -147,7 +152,8 @@ size_t dcs_arena_bytes(const dcs_config* cfg);
  * DCS_MAX_CHI_FUSED with DCS_PATH_SHARED).
  * Arena layout: per slot two MPS buffers and one environment cache, sized by the bond
  * capacities cap_b = min(C, 2^min(b, n-b)) (C >= chi_max the bond cap of the kernel path):
- * site j holds cap_j x 2 x cap_{j+1} complex64, bond b's environment cap_b x 4 x cap_b. */
+ * site j holds cap_j x 2 x cap_{j+1} complex64, bond b's environment cap_b x D x cap_b with
+ * D = 4^max(1, chunk_layers) the MPO bond cap. */
 dcs_status_t dcs_create(dcs_ctx_t* ctx, const dcs_config* cfg, void* dev_arena,
                         size_t arena_bytes, dcs_stream_t stream);
 
@@ -164,12 +170,14 @@ const char* dcs_last_error(dcs_ctx_t ctx);
 dcs_status_t dcs_init_state(dcs_ctx_t ctx, int n_active, int multipath, uint64_t shot0);
 
 /* CompressionStep for one chunk on every active slot.  gates: n_gates GATE1/GATE2 ops that
- * form one chunk (disjoint nearest-neighbour blocks: no qubit in two two-qubit gates);
+ * form one chunk: cut into sub-layers where a two-qubit gate meets a qubit that already
+ * carries one of the current sub-layer, at most max(1, chunk_layers) of them (each a layer
+ * of disjoint nearest-neighbour blocks);
  * conditions are evaluated per slot on its register, and a slot on which every gate is
  * skipped is left unchanged (no compression, f = 1).  Otherwise the ket is replaced by
  * the compressed bra and F *= f.  fid_out: optional DEVICE pointer to n_slots doubles
- * receiving f per slot (1 for skipped slots).  Returns DCS_ERR_INVALID if the gates do
- * not form one chunk. */
+ * receiving f per slot (1 for skipped slots).  Returns DCS_ERR_INVALID if the gates need
+ * more sub-layers than that. */
 dcs_status_t dcs_apply_layer(dcs_ctx_t ctx, const dcs_op* gates, int n_gates,
                              double* fid_out);
 
@@ -238,8 +246,10 @@ dcs_status_t dcs_import_mps(dcs_ctx_t ctx, int slot, const void* host_buf, size_
 
 /* Runs a whole dynamic circuit (ops in order) from the current state: resets are lowered
  * to measurement + conditional X; operations are grouped into chunks (a chunk closes at a
- * measurement, before a two-qubit gate touching a qubit that already carries one in the
- * chunk, and at chunk_k operations); each chunk is one dcs_apply_layer; runs of
+ * measurement, at chunk_k operations, and before a two-qubit gate touching a qubit that
+ * already carries one in the chunk's current sub-layer once the chunk holds
+ * max(1, chunk_layers) sub-layers; below that the gate opens the next sub-layer); each
+ * chunk is one dcs_apply_layer; runs of
  * measurements are sampled (single-path, measurement ordinals counted from meas_idx0) or
  * split and pruned to M branches (multi-path, M = max_branches; 0 = no pruning).  The
  * circuit's tables are copied to the device once per call.  Asynchronous. */

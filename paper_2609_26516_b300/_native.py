@@ -11,6 +11,7 @@ CWORDS = 8
 MAX_QUBITS = 128
 MAX_CHI_FUSED = 32
 MAX_CHI = 1024
+MAX_CHUNK_LAYERS = 4
 PATH_AUTO, PATH_SHARED, PATH_GLOBAL = 0, 1, 2
 GEMM_SIMT, GEMM_TENSOR, GEMM_TENSOR_BF16X3 = 0, 1, 2
 PREC_FP32, PREC_TF32X3, PREC_BF16X3 = 0, 1, 2
@@ -39,7 +40,8 @@ class dcs_op(ctypes.Structure):
 class dcs_config(ctypes.Structure):
     _fields_ = [("n_qubits", ctypes.c_int32), ("chi_max", ctypes.c_int32),
                 ("tol", ctypes.c_double), ("sweeps", ctypes.c_int32),
-                ("chunk_k", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("chunk_k", ctypes.c_int32), ("chunk_layers", ctypes.c_int32),
+                ("precision", ctypes.c_int32),
                 ("kernel_path", ctypes.c_int32),
                 ("n_cbits", ctypes.c_int32), ("n_slots", ctypes.c_int32),
                 ("seed", ctypes.c_uint64)]

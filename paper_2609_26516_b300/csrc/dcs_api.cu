@@ -31,26 +31,30 @@ struct Layout {
   bool big;
   size_t work_stride;
   int chi_cap;
+  int dmax;  // MPO bond cap of a chunk (4 per sub-layer, multiplied over sub-layers)
   size_t mps_slot_stride, env_slot_stride;
 };
 
 bool valid_cfg(const dcs_config* c) {
   return c && c->n_qubits >= 1 && c->n_qubits <= DCS_MAX_QUBITS && c->chi_max >= 1 &&
          c->sweeps >= 1 && c->n_slots >= 1 && c->n_cbits >= 0 && c->n_cbits <= 64 * DCS_CWORDS &&
-         c->tol >= 0.0 && c->chunk_k >= 0 &&
+         c->tol >= 0.0 && c->chunk_k >= 0 && c->chunk_layers >= 0 &&
+         c->chunk_layers <= DCS_MAX_CHUNK_LAYERS &&
          (c->precision == DCS_PREC_FP32 || c->precision == DCS_PREC_TF32X3 ||
           c->precision == DCS_PREC_BF16X3) &&
          c->kernel_path >= DCS_PATH_AUTO && c->kernel_path <= DCS_PATH_GLOBAL;
 }
 
 // shared-memory tiles or the global work area; false if chi_max cannot be held
+// (chunks of several layers: the global work area only)
 bool pick_path(const dcs_config* c, bool& big) {
   if (c->chi_max > DCS_MAX_CHI) return false;
+  const bool multi = c->chunk_layers > 1;
   if (c->kernel_path == DCS_PATH_SHARED) {
     big = false;
-    return fused_chi(c->chi_max) != 0;
+    return !multi && fused_chi(c->chi_max) != 0;
   }
-  big = c->kernel_path == DCS_PATH_GLOBAL || fused_chi(c->chi_max) == 0;
+  big = multi || c->kernel_path == DCS_PATH_GLOBAL || fused_chi(c->chi_max) == 0;
   return true;
 }
 
@@ -59,8 +63,10 @@ Layout make_layout(const dcs_config* c) {
   const size_t n = (size_t)c->n_qubits, S = (size_t)c->n_slots;
   pick_path(c, L.big);
   L.chi_cap = L.big ? big_chi(c->chi_max) : fused_chi(c->chi_max);
-  L.work_stride = L.big ? big_work_elems(L.chi_cap) : 0;
-  layout_offsets((int)n, L.chi_cap, nullptr, nullptr, &L.mps_slot_stride, &L.env_slot_stride);
+  L.dmax = chunk_dmax(c->chunk_layers);
+  L.work_stride = L.big ? big_work_elems(L.chi_cap, L.dmax) : 0;
+  layout_offsets((int)n, L.chi_cap, L.dmax, nullptr, nullptr, &L.mps_slot_stride,
+                 &L.env_slot_stride);
   size_t off = 0;
   auto take = [&](size_t bytes) {
     const size_t o = off;
@@ -102,12 +108,13 @@ struct Program {
   bool overflow() const { return false; }
 };
 
-// build_layer plus the step that launches the chunk
-std::string add_layer(Program& P, int n, const std::vector<dcs_op>& gates) {
-  const char* e = build_layer(P, n, gates.data(), (int)gates.size());
-  if (e) return e;
-  P.steps.push_back({0, (int)P.layers.size() - 1, 0});
-  return "";
+// a chunk's sub-layers (add_chunk) and the step that launches it; no more sub-layers than
+// the context's chunk_layers
+std::string add_layer(Program& P, int n, const std::vector<dcs_op>& gates, int max_sub) {
+  if ((int)split_sublayers(gates.data(), (int)gates.size(), n).size() > max_sub)
+    return "a qubit carries more two-qubit gates than the chunk has layers";
+  const char* e = add_chunk(P, n, gates.data(), (int)gates.size());
+  return e ? e : "";
 }
 
 }  // namespace
@@ -268,9 +275,9 @@ dcs_status_t run_steps(dcs_ctx_t c, const Program& P, int max_branches,
   if (st != DCS_OK) return st;
   for (const Step& s : P.steps) {
     if (s.kind == 0) {
-      grow_bounds(c, P, P.layers[s.idx]);
-      launch_compress(c->dev, c->tile(), dp.layers + s.idx, dp.blocks, dp.g1, dp.conds, fid_out,
-                      c->stream);
+      for (int l = 0; l < s.n; ++l) grow_bounds(c, P, P.layers[s.idx + l]);
+      launch_compress(c->dev, c->tile(), dp.layers + s.idx, s.n, dp.blocks, dp.g1, dp.conds,
+                      fid_out, c->stream);
       c->launches++;
       if ((st = post_launch(c, "compress")) != DCS_OK) return st;
     } else if (!c->multipath) {
@@ -323,6 +330,7 @@ dcs_status_t dcs_create(dcs_ctx_t* out, const dcs_config* cfg, void* dev_arena, 
   DevCtx& d = c->dev;
   d.n = cfg->n_qubits;
   d.chi_cap = lay.chi_cap;
+  d.dmax = lay.dmax;
   d.n_slots = cfg->n_slots;
   d.mps_slot_stride = lay.mps_slot_stride;
   d.env_slot_stride = lay.env_slot_stride;
@@ -359,7 +367,8 @@ dcs_status_t dcs_create(dcs_ctx_t* out, const dcs_config* cfg, void* dev_arena, 
   c->site_off.assign(cfg->n_qubits + 1, 0);
   c->env_off.assign(cfg->n_qubits + 1, 0);
   size_t me = 0, ee = 0;
-  layout_offsets(cfg->n_qubits, lay.chi_cap, c->site_off.data(), c->env_off.data(), &me, &ee);
+  layout_offsets(cfg->n_qubits, lay.chi_cap, lay.dmax, c->site_off.data(), c->env_off.data(), &me,
+                 &ee);
   if (cudaEventCreateWithFlags(&c->stage_done, cudaEventDisableTiming) != cudaSuccess) {
     delete c;
     return DCS_ERR_CUDA;
@@ -416,7 +425,7 @@ dcs_status_t dcs_apply_layer(dcs_ctx_t c, const dcs_op* gates, int n_gates, doub
   }
   if (g.empty()) return DCS_OK;
   Program P;
-  std::string e = add_layer(P, c->cfg.n_qubits, g);
+  std::string e = add_layer(P, c->cfg.n_qubits, g, std::max(1, c->cfg.chunk_layers));
   if (!e.empty()) return fail(c, DCS_ERR_INVALID, e);
   return run_steps(c, P, 0, fid_out);
 }
@@ -670,7 +679,8 @@ dcs_status_t dcs_run_circuit(dcs_ctx_t c, const dcs_op* ops, int n_ops, uint64_t
   // resets lowered, chunks and measurement runs (Sec. "Handling unitary chunks in dynamic
   // circuits", one-layer reading)
   Program P;
-  if (const char* e = plan_circuit(P, c->cfg.n_qubits, c->cfg.chunk_k, ops, n_ops, meas_idx0))
+  if (const char* e = plan_circuit(P, c->cfg.n_qubits, c->cfg.chunk_k, ops, n_ops, meas_idx0,
+                                   c->cfg.chunk_layers))
     return fail(c, DCS_ERR_INVALID, e);
   if (P.layers.size() * sizeof(DLayer) > kProgBytes / 2)
     return fail(c, DCS_ERR_OOM, "too many chunks for one call");

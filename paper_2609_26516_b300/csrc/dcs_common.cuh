@@ -321,6 +321,7 @@ struct Work {
   float2* R;   // far environment, or Q
   float2* F;   // F (QR work)
   float2* T2;  // mixed T (large path)
+  float2* Wc;  // composed MPO tensor of a chunk of several layers, then 3 x 64 factors
   float2* W;   // 64     MPO tensor of the site
   float2* W2;  // 64     mirrored MPO tensor
   float2* G;   // 16     block matrix / single-qubit gate
@@ -365,11 +366,26 @@ __host__ __device__ inline size_t work_small_bytes(int C, bool big, bool tc = fa
   (void)tc;
   return work_arrays_bytes(C, big) + (big ? BIG_HEAD_BYTES + big_stage_bytes(C) : 0);
 }
-__host__ __device__ inline size_t work_tile_elems(int C, bool big) {
-  return (size_t)(big ? 28 : 20) * C * C;
+// Composed chunk MPO tensors (complex elements): the final one of bond <= dmax and the
+// intermediates (at least one factor's 64).
+__host__ __device__ inline size_t chunk_w_fin_elems(int dmax) { return 4 * (size_t)dmax * dmax; }
+__host__ __device__ inline size_t chunk_w_mid_elems(int d) {
+  const size_t e = 4 * (size_t)d * d;
+  return e < 64 ? 64 : e;
+}
+// Large path: E dmax C^2, S 2 C^2, T 2 dmax C^2, R dmax C^2, F 2 C^2, T2 2 dmax C^2 and, for
+// chunks of several layers, the composed MPO tensor, two intermediates and one 2 x 2 x 4 x 4
+// factor per layer; with dmax = 4 the tiles are 28 C^2.
+__host__ __device__ inline size_t work_tile_elems(int C, bool big, int dmax = 4) {
+  if (!big) return (size_t)20 * C * C;
+  return (size_t)(6 * dmax + 4) * C * C +
+         (dmax > 4 ? chunk_w_fin_elems(dmax) + chunk_w_mid_elems(dmax / 4) +
+                         chunk_w_mid_elems(dmax / 16) + 64 * DCS_MAX_CHUNK_LAYERS
+                   : 0);
 }
 
-static __device__ void carve(Work& w, unsigned char* raw, int C, float2* big_area, bool tc = false) {
+static __device__ void carve(Work& w, unsigned char* raw, int C, float2* big_area, bool tc = false,
+                             int dmax = 4) {
   w.C = C;
   w.use_tc = tc;
   w.stage = nullptr;
@@ -406,12 +422,14 @@ static __device__ void carve(Work& w, unsigned char* raw, int C, float2* big_are
     w.gA = w.gB = nullptr;
   }
   float2* t = big_area ? big_area : tiles;
+  const int dm = big_area ? dmax : 4;
   w.E = t;
-  w.S = w.E + 4 * C * C;
+  w.S = w.E + (size_t)dm * C * C;
   w.T = w.S + 2 * C * C;
-  w.R = w.T + 8 * C * C;
-  w.F = w.R + 4 * C * C;
+  w.R = w.T + (size_t)2 * dm * C * C;
+  w.F = w.R + (size_t)dm * C * C;
   w.T2 = big_area ? w.F + 2 * C * C : nullptr;
+  w.Wc = (big_area && dm > 4) ? w.T2 + (size_t)2 * dm * C * C : nullptr;
   float2* after = big_area ? tiles : w.F + 2 * C * C;
   w.tau = reinterpret_cast<float*>(after);
   w.sigf = w.tau + 2 * C;
@@ -945,7 +963,7 @@ struct MinBlocks {
 constexpr int BIG_NT = 512;
 
 // launchers of the compression kernels (defined in dcs_k_small.cu / dcs_k_big.cu)
-void launch_compress_big(const DevCtx& c, const DLayer* L, const DBlock* B, const DGate1* G1,
-                         const DCond* CD, double* fid_out, cudaStream_t s);
+void launch_compress_big(const DevCtx& c, const DLayer* L, int nsub, const DBlock* B,
+                         const DGate1* G1, const DCond* CD, double* fid_out, cudaStream_t s);
 
 }  // namespace dcs

@@ -4,19 +4,19 @@
 
 namespace dcs {
 
-void launch_compress_big_tc(const DevCtx& c, const DLayer* L, const DBlock* B, const DGate1* G1,
-                            const DCond* CD, double* fid_out, cudaStream_t s);
+void launch_compress_big_tc(const DevCtx& c, const DLayer* L, int nsub, const DBlock* B,
+                            const DGate1* G1, const DCond* CD, double* fid_out, cudaStream_t s);
 
-void launch_compress_big(const DevCtx& c, const DLayer* L, const DBlock* B, const DGate1* G1,
-                         const DCond* CD, double* fid_out, cudaStream_t s) {
+void launch_compress_big(const DevCtx& c, const DLayer* L, int nsub, const DBlock* B,
+                         const DGate1* G1, const DCond* CD, double* fid_out, cudaStream_t s) {
   // the tensor-core tiles live in the staging region; the bond cap keeps it large enough
   if (c.use_tc && big_stage_bytes(c.chi_cap) >= sizeof(float) * TC_SMEM_FLOATS) {
-    launch_compress_big_tc(c, L, B, G1, CD, fid_out, s);
+    launch_compress_big_tc(c, L, nsub, B, G1, CD, fid_out, s);
     return;
   }
   const size_t sm = work_small_bytes(c.chi_cap, true, false);
   cudaFuncSetAttribute(k_compress_big<BIG_NT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_compress_big<BIG_NT, false><<<c.n_slots, BIG_NT, sm, s>>>(c, c.chi_cap, L, B, G1, CD, fid_out);
+  k_compress_big<BIG_NT, false><<<c.n_slots, BIG_NT, sm, s>>>(c, c.chi_cap, L, nsub, B, G1, CD, fid_out);
 }
 
 }  // namespace dcs

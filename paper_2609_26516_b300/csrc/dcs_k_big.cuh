@@ -20,9 +20,77 @@ namespace dcs {
 // T2[b][s][e][x] = sum_{d,t} T1(b, d, t, x) W(d, s, t, e) with T1 at
 // b*ib + d*id + t*it + x*ix and T2 natural (b-stride 2 ne nx); mirrored: the coefficient is
 // W[e][s][t][d] (the MPO read right to left).
+// W of site j for the chunk's sub-layers L[0 .. nsub): one layer -> build_W into sm.W; more
+// -> each layer's factor (build_W, thread 0) composed in order into sm.Wc, bonds grouped
+// (earlier layer's, later layer's) on both sides:
+//   W[(a, d)][s][v][(f, e)] = sum_u Wlater[d][s][u][e] Wearlier[a][u][v][f].
+// Sets sm.iv[0], sm.iv[1] to the composed bond dimensions.  All threads call.
+template <int NT>
+__device__ const float2* chunk_W(int j, const DLayer* L, int nsub, const DBlock* BK,
+                                 const DGate1* G1, Work& sm, int dmax) {
+  if (nsub <= 1) {
+    if (threadIdx.x == 0) build_W(j, L, BK, G1, sm.creg, sm.W, &sm.iv[0], &sm.iv[1]);
+    __syncthreads();
+    return sm.W;
+  }
+  // the composed tensor and two intermediates used in turn, the last product landing in fin:
+  // after sub-layer l the bond is at most 4^(l+1) = dmax / 4^(nsub-1-l)
+  float2* fin = sm.Wc;                                      // 4 dmax^2
+  float2* midA = fin + chunk_w_fin_elems(dmax);             // 4 (dmax/4)^2: product nsub-2
+  float2* midB = midA + chunk_w_mid_elems(dmax / 4);        // 4 (dmax/16)^2: product nsub-3
+  float2* fac = midB + chunk_w_mid_elems(dmax / 16);        // DCS_MAX_CHUNK_LAYERS x 64
+  if (threadIdx.x == 0)
+    for (int l = 0; l < nsub; ++l)
+      build_W(j, L + l, BK, G1, sm.creg, fac + 64 * l, &sm.iv[8 + 2 * l], &sm.iv[9 + 2 * l]);
+  __syncthreads();
+  const float2* cur = fac;
+  int cd = sm.iv[8], ce = sm.iv[9];
+  for (int l = 1; l < nsub; ++l) {
+    const float2* nx = fac + 64 * l;
+    const int nd = sm.iv[8 + 2 * l], ne = sm.iv[9 + 2 * l];
+    float2* out = (l == nsub - 1) ? fin : ((nsub - 1 - l) & 1 ? midA : midB);
+    const int od = cd * nd, oe = ce * ne;
+    for (int idx = threadIdx.x; idx < od * 4 * oe; idx += NT) {
+      const int oei = idx % oe, v = (idx / oe) & 1, s = (idx / (2 * oe)) & 1, odi = idx / (4 * oe);
+      const int a = odi / nd, d = odi % nd, f = oei / ne, e = oei % ne;
+      float2 acc = cz();
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+        cfma(acc, nx[((d * 2 + s) * 2 + u) * ne + e], cur[((a * 2 + u) * 2 + v) * ce + f]);
+      out[idx] = acc;
+    }
+    __syncthreads();
+    cur = out;
+    cd = od;
+    ce = oe;
+  }
+  if (threadIdx.x == 0) {
+    sm.iv[0] = cd;
+    sm.iv[1] = ce;
+  }
+  __syncthreads();
+  return fin;
+}
+
 template <int NT>
 __device__ void mix_big(const float2* T1, int ib, int id, int it, int ix, float2* T2, const float2* W,
                         int nb, int nd, int ne, int nx, bool mirrored) {
+  if (nd > 4 || ne > 4) {  // MPO bonds of a chunk of several layers: plain loops
+    for (int idx = threadIdx.x; idx < nb * nx * 2 * ne; idx += NT) {
+      const int x = idx % nx, e = (idx / nx) % ne, sv = (idx / (nx * ne)) & 1,
+                b = idx / (nx * ne * 2);
+      float2 acc = cz();
+      for (int d = 0; d < nd; ++d)
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+          const float2 w = mirrored ? W[((e * 2 + sv) * 2 + t) * nd + d] : W[((d * 2 + sv) * 2 + t) * ne + e];
+          cfma(acc, T1[(size_t)b * ib + d * id + t * it + (size_t)x * ix], w);
+        }
+      T2[(size_t)b * 2 * ne * nx + (sv * ne + e) * nx + x] = acc;
+    }
+    __syncthreads();
+    return;
+  }
   for (int idx = threadIdx.x; idx < nb * nx; idx += NT) {
     const int x = idx % nx, b = idx / nx;
     float2 v[8];
@@ -58,7 +126,7 @@ __device__ void mix_big(const float2* T1, int ib, int id, int it, int ix, float2
 // right-to-left steps read the same products on the mirrored chain.
 template <int NT, bool TC>
 __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const DLayer* __restrict__ L,
-                                                        const DBlock* __restrict__ BK,
+                                                        int nsub, const DBlock* __restrict__ BK,
                                                         const DGate1* __restrict__ G1,
                                                         const DCond* __restrict__ CD, double* fid_out) {
   const int pos = blockIdx.x;
@@ -66,14 +134,18 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
   const int slot = c.order[pos];
   extern __shared__ __align__(16) unsigned char smraw[];
   Work sm;
-  carve(sm, smraw, C, c.work + (size_t)slot * c.work_stride, TC);
+  carve(sm, smraw, C, c.work + (size_t)slot * c.work_stride, TC, c.dmax);
   const int n = c.n;
   if (threadIdx.x < DCS_CWORDS) sm.creg[threadIdx.x] = c.creg[(size_t)slot * DCS_CWORDS + threadIdx.x];
   __syncthreads();
-  if (!L->uncond) {
+  bool uncond = false;
+  for (int l = 0; l < nsub; ++l) uncond = uncond || L[l].uncond;
+  if (!uncond) {
     if (threadIdx.x == 0) {
       int any = 0;
-      for (int i = 0; i < L->n_conds && !any; ++i) any = cond_holds(CD[L->cond_off + i], sm.creg);
+      for (int l = 0; l < nsub && !any; ++l)
+        for (int i = 0; i < L[l].n_conds && !any; ++i)
+          any = cond_holds(CD[L[l].cond_off + i], sm.creg);
       sm.iv[4] = any;
     }
     __syncthreads();
@@ -104,12 +176,21 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
   // ---- initial guess: the chunk applied block by block to a copy of the sites it touches
   int lo, hi;
   guess_range(L, BK, n, centre, lo, hi);
+  for (int l = 1; l < nsub; ++l) {  // the sites any sub-layer touches
+    int lo2, hi2;
+    guess_range(L + l, BK, n, centre, lo2, hi2);
+    lo = lo2 < lo ? lo2 : lo;
+    hi = hi2 > hi ? hi2 : hi;
+  }
   for (int j = lo; j <= hi; ++j)
     gcopy<NT>(site_ptr(c, bb, slot, j), site_ptr(c, kb, slot, j), at[j] * 2 * at[j + 1]);
   __syncthreads();
+  // the sub-layers in order: each one's single-qubit sites, then its blocks
+  for (int l = 0; l < nsub; ++l) {
+  const DLayer* Ll = L + l;
   for (int j = 0; j < n; ++j) {
-    if (L->site[j].kind != 1) continue;
-    if (threadIdx.x == 0) prod1q(G1, L->site[j].g_off, L->site[j].g_n, sm.creg, sm.G);
+    if (Ll->site[j].kind != 1) continue;
+    if (threadIdx.x == 0) prod1q(G1, Ll->site[j].g_off, Ll->site[j].g_n, sm.creg, sm.G);
     __syncthreads();
     float2* p = site_ptr(c, bb, slot, j);
     const int bl = bt[j], br = bt[j + 1];
@@ -127,9 +208,9 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
     __syncthreads();
   }
   PHASE_MARK(0);
-  const bool asc = guess_ascending(L, BK, centre);
-  for (int t = 0; t < L->n_blocks; ++t) {
-    const DBlock& blk = BK[L->blk_off + (asc ? L->n_blocks - 1 - t : t)];
+  const bool asc = guess_ascending(Ll, BK, centre);
+  for (int t = 0; t < Ll->n_blocks; ++t) {
+    const DBlock& blk = BK[Ll->blk_off + (asc ? Ll->n_blocks - 1 - t : t)];
     const int q = blk.q;
     move_centre<NT>(c, sm, bb, slot, centre, centre <= q ? q : q + 1);
     PHASE_MARK(1);
@@ -238,6 +319,7 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
     __syncthreads();
     PHASE_MARK(4);
   }
+  }  // sub-layers
   double fval = 0.0;
   const bool exact = sm.iv[7] != 0;  // exact guess: the sweeps are skipped (see k_compress)
   if (exact) {
@@ -256,14 +338,13 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
   __syncthreads();
   // ---- left environments of the guess (env updates with B given; first sweep right to left)
   for (int j = 0; first == 1 && j < n - 1; ++j) {
-    if (threadIdx.x == 0) build_W(j, L, BK, G1, sm.creg, sm.W, &sm.iv[0], &sm.iv[1]);
-    __syncthreads();
+    const float2* Wj = chunk_W<NT>(j, L, nsub, BK, G1, sm, c.dmax);
     const int dl = sm.iv[0], dr = sm.iv[1];
     const int nb = bt[j], nc = bt[j + 1], na = at[j], nx = at[j + 1];
     const float2* A = site_ptr(c, kb, slot, j);
     const float2* Bj = site_ptr(c, bb, slot, j);
     wgemm<NT>(sm, nb * dl, 2 * nx, na, sm.E, na, 1, false, A, 2 * nx, 1, false, sm.T, 2 * nx, 1);
-    mix_big<NT>(sm.T, dl * 2 * nx, 2 * nx, nx, 1, sm.T2, sm.W, nb, dl, dr, nx, false);
+    mix_big<NT>(sm.T, dl * 2 * nx, 2 * nx, nx, 1, sm.T2, Wj, nb, dl, dr, nx, false);
     // L_{j+1}[c, (e x)] = sum_{(b s)} conj(B_j[(b s), c]) T2[(b s), (e x)]
     wgemm<NT>(sm, nc, dr * nx, 2 * nb, Bj, 1, nc, true, sm.T2, dr * nx, 1, false, sm.E, dr * nx, 1);
     gcopy<NT>(env_ptr(c, slot, j + 1), sm.E, nc * dr * nx);
@@ -271,8 +352,7 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
   }
   // ---- right environments of the guess (mirrored env updates with B given)
   for (int j = n - 1; first == 0 && j >= 1; --j) {
-    if (threadIdx.x == 0) build_W(j, L, BK, G1, sm.creg, sm.W, &sm.iv[0], &sm.iv[1]);
-    __syncthreads();
+    const float2* Wj = chunk_W<NT>(j, L, nsub, BK, G1, sm, c.dmax);
     const int dl = sm.iv[0], dr = sm.iv[1];
     const float2* A = site_ptr(c, kb, slot, j);
     const int al = at[j], ar = at[j + 1];
@@ -286,7 +366,7 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
     // T1[(c e), (a t)] = sum_x E[(c e), x] A[(a t), x]
     wgemm<NT>(sm, br * dr, 2 * al, ar, sm.E, ar, 1, false, A, 1, ar, false, sm.T, 2 * al, 1);
     // T2[c][s][d][a] from T1[c][e][a][t]: fibre (c, a), incoming MPO index e, outgoing d
-    mix_big<NT>(sm.T, dr * 2 * al, 2 * al, 1, 2, sm.T2, sm.W, br, dr, dl, al, true);
+    mix_big<NT>(sm.T, dr * 2 * al, 2 * al, 1, 2, sm.T2, Wj, br, dr, dl, al, true);
     // R_j[b, (d a)] = sum_{(c s)} conj(Q'[(c s), b]) T2[(c s), (d a)]
     wgemm<NT>(sm, bl, dl * al, 2 * br, sm.R, ldq, 1, true, sm.T2, dl * al, 1, false, sm.E, dl * al,
                   1);
@@ -303,8 +383,7 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
     __syncthreads();
     if (((sw + first) & 1) == 0) {  // left to right
       for (int j = 0; j < n; ++j) {
-        if (threadIdx.x == 0) build_W(j, L, BK, G1, sm.creg, sm.W, &sm.iv[0], &sm.iv[1]);
-        __syncthreads();
+        const float2* Wj = chunk_W<NT>(j, L, nsub, BK, G1, sm, c.dmax);
         const int dl = sm.iv[0], dr = sm.iv[1];
         const int nb = bt[j], nc = bt[j + 1], na = at[j], nx = at[j + 1];
         const float2* A = site_ptr(c, kb, slot, j);
@@ -313,7 +392,7 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
         else if (threadIdx.x == 0) sm.R[0] = make_float2(1.f, 0.f);
         __syncthreads();
         wgemm<NT>(sm, nb * dl, 2 * nx, na, sm.E, na, 1, false, A, 2 * nx, 1, false, sm.T, 2 * nx, 1);
-        mix_big<NT>(sm.T, dl * 2 * nx, 2 * nx, nx, 1, sm.T2, sm.W, nb, dl, dr, nx, false);
+        mix_big<NT>(sm.T, dl * 2 * nx, 2 * nx, nx, 1, sm.T2, Wj, nb, dl, dr, nx, false);
         const int m = 2 * nb;
         wgemm<NT>(sm, m, nc, dr * nx, sm.T2, dr * nx, 1, false, Rn, 1, dr * nx, false, sm.F, 1, m);
         PHASE_MARK(7);
@@ -344,8 +423,7 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
       centre = n - 1;
     } else {  // right to left, mirrored
       for (int j = n - 1; j >= 0; --j) {
-        if (threadIdx.x == 0) build_W(j, L, BK, G1, sm.creg, sm.W, &sm.iv[0], &sm.iv[1]);
-        __syncthreads();
+        const float2* Wj = chunk_W<NT>(j, L, nsub, BK, G1, sm, c.dmax);
         const int dl = sm.iv[0], dr = sm.iv[1];
         const int nb = bt[j + 1], nc = bt[j], na = at[j + 1], nx = at[j];
         const float2* A = site_ptr(c, kb, slot, j);
@@ -355,7 +433,7 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
         __syncthreads();
         // T1[(c e), (a t)] = sum_x E[(c e), x] A[(a t), x]
         wgemm<NT>(sm, nb * dr, 2 * nx, na, sm.E, na, 1, false, A, 1, na, false, sm.T, 2 * nx, 1);
-        mix_big<NT>(sm.T, dr * 2 * nx, 2 * nx, 1, 2, sm.T2, sm.W, nb, dr, dl, nx, true);
+        mix_big<NT>(sm.T, dr * 2 * nx, 2 * nx, 1, 2, sm.T2, Wj, nb, dr, dl, nx, true);
         const int m = 2 * nb;
         // F'[(c s), b] = sum_{(d a)} T2[(c s), (d a)] L[b, (d a)]
         wgemm<NT>(sm, m, nc, dl * nx, sm.T2, dl * nx, 1, false, Ln, 1, dl * nx, false, sm.F, 1, m);

@@ -20,7 +20,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_measure(DevCtx c, 
   const int slot = c.order[pos];
   extern __shared__ __align__(16) unsigned char smraw[];
   Work sm;
-  carve(sm, smraw, C, BIG ? c.work + (size_t)slot * c.work_stride : nullptr);
+  carve(sm, smraw, C, BIG ? c.work + (size_t)slot * c.work_stride : nullptr, false, c.dmax);
   const int n = c.n;
   const int kb = c.ketbuf[slot];
   int* kbonds = bonds_ptr(c, slot, kb);
@@ -108,8 +108,8 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_measure(DevCtx c, 
 __global__ void k_layout(DevCtx c) {
   if (threadIdx.x == 0) {
     size_t me = 0, ee = 0;
-    layout_offsets(c.n, c.chi_cap, const_cast<size_t*>(c.site_off), const_cast<size_t*>(c.env_off),
-                   &me, &ee);
+    layout_offsets(c.n, c.chi_cap, c.dmax, const_cast<size_t*>(c.site_off),
+                   const_cast<size_t*>(c.env_off), &me, &ee);
   }
 }
 
@@ -385,7 +385,7 @@ int fused_chi(int chi_max) {
 
 int big_chi(int chi_max) { return (chi_max + 7) / 8 * 8; }
 
-size_t big_work_elems(int chi_cap) { return work_tile_elems(chi_cap, true); }
+size_t big_work_elems(int chi_cap, int dmax) { return work_tile_elems(chi_cap, true, dmax); }
 
 template <int NT, bool BIG>
 static void measure_c(const DevCtx& c, int C, const DMeas* meas, int n_meas, int mode,

@@ -392,12 +392,13 @@ static void compress_c(const DevCtx& c, int C, const DLayer* L, const DBlock* B,
   k_compress<NT><<<c.n_slots, NT, sm, s>>>(c, C, L, B, G1, CD, fid_out);
 }
 
-void launch_compress(const DevCtx& c, int tile_chi, const DLayer* L, const DBlock* B,
+void launch_compress(const DevCtx& c, int tile_chi, const DLayer* L, int nsub, const DBlock* B,
                      const DGate1* G1, const DCond* CD, double* fid_out, cudaStream_t s) {
   if (c.work) {
-    launch_compress_big(c, L, B, G1, CD, fid_out, s);
+    launch_compress_big(c, L, nsub, B, G1, CD, fid_out, s);
     return;
   }
+  if (nsub != 1) return;  // chunks of several layers take the large-tile path
   switch (tile_chi) {
     case 4: compress_c<32>(c, 4, L, B, G1, CD, fid_out, s); break;
     case 8: compress_c<32>(c, 8, L, B, G1, CD, fid_out, s); break;

@@ -63,6 +63,7 @@ struct DMeas {
 struct DevCtx {
   int32_t n;         // sites
   int32_t chi_cap;   // bond capacity (>= chi_max); bond b holds at most bond_cap(b, n, chi_cap)
+  int32_t dmax;      // MPO bond capacity of a chunk: 4 per layer of the chunk, multiplied
   int32_t n_slots;
   const size_t* site_off;    // [n+1] complex-element offset of site j in a slot's MPS buffer
   const size_t* env_off;     // [n+1] offset of the environment of bond b in a slot's cache
@@ -106,17 +107,18 @@ __host__ __device__ inline int bond_cap(int b, int n, int C) {
 }
 
 // Bond-sized layout of one slot: site j ([chi_j][2][chi_{j+1}], complex) at site_off[j],
-// the environment of bond b ([beta_b][D <= 4][alpha_b]) at env_off[b]; every region starts
-// on a 256-byte boundary.  Returns the per-slot sizes through mps_elems / env_elems.
-__host__ __device__ inline void layout_offsets(int n, int C, size_t* site_off, size_t* env_off,
-                                               size_t* mps_elems, size_t* env_elems) {
+// the environment of bond b ([beta_b][D <= dmax][alpha_b]) at env_off[b]; every region
+// starts on a 256-byte boundary.  Returns the per-slot sizes through mps_elems / env_elems.
+__host__ __device__ inline void layout_offsets(int n, int C, int dmax, size_t* site_off,
+                                               size_t* env_off, size_t* mps_elems,
+                                               size_t* env_elems) {
   size_t s = 0, e = 0;
   for (int b = 0; b <= n; ++b) {
     const size_t cb = (size_t)bond_cap(b, n, C);
     if (site_off) site_off[b] = s;
     if (env_off) env_off[b] = e;
     if (b < n) s += ((cb * 2 * (size_t)bond_cap(b + 1, n, C)) + 31) / 32 * 32;
-    e += (4 * cb * cb + 31) / 32 * 32;
+    e += ((size_t)dmax * cb * cb + 31) / 32 * 32;
   }
   *mps_elems = s;
   *env_elems = e;
@@ -129,7 +131,8 @@ constexpr int PLAN_HDR = 4;
 // two launches: the layout offset tables, then the initial state of every slot
 void launch_init(const DevCtx& c, int n_active, int multipath, uint64_t shot0, cudaStream_t s);
 // tile_chi: shared-memory tile (4, 8, 16 or 32), at least every bond the launch can meet
-void launch_compress(const DevCtx& c, int tile_chi, const DLayer* L, const DBlock* B,
+// L: the chunk's nsub sub-layers (nsub > 1 only on the large-tile path)
+void launch_compress(const DevCtx& c, int tile_chi, const DLayer* L, int nsub, const DBlock* B,
                      const DGate1* G1, const DCond* C, double* fid_out, cudaStream_t s);
 void launch_measure(const DevCtx& c, int tile_chi, const DMeas* meas, int n_meas, int mode,
                     const uint8_t* forced, double* p0_out, cudaStream_t s);
@@ -140,7 +143,9 @@ void launch_branch_split(const DevCtx& c, int q, int cbit, double eps, int M, do
 void launch_branch_topk(const DevCtx& c, int M, cudaStream_t s);
 int fused_chi(int chi_max);          // shared-memory tile for chi_max (0 if above 32)
 int big_chi(int chi_max);            // slot capacity per bond of the large-tile path
-size_t big_work_elems(int chi_cap);  // complex elements of one slot's work area
+size_t big_work_elems(int chi_cap, int dmax);  // complex elements of one slot's work area
+// MPO bond capacity of chunks of up to `layers` layers: 4^layers
+inline int chunk_dmax(int layers) { return layers <= 1 ? 4 : 1 << (2 * layers); }
 
 // measurement modes
 constexpr int MEAS_SAMPLE = 0;

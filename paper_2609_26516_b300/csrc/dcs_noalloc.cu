@@ -223,6 +223,7 @@ extern "C" dcs_status_t dcs_compress_noalloc(int32_t n_qubits, int32_t chi_max, 
   DevCtx d{};
   d.n = n_qubits;
   d.chi_cap = C;
+  d.dmax = 4;
   d.n_slots = 1;
   d.mps_slot_stride = (size_t)n_qubits * 2 * C * C;
   d.env_slot_stride = (size_t)(n_qubits + 1) * 4 * C * C;
@@ -273,7 +274,7 @@ extern "C" dcs_status_t dcs_compress_noalloc(int32_t n_qubits, int32_t chi_max, 
          cudaMemcpyAsync(dc, g_prog.conds.data(), sizeof(DCond) * g_prog.conds.size(),
                          cudaMemcpyHostToDevice, s) != cudaSuccess))
       return DCS_ERR_CUDA;
-    launch_compress(d, C, dl, db, dg, dc, f, s);
+    launch_compress(d, C, dl, 1, db, dg, dc, f, s);
     if (cudaGetLastError() != cudaSuccess) return DCS_ERR_CUDA;
   }
   // an empty chunk has nothing to compress: k_noalloc_finish writes f = 1

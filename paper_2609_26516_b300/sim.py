@@ -104,12 +104,13 @@ class Simulator:
     def __init__(self, n_qubits: int, chi_max: int, n_slots: int, n_cbits: int,
                  tol: float = 1e-10, sweeps: int = 2, seed: int = 0, chunk_k: int = 0,
                  device: str = "cuda:0", stream: Optional[torch.cuda.Stream] = None,
-                 kernel_path: int = 0, precision: int = 0):
+                 kernel_path: int = 0, precision: int = 0, chunk_layers: int = 0):
         if not torch.cuda.is_available():
             raise RuntimeError("libdcs needs a CUDA device; there is no CPU path")
         self.lib = N.load()
         self.cfg = N.dcs_config(n_qubits=n_qubits, chi_max=chi_max, tol=tol, sweeps=sweeps,
-                                chunk_k=chunk_k, precision=precision, kernel_path=kernel_path,
+                                chunk_k=chunk_k, chunk_layers=chunk_layers,
+                                precision=precision, kernel_path=kernel_path,
                                 n_cbits=n_cbits,
                                 n_slots=n_slots, seed=seed)
         self.device = torch.device(device)

@@ -1,8 +1,10 @@
 // Host-only driver of libdcs's table builder and circuit planner for the CPU tests.
 //   harness n ops.bin                      one chunk (dcs_op records, circuit order) through
 //                                          build_layer (dcs_tables.h): its tables as text
-//   harness plan n chunk_k idx0 ops.bin    a whole circuit through plan_circuit
-//                                          (dcs_plan.h): steps, chunks and measurements
+//   harness plan n chunk_k idx0 ops.bin [layers]
+//                                          a whole circuit through plan_circuit
+//                                          (dcs_plan.h): steps, chunks (one CHUNK line per
+//                                          sub-layer) and measurements
 // No CUDA call is made; it runs without a GPU.
 #include <cstdio>
 #include <cstdlib>
@@ -35,10 +37,10 @@ std::vector<dcs_op> read_ops(const char* path) {
   return ops;
 }
 
-int plan_main(int n, int chunk_k, unsigned long long idx0, const char* path) {
+int plan_main(int n, int chunk_k, unsigned long long idx0, const char* path, int layers) {
   std::vector<dcs_op> ops = read_ops(path);
   Prog P;
-  const char* e = plan_circuit(P, n, chunk_k, ops.data(), (int)ops.size(), idx0);
+  const char* e = plan_circuit(P, n, chunk_k, ops.data(), (int)ops.size(), idx0, layers);
   if (e) {
     std::printf("ERR %s\n", e);
     return 0;
@@ -46,10 +48,12 @@ int plan_main(int n, int chunk_k, unsigned long long idx0, const char* path) {
   for (const Step& st : P.steps) {
     std::printf("STEP %d %d %d\n", st.kind, st.idx, st.n);
     if (st.kind == 0) {
-      const DLayer& L = P.layers[st.idx];
-      std::printf("CHUNK %d %d %d", L.n_blocks, L.uncond, L.n_conds);
-      for (int j = 0; j < n; ++j) std::printf(" %d", L.site[j].kind);
-      std::printf("\n");
+      for (int l = 0; l < st.n; ++l) {
+        const DLayer& L = P.layers[st.idx + l];
+        std::printf("CHUNK %d %d %d", L.n_blocks, L.uncond, L.n_conds);
+        for (int j = 0; j < n; ++j) std::printf(" %d", L.site[j].kind);
+        std::printf("\n");
+      }
     } else {
       for (int i = 0; i < st.n; ++i) {
         const DMeas& m = P.meas[st.idx + i];
@@ -74,9 +78,9 @@ void put_cond(const DCond& c) {
 }  // namespace
 
 int main(int argc, char** argv) {
-  if (argc == 6 && std::strcmp(argv[1], "plan") == 0)
+  if ((argc == 6 || argc == 7) && std::strcmp(argv[1], "plan") == 0)
     return plan_main(std::atoi(argv[2]), std::atoi(argv[3]), std::strtoull(argv[4], nullptr, 10),
-                     argv[5]);
+                     argv[5], argc == 7 ? std::atoi(argv[6]) : 1);
   if (argc != 3) {
     std::fprintf(stderr, "usage: %s n ops.bin | %s plan n chunk_k idx0 ops.bin\n", argv[0],
                  argv[0]);

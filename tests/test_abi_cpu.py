@@ -114,6 +114,37 @@ def test_arena_bytes_and_argument_checks(lib):
     assert lib.dcs_last_error(None) == b"null context"
 
 
+def test_chunk_layers_configuration(lib):
+    # chunks of several layers run on the global work area only, up to four layers; their
+    # environment caches hold the composed MPO bond 4^layers
+    from paper_2609_26516_b300 import _native as N
+    n, chi, S = 24, 64, 4
+    one = lib.dcs_arena_bytes(ctypes.byref(_cfg(N, n_qubits=n, chi_max=chi, n_slots=S)))
+    assert one > 0
+    assert lib.dcs_arena_bytes(ctypes.byref(_cfg(N, n_qubits=n, chi_max=chi, n_slots=S,
+                                                 chunk_layers=1))) == one
+    sizes = [one]
+    for layers in (2, 3, 4):
+        nb = lib.dcs_arena_bytes(ctypes.byref(_cfg(N, n_qubits=n, chi_max=chi, n_slots=S,
+                                                   chunk_layers=layers)))
+        cap = [min(chi, 2 ** min(b, n - b)) for b in range(n + 1)]
+        env = S * sum(4 ** layers * c * c for c in cap) * 8
+        assert nb > env
+        sizes.append(nb)
+    assert sizes[0] < sizes[1] < sizes[2] < sizes[3]
+    assert lib.dcs_arena_bytes(ctypes.byref(_cfg(N, chunk_layers=N.MAX_CHUNK_LAYERS + 1))) == 0
+    assert lib.dcs_arena_bytes(ctypes.byref(_cfg(N, chunk_layers=-1))) == 0
+    # the shared-memory tiles hold one layer's MPO only
+    assert lib.dcs_arena_bytes(ctypes.byref(_cfg(N, chi_max=8, kernel_path=N.PATH_SHARED,
+                                                 chunk_layers=2))) == 0
+    ctx = ctypes.c_void_p()
+    assert lib.dcs_create(ctypes.byref(ctx), ctypes.byref(_cfg(N, kernel_path=N.PATH_SHARED,
+                                                               chunk_layers=2)),
+                          None, 0, None) == N.ERR_UNSUPPORTED
+    assert lib.dcs_create(ctypes.byref(ctx), ctypes.byref(_cfg(N, chunk_layers=5)), None, 0,
+                          None) == N.ERR_INVALID
+
+
 def test_encode_ops_round_trip():
     import numpy as np
     import circuits as C

@@ -77,10 +77,10 @@ def tables(tmp_path_factory):
         assert out.returncode == 0, out.stderr
         return _parse(out.stdout)
 
-    def plan(n, ops, chunk_k=0, idx0=0):
+    def plan(n, ops, chunk_k=0, idx0=0, layers=1):
         p = d / "circ.bin"
         p.write_bytes(bytes(encode_ops(ops)) if ops else b"")
-        out = subprocess.run([exe, "plan", str(n), str(chunk_k), str(idx0), str(p)],
+        out = subprocess.run([exe, "plan", str(n), str(chunk_k), str(idx0), str(p), str(layers)],
                              capture_output=True, text=True, timeout=60)
         assert out.returncode == 0, out.stderr
         steps = []
@@ -90,7 +90,7 @@ def tables(tmp_path_factory):
                 return {"err": ln[4:]}
             if t[0] == "STEP":
                 steps.append({"kind": int(t[1]), "n": int(t[3]), "items": []})
-            elif t[0] == "CHUNK":
+            elif t[0] == "CHUNK":  # one line per sub-layer
                 v = [int(x) for x in t[1:]]
                 steps[-1]["items"].append({"n_blocks": v[0], "uncond": v[1], "n_conds": v[2],
                                            "kinds": v[3:]})
@@ -281,24 +281,45 @@ def _oracle_chunk_summary(n, chunk):
             "n_conds": sum(g.cond is not None for g in chunk), "kinds": kinds}
 
 
-@pytest.mark.parametrize("chunk_k", [0, 3])
+@pytest.mark.parametrize("layers", [1, 2, 3, 4])
+@pytest.mark.parametrize("chunk_k", [0, 3, 11])
 @pytest.mark.parametrize("name", ["teleport", "ghz", "brickwork"])
-def test_circuit_plan_matches_the_oracle_chunking(tables, name, chunk_k):
+def test_circuit_plan_matches_the_oracle_chunking(tables, name, chunk_k, layers):
     circ = {"teleport": C.teleport(2), "ghz": C.ghz_dynamic(20),
             "brickwork": C.brickwork(9, 6, 0.3, 7)}[name]
     idx0 = 5
-    steps = tables.plan(circ.n_qubits, circ.ops, chunk_k, idx0)
-    n, ref = LY.chunk_circuit(circ, chunk_k)
+    steps = tables.plan(circ.n_qubits, circ.ops, chunk_k, idx0, layers)
+    n, ref = LY.chunk_circuit(circ, chunk_k, layers)
     want, runs, ord_ = [], 0, idx0
     for i, st in enumerate(ref):
         if isinstance(st, list):
-            want.append(_oracle_chunk_summary(n, st))
+            # one launch per chunk, its sub-layers in order
+            want.append([_oracle_chunk_summary(n, sub) for sub in LY.sublayers(st)])
         else:
             want.append((st.qubit, st.cbit, ord_))
             ord_ += 1
             runs += int(i == 0 or isinstance(ref[i - 1], list))
-    got = [item for s in steps for item in s["items"]]
+    got = []
+    for s in steps:
+        if s["kind"] == 0:
+            got.append(s["items"])
+        else:
+            got += s["items"]
     assert got == want
     # one launch per chunk and one per maximal run of consecutive measurements
     assert sum(s["kind"] == 1 for s in steps) == runs
-    assert all(s["n"] == len(s["items"]) for s in steps if s["kind"] == 1)
+    assert all(s["n"] == len(s["items"]) for s in steps)
+    assert all(1 <= s["n"] <= max(layers, 1) for s in steps if s["kind"] == 0)
+
+
+@pytest.mark.parametrize("layers", [1, 2, 3, 4])
+def test_unitary_brickwork_chunks_hold_the_layer_count(tables, layers):
+    # without measurements, depth 7 gives ceil(7 / layers) chunks of `layers` sub-layers
+    # (the last one shorter), each sub-layer one brickwork layer
+    circ = C.brickwork(9, 7, 0.0, 3)
+    steps = tables.plan(circ.n_qubits, circ.ops, 0, 0, layers)
+    assert all(s["kind"] == 0 for s in steps)
+    sizes = [s["n"] for s in steps]
+    assert sizes == [layers] * (7 // layers) + ([7 % layers] if 7 % layers else [])
+    blocks = [it["n_blocks"] for s in steps for it in s["items"]]
+    assert blocks == [4] * 7  # n = 9: pairs from 0 and from 1 both give four blocks
