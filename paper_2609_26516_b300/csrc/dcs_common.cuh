@@ -475,7 +475,9 @@ __host__ __device__ inline size_t qr_blocked_scratch(int m, int n) {
 // T upper triangular (T_jj = tau_j, T[0:j, j] = -tau_j T[0:j, 0:j] U[:, 0:j]^H u_j); the
 // columns right of the panel take F -= U T^H (U^H F) in three GEMMs, and Q is accumulated
 // from the right, Q -= U T (U^H Q) per panel.  The GEMMs go through wgemm (tensor cores on
-// the TF32X3 path).  ws: qr_blocked_scratch(m, n) complex in global memory.
+// the TF32X3 path).  ws: qr_blocked_scratch(m, n) complex in global memory.  With Q null
+// only the factorisation runs: R is then F's strict upper triangle with the diagonal in
+// sm.alph[0 .. r).
 template <int NT>
 static __device__ int cta_qr_blocked(Work& sm, float2* F, int m, int n, float2* Q, int ldq, float2* ws) {
   const int r = m < n ? m : n;
@@ -531,6 +533,7 @@ static __device__ int cta_qr_blocked(Work& sm, float2* F, int m, int n, float2* 
       __syncthreads();
     }
   }
+  if (Q == nullptr) return r;
   // Q = H_0 ... H_{r-1} [I_r; 0], panels applied from the last one
   for (int idx = threadIdx.x; idx < m * r; idx += NT) {
     const int i = idx % m, j = idx / m;

@@ -15,6 +15,11 @@ namespace dcs {
 #ifndef DCS_SVD_CPW
 #define DCS_SVD_CPW 2
 #endif
+// Blocks of at least 128 x 128 are preconditioned by a norm-sorted QR before the Jacobi
+// sweeps (DCS_SVD_QRPRE 0: Jacobi on the two-site tensor itself).
+#ifndef DCS_SVD_QRPRE
+#define DCS_SVD_QRPRE 1
+#endif
 
 
 // T2[b][s][e][x] = sum_{d,t} T1(b, d, t, x) W(d, s, t, e) with T1 at
@@ -247,18 +252,79 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
     // (descending: V S) without accumulating the rotations, and the factor on the other
     // side comes from one GEMM with an untouched copy of Theta: S_k V_k^H = U_k^H Theta
     // (ascending), U_k S_k = Theta V_k (descending).  Neither needs S^-1.
-    float2* Y = sm.T2;  // ascending: a copy of Theta; descending: Theta^H (nn x m)
+    //
+    // Large blocks are preconditioned first (Drmac-Veselic: QR with the columns in order of
+    // decreasing norm, then Jacobi on R^H, which is far closer to orthogonal columns and
+    // converges in fewer sweeps).  P = Theta^H (ascending) or Theta (descending) has its
+    // columns sorted by norm (permutation pi), P pi = Q R (blocked Householder, GEMMs on the
+    // tensor cores in the TF32X3 / BF16X3 kernels), and Z = R^H satisfies
+    // pi^T P^H = Z Q^H: Z has the column space and singular values of Theta (ascending) or
+    // Theta^H (descending) with its rows permuted by pi, so the orthogonalised columns of Z
+    // are U (or V) with row i standing for row pi(i).  Q is not formed.
+    float2* Y = sm.T2;  // ascending: a copy of Theta; descending: Theta^H (nn x m) or Z
+    const int rp = asc ? nn : m, cp = asc ? m : nn;  // P: rp x cp
+    const bool pre = DCS_SVD_QRPRE && rp >= 128 && cp >= 128 &&
+                     qr_blocked_scratch(rp, cp) <= (size_t)(c.dmax + 2) * C * C;
     for (int idx = threadIdx.x; idx < m * nn; idx += NT) {
       if (asc) {
         Y[idx] = X[idx];
-      } else {
+      } else if (!pre) {
         const int row = idx % m, col = idx / m;
         Y[col + (size_t)row * nn] = cconj(X[idx]);
       }
     }
     __syncthreads();
     float2* Z = asc ? X : Y;
-    const int zr = asc ? m : nn, zc = asc ? nn : m;
+    int zr = asc ? m : nn, zc = asc ? nn : m;
+    const int* piv = nullptr;  // row i of Z stands for row piv[i] of U (V)
+    if (pre) {
+      int* pv = reinterpret_cast<int*>(sm.F);  // the F tile is free during the guess
+      float* nrm = sm.sigf;
+      if (asc) {  // squared norms of Theta's rows
+        for (int i = threadIdx.x; i < m; i += NT) {
+          float a = 0.f;
+          for (int j = 0; j < nn; ++j) a += cabs2(X[i + (size_t)j * m]);
+          nrm[i] = a;
+        }
+      } else {    // of its columns, one warp per column
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        for (int j = warp; j < nn; j += NT / 32) {
+          float a = 0.f;
+          for (int i = lane; i < m; i += 32) a += cabs2(X[i + (size_t)j * m]);
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(FULL_MASK, a, o);
+          if (lane == 0) nrm[j] = a;
+        }
+      }
+      __syncthreads();
+      for (int j = threadIdx.x; j < cp; j += NT) {  // decreasing norm, ties by index
+        const float v = nrm[j];
+        int rank = 0;
+        for (int k = 0; k < cp; ++k) {
+          const float w = nrm[k];
+          rank += (w > v) || (w == v && k < j);
+        }
+        pv[rank] = j;
+      }
+      __syncthreads();
+      float2* Fq = sm.R;  // P pi, rp x cp column-major
+      for (int idx = threadIdx.x; idx < rp * cp; idx += NT) {
+        const int i = idx % rp, j = idx / rp;
+        Fq[idx] = asc ? cconj(X[pv[j] + (size_t)i * m]) : X[i + (size_t)pv[j] * m];
+      }
+      __syncthreads();
+      const int r = cta_qr_blocked<NT>(sm, Fq, rp, cp, nullptr, 0, sm.E);
+      // Z = R^H (cp x r, lower triangular): ascending over Theta in X (its copy is in Y),
+      // descending in Y (X keeps Theta)
+      for (int idx = threadIdx.x; idx < cp * r; idx += NT) {
+        const int i = idx % cp, j = idx / cp;
+        Z[idx] = j < i ? cconj(Fq[j + (size_t)i * rp]) : (j == i ? cconj(sm.alph[j]) : cz());
+      }
+      __syncthreads();
+      zr = cp;
+      zc = r;
+      piv = pv;
+    }
     // columns of up to 512 rows: the register-resident variant
     const int svd_sweeps =
         (DCS_SVD_REGS && zr <= 512 && zc >= 2 * (NT / 32))
@@ -294,7 +360,8 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
       for (int idx = threadIdx.x; idx < m * kk; idx += NT) {
         const int row = idx / kk, k2 = idx % kk;
         const float sg = sm.sigf[sm.perm[k2]];
-        pq[idx] = cscale(X[row + (size_t)sm.perm[k2] * m], sg > 0.f ? 1.f / sqrtf(sg) : 0.f);
+        const int dst = piv ? piv[row] * kk + k2 : idx;
+        pq[dst] = cscale(Z[row + (size_t)sm.perm[k2] * zr], sg > 0.f ? 1.f / sqrtf(sg) : 0.f);
       }
       __syncthreads();
       wgemm<NT>(sm, kk, nn, m, pq, 1, kk, true, Y, 1, m, false, pq1, nn, 1);
@@ -306,7 +373,8 @@ __global__ void __launch_bounds__(NT, 1) k_compress_big(DevCtx c, int C, const D
       for (int idx = threadIdx.x; idx < kk * nn; idx += NT) {
         const int k2 = idx / nn, col = idx % nn;
         const float sg = sm.sigf[sm.perm[k2]];
-        pq1[idx] = cscale(cconj(Y[col + (size_t)sm.perm[k2] * nn]), sg > 0.f ? 1.f / sqrtf(sg) : 0.f);
+        const int dst = piv ? k2 * nn + piv[col] : idx;
+        pq1[dst] = cscale(cconj(Z[col + (size_t)sm.perm[k2] * zr]), sg > 0.f ? 1.f / sqrtf(sg) : 0.f);
       }
       __syncthreads();
       wgemm<NT>(sm, m, kk, nn, X, 1, m, false, pq1, 1, nn, true, pq, kk, 1);

@@ -196,7 +196,9 @@ struct TcState {
   int* uses;           // [0] stages and [1] tiles run since tc_setup (the barriers' phases)
   uint32_t* tmem;      // TMEM base address (written by tmem_alloc)
   int* err;            // set to 1 if a bounded wait gave up
-  bool bf16;           // BF16x3 products instead of 3xTF32
+  bool bf16;           // BF16x3 products instead of 3xTF32; fixed for the whole kernel: the
+                       // stage size, hence the pipeline depth behind the barrier phases,
+                       // depends on it
 };
 
 // Bytes of the smem head tc_setup needs: the mbarriers, the two counters, TMEM base, error.
