@@ -277,7 +277,10 @@ dcs_status_t dcs_get_counters(dcs_ctx_t ctx, uint64_t* compressions, uint64_t* s
  * A, B, C are DEVICE complex64 arrays, strides in elements (each below 2^31).
  * mode DCS_GEMM_SIMT: FP32 CUDA-core GEMM with shared-memory tiles.
  * mode DCS_GEMM_TENSOR: tcgen05 tensor-core GEMM (TF32 inputs, FP32 accumulators in tensor
- * memory) with each operand split as x = hi + lo (3 products), FP32-level accuracy;
+ * memory) with each operand split as x = hi + lo (3 products): about 2^-22 relative per
+ * product, plus the rounding of the tensor core's FP32 accumulation, which grows with K
+ * (relative Frobenius error of random products measured at 1.4e-6 for K = 64 and 1.5e-5 for
+ * K = 1024, against 2e-7 and 8e-7 for DCS_GEMM_SIMT);
  * mode DCS_GEMM_TENSOR_BF16X3: the same with BF16 parts (kind::f16), about 2^-16 relative;
  * err_dev: DEVICE int set to 1 if a bounded completion wait gave up (result invalid).
  * One CTA per problem; asynchronous on `stream`. */

@@ -388,6 +388,7 @@ static __device__ void carve(Work& w, unsigned char* raw, int C, float2* big_are
                              int dmax = 4) {
   w.C = C;
   w.use_tc = tc;
+  w.tc.bf16 = false;  // set by the tensor-core kernels after tc_setup; read by the gauge moves
   w.stage = nullptr;
   w.stage_elems = 0;
   if (big_area) {  // head (barriers, counters), then the 128-byte aligned staging region

@@ -1,7 +1,9 @@
 // Tensor-core complex GEMM for sm_103a: tcgen05.mma (kind::tf32) with the accumulators in
 // tensor memory (TMEM), issued by one thread of the CTA, completion signalled on mbarriers.
 //
-// C[m, n] = sum_k opA(m, k) opB(k, n) in complex64 with FP32 accuracy:
+// C[m, n] = sum_k opA(m, k) opB(k, n) in complex64 with FP32 accumulators in TMEM (each MMA's
+// rounding into the accumulator adds an error that grows with K, above CUDA-core FP32 for
+// long products):
 //  * real embedding: A_r[m][2k] = Re a, A_r[m][2k+1] = Im a;
 //    B_r[2k][2n] = Re b, B_r[2k+1][2n] = -Im b, B_r[2k][2n+1] = Im b, B_r[2k+1][2n+1] = Re b,
 //    so that (A_r B_r)[m][2n] = Re c and [m][2n+1] = Im c;

@@ -1,8 +1,11 @@
 """dcs_cgemm (the contraction primitive of the large-bond kernels) against PyTorch complex128
 matmul: FP32 SIMT, tcgen05 tensor-core 3xTF32 and BF16x3 modes, ragged sizes, strided and
-conjugated operands.  Bars: relative Frobenius error <= 1e-5 (FP32 accuracy; SIMT, 3xTF32)
+conjugated operands.  Bars: relative Frobenius error <= 1e-5 (SIMT, 3xTF32 up to K = 500)
 and <= 3e-5 for BF16x3, whose split x = hi + lo keeps x to 2^-18 relative and drops a
-lo lo term of at most 2^-18 |a||b| per product (three such terms: <= 1.2e-5 per product)."""
+lo lo term of at most 2^-18 |a||b| per product (three such terms: <= 1.2e-5 per product).
+The tensor modes also round once per MMA into the FP32 accumulator in tensor memory, an
+error that grows with K (measured: 3xTF32 1.4e-6 at K = 64, 1.5e-5 at K = 1024, 5.9e-5 at
+K = 4096; SIMT 2e-7, 8e-7, 1.6e-6): the long-K test bounds it."""
 import ctypes
 
 import numpy as np
@@ -59,6 +62,16 @@ IDS = ["simt", "tensor", "tensor_bf16x3"]
                                    (1, 64, 300, 500), (1, 7, 5, 3)])
 def test_cgemm_plain(mode, shape):
     assert _run(mode, *shape) <= BAR[mode]
+
+
+@pytest.mark.parametrize("mode", MODES, ids=IDS)
+def test_cgemm_long_k(mode):
+    # the site-contraction shape of chi 256 (K = 1024) and a four times longer product: the
+    # tensor modes' accumulation error grows about linearly with K, the SIMT mode's slowly
+    bars = {0: 8e-6, 1: 1.2e-4, 2: 1.2e-4}
+    e1 = _run(mode, 1, 512, 256, 1024, transB=True, seed=5)
+    e4 = _run(mode, 1, 256, 256, 4096, seed=5)
+    assert e1 <= bars[mode] / 4 and e4 <= bars[mode]
 
 
 @pytest.mark.parametrize("mode", MODES, ids=IDS)
