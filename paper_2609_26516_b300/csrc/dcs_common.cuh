@@ -502,21 +502,36 @@ static __device__ int cta_qr_blocked(Work& sm, float2* F, int m, int n, float2* 
     house_columns<NT>(F, m, m, p0, p0 + pb, p0 + pb, sm.tau, sm.alph, sm.red);
     __syncthreads();
     gather_u(p0, pb);
-    // S = U^H U into W, then T column by column (one thread per row of T)
+    // S = U^H U into W, then T column by column (one thread per row of T), both in the
+    // staging area (free between GEMMs) when it holds them, T copied out for the GEMMs
     float2* T = Tall + (size_t)p * QR_PB * QR_PB;
     wgemm<NT>(sm, pb, pb, mu, U, mu, 1, true, U, 1, mu, false, W, pb, 1);
+    const bool staged = sm.stage != nullptr && sm.stage_elems >= (size_t)2 * QR_PB * QR_PB;
+    float2* sS = staged ? sm.stage : W;                       // S, ld pb
+    float2* sT = staged ? sm.stage + QR_PB * QR_PB : T;       // T, ld QR_PB
+    if (staged) {
+      for (int idx = threadIdx.x; idx < pb * pb; idx += NT) sS[idx] = W[idx];
+      __syncthreads();
+    }
     for (int j = 0; j < pb; ++j) {
       const float tj = sm.tau[p0 + j];
       if ((int)threadIdx.x < pb) {
         const int i = threadIdx.x;
         float2 v = cz();
         if (i < j) {
-          for (int l = i; l < j; ++l) cfma(v, T[i * QR_PB + l], W[l * pb + j]);
+          for (int l = i; l < j; ++l) cfma(v, sT[i * QR_PB + l], sS[l * pb + j]);
           v = cscale(v, -tj);
         } else if (i == j) {
           v = make_float2(tj, 0.f);
         }
-        T[i * QR_PB + j] = v;
+        sT[i * QR_PB + j] = v;
+      }
+      __syncthreads();
+    }
+    if (staged) {
+      for (int idx = threadIdx.x; idx < pb * QR_PB; idx += NT) {
+        const int i = idx / QR_PB, j = idx % QR_PB;
+        if (j < pb) T[idx] = sT[idx];
       }
       __syncthreads();
     }

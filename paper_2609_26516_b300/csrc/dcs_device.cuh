@@ -205,21 +205,45 @@ __device__ void house_columns(float2* X, int m, int ld, int k0, int k1, int napp
     }
     __syncthreads();
     if (!skip) {
+      // rows in chunks of 32 HC per warp, each chunk's loads issued together (X may sit in
+      // global memory, where one dependent load per row would serialise the latencies); the
+      // sums run in row order as a plain loop would
+      constexpr int HC = 8;
       for (int j = k + 1 + warp; j < napply; j += NW) {
         float2 d = cz();
-        for (int i = k + lane; i < m; i += 32) cfmac(d, X[i + k * ld], X[i + j * ld]);
+        for (int i0 = k + lane; i0 < m; i0 += 32 * HC) {
+          float2 u[HC], x[HC];
+#pragma unroll
+          for (int t = 0; t < HC; ++t) {
+            const int i = i0 + 32 * t;
+            u[t] = i < m ? X[i + k * ld] : cz();
+            x[t] = i < m ? X[i + j * ld] : cz();
+          }
+#pragma unroll
+          for (int t = 0; t < HC; ++t) cfmac(d, u[t], x[t]);
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
           d.x += __shfl_xor_sync(0xffffffffu, d.x, o);
           d.y += __shfl_xor_sync(0xffffffffu, d.y, o);
         }
         d = cscale(d, 2.f);
-        for (int i = k + lane; i < m; i += 32) {
-          float2 v = X[i + k * ld];
-          float2 a = X[i + j * ld];
-          a.x -= v.x * d.x - v.y * d.y;
-          a.y -= v.x * d.y + v.y * d.x;
-          X[i + j * ld] = a;
+        for (int i0 = k + lane; i0 < m; i0 += 32 * HC) {
+          float2 u[HC], x[HC];
+#pragma unroll
+          for (int t = 0; t < HC; ++t) {
+            const int i = i0 + 32 * t;
+            u[t] = i < m ? X[i + k * ld] : cz();
+            x[t] = i < m ? X[i + j * ld] : cz();
+          }
+#pragma unroll
+          for (int t = 0; t < HC; ++t) {
+            const int i = i0 + 32 * t;
+            float2 a = x[t];
+            a.x -= u[t].x * d.x - u[t].y * d.y;
+            a.y -= u[t].x * d.y + u[t].y * d.x;
+            if (i < m) X[i + j * ld] = a;
+          }
         }
       }
     }
