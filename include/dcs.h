@@ -321,7 +321,7 @@ dcs_status_t dcs_cgemm(int32_t mode, int32_t batch, int32_t M, int32_t N, int32_
  *   device wait that gave up gives f = NaN.
  *
  * The first call on a device looks up the scratch array's device address for that device
- * (with the device current); make that first call before any stream capture.  Calls share
+ * (with the device current).  Calls share
  * the scratch and it keeps the last call's contents, so calls that overlap on the GPU (on
  * different streams) race.  The call copies the chunk's tables from static host storage and
  * returns after they have been staged, which waits for earlier work on the stream.

@@ -17,56 +17,88 @@ constexpr int GEMM_SIMT_SMEM_ELEMS = GBM * GSA_LD + GBK * GSB_LD;
 // conjA), opB(k, n) = B[k sbk + n sbn] (conjugated if conjB), C[m scm + n scn].  FP32 SIMT
 // with 64 x 64 x 16 shared-memory tiles (sA, sB: GEMM_SIMT_SMEM_ELEMS complex); each thread
 // owns an 8-element micro tile, 2 rows x 4 columns at 512 threads, so a k step costs two
-// broadcast loads of A and two 16-byte loads of B for eight complex FMAs.
+// broadcast loads of A and two 16-byte loads of B for eight complex FMAs.  The next k tile's
+// elements are loaded into registers while the current one is multiplied.
 template <int NT>
 __device__ void cta_cgemm(int M, int N, int K, const float2* A, int sam, int sak, bool conjA,
                           const float2* B, int sbk, int sbn, bool conjB, float2* Cm, int scm,
                           int scn, float2* sA, float2* sB, bool accumulate = false) {
   static_assert((GBM * GBN) % NT == 0, "tile / threads");
   constexpr int PER = GBM * GBN / NT;  // outputs per thread
+  constexpr int LA = (GBM * GBK + NT - 1) / NT, LB = (GBK * GBN + NT - 1) / NT;
   const int tid = threadIdx.x;
   for (int m0 = 0; m0 < M; m0 += GBM)
     for (int n0 = 0; n0 < N; n0 += GBN) {
       float2 acc[PER];
 #pragma unroll
       for (int i = 0; i < PER; ++i) acc[i] = cz();
-      for (int k0 = 0; k0 < K; k0 += GBK) {
-        // stage A tile (GBM x GBK) as sA[m][k] and B tile (GBK x GBN) as sB[k][n]
-        for (int idx = tid; idx < GBM * GBK; idx += NT) {
+      // element r of this thread in the A tile (GBM x GBK, stored sA[m][k]) and the B tile
+      // (GBK x GBN, stored sB[k][n]), in the order that keeps the global loads coalesced
+      auto a_pos = [&](int idx, int& mm, int& kk) {
+        if (sak == 1) {
+          mm = idx / GBK;
+          kk = idx % GBK;
+        } else {
+          kk = idx / GBM;
+          mm = idx % GBM;
+        }
+      };
+      auto b_pos = [&](int idx, int& kk, int& nn) {
+        if (sbn == 1) {
+          kk = idx / GBN;
+          nn = idx % GBN;
+        } else {
+          nn = idx / GBK;
+          kk = idx % GBK;
+        }
+      };
+      float2 ra[LA], rb[LB];
+      auto load_tile = [&](int k0) {
+#pragma unroll
+        for (int r = 0; r < LA; ++r) {
+          const int idx = tid + r * NT;
           int mm, kk;
-          if (sak == 1) {
-            mm = idx / GBK;
-            kk = idx % GBK;
-          } else {
-            kk = idx / GBM;
-            mm = idx % GBM;
-          }
+          a_pos(idx, mm, kk);
           const int gm = m0 + mm, gk = k0 + kk;
           float2 v = cz();
-          if (gm < M && gk < K) {
+          if (idx < GBM * GBK && gm < M && gk < K) {
             v = A[(size_t)gm * sam + (size_t)gk * sak];
             if (conjA) v.y = -v.y;
           }
-          sA[mm * GSA_LD + kk] = v;
+          ra[r] = v;
         }
-        for (int idx = tid; idx < GBK * GBN; idx += NT) {
+#pragma unroll
+        for (int r = 0; r < LB; ++r) {
+          const int idx = tid + r * NT;
           int kk, nn;
-          if (sbn == 1) {
-            kk = idx / GBN;
-            nn = idx % GBN;
-          } else {
-            nn = idx / GBK;
-            kk = idx % GBK;
-          }
+          b_pos(idx, kk, nn);
           const int gk = k0 + kk, gn = n0 + nn;
           float2 v = cz();
-          if (gk < K && gn < N) {
+          if (idx < GBK * GBN && gk < K && gn < N) {
             v = B[(size_t)gk * sbk + (size_t)gn * sbn];
             if (conjB) v.y = -v.y;
           }
-          sB[kk * GSB_LD + nn] = v;
+          rb[r] = v;
+        }
+      };
+      load_tile(0);
+      for (int k0 = 0; k0 < K; k0 += GBK) {
+#pragma unroll
+        for (int r = 0; r < LA; ++r) {
+          const int idx = tid + r * NT;
+          int mm, kk;
+          a_pos(idx, mm, kk);
+          if (idx < GBM * GBK) sA[mm * GSA_LD + kk] = ra[r];
+        }
+#pragma unroll
+        for (int r = 0; r < LB; ++r) {
+          const int idx = tid + r * NT;
+          int kk, nn;
+          b_pos(idx, kk, nn);
+          if (idx < GBK * GBN) sB[kk * GSB_LD + nn] = rb[r];
         }
         __syncthreads();
+        if (k0 + GBK < K) load_tile(k0 + GBK);
         if constexpr (NT == 512) {
           // rows 2 ty, 2 ty + 1 and columns 4 tx .. 4 tx + 3, tx = tid mod 16
           const int tx = tid & 15, ty = tid >> 4;
