@@ -1,5 +1,5 @@
 """Parity with the FP64 oracle in the truncated regime, at the large-bond workloads' bond
-sizes (chi_max = 256 single-path, chi_max = 64 multi-path with M = 64 and pruning).
+sizes (chi_max = 256 single-path, chi_max = 64 and 128 multi-path with M = 64 and pruning).
 
 Per-step parity: the oracle's state after a saturated layer is imported into the GPU (rounded
 to complex64) and both run the same compression step (Sec. "Simulating unitary quantum
@@ -103,6 +103,32 @@ def test_multi_path_m64_truncated_pruned(prec):
     assert max(b.F for b in ref) < 1 - 1e-4
     assert sum(b.p for b in ref) < 0.5
     for i, b in enumerate(ref):
+        assert abs(res["F"][i] - b.F) < f_tol(n, depth)
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=PREC_IDS)
+def test_multi_path_m64_chi128_truncated(prec):
+    # the multi-path ensemble at a larger bond: n = 18, every one of the M = 64 retained
+    # branches truncated at chi_max = 128 (each loses fidelity), 64 distinct keys, top-M cut
+    # through many more paths (Alg. 2; the one-site updates of Sec. "Simulating unitary
+    # quantum circuits with DMRG" on every branch)
+    n, depth, p, seed, chi, M = 18, 16, 0.03, 3, 128, 64
+    circ = C.brickwork(n, depth, p, seed)
+    ref = _ref_multi(n, depth, p, seed, chi, M)
+    sim = _sim(n, chi, 2 * M, circ.n_cbits, prec=prec)
+    sim.init_state(1, multipath=True)
+    sim.run_circuit(circ, max_branches=M)
+    res = sim.results()
+    assert res["n_active"] == len(ref) == M
+    ps = np.array([b.p for b in ref])
+    assert len(np.unique(np.round(ps / (1e-5 * ps.max())))) == M
+    assert min(max(b.mps.bonds()) for b in ref) == chi
+    assert max(b.F for b in ref) < 1 - 1e-6
+    assert sum(b.p for b in ref) < 0.5
+    for i, b in enumerate(ref):
+        assert res["bits"][i].tolist() == [int(x) for x in b.c], f"branch {i}"
+        assert abs(res["p"][i] - b.p) < P_TOL
+        assert _state_fid(sim, i, b.mps) >= 1 - STATE_TOL
         assert abs(res["F"][i] - b.F) < f_tol(n, depth)
 
 
