@@ -217,6 +217,29 @@ dcs_status_t dcs_set_pruning(dcs_ctx_t ctx, double p_min);
  * The retained branches keep their relative order; p is not renormalised. */
 dcs_status_t dcs_branch_topk(dcs_ctx_t ctx, int M);
 
+/* Branch compaction by an explicit selection: entry i of the active list (the order of
+ * dcs_get_results) stays iff keep[i] != 0; the kept branches keep their relative order, the
+ * dropped slots are free for the next split; p is not renormalised.  keep is a HOST array of
+ * n bytes, staged through the context's pinned buffer; n must equal the active count, which
+ * the device checks: a different count leaves the list unchanged, and dcs_get_results
+ * returns DCS_ERR_INVALID from then until the next dcs_init_state.  This is the last step of
+ * TopKByWeight (Alg. 2) when the ensemble is sharded over several contexts (one per GPU):
+ * each rank gathers every rank's p, selects with dcs_topk_select_global, and keeps its own
+ * slice.  DCS_ERR_INVALID for a null mask, n < 0, n > n_slots or a single-path context. */
+dcs_status_t dcs_branch_keep(dcs_ctx_t ctx, const uint8_t* keep, int n);
+
+/* Host-only, needs no context or device: TopKByWeight (Alg. 2) and adaptive pruning over
+ * an ensemble spread across ranks.  p holds the n path probabilities of every rank's active
+ * branches, concatenated in rank order (each rank's list in the order of dcs_get_results),
+ * which is the list order of the whole ensemble.  keep (n bytes) receives 1 for the
+ * retained branches: if n > M the M largest by the key round(p / (1e-5 * max p)) of
+ * dcs_branch_topk, the maximum taken over all n, equal keys keeping list order; then, when
+ * p_min > 0, every retained branch with p < p_min is dropped except the first of the key
+ * order (the rule of dcs_set_pruning).  The result equals what one context holding the whole
+ * list would keep.  DCS_ERR_INVALID for n < 0, M < 1, null pointers with n > 0, p_min outside
+ * [0, 1), or a p that is negative or not finite. */
+dcs_status_t dcs_topk_select_global(const double* p, int n, int M, double p_min, uint8_t* keep);
+
 /* Synchronises and copies results to HOST buffers (each may be NULL, each sized for
  * n_slots entries): for the active slots in list order, p (n doubles), F (n doubles), the
  * register (n * DCS_CWORDS words), flags (n bytes), and the number n of active slots.  The

@@ -61,6 +61,8 @@ SIGNATURES = {
     "dcs_collapse": (_c.c_int, [_P, _c.c_int, _c.c_int, _c.POINTER(_c.c_uint8)]),
     "dcs_branch_split": (_c.c_int, [_P, _c.c_int, _c.c_int, _c.c_double]),
     "dcs_branch_topk": (_c.c_int, [_P, _c.c_int]),
+    "dcs_branch_keep": (_c.c_int, [_P, _P, _c.c_int]),
+    "dcs_topk_select_global": (_c.c_int, [_P, _c.c_int, _c.c_int, _c.c_double, _P]),
     "dcs_set_pruning": (_c.c_int, [_P, _c.c_double]),
     "dcs_get_results": (_c.c_int, [_P, _P, _P, _P, _c.POINTER(_c.c_int), _P]),
     "dcs_get_bonds": (_c.c_int, [_P, _P, _c.POINTER(_c.c_int)]),

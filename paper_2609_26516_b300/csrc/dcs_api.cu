@@ -488,6 +488,45 @@ dcs_status_t dcs_branch_topk(dcs_ctx_t c, int M) {
   return post_launch(c, "topk");
 }
 
+dcs_status_t dcs_branch_keep(dcs_ctx_t c, const uint8_t* keep, int n) {
+  if (!c || n < 0 || (n > 0 && !keep)) return fail(c, DCS_ERR_INVALID, "null mask or negative length");
+  if (!c->multipath) return fail(c, DCS_ERR_INVALID, "branch keep needs multi-path mode");
+  if (n > c->cfg.n_slots) return fail(c, DCS_ERR_INVALID, "mask longer than the branch pool");
+  Program P;
+  std::vector<uint8_t> mask(keep, keep + n);
+  DevProg dp;
+  dcs_status_t st = upload(c, P, mask, dp);
+  if (st != DCS_OK) return st;
+  launch_branch_keep(c->dev, dp.bytes, n, c->stream);
+  c->launches++;
+  return post_launch(c, "branch keep");
+}
+
+dcs_status_t dcs_topk_select_global(const double* p, int n, int M, double p_min, uint8_t* keep) {
+  if (n < 0 || M < 1 || (n > 0 && (!p || !keep)) || !(p_min >= 0.0) || p_min >= 1.0)
+    return DCS_ERR_INVALID;
+  double pmax = 0.0;
+  for (int i = 0; i < n; ++i) {
+    if (!(p[i] >= 0.0) || !std::isfinite(p[i])) return DCS_ERR_INVALID;
+    pmax = std::max(pmax, p[i]);
+  }
+  if (n == 0) return DCS_OK;
+  // the key of dcs_branch_topk, with the maximum over every rank's branches
+  std::vector<long long> key(n);
+  for (int i = 0; i < n; ++i)
+    key[i] = pmax > 0.0 ? (long long)std::floor(p[i] / (1e-5 * pmax) + 0.5) : 0;
+  std::vector<int> ord(n);
+  for (int i = 0; i < n; ++i) ord[i] = i;
+  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return key[a] > key[b]; });
+  for (int i = 0; i < n; ++i) keep[i] = n <= M ? 1 : 0;
+  if (n > M)
+    for (int r = 0; r < M; ++r) keep[ord[r]] = 1;
+  if (p_min > 0.0)
+    for (int i = 0; i < n; ++i)
+      if (keep[i] && p[i] < p_min && i != ord[0]) keep[i] = 0;
+  return DCS_OK;
+}
+
 dcs_status_t dcs_get_results(dcs_ctx_t c, double* p, double* fid, uint64_t* cbits, int* n_active,
                              uint8_t* flags) {
   if (!c) return DCS_ERR_INVALID;
@@ -547,6 +586,8 @@ dcs_status_t dcs_get_results(dcs_ctx_t c, double* p, double* fid, uint64_t* cbit
   if (st != DCS_OK) return st;
   if (status & (1 << DCS_ERR_OOM)) return fail(c, DCS_ERR_OOM, "branch pool exhausted");
   if (status & (1 << DCS_ERR_UNSUPPORTED)) return fail(c, DCS_ERR_UNSUPPORTED, "branch pool above 1024 slots");
+  if (status & (1 << DCS_ERR_INVALID))
+    return fail(c, DCS_ERR_INVALID, "branch keep mask length differed from the active count");
   return DCS_OK;
 }
 

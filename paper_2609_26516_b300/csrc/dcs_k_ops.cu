@@ -374,6 +374,23 @@ __global__ void k_branch_topk(DevCtx c, int M) {
   }
 }
 
+// Compaction of the current list by a caller's keep mask (one thread): entry i of the list
+// stays iff keep[i] != 0, the kept entries in their relative order; the dropped slots become
+// free for the next split.  A mask whose length n differs from the active count leaves the
+// list as it is and raises DCS_ERR_INVALID in the status word.
+__global__ void k_branch_keep(DevCtx c, const uint8_t* keep, int n) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int cnt = *c.count;
+  if (cnt != n) {
+    *c.status |= 1 << DCS_ERR_INVALID;
+    return;
+  }
+  int k = 0;
+  for (int i = 0; i < cnt; ++i)
+    if (keep[i]) c.order[k++] = c.order[i];
+  *c.count = k;
+}
+
 // ----------------------------------------------------------------------------- launchers
 int fused_chi(int chi_max) {
   if (chi_max <= 4) return 4;
@@ -425,6 +442,10 @@ void launch_branch_split(const DevCtx& c, int q, int cbit, double eps, int M, do
 
 void launch_branch_topk(const DevCtx& c, int M, cudaStream_t s) {
   k_branch_topk<<<1, 256, 0, s>>>(c, M);
+}
+
+void launch_branch_keep(const DevCtx& c, const uint8_t* keep, int n, cudaStream_t s) {
+  k_branch_keep<<<1, 32, 0, s>>>(c, keep, n);
 }
 
 }  // namespace dcs

@@ -12,6 +12,19 @@ import torch
 from . import _native as N
 
 
+def topk_select_global(p, M: int, p_min: float = 0.0) -> np.ndarray:
+    """dcs_topk_select_global (host-only): the keep mask (uint8 per entry) of TopKByWeight and
+    adaptive pruning over p, every rank's branch probabilities in rank order."""
+    lib = N.load()
+    pa = np.ascontiguousarray(p, dtype=np.float64)
+    keep = np.zeros(pa.size, dtype=np.uint8)
+    st = lib.dcs_topk_select_global(pa.ctypes.data_as(ctypes.c_void_p), int(pa.size), int(M),
+                                    float(p_min), keep.ctypes.data_as(ctypes.c_void_p))
+    if st != N.OK:
+        raise DCSError(st, "dcs_topk_select_global: invalid arguments")
+    return keep
+
+
 class DCSError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"libdcs {N.STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
@@ -201,6 +214,12 @@ class Simulator:
 
     def branch_topk(self, M: int):
         self._check(self.lib.dcs_branch_topk(self.ctx, M))
+
+    def branch_keep(self, keep):
+        """dcs_branch_keep: keep entry i of the active list iff keep[i] is true."""
+        k = np.ascontiguousarray(np.asarray(keep) != 0, dtype=np.uint8)
+        self._check(self.lib.dcs_branch_keep(self.ctx, k.ctypes.data_as(ctypes.c_void_p),
+                                             int(k.size)))
 
     def results(self) -> dict:
         S = self.n_slots
