@@ -169,6 +169,17 @@ const char* dcs_last_error(dcs_ctx_t ctx);
  * the rest of the pool free. */
 dcs_status_t dcs_init_state(dcs_ctx_t ctx, int n_active, int multipath, uint64_t shot0);
 
+/* Hybrid single-path start (Sec. "Dynamic procedure for GHZ state preparation": multi-path
+ * evaluates the part of the circuit before the first measurement once, while independent
+ * single-path runs repeat it): after dcs_init_state(ctx, 1, 0, shot0) and the
+ * measurement-free prefix of the circuit run on that one shot, copies its state, register, p and F into list positions 1 .. n_active - 1, each
+ * shot keeping its own sampler counter shot0 + position, so that the list holds n_active
+ * shots exactly as if all of them had run the prefix.  Asynchronous.  The device checks that
+ * the list held one shot; otherwise nothing changes and dcs_get_results returns
+ * DCS_ERR_INVALID until the next dcs_init_state.  DCS_ERR_INVALID on the host for a
+ * multi-path context or n_active outside [1, n_slots]. */
+dcs_status_t dcs_fork_shots(dcs_ctx_t ctx, int n_active);
+
 /* CompressionStep for one chunk on every active slot.  gates: n_gates GATE1/GATE2 ops that
  * form one chunk: cut into sub-layers where a two-qubit gate meets a qubit that already
  * carries one of the current sub-layer, at most max(1, chunk_layers) of them (each a layer

@@ -55,6 +55,7 @@ SIGNATURES = {
     "dcs_destroy": (_c.c_int, [_P]),
     "dcs_last_error": (_c.c_char_p, [_P]),
     "dcs_init_state": (_c.c_int, [_P, _c.c_int, _c.c_int, _c.c_uint64]),
+    "dcs_fork_shots": (_c.c_int, [_P, _c.c_int]),
     "dcs_apply_layer": (_c.c_int, [_P, _c.POINTER(dcs_op), _c.c_int, _P]),
     "dcs_measure_prob": (_c.c_int, [_P, _c.c_int, _P]),
     "dcs_measure_sample": (_c.c_int, [_P, _c.c_int, _c.c_int, _c.c_uint64]),

@@ -414,6 +414,15 @@ dcs_status_t dcs_init_state(dcs_ctx_t c, int n_active, int multipath, uint64_t s
   return post_launch(c, "init");
 }
 
+dcs_status_t dcs_fork_shots(dcs_ctx_t c, int n_active) {
+  if (!c) return DCS_ERR_INVALID;
+  if (c->multipath) return fail(c, DCS_ERR_INVALID, "forking shots needs single-path mode");
+  if (n_active < 1 || n_active > c->cfg.n_slots) return fail(c, DCS_ERR_INVALID, "n_active out of range");
+  launch_fork_shots(c->dev, n_active, c->stream);
+  c->launches += 2;
+  return post_launch(c, "fork shots");
+}
+
 dcs_status_t dcs_apply_layer(dcs_ctx_t c, const dcs_op* gates, int n_gates, double* fid_out) {
   if (!c || (n_gates > 0 && !gates)) return fail(c, DCS_ERR_INVALID, "null argument");
   std::vector<dcs_op> g(gates, gates + n_gates);
@@ -587,7 +596,7 @@ dcs_status_t dcs_get_results(dcs_ctx_t c, double* p, double* fid, uint64_t* cbit
   if (status & (1 << DCS_ERR_OOM)) return fail(c, DCS_ERR_OOM, "branch pool exhausted");
   if (status & (1 << DCS_ERR_UNSUPPORTED)) return fail(c, DCS_ERR_UNSUPPORTED, "branch pool above 1024 slots");
   if (status & (1 << DCS_ERR_INVALID))
-    return fail(c, DCS_ERR_INVALID, "branch keep mask length differed from the active count");
+    return fail(c, DCS_ERR_INVALID, "branch keep or shot fork found a list of the wrong length");
   return DCS_OK;
 }
 

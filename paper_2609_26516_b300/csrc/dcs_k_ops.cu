@@ -391,6 +391,50 @@ __global__ void k_branch_keep(DevCtx c, const uint8_t* keep, int n) {
   *c.count = k;
 }
 
+// Hybrid single-path start (one CTA per slot): the common prefix of every shot, computed once
+// on slot 0, is copied into slots 1 .. n_active - 1, each keeping its own sampler counter
+// shot0 + slot.  Nothing happens unless the list holds exactly one shot; k_fork_count then
+// sets the list to n_active shots (a separate launch, so that no block reads the count after
+// it changed).
+__global__ void k_fork_shots(DevCtx c, int n_active) {
+  const int dst = blockIdx.x;
+  if (*c.count != 1 || dst == 0 || dst >= n_active || dst >= c.n_slots) return;
+  const int src = 0;
+  const int n = c.n;
+  const int kb = c.ketbuf[src];
+  const int* sb = bonds_ptr(c, src, kb);
+  for (int j = 0; j < n; ++j) {
+    const int len = sb[j] * 2 * sb[j + 1];
+    const float2* s = site_ptr(c, kb, src, j);
+    float2* d = site_ptr(c, kb, dst, j);
+    for (int e = threadIdx.x; e < len; e += blockDim.x) d[e] = s[e];
+  }
+  int* db = bonds_ptr(c, dst, kb);
+  for (int j = threadIdx.x; j <= n; j += blockDim.x) db[j] = sb[j];
+  if (threadIdx.x < DCS_CWORDS)
+    c.creg[(size_t)dst * DCS_CWORDS + threadIdx.x] = c.creg[(size_t)src * DCS_CWORDS + threadIdx.x];
+  if (threadIdx.x == 0) {
+    c.ketbuf[dst] = kb;
+    c.centre[dst] = c.centre[src];
+    c.p[dst] = c.p[src];
+    c.F[dst] = c.F[src];
+    c.rr[2 * (size_t)dst] = c.rr[2 * (size_t)src];
+    c.rr[2 * (size_t)dst + 1] = c.rr[2 * (size_t)src + 1];
+    c.flags[dst] = c.flags[src];
+    c.shot[dst] = c.shot[src] + (uint64_t)dst;
+  }
+}
+
+// The list after k_fork_shots: n_active shots, or DCS_ERR_INVALID in the status word when it
+// did not hold exactly one.
+__global__ void k_fork_count(DevCtx c, int n_active) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (*c.count != 1)
+    *c.status |= 1 << DCS_ERR_INVALID;
+  else
+    *c.count = n_active;
+}
+
 // ----------------------------------------------------------------------------- launchers
 int fused_chi(int chi_max) {
   if (chi_max <= 4) return 4;
@@ -446,6 +490,11 @@ void launch_branch_topk(const DevCtx& c, int M, cudaStream_t s) {
 
 void launch_branch_keep(const DevCtx& c, const uint8_t* keep, int n, cudaStream_t s) {
   k_branch_keep<<<1, 32, 0, s>>>(c, keep, n);
+}
+
+void launch_fork_shots(const DevCtx& c, int n_active, cudaStream_t s) {
+  k_fork_shots<<<c.n_slots, 128, 0, s>>>(c, n_active);
+  k_fork_count<<<1, 32, 0, s>>>(c, n_active);
 }
 
 }  // namespace dcs

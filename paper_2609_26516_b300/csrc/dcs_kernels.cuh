@@ -142,6 +142,7 @@ void launch_branch_split(const DevCtx& c, int q, int cbit, double eps, int M, do
                          cudaStream_t s, int* launches);
 void launch_branch_topk(const DevCtx& c, int M, cudaStream_t s);
 void launch_branch_keep(const DevCtx& c, const uint8_t* keep, int n, cudaStream_t s);
+void launch_fork_shots(const DevCtx& c, int n_active, cudaStream_t s);
 int fused_chi(int chi_max);          // shared-memory tile for chi_max (0 if above 32)
 int big_chi(int chi_max);            // slot capacity per bond of the large-tile path
 size_t big_work_elems(int chi_cap, int dmax);  // complex elements of one slot's work area

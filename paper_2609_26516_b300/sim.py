@@ -178,6 +178,11 @@ class Simulator:
     def init_state(self, n_active: int, multipath: bool = False, shot0: int = 0):
         self._check(self.lib.dcs_init_state(self.ctx, n_active, int(multipath), shot0))
 
+    def fork_shots(self, n_active: int):
+        """dcs_fork_shots: copy the one shot's state (its measurement-free prefix run once)
+        into n_active shots, each with its own sampler counter."""
+        self._check(self.lib.dcs_fork_shots(self.ctx, n_active))
+
     def run_circuit(self, circ_or_ops, meas_idx0: int = 0, max_branches: int = 0):
         ops = circ_or_ops.ops if hasattr(circ_or_ops, "ops") else circ_or_ops
         arr = encode_ops(ops)
