@@ -6,10 +6,10 @@ own share.  The ensemble's list order is the rank-major concatenation of the ran
 children stay on their parent's rank in the paper's order (m = 0 before m = 1, parents in list
 order), so that concatenation is the order one context holding every branch would have.
 Marshalling and one collective only: the selection is the library's dcs_topk_select_global,
-the compaction its dcs_branch_keep."""
+the compaction its dcs_branch_keep, everything else the library's own multi-path calls."""
 from __future__ import annotations
 
-from typing import Optional, Tuple
+from typing import List, Optional, Tuple
 
 import numpy as np
 import torch
@@ -51,3 +51,51 @@ def topk_across_ranks(sim, M: int, p_min: float = 0.0, group=None,
     keep, total = select_across_ranks(p, M, p_min, group, device or "cpu")
     sim.branch_keep(keep)
     return int(keep.sum()), total
+
+
+def _is_measurement(op) -> bool:
+    return type(op).__name__ in ("Measure", "Reset")
+
+
+def run_multi_path_sharded(sim, ops, M: int, p_min: float = 0.0, group=None,
+                           device: Optional[str] = None) -> List[Tuple[int, int]]:
+    """Alg. 2 on an ensemble split between ranks.  Every rank calls it with the same ops and
+    its own multi-path Simulator.  The ops run in calls that end at each measurement (each a
+    dcs_run_circuit without pruning: every rank splits and compresses the branches it holds).
+    Until the list has at least one branch per rank every rank holds all of it (the same
+    computation on each) and applies the top-M and p_min rules itself; the first time it has,
+    rank r keeps the r-th of `world` contiguous shares of the list.  From then on children stay
+    on their parent's rank, and after each measurement the ensemble-wide rules are applied
+    through one all-gather (topk_across_ranks).  A reset's conditional X is applied in the call
+    that holds the reset, before the selection (which does not depend on it).  Returns, per
+    measurement after the split into shares, (branches kept here, branches kept in total)."""
+    import torch.distributed as dist
+    world, rank = dist.get_world_size(group), dist.get_rank(group)
+    sim.init_state(1, multipath=True)
+    ops = ops.ops if hasattr(ops, "ops") else list(ops)
+    shared = world > 1
+    history: List[Tuple[int, int]] = []
+    seg = []
+    for op in ops:
+        seg.append(op)
+        if not _is_measurement(op):
+            continue
+        sim.run_circuit(seg)
+        seg = []
+        if not shared:
+            history.append(topk_across_ranks(sim, M, p_min, group, device))
+            continue
+        # the whole list is on every rank: select here, then split into shares if it is long
+        # enough
+        res = sim.results()
+        keep = topk_select_global(res["p"][: res["n_active"]], M, p_min)
+        idx = np.flatnonzero(keep)
+        if idx.size >= world:
+            lo, hi = rank * idx.size // world, (rank + 1) * idx.size // world
+            keep = np.zeros_like(keep)
+            keep[idx[lo:hi]] = 1
+            shared = False
+        sim.branch_keep(keep)
+    if seg:
+        sim.run_circuit(seg)
+    return history

@@ -111,3 +111,80 @@ def test_branch_keep_length_mismatch_is_reported():
     assert e.value.status == 1  # DCS_ERR_INVALID
     s.init_state(1, multipath=True)  # a fresh state clears the status
     assert s.results()["n_active"] == 1
+
+
+def _reference_by_measurement(circ, M):
+    """One context holding the whole list, the ops run in the same calls as the sharded run
+    (each ending at a measurement), pruned to M at every measurement (dcs_run_circuit)."""
+    sim = _multipath(circ)
+    seg = []
+    for op in circ.ops:
+        seg.append(op)
+        if type(op).__name__ == "Measure":
+            sim.run_circuit(seg, max_branches=M)
+            seg = []
+    if seg:
+        sim.run_circuit(seg, max_branches=M)
+    return sim
+
+
+def _rank_main(rank, world, port, M, out):
+    import os
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path[:0] = [root, os.path.join(root, "tests")]
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    import torch.distributed as dist
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import circuits as Cc
+        from paper_2609_26516_b300.ranks import run_multi_path_sharded
+        from test_gpu_parity import _sim as mk
+        circ = Cc.brickwork(N, DEPTH, P, SEED)
+        sim = mk(N, CHI, SLOTS, circ.n_cbits)
+        hist = run_multi_path_sharded(sim, circ, M)
+        r = sim.results()
+        states = [sim.export_mps(i) for i in range(r["n_active"])]
+        out.put((rank, r["p"], r["F"], r["bits"], states, hist))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_processes_sharded_run_equals_one_context():
+    # Alg. 2 end to end with the list split between two ranks (two processes, gloo for the
+    # one all-gather per measurement; their kernels never wait on each other), against one
+    # context holding the whole list: the same branches, bit for bit, in the same order
+    import multiprocessing as mp
+    import socket
+    M = 40
+    circ = _circuit()
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    out = ctx.Queue()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, M, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = sorted((out.get(timeout=600) for _ in procs), key=lambda g: g[0])
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    ref = _reference_by_measurement(circ, M)
+    rr = ref.results()
+    assert rr["n_active"] == M
+    assert sum(len(g[1]) for g in got) == M
+    # the list was split between the ranks early on, and both held branches after cuts
+    assert len(got[0][5]) == len(got[1][5]) >= 4
+    assert all(t0 == t1 for (_, t0), (_, t1) in zip(got[0][5], got[1][5]))
+    assert any(k > 0 for k, _ in got[1][5]) and any(k > 0 for k, _ in got[0][5])
+    np.testing.assert_array_equal(np.concatenate([g[1] for g in got]), rr["p"])
+    np.testing.assert_array_equal(np.concatenate([g[2] for g in got]), rr["F"])
+    np.testing.assert_array_equal(np.concatenate([g[3] for g in got]), rr["bits"])
+    states = [s for g in got for s in g[4]]
+    for i, (bonds, centre, T) in enumerate(states):
+        b2, c2, T2 = ref.export_mps(i)
+        assert bonds.tolist() == b2.tolist() and centre == c2
+        for x, y in zip(T, T2):
+            np.testing.assert_array_equal(x, y)
