@@ -101,3 +101,95 @@ def test_two_ranks_keep_what_one_list_keeps(split):
     keep = got[0][1] + got[1][1]
     assert np.flatnonzero(keep).tolist() == prune_select(ps, M, p_min)
     assert got[0][2] == got[1][2] == sum(keep)
+
+
+class _OracleSim:
+    """CPU stand-in for a multi-path Simulator, for the host logic of the sharded run: the
+    oracle's state-vector branches behind the library's call semantics (dcs_run_circuit
+    splits every branch at a measurement without pruning, children m = 0 before m = 1;
+    dcs_get_results lists p in list order; dcs_branch_keep compacts the list)."""
+
+    def __init__(self, n_qubits, n_cbits):
+        self.n, self.ncb = n_qubits, n_cbits
+
+    def init_state(self, n_active, multipath=False):
+        from oracle import statevector as SV
+        self.L = [SV.Branch(1.0, np.zeros(self.ncb, dtype=np.int64), SV.zero_state(self.n))]
+
+    def run_circuit(self, ops, meas_idx0=0, max_branches=0):
+        from circuits import Gate, Measure
+        from oracle import statevector as SV
+        assert max_branches == 0
+        for op in ops:
+            if isinstance(op, Gate):
+                for b in self.L:
+                    if SV.cond_holds(op.cond, b.c):
+                        b.psi = SV.apply_gate(b.psi, op.qubits, op.matrix)
+            elif isinstance(op, Measure):
+                nxt = []
+                for b in self.L:
+                    r0, r1 = SV.probabilities(b.psi, op.qubit)
+                    for m, rm in ((0, r0), (1, r1)):
+                        pm = rm / (r0 + r1)
+                        if pm > SV.P_EPS:
+                            c = b.c.copy()
+                            c[op.cbit] = m
+                            nxt.append(SV.Branch(b.p * pm, c, SV.project(b.psi, op.qubit, m, rm),
+                                                 b.path + [m]))
+                self.L = nxt
+            else:
+                raise TypeError(op)
+
+    def results(self):
+        return {"n_active": len(self.L), "p": np.array([b.p for b in self.L])}
+
+    def branch_keep(self, keep):
+        keep = list(keep)
+        assert len(keep) == len(self.L)
+        self.L = [b for b, k in zip(self.L, keep) if k]
+
+
+def _sharded_rank(rank, world, port, M, p_min, out):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    sys.path.insert(0, ROOT)
+    import circuits as C
+    from paper_2609_26516_b300.ranks import run_multi_path_sharded
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        circ = C.brickwork(8, 6, 0.15, 2)
+        sim = _OracleSim(circ.n_qubits, circ.n_cbits)
+        hist = run_multi_path_sharded(sim, circ, M, p_min)
+        out.put((rank, [(b.p, b.c.tolist(), b.path) for b in sim.L], hist))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world,M,p_min", [(2, 6, 0.0), (3, 10, 2e-3)])
+def test_sharded_run_keeps_the_oracles_ensemble(world, M, p_min):
+    # the driver's host logic (replicas, contiguous shares, one exchange per measurement) on
+    # world gloo ranks against Alg. 2 on one list (the oracle's run_multi_path)
+    import circuits as C
+    from oracle import statevector as SV
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    out = ctx.Queue()
+    procs = [ctx.Process(target=_sharded_rank, args=(r, world, port, M, p_min, out))
+             for r in range(world)]
+    for p in procs:
+        p.start()
+    got = sorted((out.get(timeout=300) for _ in procs), key=lambda g: g[0])
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    ref = SV.run_multi_path(C.brickwork(8, 6, 0.15, 2), M, p_min)
+    mine = [b for g in got for b in g[1]]
+    assert [b[2] for b in mine] == [b.path for b in ref]
+    assert [b[1] for b in mine] == [b.c.tolist() for b in ref]
+    assert [b[0] for b in mine] == [b.p for b in ref]
+    # the list was split into shares and the cuts were ensemble-wide
+    assert len(got[0][2]) > 0 and all(g[2][-1][1] == len(ref) for g in got)
+    assert sum(1 for g in got if any(k for k, _ in g[2])) >= 2
