@@ -278,6 +278,17 @@ dcs_status_t dcs_export_mps(dcs_ctx_t ctx, int slot, void* host_buf, size_t* byt
  * (see dcs_create), bonds 0 and n must be 1; otherwise DCS_ERR_INVALID. */
 dcs_status_t dcs_import_mps(dcs_ctx_t ctx, int slot, const void* host_buf, size_t bytes);
 
+/* Appends one branch at the end of the active list of a multi-path context, in a free slot:
+ * its MPS from a HOST buffer in the dcs_export_mps format (bond b in 1 .. cap_b, bonds 0 and
+ * n equal to 1), its path probability p, fidelity estimate F, register (DCS_CWORDS words)
+ * and flags.  This is how a branch moves between ranks of an ensemble split over several
+ * contexts (Alg. 2; the sender exports it, reads p, F, register and flags with
+ * dcs_get_results, and drops it with dcs_branch_keep).  Synchronises the device.
+ * DCS_ERR_OOM if every slot is active; DCS_ERR_INVALID for null pointers, a single-path
+ * context, a malformed buffer, p negative or not finite, or F not finite. */
+dcs_status_t dcs_branch_append(dcs_ctx_t ctx, const void* host_buf, size_t bytes, double p,
+                               double F, const uint64_t* cwords, uint8_t flags);
+
 /* Runs a whole dynamic circuit (ops in order) from the current state: resets are lowered
  * to measurement + conditional X; operations are grouped into chunks (a chunk closes at a
  * measurement, at chunk_k operations, and before a two-qubit gate touching a qubit that

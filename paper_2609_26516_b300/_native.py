@@ -69,6 +69,8 @@ SIGNATURES = {
     "dcs_get_bonds": (_c.c_int, [_P, _P, _c.POINTER(_c.c_int)]),
     "dcs_export_mps": (_c.c_int, [_P, _c.c_int, _P, _c.POINTER(_c.c_size_t)]),
     "dcs_import_mps": (_c.c_int, [_P, _c.c_int, _P, _c.c_size_t]),
+    "dcs_branch_append": (_c.c_int, [_P, _P, _c.c_size_t, _c.c_double, _c.c_double, _P,
+                                     _c.c_uint8]),
     "dcs_run_circuit": (_c.c_int, [_P, _c.POINTER(dcs_op), _c.c_int, _c.c_uint64, _c.c_int]),
     "dcs_kernel_launches": (_c.c_uint64, [_P]),
     "dcs_bytes_uploaded": (_c.c_uint64, [_P]),

@@ -719,6 +719,76 @@ dcs_status_t dcs_import_mps(dcs_ctx_t c, int pos, const void* host_buf, size_t b
   return cuda_check(c, cudaGetLastError(), "import");
 }
 
+dcs_status_t dcs_branch_append(dcs_ctx_t c, const void* host_buf, size_t bytes, double p,
+                               double F, const uint64_t* cwords, uint8_t flags) {
+  if (!c || !host_buf || !cwords) return fail(c, DCS_ERR_INVALID, "null argument");
+  if (!c->multipath) return fail(c, DCS_ERR_INVALID, "appending a branch needs multi-path mode");
+  if (!(p >= 0.0) || !std::isfinite(p) || !std::isfinite(F))
+    return fail(c, DCS_ERR_INVALID, "p must be finite and >= 0, F finite");
+  const int n = c->cfg.n_qubits;
+  const char* in = static_cast<const char*>(host_buf);
+  if (bytes < sizeof(int32_t) * (n + 3)) return fail(c, DCS_ERR_INVALID, "branch buffer too small");
+  int32_t hn, centre;
+  std::memcpy(&hn, in, 4);
+  if (hn != n) return fail(c, DCS_ERR_INVALID, "qubit count mismatch");
+  std::vector<int> b(n + 1);
+  std::memcpy(b.data(), in + 4, 4 * (n + 1));
+  std::memcpy(&centre, in + 4 * (n + 2), 4);
+  if (b[0] != 1 || b[n] != 1 || centre < 0 || centre >= n)
+    return fail(c, DCS_ERR_INVALID, "malformed MPS header");
+  size_t need = sizeof(int32_t) * (n + 3);
+  for (int j = 0; j <= n; ++j)
+    if (b[j] < 1 || b[j] > bond_cap(j, n, c->dev.chi_cap))
+      return fail(c, DCS_ERR_INVALID, "bond above capacity");
+  for (int j = 0; j < n; ++j) need += sizeof(float2) * (size_t)b[j] * 2 * b[j + 1];
+  if (bytes < need) return fail(c, DCS_ERR_INVALID, "branch buffer too small");
+  // the active list, read back after the queued work: a free slot is one not on it
+  dcs_status_t st = cuda_check(c, cudaStreamSynchronize(c->stream), "synchronize");
+  if (st != DCS_OK) return st;
+  const int S = c->cfg.n_slots;
+  int cnt = 0;
+  std::vector<int> order(S);
+  cudaMemcpy(&cnt, c->dev.count, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaMemcpy(order.data(), c->dev.order, S * sizeof(int), cudaMemcpyDeviceToHost);
+  if ((st = cuda_check(c, cudaGetLastError(), "list query")) != DCS_OK) return st;
+  if (cnt < 0 || cnt > S) return fail(c, DCS_ERR_CUDA, "active count out of range");
+  if (cnt == S) return fail(c, DCS_ERR_OOM, "branch pool full");
+  std::vector<char> used(S, 0);
+  for (int i = 0; i < cnt; ++i) {
+    if (order[i] < 0 || order[i] >= S) return fail(c, DCS_ERR_CUDA, "slot list out of range");
+    used[order[i]] = 1;
+  }
+  int slot = 0;
+  while (used[slot]) ++slot;
+  const int kb = 0;
+  size_t off = 4 * (size_t)(n + 3);
+  for (int j = 0; j < n; ++j) {
+    const size_t len = (size_t)b[j] * 2 * b[j + 1];
+    cudaMemcpy(c->dev.mps[kb] + (size_t)slot * c->dev.mps_slot_stride + c->site_off[j], in + off,
+               len * sizeof(float2), cudaMemcpyHostToDevice);
+    off += len * sizeof(float2);
+  }
+  const uint32_t fl = flags;
+  const double rr[2] = {1.0, 0.0};
+  cudaMemcpy(c->dev.bonds + ((size_t)slot * 2 + kb) * (n + 1), b.data(), (n + 1) * sizeof(int),
+             cudaMemcpyHostToDevice);
+  cudaMemcpy(c->dev.centre + slot, &centre, sizeof(int), cudaMemcpyHostToDevice);
+  cudaMemcpy(c->dev.ketbuf + slot, &kb, sizeof(int), cudaMemcpyHostToDevice);
+  cudaMemcpy(c->dev.p + slot, &p, sizeof(double), cudaMemcpyHostToDevice);
+  cudaMemcpy(c->dev.F + slot, &F, sizeof(double), cudaMemcpyHostToDevice);
+  cudaMemcpy(c->dev.rr + 2 * (size_t)slot, rr, 2 * sizeof(double), cudaMemcpyHostToDevice);
+  cudaMemcpy(c->dev.flags + slot, &fl, sizeof(uint32_t), cudaMemcpyHostToDevice);
+  cudaMemcpy(c->dev.creg + (size_t)slot * DCS_CWORDS, cwords, DCS_CWORDS * sizeof(uint64_t),
+             cudaMemcpyHostToDevice);
+  const int cnt1 = cnt + 1;
+  cudaMemcpy(c->dev.order + cnt, &slot, sizeof(int), cudaMemcpyHostToDevice);
+  cudaMemcpy(c->dev.count, &cnt1, sizeof(int), cudaMemcpyHostToDevice);
+  for (int j = 0; j <= n; ++j) c->ub[j] = std::max(c->ub[j], b[j]);
+  // the copies above run on the default stream: finish them before later work on the
+  // context's stream reads the branch
+  return cuda_check(c, cudaDeviceSynchronize(), "branch append");
+}
+
 dcs_status_t dcs_run_circuit(dcs_ctx_t c, const dcs_op* ops, int n_ops, uint64_t meas_idx0,
                              int max_branches) {
   if (!c || (n_ops > 0 && !ops)) return fail(c, DCS_ERR_INVALID, "null argument");

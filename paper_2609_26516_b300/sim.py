@@ -249,6 +249,25 @@ class Simulator:
                                            ctypes.byref(cnt)))
         return out[: cnt.value]
 
+    def export_mps_bytes(self, pos: int) -> bytes:
+        """dcs_export_mps of active slot ``pos`` as the raw bytes of its format."""
+        size = ctypes.c_size_t(0)
+        self._check(self.lib.dcs_export_mps(self.ctx, pos, None, ctypes.byref(size)))
+        buf = (ctypes.c_uint8 * size.value)()
+        self._check(self.lib.dcs_export_mps(self.ctx, pos, buf, ctypes.byref(size)))
+        return bytes(buf)
+
+    def branch_append(self, raw: bytes, p: float, F: float, cwords, flags: int = 0):
+        """dcs_branch_append: one branch (MPS bytes of export_mps_bytes, p, F, register words,
+        flags) at the end of the active list."""
+        cw = np.zeros(N.CWORDS, dtype=np.uint64)
+        src = np.asarray(cwords, dtype=np.uint64).ravel()
+        cw[: src.size] = src
+        buf = (ctypes.c_uint8 * len(raw)).from_buffer_copy(raw)
+        self._check(self.lib.dcs_branch_append(self.ctx, buf, len(raw), float(p), float(F),
+                                               cw.ctypes.data_as(ctypes.c_void_p),
+                                               int(flags) & 0xFF))
+
     def export_mps(self, pos: int):
         """(bonds, centre, [tensors [chi_l, 2, chi_r] complex64]) of active slot ``pos``."""
         size = ctypes.c_size_t(0)

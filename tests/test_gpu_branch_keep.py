@@ -51,6 +51,17 @@ def _same_branches(a_sims, b):
             pos += 1
 
 
+def _fid(Ta, Tb):
+    """|<a|b>|^2 / (<a|a><b|b>) of two MPS given by their site tensors."""
+    def ov(X, Y):
+        E = np.ones((1, 1), dtype=np.complex128)
+        for x, y in zip(X, Y):
+            E = np.einsum("ab,asc,bsd->cd", E, np.conj(x.astype(np.complex128)),
+                          y.astype(np.complex128))
+        return E[0, 0]
+    return abs(ov(Ta, Tb)) ** 2 / (ov(Ta, Ta).real * ov(Tb, Tb).real)
+
+
 def _multipath(circ):
     sim = _sim(N, CHI, SLOTS, circ.n_cbits)
     sim.init_state(1, multipath=True)
@@ -143,10 +154,10 @@ def _rank_main(rank, world, port, M, out):
         from test_gpu_parity import _sim as mk
         circ = Cc.brickwork(N, DEPTH, P, SEED)
         sim = mk(N, CHI, SLOTS, circ.n_cbits)
-        hist = run_multi_path_sharded(sim, circ, M)
+        keys, hist = run_multi_path_sharded(sim, circ, M)
         r = sim.results()
         states = [sim.export_mps(i) for i in range(r["n_active"])]
-        out.put((rank, r["p"], r["F"], r["bits"], states, hist))
+        out.put((rank, keys, r["p"], r["F"], r["bits"], states, hist))
     finally:
         dist.destroy_process_group()
 
@@ -174,17 +185,57 @@ def test_two_processes_sharded_run_equals_one_context():
     ref = _reference_by_measurement(circ, M)
     rr = ref.results()
     assert rr["n_active"] == M
-    assert sum(len(g[1]) for g in got) == M
-    # the list was split between the ranks early on, and both held branches after cuts
-    assert len(got[0][5]) == len(got[1][5]) >= 4
-    assert all(t0 == t1 for (_, t0), (_, t1) in zip(got[0][5], got[1][5]))
-    assert any(k > 0 for k, _ in got[1][5]) and any(k > 0 for k, _ in got[0][5])
-    np.testing.assert_array_equal(np.concatenate([g[1] for g in got]), rr["p"])
-    np.testing.assert_array_equal(np.concatenate([g[2] for g in got]), rr["F"])
-    np.testing.assert_array_equal(np.concatenate([g[3] for g in got]), rr["bits"])
-    states = [s for g in got for s in g[4]]
-    for i, (bonds, centre, T) in enumerate(states):
+    # every branch with its order key; the ensemble's order is ascending key
+    rows = sorted(((int(k), g[2][i], g[3][i], g[4][i], g[5][i]) for g in got
+                   for i, k in enumerate(g[1])), key=lambda r: r[0])
+    assert [r[0] for r in rows] == list(range(M))
+    np.testing.assert_array_equal(np.array([r[1] for r in rows]), rr["p"])
+    np.testing.assert_array_equal(np.array([r[2] for r in rows]), rr["F"])
+    np.testing.assert_array_equal(np.array([r[3] for r in rows]), rr["bits"])
+    for i, r in enumerate(rows):
+        bonds, centre, T = r[4]
         b2, c2, T2 = ref.export_mps(i)
         assert bonds.tolist() == b2.tolist() and centre == c2
         for x, y in zip(T, T2):
             np.testing.assert_array_equal(x, y)
+    # the list was split between the ranks early on and the shares stayed even
+    h0, h1 = got[0][6], got[1][6]
+    assert len(h0) == len(h1) >= 4
+    for (a, t0), (b, t1) in zip(h0, h1):
+        assert t0 == t1 == a + b and abs(a - b) <= 1
+
+
+def test_branch_append_moves_a_branch_between_contexts():
+    # export + dcs_branch_append: the moved branches are the same branches, and they evolve
+    # the same afterwards; a full pool refuses the append
+    from paper_2609_26516_b300 import DCSError
+    circ = _circuit()
+    cut = _split_after_measurements(circ.ops, 3)
+    a, b = _multipath(circ), _multipath(circ)
+    a.run_circuit(circ.ops[:cut])
+    b.branch_keep([0])  # an empty list
+    ra = a.results()
+    for i in range(ra["n_active"]):
+        b.branch_append(a.export_mps_bytes(i), ra["p"][i], ra["F"][i], ra["cwords"][i],
+                        ra["flags"][i])
+    _same_branches([b], a)
+    # evolved further, the moved branches stay the same branches; the receiving context sized
+    # its tiles from the bonds it was given, not from the circuit's bond bound, so its kernels
+    # may round differently: compared to the accuracy contract
+    a.run_circuit(circ.ops[cut:])
+    b.run_circuit(circ.ops[cut:])
+    ra, rb = a.results(), b.results()
+    assert ra["n_active"] == rb["n_active"]
+    np.testing.assert_array_equal(ra["bits"], rb["bits"])
+    np.testing.assert_allclose(rb["p"], ra["p"], rtol=0, atol=1e-7)
+    np.testing.assert_allclose(rb["F"], ra["F"], rtol=0, atol=1e-5)
+    for i in range(ra["n_active"]):
+        Ta, Tb = a.export_mps(i)[2], b.export_mps(i)[2]
+        assert _fid(Ta, Tb) >= 1 - 1e-6
+    small = _sim(N, CHI, 2, circ.n_cbits)
+    small.init_state(1, multipath=True)
+    raw = a.export_mps_bytes(0)
+    small.branch_append(raw, 0.5, 1.0, np.zeros(8, dtype=np.uint64))
+    with pytest.raises(DCSError) as e:
+        small.branch_append(raw, 0.5, 1.0, np.zeros(8, dtype=np.uint64))
+    assert e.value.status == 2  # DCS_ERR_OOM

@@ -141,15 +141,29 @@ class _OracleSim:
                 raise TypeError(op)
 
     def results(self):
-        return {"n_active": len(self.L), "p": np.array([b.p for b in self.L])}
+        n = len(self.L)
+        return {"n_active": n, "p": np.array([b.p for b in self.L]),
+                "F": np.ones(n), "flags": np.zeros(n, dtype=np.uint8),
+                "cwords": np.zeros((n, 8), dtype=np.uint64),
+                "bits": np.array([b.c for b in self.L]).reshape(n, self.ncb)}
 
     def branch_keep(self, keep):
         keep = list(keep)
         assert len(keep) == len(self.L)
         self.L = [b for b, k in zip(self.L, keep) if k]
 
+    def export_mps_bytes(self, pos):
+        import pickle
+        return pickle.dumps(self.L[pos])
 
-def _sharded_rank(rank, world, port, M, p_min, out):
+    def branch_append(self, raw, p, F, cwords, flags=0):
+        import pickle
+        b = pickle.loads(raw)
+        assert b.p == p and F == 1.0
+        self.L.append(b)
+
+
+def _sharded_rank(rank, world, port, M, p_min, balance, out):
     import torch.distributed as dist
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
@@ -160,16 +174,19 @@ def _sharded_rank(rank, world, port, M, p_min, out):
     try:
         circ = C.brickwork(8, 6, 0.15, 2)
         sim = _OracleSim(circ.n_qubits, circ.n_cbits)
-        hist = run_multi_path_sharded(sim, circ, M, p_min)
-        out.put((rank, [(b.p, b.c.tolist(), b.path) for b in sim.L], hist))
+        keys, hist = run_multi_path_sharded(sim, circ, M, p_min, balance=balance)
+        assert len(keys) == len(sim.L)
+        out.put((rank, [(int(k), b.p, b.c.tolist(), b.path) for k, b in zip(keys, sim.L)], hist))
     finally:
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("world,M,p_min", [(2, 6, 0.0), (3, 10, 2e-3)])
-def test_sharded_run_keeps_the_oracles_ensemble(world, M, p_min):
-    # the driver's host logic (replicas, contiguous shares, one exchange per measurement) on
-    # world gloo ranks against Alg. 2 on one list (the oracle's run_multi_path)
+@pytest.mark.parametrize("world,M,p_min,balance", [(2, 6, 0.0, False), (3, 10, 2e-3, False),
+                                                   (2, 6, 0.0, True), (3, 10, 2e-3, True)])
+def test_sharded_run_keeps_the_oracles_ensemble(world, M, p_min, balance):
+    # the driver's host logic (replicas, contiguous shares, order keys, one exchange per
+    # measurement, moves that even out the shares) on world gloo ranks against Alg. 2 on one
+    # list (the oracle's run_multi_path)
     import circuits as C
     from oracle import statevector as SV
     with socket.socket() as sk:
@@ -177,7 +194,7 @@ def test_sharded_run_keeps_the_oracles_ensemble(world, M, p_min):
         port = sk.getsockname()[1]
     ctx = mp.get_context("spawn")
     out = ctx.Queue()
-    procs = [ctx.Process(target=_sharded_rank, args=(r, world, port, M, p_min, out))
+    procs = [ctx.Process(target=_sharded_rank, args=(r, world, port, M, p_min, balance, out))
              for r in range(world)]
     for p in procs:
         p.start()
@@ -186,10 +203,28 @@ def test_sharded_run_keeps_the_oracles_ensemble(world, M, p_min):
         p.join(timeout=120)
         assert p.exitcode == 0
     ref = SV.run_multi_path(C.brickwork(8, 6, 0.15, 2), M, p_min)
-    mine = [b for g in got for b in g[1]]
-    assert [b[2] for b in mine] == [b.path for b in ref]
-    assert [b[1] for b in mine] == [b.c.tolist() for b in ref]
-    assert [b[0] for b in mine] == [b.p for b in ref]
+    mine = sorted((b for g in got for b in g[1]), key=lambda b: b[0])
+    assert [b[0] for b in mine] == list(range(len(ref)))  # dense keys: the list order
+    assert [b[3] for b in mine] == [b.path for b in ref]
+    assert [b[2] for b in mine] == [b.c.tolist() for b in ref]
+    assert [b[1] for b in mine] == [b.p for b in ref]
     # the list was split into shares and the cuts were ensemble-wide
     assert len(got[0][2]) > 0 and all(g[2][-1][1] == len(ref) for g in got)
     assert sum(1 for g in got if any(k for k, _ in g[2])) >= 2
+    if balance:  # shares even after every measurement
+        for step in zip(*[g[2] for g in got]):
+            held = [k for k, _ in step]
+            assert max(held) - min(held) <= 1
+
+
+def test_balance_moves():
+    from paper_2609_26516_b300.ranks import _balance_moves
+    assert _balance_moves([5, 0, 1]) == [(0, 1, 2), (0, 2, 1)]
+    assert _balance_moves([0, 7]) == [(1, 0, 4)]
+    assert _balance_moves([3, 3]) == []
+    for counts in ([9, 0, 0, 0], [1, 2, 30, 4], [0, 0, 5]):
+        after = list(counts)
+        for s_, d_, m in _balance_moves(counts):
+            after[s_] -= m
+            after[d_] += m
+        assert sum(after) == sum(counts) and max(after) - min(after) <= 1
