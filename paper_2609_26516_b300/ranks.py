@@ -14,6 +14,7 @@ from typing import List, Optional, Tuple
 import numpy as np
 import torch
 
+from . import _native as N
 from .sim import topk_select_global
 
 
@@ -105,12 +106,21 @@ def _balance_moves(counts: List[int]) -> List[Tuple[int, int, int]]:
     return moves
 
 
+# one moved branch: p, F (float64); order key, flags, MPS byte count (int64); the register
+# (N.CWORDS uint64 words); then the MPS in the dcs_export_mps format
+_CWORDS = N.CWORDS
+_HEAD = 2 * 8 + 3 * 8 + _CWORDS * 8
+
+
 def _send_branch(sim, pos: int, res: dict, key: int, dst: int, group, device):
     import torch.distributed as dist
     raw = sim.export_mps_bytes(pos)
+    cw = np.zeros(_CWORDS, dtype=np.uint64)
+    src = np.asarray(res["cwords"][pos], dtype=np.uint64).ravel()
+    cw[: src.size] = src
     head = (np.array([res["p"][pos], res["F"][pos]], dtype=np.float64).tobytes()
             + np.array([key, int(res["flags"][pos]), len(raw)], dtype=np.int64).tobytes()
-            + np.asarray(res["cwords"][pos], dtype=np.uint64).tobytes())
+            + cw.tobytes())
     msg = np.frombuffer(head + raw, dtype=np.uint8)
     dist.send(torch.tensor([msg.size], dtype=torch.int64, device=device), dst, group=group)
     dist.send(torch.as_tensor(msg.copy(), device=device), dst, group=group)
@@ -125,8 +135,8 @@ def _recv_branch(sim, src: int, group, device) -> int:
     b = msg.cpu().numpy().tobytes()
     p, F = np.frombuffer(b, dtype=np.float64, count=2)
     key, flags, nraw = np.frombuffer(b, dtype=np.int64, count=3, offset=16)
-    cw = np.frombuffer(b, dtype=np.uint64, count=8, offset=40)
-    raw = b[104: 104 + int(nraw)]
+    cw = np.frombuffer(b, dtype=np.uint64, count=_CWORDS, offset=40)
+    raw = b[_HEAD: _HEAD + int(nraw)]
     sim.branch_append(raw, float(p), float(F), cw, int(flags))
     return int(key)
 
