@@ -256,9 +256,13 @@ dcs_status_t dcs_topk_select_global(const double* p, int n, int M, double p_min,
  * register (n * DCS_CWORDS words), flags (n bytes), and the number n of active slots.  The
  * data comes down through the context's pinned host staging buffer, which grows (one
  * cudaMallocHost) the first time it is too small.  DCS_ERR_OOM if the branch pool ran out
- * during the circuit, DCS_ERR_CUDA on a copy or earlier asynchronous error, or when the
- * device's active count or slot list lies outside the pool (corrupted device state; nothing
- * is written to the buffers then). */
+ * during the circuit, DCS_ERR_TIMEOUT if a bounded wait of the tensor-core pipeline gave up
+ * (that step's results are not to be trusted), DCS_ERR_INVALID after a dcs_branch_keep or
+ * dcs_fork_shots that found a list of the wrong length, DCS_ERR_CUDA on a copy or earlier
+ * asynchronous error, or when the device's active count or slot list lies outside the pool
+ * (corrupted device state; nothing is written to the buffers then).  The buffers are
+ * written before the device status is reported; the status stays set until the next
+ * dcs_init_state. */
 dcs_status_t dcs_get_results(dcs_ctx_t ctx, double* p, double* fid, uint64_t* cbits,
                              int* n_active, uint8_t* flags);
 

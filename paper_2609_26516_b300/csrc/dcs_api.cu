@@ -595,6 +595,8 @@ dcs_status_t dcs_get_results(dcs_ctx_t c, double* p, double* fid, uint64_t* cbit
   if (st != DCS_OK) return st;
   if (status & (1 << DCS_ERR_OOM)) return fail(c, DCS_ERR_OOM, "branch pool exhausted");
   if (status & (1 << DCS_ERR_UNSUPPORTED)) return fail(c, DCS_ERR_UNSUPPORTED, "branch pool above 1024 slots");
+  if (status & (1 << DCS_ERR_TIMEOUT))
+    return fail(c, DCS_ERR_TIMEOUT, "a bounded wait of the tensor-core pipeline gave up");
   if (status & (1 << DCS_ERR_INVALID))
     return fail(c, DCS_ERR_INVALID, "branch keep or shot fork found a list of the wrong length");
   return DCS_OK;

@@ -228,3 +228,61 @@ def test_balance_moves():
             after[s_] -= m
             after[d_] += m
         assert sum(after) == sum(counts) and max(after) - min(after) <= 1
+
+
+class _FailingSim(_OracleSim):
+    """A stand-in whose host raises at its `fail_at`-th call (a rank that fails between
+    measurements)."""
+
+    def __init__(self, n_qubits, n_cbits, fail_at):
+        super().__init__(n_qubits, n_cbits)
+        self.calls, self.fail_at = 0, fail_at
+
+    def run_circuit(self, ops, meas_idx0=0, max_branches=0):
+        self.calls += 1
+        if self.calls == self.fail_at:
+            raise RuntimeError("injected rank failure")
+        super().run_circuit(ops, meas_idx0, max_branches)
+
+
+def _failing_rank(rank, world, port, out):
+    import datetime
+    import time
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    sys.path.insert(0, ROOT)
+    import circuits as C
+    from paper_2609_26516_b300.ranks import run_multi_path_sharded
+    dist.init_process_group("gloo", rank=rank, world_size=world,
+                            timeout=datetime.timedelta(seconds=20))
+    circ = C.brickwork(8, 6, 0.15, 2)
+    sim = _FailingSim(circ.n_qubits, circ.n_cbits, fail_at=4 if rank == 1 else 0)
+    t0 = time.time()
+    try:
+        run_multi_path_sharded(sim, circ, 6)
+        out.put((rank, "finished", time.time() - t0))
+    except Exception as e:  # noqa: BLE001 - the failure is the result
+        out.put((rank, type(e).__name__ + ": " + str(e)[:80], time.time() - t0))
+    # a failed rank leaves without joining further collectives; its exit closes its links
+
+
+def test_a_failed_rank_ends_the_others_next_exchange():
+    # failure detection on the host: rank 1 raises between measurements (after the list was
+    # split into shares); rank 0 must not hang, its next all-gather fails within the process
+    # group's timeout
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    out = ctx.Queue()
+    procs = [ctx.Process(target=_failing_rank, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = sorted((out.get(timeout=120) for _ in procs), key=lambda g: g[0])
+    for p in procs:
+        p.join(timeout=60)
+        if p.is_alive():
+            p.kill()
+    assert "injected rank failure" in got[1][1]
+    assert got[0][1] != "finished" and got[0][2] < 60
