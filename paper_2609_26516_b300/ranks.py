@@ -1,12 +1,16 @@
 """Multi-path ensembles sharded over ranks, one context per GPU (Alg. 2 with the branch list
 split between processes).  Between measurements the ranks' branches evolve independently;
 TopKByWeight needs one exchange per measurement: an all-gather of every rank's path
-probabilities, after which every rank computes the same ensemble-wide selection and keeps its
-own share.  The ensemble's list order is the rank-major concatenation of the ranks' lists:
-children stay on their parent's rank in the paper's order (m = 0 before m = 1, parents in list
-order), so that concatenation is the order one context holding every branch would have.
-Marshalling and one collective only: the selection is the library's dcs_topk_select_global,
-the compaction its dcs_branch_keep, everything else the library's own multi-path calls."""
+probabilities (with each branch's place in the ensemble's list order), after which every rank
+computes the same ensemble-wide selection and keeps its own share.
+
+Two ways to keep the list order across ranks: ``select_across_ranks`` / ``topk_across_ranks``
+take it to be the rank-major concatenation of the ranks' lists (true while children stay on
+their parent's rank, since a split keeps the paper's order: m = 0 before m = 1, parents in
+list order); ``run_multi_path_sharded`` gives every branch an order key instead, so branches
+can also move between ranks to even out their shares.  The selection is the library's
+dcs_topk_select_global, the compaction its dcs_branch_keep, a move dcs_export_mps and
+dcs_branch_append; everything else is the library's own multi-path calls."""
 from __future__ import annotations
 
 from typing import List, Optional, Tuple
@@ -18,28 +22,34 @@ from . import _native as N
 from .sim import topk_select_global
 
 
-def select_across_ranks(p_local, M: int, p_min: float = 0.0, group=None,
-                        device="cpu") -> Tuple[np.ndarray, int]:
-    """The keep mask of this rank's branches (its list order) under the top-M and pruning
-    rules applied to the whole ensemble, and the number of branches kept on all ranks.
-    p_local holds this rank's path probabilities in list order; `device` is where the
-    collective's buffers live (CPU for gloo, this rank's GPU for NCCL)."""
+def _gather(values: np.ndarray, dtype, group, device) -> List[np.ndarray]:
+    """Every rank's 1-D array (lengths may differ), in rank order."""
     import torch.distributed as dist
     world = dist.get_world_size(group)
-    rank = dist.get_rank(group)
-    p = torch.as_tensor(np.ascontiguousarray(p_local, dtype=np.float64), device=device)
-    n = torch.tensor([p.numel()], dtype=torch.int64, device=device)
+    n = torch.tensor([values.size], dtype=torch.int64, device=device)
     counts_t = [torch.zeros_like(n) for _ in range(world)]
     dist.all_gather(counts_t, n, group=group)
     counts = [int(c.item()) for c in counts_t]
-    buf = torch.zeros(max(max(counts), 1), dtype=torch.float64, device=device)
-    buf[: p.numel()] = p
+    buf = torch.zeros(max(max(counts), 1), dtype=dtype, device=device)
+    buf[: values.size] = torch.as_tensor(values, dtype=dtype, device=device)
     got = [torch.zeros_like(buf) for _ in range(world)]
     dist.all_gather(got, buf, group=group)
-    p_all = np.concatenate([g[:c].cpu().numpy() for g, c in zip(got, counts)])
-    keep = topk_select_global(p_all, M, p_min)
-    off = sum(counts[:rank])
-    return keep[off: off + counts[rank]], int(keep.sum())
+    return [g[:c].cpu().numpy() for g, c in zip(got, counts)]
+
+
+def select_across_ranks(p_local, M: int, p_min: float = 0.0, group=None,
+                        device="cpu") -> Tuple[np.ndarray, int]:
+    """The keep mask of this rank's branches (its list order) under the top-M and pruning
+    rules applied to the whole ensemble, and the number of branches kept on all ranks, for an
+    ensemble whose list order is the rank-major concatenation of the ranks' lists.  p_local
+    holds this rank's path probabilities in list order; `device` is where the collective's
+    buffers live (CPU for gloo, this rank's GPU for NCCL)."""
+    import torch.distributed as dist
+    rank = dist.get_rank(group)
+    parts = _gather(np.ascontiguousarray(p_local, dtype=np.float64), torch.float64, group, device)
+    keep = topk_select_global(np.concatenate(parts), M, p_min)
+    off = sum(len(x) for x in parts[:rank])
+    return keep[off: off + len(parts[rank])], int(keep.sum())
 
 
 def topk_across_ranks(sim, M: int, p_min: float = 0.0, group=None,
@@ -56,21 +66,6 @@ def topk_across_ranks(sim, M: int, p_min: float = 0.0, group=None,
 
 def _is_measurement(op) -> bool:
     return type(op).__name__ in ("Measure", "Reset")
-
-
-def _gather(values: np.ndarray, dtype, group, device) -> List[np.ndarray]:
-    """Every rank's 1-D array (lengths may differ), in rank order."""
-    import torch.distributed as dist
-    world = dist.get_world_size(group)
-    n = torch.tensor([values.size], dtype=torch.int64, device=device)
-    counts_t = [torch.zeros_like(n) for _ in range(world)]
-    dist.all_gather(counts_t, n, group=group)
-    counts = [int(c.item()) for c in counts_t]
-    buf = torch.zeros(max(max(counts), 1), dtype=dtype, device=device)
-    buf[: values.size] = torch.as_tensor(values, dtype=dtype, device=device)
-    got = [torch.zeros_like(buf) for _ in range(world)]
-    dist.all_gather(got, buf, group=group)
-    return [g[:c].cpu().numpy() for g, c in zip(got, counts)]
 
 
 def _child_keys(bits: np.ndarray, cbit: int, parent_keys: np.ndarray) -> np.ndarray:
