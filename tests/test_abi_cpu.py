@@ -240,3 +240,14 @@ def test_noalloc_argument_checks_need_no_device(lib):
     g[0].m[0] = g[0].m[6] = 1.0
     g[0].cond.op = 7  # neither NONE, XOR nor AND
     assert call(n_gates=1, gates=g) == N.ERR_INVALID
+
+
+def test_list_calls_refuse_a_null_context(lib):
+    # the sharded-ensemble and shot-fork calls answer before any device access
+    from paper_2609_26516_b300 import _native as N
+    keep = (ctypes.c_uint8 * 2)(1, 0)
+    assert lib.dcs_branch_keep(None, keep, 2) == N.ERR_INVALID
+    assert lib.dcs_fork_shots(None, 4) == N.ERR_INVALID
+    buf = (ctypes.c_uint8 * 64)()
+    cw = (ctypes.c_uint64 * N.CWORDS)()
+    assert lib.dcs_branch_append(None, buf, 64, 0.5, 1.0, cw, 0) == N.ERR_INVALID
