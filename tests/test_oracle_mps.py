@@ -514,3 +514,48 @@ def test_multi_layer_truncated_fidelity_is_monotone():
         assert info.f >= prev - 1e-12
         prev = info.f
     assert prev < 1 - 1e-3
+
+
+def _brute_site_env(B, psi, j):
+    """The optimal local tensor at site j, from dense vectors only: <B with site j left
+    out | psi> (B centred at j, so its left and right parts are isometries)."""
+    n = B.n
+    left = np.ones((1, 1), dtype=np.complex128)
+    for k in range(j):
+        t = B.T[k]
+        left = np.einsum("xa,asb->xsb", left, t).reshape(-1, t.shape[2])
+    right = np.ones((1, 1), dtype=np.complex128)
+    for k in range(n - 1, j, -1):
+        t = B.T[k]
+        right = np.einsum("asb,by->asy", t, right).reshape(t.shape[0], -1)
+    P = psi.reshape(left.shape[0], 2, right.shape[1])
+    return np.einsum("xb,xsy,cy->bsc", left.conj(), P, right.conj())
+
+
+@pytest.mark.parametrize("seed,layers", [(1, 1), (2, 1), (3, 2)])
+def test_converged_sweeps_are_stationary(seed, layers):
+    # Sec. "Simulating unitary quantum circuits with DMRG": each one-site update replaces the
+    # site by F/||F||, the optimum for the rest of the bra held fixed.  Once the sweeps have
+    # converged in the truncated regime the bra is a fixed point: at every site the optimal
+    # local tensor, computed here by brute force from the dense target state (none of the
+    # oracle's environment sums), is the site itself up to a phase and its norm^2 is f.
+    rng = np.random.default_rng(seed)
+    n = 8
+    A = random_mps(rng, n, 3)
+    if layers == 1:
+        chunk = _layer_blocks(rng, n, seed % 2)
+        W = LY.blocks_mpo(n, chunk)
+    else:
+        ops = list(C.brickwork(n, layers, 0.0, 30 + seed).ops)
+        chunk, _ = LY.chunk_sublayer_blocks(n, ops, np.zeros(1, dtype=np.int64))
+        W = LY.compose_mpo([LY.blocks_mpo(n, b) for b in chunk])
+    psi = LY.chunk_unitary_dense(n, W) @ dense(A)
+    B, info = M.compress(A.copy(), chunk, W, 3, 0.0, 60, skip_exact=False)
+    assert info.f < 1 - 1e-4  # truncated
+    for j in range(n):
+        Bc = B.copy()
+        M.move_centre(Bc, j)
+        F = _brute_site_env(Bc, psi, j)
+        nf = np.vdot(F, F).real
+        assert abs(nf - info.f) < 1e-10
+        assert 1 - abs(np.vdot(F / np.sqrt(nf), Bc.T[j])) < 1e-10
