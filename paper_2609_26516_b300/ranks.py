@@ -68,18 +68,31 @@ def _is_measurement(op) -> bool:
     return type(op).__name__ in ("Measure", "Reset")
 
 
-def _child_keys(bits: np.ndarray, cbit: int, parent_keys: np.ndarray) -> np.ndarray:
-    """Order keys of the children a split left in the list: the children of a parent are
-    consecutive, m = 0 before m = 1, so a new parent starts at every m = 0 child and after
-    every m = 1 child; child key = 2 parent key + m keeps the ensemble's list order."""
-    keys = np.zeros(len(bits), dtype=np.int64)
-    j, prev = -1, 1
-    for i, row in enumerate(bits):
-        m = int(row[cbit])
-        if m == 0 or prev == 1:
-            j += 1
+def _child_keys(bits: np.ndarray, p_child: np.ndarray, cbit: int, parent_keys: np.ndarray,
+                p_parent: np.ndarray, eps: float = 1e-12) -> np.ndarray:
+    """Order keys of the children a split left in the list (child key = 2 parent key + m,
+    which keeps the ensemble's list order).  A parent's children are consecutive, m = 0 before
+    m = 1, and a parent has two children exactly when both outcomes have p_m > eps (the
+    split's rule), i.e. when its m = 0 child carries less than p_parent (1 - eps); its m = 1
+    child then follows, the two summing to p_parent.  So a parent whose only child is m = 0
+    followed by one whose only child is m = 1 (deterministic re-measurements, as in resets)
+    is told apart from one parent with both."""
+    n = len(bits)
+    keys = np.zeros(n, dtype=np.int64)
+    i = j = 0
+    while i < n:
+        m = int(bits[i][cbit])
         keys[i] = 2 * parent_keys[j] + m
-        prev = m
+        two = (m == 0 and i + 1 < n and int(bits[i + 1][cbit]) == 1
+               and p_child[i] < p_parent[j] * (1.0 - eps)
+               and abs(p_child[i] + p_child[i + 1] - p_parent[j]) <= 1e-10 * p_parent[j])
+        if two:
+            keys[i + 1] = 2 * parent_keys[j] + 1
+            i += 2
+        else:
+            i += 1
+        j += 1
+    assert j == len(parent_keys), "children do not match their parents"
     return keys
 
 
@@ -166,6 +179,7 @@ def run_multi_path_sharded(sim, ops, M: int, p_min: float = 0.0, group=None,
         seg.append(op)
         if not _is_measurement(op):
             continue
+        p_parent = None if shared else sim.results()["p"]
         sim.run_circuit(seg)
         seg = []
         res = sim.results()
@@ -184,7 +198,7 @@ def run_multi_path_sharded(sim, ops, M: int, p_min: float = 0.0, group=None,
                 shared = False
             sim.branch_keep(keep)
             continue
-        ckeys = _child_keys(res["bits"][:n], op.cbit, keys)
+        ckeys = _child_keys(res["bits"][:n], res["p"][:n], op.cbit, keys, p_parent)
         all_p = _gather(res["p"][:n], torch.float64, group, device)
         all_k = _gather(ckeys, torch.int64, group, device)
         owner = np.concatenate([np.full(len(k), r) for r, k in enumerate(all_k)])

@@ -117,7 +117,7 @@ class _OracleSim:
         self.L = [SV.Branch(1.0, np.zeros(self.ncb, dtype=np.int64), SV.zero_state(self.n))]
 
     def run_circuit(self, ops, meas_idx0=0, max_branches=0):
-        from circuits import Gate, Measure
+        from circuits import Gate, Measure, Reset, X
         from oracle import statevector as SV
         assert max_branches == 0
         for op in ops:
@@ -125,7 +125,7 @@ class _OracleSim:
                 for b in self.L:
                     if SV.cond_holds(op.cond, b.c):
                         b.psi = SV.apply_gate(b.psi, op.qubits, op.matrix)
-            elif isinstance(op, Measure):
+            elif isinstance(op, (Measure, Reset)):
                 nxt = []
                 for b in self.L:
                     r0, r1 = SV.probabilities(b.psi, op.qubit)
@@ -137,6 +137,10 @@ class _OracleSim:
                             nxt.append(SV.Branch(b.p * pm, c, SV.project(b.psi, op.qubit, m, rm),
                                                  b.path + [m]))
                 self.L = nxt
+                if isinstance(op, Reset):  # measure into the bit, then X if it reads 1
+                    for b in self.L:
+                        if b.c[op.cbit] == 1:
+                            b.psi = SV.apply_gate(b.psi, (op.qubit,), X)
             else:
                 raise TypeError(op)
 
@@ -163,7 +167,14 @@ class _OracleSim:
         self.L.append(b)
 
 
-def _sharded_rank(rank, world, port, M, p_min, balance, out):
+def _sharded_circuit(which):
+    import circuits as C
+    # brickwork: every measurement splits every branch; dynamic GHZ: the resets re-measure
+    # collapsed ancillas, so parents with only an m = 0 or only an m = 1 child alternate
+    return C.brickwork(8, 6, 0.15, 2) if which == "brick" else C.ghz_dynamic(9)
+
+
+def _sharded_rank(rank, world, port, M, p_min, balance, which, out):
     import torch.distributed as dist
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
@@ -172,7 +183,7 @@ def _sharded_rank(rank, world, port, M, p_min, balance, out):
     from paper_2609_26516_b300.ranks import run_multi_path_sharded
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
-        circ = C.brickwork(8, 6, 0.15, 2)
+        circ = _sharded_circuit(which)
         sim = _OracleSim(circ.n_qubits, circ.n_cbits)
         keys, hist = run_multi_path_sharded(sim, circ, M, p_min, balance=balance)
         assert len(keys) == len(sim.L)
@@ -181,9 +192,11 @@ def _sharded_rank(rank, world, port, M, p_min, balance, out):
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("world,M,p_min,balance", [(2, 6, 0.0, False), (3, 10, 2e-3, False),
-                                                   (2, 6, 0.0, True), (3, 10, 2e-3, True)])
-def test_sharded_run_keeps_the_oracles_ensemble(world, M, p_min, balance):
+@pytest.mark.parametrize("world,M,p_min,balance,which",
+                         [(2, 6, 0.0, False, "brick"), (3, 10, 2e-3, False, "brick"),
+                          (2, 6, 0.0, True, "brick"), (3, 10, 2e-3, True, "brick"),
+                          (2, 64, 0.0, True, "ghz"), (3, 5, 0.0, True, "ghz")])
+def test_sharded_run_keeps_the_oracles_ensemble(world, M, p_min, balance, which):
     # the driver's host logic (replicas, contiguous shares, order keys, one exchange per
     # measurement, moves that even out the shares) on world gloo ranks against Alg. 2 on one
     # list (the oracle's run_multi_path)
@@ -194,7 +207,8 @@ def test_sharded_run_keeps_the_oracles_ensemble(world, M, p_min, balance):
         port = sk.getsockname()[1]
     ctx = mp.get_context("spawn")
     out = ctx.Queue()
-    procs = [ctx.Process(target=_sharded_rank, args=(r, world, port, M, p_min, balance, out))
+    procs = [ctx.Process(target=_sharded_rank,
+                         args=(r, world, port, M, p_min, balance, which, out))
              for r in range(world)]
     for p in procs:
         p.start()
@@ -202,7 +216,7 @@ def test_sharded_run_keeps_the_oracles_ensemble(world, M, p_min, balance):
     for p in procs:
         p.join(timeout=120)
         assert p.exitcode == 0
-    ref = SV.run_multi_path(C.brickwork(8, 6, 0.15, 2), M, p_min)
+    ref = SV.run_multi_path(_sharded_circuit(which), M, p_min)
     mine = sorted((b for g in got for b in g[1]), key=lambda b: b[0])
     assert [b[0] for b in mine] == list(range(len(ref)))  # dense keys: the list order
     assert [b[3] for b in mine] == [b.path for b in ref]
@@ -286,3 +300,17 @@ def test_a_failed_rank_ends_the_others_next_exchange():
             p.kill()
     assert "injected rank failure" in got[1][1]
     assert got[0][1] != "finished" and got[0][2] < 60
+
+
+def test_child_keys_tell_single_child_parents_apart():
+    # parents A (only m = 0), B (only m = 1), C (both): children in list order 0, 1, 0, 1
+    from paper_2609_26516_b300.ranks import _child_keys
+    p_parent = np.array([0.5, 0.3, 0.2])
+    p_child = np.array([0.5 * (1 - 1e-14), 0.3, 0.2 * 0.4, 0.2 * 0.6])
+    bits = np.array([[0], [1], [0], [1]])
+    got = _child_keys(bits, p_child, 0, np.array([0, 1, 2]), p_parent)
+    assert got.tolist() == [0, 3, 4, 5]
+    # the same bits from two parents with both children each
+    got = _child_keys(bits, np.array([0.2, 0.3, 0.1, 0.4]), 0, np.array([7, 9]),
+                      np.array([0.5, 0.5]))
+    assert got.tolist() == [14, 15, 18, 19]
