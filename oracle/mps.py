@@ -38,6 +38,14 @@ The paper states only the one-site update.  Readings used for what it leaves ope
    at the end the last sweep runs to.  Bond dimensions do not change in the sweeps.
 4. f is ||F||^2 at the last update of the last sweep: B is normalised with every other
    site orthonormal, W unitary and A normalised, so ||F|| = |<B|W A>|.
+
+Pins (tests/test_oracle_mps.py): the exact regime equals the dense state; every truncation
+of the guess is the Eckart-Young projection at its bond with the kept weight fraction; f is
+|<B|W A>|^2 recomputed densely, <= 1 and non-decreasing over sweeps; with one truncated bond
+the sweeps reach the optimal truncation; converged sweeps are a stationary point (the
+brute-force local optimum equals every site).  The state after a fixed small number of
+sweeps in the truncated regime has no value fixed by the paper: parity unpinned beyond
+these invariants.
 """
 from __future__ import annotations
 
