@@ -279,7 +279,8 @@ dcs_status_t dcs_get_bonds(dcs_ctx_t ctx, int32_t* bonds, int* n_active);
 dcs_status_t dcs_export_mps(dcs_ctx_t ctx, int slot, void* host_buf, size_t* bytes);
 
 /* Restore a slot's MPS from the dcs_export_mps format.  Bond b must lie in 1 .. cap_b
- * (see dcs_create), bonds 0 and n must be 1; otherwise DCS_ERR_INVALID. */
+ * (see dcs_create), bonds 0 and n must be 1; otherwise DCS_ERR_INVALID.  Synchronises the
+ * device. */
 dcs_status_t dcs_import_mps(dcs_ctx_t ctx, int slot, const void* host_buf, size_t bytes);
 
 /* Appends one branch at the end of the active list of a multi-path context, in a free slot:

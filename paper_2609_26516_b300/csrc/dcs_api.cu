@@ -718,7 +718,9 @@ dcs_status_t dcs_import_mps(dcs_ctx_t c, int pos, const void* host_buf, size_t b
              cudaMemcpyHostToDevice);
   cudaMemcpy(c->dev.centre + slot, &centre, sizeof(int), cudaMemcpyHostToDevice);
   for (int j = 0; j <= n; ++j) c->ub[j] = std::max(c->ub[j], b[j]);
-  return cuda_check(c, cudaGetLastError(), "import");
+  // the copies above run on the default stream and may return before their DMA is done:
+  // finish them before later work on the context's stream reads the slot
+  return cuda_check(c, cudaDeviceSynchronize(), "import");
 }
 
 dcs_status_t dcs_branch_append(dcs_ctx_t c, const void* host_buf, size_t bytes, double p,
